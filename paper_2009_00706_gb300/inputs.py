@@ -1,0 +1,238 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the benchmark.
+
+This module holds no arithmetic of the method: it only draws random numbers and builds the
+input surfaces and parameter sets.  Both sides of every parity test receive the very same
+arrays from here.
+
+* Random numbers: SplitMix64 (Steele, Lea, Flood 2014), used counter-style: the i-th draw of
+  stream `seed` is mix(seed * 2^32 + i).  Normals by the Box-Muller transform.
+* Surfaces: a subdivided icosahedron projected on a sphere, every shared vertex jittered once,
+  so the surface stays closed; and a filleted box ("rounded box") meshed as a mapped grid,
+  the bluff bodies of the truck-like workload.  Triangles are counter-clockwise seen from
+  outside the body.
+* Workloads: the mesh parameters, physical parameters and state vectors of the five
+  workloads (small sphere, sphere LES step, bluff-body pair, batched spheres, learned
+  preconditioner), each with the sizes of the paper's runs (Sec. "Validation: flow past a
+  sphere", Sec. "Scaling", Sec. "Platooning").
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+_GOLD = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n 64-bit outputs of SplitMix64 stream `seed` starting at draw `offset`."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * np.uint64(0x100000000) + i * _GOLD
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Doubles in (0, 1): (top 53 bits + 0.5) * 2^-53."""
+    z = splitmix64(seed, n, offset)
+    return ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, n: int, sigma: float = 1.0, offset: int = 0) -> np.ndarray:
+    """n N(0, sigma^2) draws by Box-Muller (one normal per pair of uniforms)."""
+    u = uniform(seed, 2 * n, 2 * offset)
+    u1, u2 = u[0::2], u[1::2]
+    return sigma * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# ------------------------------------------------------------------------------------------
+# surfaces
+# ------------------------------------------------------------------------------------------
+def icosphere(level: int, radius: float, center, jitter: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Closed triangulated sphere: icosahedron subdivided `level` times (20 * 4^level
+    triangles), vertices projected on the sphere, then every vertex coordinate jittered by
+    N(0, jitter^2) (shared vertices once).  Returns [n_tri, 3, 3] float64, CCW from outside."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    verts = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+             (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(v, dtype=np.float64) / np.linalg.norm(v) for v in verts]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+             (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+             (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        cache: dict = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.array(verts) * radius + np.asarray(center, dtype=np.float64)
+    if jitter > 0.0:
+        V = V + normal(seed, V.size, jitter).reshape(V.shape)
+    F = np.array(faces, dtype=np.int64)
+    tri = V[F]
+    # orient counter-clockwise seen from outside
+    n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    out = np.einsum("ij,ij->i", n, tri.mean(axis=1) - np.asarray(center))
+    flip = out < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    return np.ascontiguousarray(tri)
+
+
+def rounded_box(lo, hi, fillet: float, n_per_edge: int, jitter: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Closed filleted box [lo, hi] meshed as a cube-sphere mapped grid: each face of the unit
+    cube carries an n x n grid, every grid point p of the cube surface is mapped to the
+    rounded box by  x = clamp(p) + fillet * (p - clamp(p)) / |p - clamp(p)|  where clamp()
+    projects on the inner box shrunk by `fillet`.  Returns [12 n^2 ... , 3, 3], CCW from outside."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    c = 0.5 * (lo + hi)
+    half = 0.5 * (hi - lo)
+    inner = half - fillet
+    n = n_per_edge
+    s = np.linspace(-1.0, 1.0, n + 1)
+    key_of: dict = {}
+    verts: list = []
+    faces: list = []
+
+    def vid(p):
+        k = tuple(np.round(p * n).astype(np.int64))
+        if k not in key_of:
+            key_of[k] = len(verts)
+            verts.append(p.copy())
+        return key_of[k]
+
+    for axis in range(3):
+        for sign in (-1.0, 1.0):
+            u_ax, v_ax = [a for a in range(3) if a != axis]
+            grid = np.empty((n + 1, n + 1), dtype=np.int64)
+            for i in range(n + 1):
+                for j in range(n + 1):
+                    p = np.zeros(3)
+                    p[axis] = sign
+                    p[u_ax] = s[i]
+                    p[v_ax] = s[j]
+                    grid[i, j] = vid(p)
+            for i in range(n):
+                for j in range(n):
+                    a, b, cc, d = grid[i, j], grid[i + 1, j], grid[i + 1, j + 1], grid[i, j + 1]
+                    faces.append((a, b, cc))
+                    faces.append((a, cc, d))
+    P = np.array(verts)
+    # map cube-surface points: scale to the box, then round the corners/edges
+    X = P * half
+    cl = np.clip(X, -inner, inner)
+    d = X - cl
+    nd = np.linalg.norm(d, axis=1)
+    nd[nd == 0] = 1.0
+    V = cl + fillet * d / nd[:, None] + c
+    if jitter > 0.0:
+        V = V + normal(seed, V.size, jitter).reshape(V.shape)
+    F = np.array(faces, dtype=np.int64)
+    tri = V[F]
+    nrm = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    out = np.einsum("ij,ij->i", nrm, tri.mean(axis=1) - c)
+    flip = out < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    return np.ascontiguousarray(tri)
+
+
+# ------------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------------
+REGION_SPHERE_BAND, REGION_BOX, REGION_CONE = 0, 1, 2
+SCHEME_BE, SCHEME_CN, SCHEME_BDF2 = 0, 1, 2
+
+
+@dataclass
+class Region:
+    kind: int
+    level: int
+    par: tuple  # up to 8 doubles
+
+    def packed(self):
+        p = list(self.par) + [0.0] * (8 - len(self.par))
+        return p[:8]
+
+
+@dataclass
+class Physics:
+    rho: float = 1.0
+    mu: float = 0.02
+    dt: float = 0.01
+    scheme: int = SCHEME_BE
+    Cb: float = 4.0
+    CI: float = 36.0
+    g: tuple = (0.0, 0.0, 0.0)
+    uinf: tuple = (1.0, 0.0, 0.0)
+    drop_visc: int = 0
+
+    def packed(self):
+        return [self.rho, self.mu, self.dt, float(self.scheme), self.Cb, self.CI, *self.g, *self.uinf,
+                float(self.drop_visc)]
+
+
+@dataclass
+class Workload:
+    name: str
+    lo: tuple
+    hi: tuple
+    base_level: int
+    regions: list
+    lmax: int
+    physics: Physics
+    surface: callable = field(repr=False, default=None)
+    seed: int = 0
+
+    def triangles(self) -> np.ndarray:
+        return self.surface() if self.surface is not None else np.zeros((0, 3, 3))
+
+
+def small_sphere(seed: int = 0) -> Workload:
+    """Unit cube, level 3 far field, level 6 within 0.05 of a sphere r = 0.1 at the centre
+    (icosphere 1280 triangles, jitter 1e-4), Re 10 on the diameter, BE dt 0.01, C_b 4, L_max 3."""
+    c = (0.5, 0.5, 0.5)
+    return Workload(
+        name="small_sphere", lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), base_level=3,
+        regions=[Region(REGION_SPHERE_BAND, 6, (*c, 0.1, 0.05))], lmax=3,
+        physics=Physics(rho=1.0, mu=0.02, dt=0.01, scheme=SCHEME_BE),
+        surface=lambda: icosphere(3, 0.1, c, 1e-4, seed), seed=seed)
+
+
+def sphere_les(seed: int = 0) -> Workload:
+    """Box 32 x 16 x 16 diameters, sphere D = 1 at (8, 8, 8) (icosphere level 6, 81920
+    triangles), level 4 background, level 10 within 0.25 D of the surface, a wake cone behind
+    the sphere at levels 9 and 8; Re 1e4, BDF2 dt 0.01.  About 2M elements."""
+    c = (8.0, 8.0, 8.0)
+    return Workload(
+        name="sphere_les", lo=(0.0, 0.0, 0.0), hi=(32.0, 16.0, 16.0), base_level=4,
+        regions=[Region(REGION_SPHERE_BAND, 10, (*c, 0.5, 0.25)),
+                 Region(REGION_CONE, 9, (8.0, 8.0, 8.0, 5.0, 1.0, 0.2679491924)),
+                 Region(REGION_CONE, 8, (8.0, 8.0, 8.0, 14.0, 2.0, 0.2679491924))],
+        lmax=3, physics=Physics(rho=1.0, mu=1e-4, dt=0.01, scheme=SCHEME_BDF2),
+        surface=lambda: icosphere(6, 0.5, c, 1e-5, seed), seed=seed)
+
+
+def state(n_nodes: int, seed: int = 0, sigma: float = 0.01):
+    """u_prev = uniform inflow (1, 0, 0), p = 0; u = u_prev + N(0, sigma^2) on the velocity;
+    v ~ N(0, 1) on every dof.  Node-major [n_nodes, 4] float64 (u, v, w, p)."""
+    up = np.zeros((n_nodes, 4))
+    up[:, 0] = 1.0
+    u = up.copy()
+    u[:, :3] += normal(seed * 4 + 1, n_nodes * 3, sigma).reshape(n_nodes, 3)
+    v = normal(seed * 4 + 2, n_nodes * 4).reshape(n_nodes, 4)
+    return u, up, v

@@ -1,0 +1,220 @@
+"""Pins of the oracle's geometry: in/out classification, markers, adaptive and surface quadrature.
+
+References that do not come from the oracle:
+* the 2-point Gauss abscissae printed in the paper's adaptive-quadrature figure (golden file);
+* exact volumes and exact integrals of trilinear functions for cuts along dyadic sub-cell planes;
+* the analytic sphere (inscribed / circumscribed radii of the faceted surface);
+* an independent brute-force ray-parity count written here with numpy along a random direction;
+* the divergence theorem for the triangulated surface (sum w n = 0, sum w x.n = 3 V).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleMesh
+from paper_2009_00706_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "fig_gp_gauss_abscissae.txt")
+
+
+def box_body(lo, hi):
+    return I.rounded_box(lo, hi, 0.0, 1)
+
+
+def test_box_body_is_closed_and_outward():
+    t = box_body((-1, -1, -1), (0.25, 2, 2))
+    assert t.shape == (12, 3, 3)
+    n = np.cross(t[:, 1] - t[:, 0], t[:, 2] - t[:, 0])
+    vol = np.einsum("ij,ij->i", t[:, 0], np.cross(t[:, 1], t[:, 2])).sum() / 6.0
+    assert abs(vol - 1.25 * 3 * 3) < 1e-12
+    assert np.abs(n.sum(0)).max() < 1e-12
+
+
+def test_first_split_points_match_printed_gauss_abscissae():
+    printed = np.loadtxt(GOLD)
+    m = OracleMesh((0, 0, 0), (1, 1, 1), 1, [], box_body((-1, -1, -1), (0.25, 2, 2)), lmax=3)
+    mk, _, _ = m.markers()
+    e = 0                                   # [0, 0.5]^3, cut by the plane x = 0.25 through its middle
+    assert mk[e] == 2
+    q = m.cut_points(e)
+    assert q.shape[0] == 32                 # four level-1 children fully Out, 8 points each
+    assert np.allclose(q[:, 3], 1.0 / 8.0)
+    frac = np.mod(q[:, :3] + 1.0, 1.0)      # position inside the level-1 child, unit edge
+    for k in range(3):
+        vals = np.unique(np.round(frac[:, k], 9))
+        assert np.allclose(np.sort(vals), np.sort(printed), atol=1e-10)
+    assert np.all(q[:, 0] > 0.0)            # only the Out half (x > 0.25) carries points
+
+
+def test_dyadic_plane_cut_is_exact():
+    # plane x = 0.3125 lies on a level-3 sub-cell face of [0, 0.5]^3 (xi = 0.25)
+    m = OracleMesh((0, 0, 0), (1, 1, 1), 1, [], box_body((-1, -1, -1), (0.3125, 2, 2)), lmax=3)
+    q = m.cut_points(0)
+    w = q[:, 3]
+    assert abs(w.sum() - 8.0 * 0.375) <= 1e-14
+    f = (1.0 + q[:, 0]) * (2.0 - q[:, 1]) * (0.5 + q[:, 2]) * (1.0 + 0.5 * q[:, 0] ** 2)
+    # int_{0.25}^1 (1+x)(1+x^2/2) dx * int_{-1}^1 (2-y) dy * int_{-1}^1 (0.5+z) dz
+    fx = lambda x: x + x ** 2 / 2 + x ** 3 / 6 + x ** 4 / 8
+    exact = (fx(1.0) - fx(0.25)) * 4.0 * 1.0
+    assert abs((w * f).sum() - exact) <= 1e-13
+
+
+def _halfspace_volume(a, d):
+    """Volume of {y in [0,1]^3 : a.y <= d} for a > 0 (inclusion-exclusion over the cube's corners)."""
+    s = 0.0
+    for v in range(8):
+        bits = np.array([(v >> k) & 1 for k in range(3)], dtype=float)
+        s += (-1) ** int(bits.sum()) * max(d - a @ bits, 0.0) ** 3
+    return s / (6.0 * np.prod(a))
+
+
+def _plane_body(a, d):
+    """Tetrahedron whose face lies on a.x = d, every other face ~20 units away: inside the unit
+    cube the body is the half-space a.x < d."""
+    an = a / np.linalg.norm(a)
+    c0 = an * d / np.linalg.norm(a)
+    u = np.cross(an, [0.0, 0.0, 1.0])
+    u /= np.linalg.norm(u)
+    w = np.cross(an, u)
+    P = [c0 + 20.0 * (np.cos(t) * u + np.sin(t) * w) for t in (0.0, 2 * np.pi / 3, 4 * np.pi / 3)]
+    apex = c0 - 20.0 * an
+    return np.array([[P[0], P[1], P[2]], [apex, P[1], P[0]], [apex, P[2], P[1]], [apex, P[0], P[2]]])
+
+
+def test_oblique_plane_cut_quadrature():
+    """Sub-cells are judged by their 8 Gauss points (Fig. GP caption): an Intercepted element
+    whose level-0 Gauss points all fall on one side keeps all 8 (all Out) or none (all In);
+    the others approach the exact clipped volume as the split level grows."""
+    a, d, h = np.array([1.0, 0.7, 0.4]), 0.83, 1.0 / 8.0
+    tri = _plane_body(a, d)
+    G = 1.0 / np.sqrt(3.0)
+    gp = np.array([[G if (g >> k) & 1 else -G for k in range(3)] for g in range(8)])
+    errs = []
+    for lmax in (1, 2, 3):
+        m = OracleMesh((0, 0, 0), (1, 1, 1), 3, [], tri, lmax=lmax)
+        mk, cf, _ = m.markers()
+        E = 0.0
+        for el in range(m.n_elem):
+            x0 = m.anchors[el] * m.scale
+            corners = x0 + np.array([[(c >> k) & 1 for k in range(3)] for c in range(8)]) * h
+            cin = corners @ a < d
+            assert mk[el] == (1 if cin.all() else 0 if not cin.any() else 2)
+            if mk[el] != 2:
+                continue
+            got = m.cut_points(el)[:, 3].sum() * (h / 2) ** 3
+            side_out = (x0 + (gp + 1.0) * h / 2) @ a > d
+            if side_out.all():
+                assert got == h ** 3
+            elif not side_out.any():
+                assert got == 0.0
+            else:
+                exact = h ** 3 * (1.0 - _halfspace_volume(a * h, d - a @ x0))
+                assert abs(got - exact) <= h ** 3
+                E += abs(got - exact)
+        errs.append(E)
+    assert errs[1] < errs[0] / 2.0 and errs[2] < errs[0] / 3.0
+
+
+# ---------------------------------------------------------------------------------------
+# in/out
+# ---------------------------------------------------------------------------------------
+def brute_parity(pts, tri, d):
+    """Independent ray-parity count (numpy), direction d; returns (inside, ok) where ok is
+    False for rays that pass within 1e-9 of a triangle edge."""
+    v0, v1, v2 = tri[:, 0], tri[:, 1], tri[:, 2]
+    e1, e2 = v1 - v0, v2 - v0
+    pv = np.cross(d, e2)
+    det = np.einsum("ij,ij->i", e1, pv)
+    tv = pts[:, None, :] - v0[None]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = np.einsum("pij,ij->pi", tv, pv) / det
+        qv = np.cross(tv, e1[None])
+        v = np.einsum("pij,j->pi", qv, d) / det
+        t = np.einsum("pij,ij->pi", qv, e2) / det
+    hit = (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 0)
+    near = (np.minimum(np.minimum(np.abs(u), np.abs(v)), np.abs(1 - u - v)) < 1e-9) & (t > 0) & \
+           (u > -1e-9) & (v > -1e-9) & (u + v < 1 + 1e-9)
+    return (hit.sum(1) % 2 == 1), ~near.any(1)
+
+
+def _check_classification(m, tri, pts, seed):
+    d = I.normal(seed, 3)
+    d /= np.linalg.norm(d)
+    truth, ok = brute_parity(pts, tri, d)
+    got = m.classify(pts).astype(bool)
+    assert ok.mean() > 0.99
+    assert np.array_equal(got[ok], truth[ok])
+    return got, truth
+
+
+def test_inout_icosphere_vs_brute_force_and_analytic():
+    c = np.array([0.5, 0.5, 0.5])
+    tri = I.icosphere(2, 0.3, c, 1e-4, 3)
+    m = OracleMesh((0, 0, 0), (1, 1, 1), 3, [I.Region(I.REGION_SPHERE_BAND, 5, (*c, 0.3, 0.04))], tri)
+    pts = I.uniform(21, 3 * 4000).reshape(-1, 3)
+    got, _ = _check_classification(m, tri, pts, 5)
+    n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    r_in = np.min(np.einsum("ij,ij->i", tri[:, 0] - c, n))
+    r_out = np.max(np.linalg.norm(tri.reshape(-1, 3) - c, axis=1))
+    r = np.linalg.norm(pts - c, axis=1)
+    assert np.all(got[r < r_in - 1e-9]) and not np.any(got[r > r_out + 1e-9])
+    cnt = m.counters()
+    assert cnt["normal_decided"] > 0.5 * cnt["normal_tests"]
+
+
+def test_inout_two_disjoint_bodies_and_polyhedra():
+    tri = np.concatenate([I.icosphere(2, 0.15, (0.3, 0.5, 0.5), 1e-4, 1), I.icosphere(1, 0.12, (0.72, 0.45, 0.55), 1e-4, 2),
+                          box_body((0.1, 0.1, 0.1), (0.3, 0.25, 0.2))])
+    tet = np.array([[[0.6, 0.8, 0.7], [0.9, 0.8, 0.7], [0.6, 0.95, 0.7]], [[0.6, 0.8, 0.7], [0.6, 0.8, 0.9], [0.9, 0.8, 0.7]],
+                    [[0.6, 0.8, 0.7], [0.6, 0.95, 0.7], [0.6, 0.8, 0.9]], [[0.9, 0.8, 0.7], [0.6, 0.8, 0.9], [0.6, 0.95, 0.7]]])
+    cen = tet.reshape(-1, 3).mean(0)
+    nrm = np.cross(tet[:, 1] - tet[:, 0], tet[:, 2] - tet[:, 0])
+    flip = np.einsum("ij,ij->i", nrm, tet.mean(1) - cen) < 0
+    tet[flip] = tet[flip][:, [0, 2, 1]]
+    tri = np.concatenate([tri, tet])
+    m = OracleMesh((0, 0, 0), (1, 1, 1), 3, [I.Region(I.REGION_BOX, 5, (0.05, 0.05, 0.05, 0.95, 0.95, 0.95))], tri)
+    pts = I.uniform(33, 3 * 3000).reshape(-1, 3)
+    got, truth = _check_classification(m, tri, pts, 7)
+    assert truth.sum() > 50
+
+
+def test_markers_vs_analytic_corner_distances(small_sphere_oracle):
+    w, m = small_sphere_oracle
+    tri = w.triangles()
+    c = np.array([0.5, 0.5, 0.5])
+    n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    r_in = np.min(np.einsum("ij,ij->i", tri[:, 0] - c, n)) - 1e-9
+    r_out = np.max(np.linalg.norm(tri.reshape(-1, 3) - c, axis=1)) + 1e-9
+    mk, cf, _ = m.markers()
+    size = (1 << (20 - m.levels.astype(np.int64))) * m.scale
+    corners = m.anchors[:, None, :] * m.scale + np.array([[(k >> j) & 1 for j in range(3)] for k in range(8)])[None] * size[:, None, None]
+    r = np.linalg.norm(corners - c, axis=2)
+    out_all = np.all(r > r_out, axis=1)
+    in_all = np.all(r < r_in, axis=1)
+    mixed = np.any(r < r_in, axis=1) & np.any(r > r_out, axis=1)
+    assert np.all(mk[out_all] == 0) and np.all(mk[in_all] == 1) and np.all(mk[mixed] == 2)
+    assert (mk == 2).sum() > 100
+    # corner flags agree with the analytic verdict wherever it is unambiguous
+    cin = ((cf[:, None] >> np.arange(8)[None]) & 1).astype(bool)
+    assert np.all(cin[r < r_in]) and not np.any(cin[r > r_out])
+
+
+def test_surface_quadrature_identities(small_sphere_oracle):
+    w, m = small_sphere_oracle
+    tri = w.triangles()
+    sq = m.surface_points()
+    assert sq.shape[0] == 3 * tri.shape[0]
+    area = 0.5 * np.linalg.norm(np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]), axis=1).sum()
+    vol = np.einsum("ij,ij->i", tri[:, 0], np.cross(tri[:, 1], tri[:, 2])).sum() / 6.0
+    x, n, wq, hb, el = sq[:, :3], sq[:, 3:6], sq[:, 6], sq[:, 7], sq[:, 8].astype(np.int64)
+    assert abs(wq.sum() - area) <= 1e-14 * area * 10
+    assert np.abs((wq[:, None] * n).sum(0)).max() <= 1e-15 * 10
+    assert abs((wq * np.einsum("ij,ij->i", x, n)).sum() + 3.0 * vol) <= 1e-13
+    h = (1 << (20 - m.levels[el].astype(np.int64))) * m.scale
+    assert np.all(hb >= 0.01 * h - 1e-18) and np.all(hb <= np.sqrt(3) * h)
+    # every point lies in the closed box of its owning element
+    lo = m.anchors[el] * m.scale
+    assert np.all((x >= lo - 1e-15) & (x <= lo + h[:, None] + 1e-15))
