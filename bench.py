@@ -1,0 +1,338 @@
+"""Benchmark: VMS Jacobian-vector products per second on the sphere LES workload (one GB300).
+
+A step is one application of J(u) v over the whole mesh: Out elements on the 2x2x2 Gauss
+rule, Intercepted elements on their adaptive sub-cell points, Nitsche surface points, scatter
+through the hanging-node operator, strong rows.  The workload is a 32 x 16 x 16 box with a
+sphere of diameter 1 (81,920 triangles), octree levels 4-10 with a wake cone, 2,001,176
+elements, Re 1e4, BDF2 dt 0.01; inputs are seeded synthetic states (uniform inflow + N(0, 0.01)
+noise, v ~ N(0, 1)).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference]
+
+Multi-GPU: every rank solves its own independent problem (a replica of the workload with its own
+seed), so the units shard with no data-path collective ("scaling": "weak").  --impl reference
+times the FP64 CPU oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2009_00706_gb300 import inputs as I  # noqa: E402
+
+METRIC = "VMS Jv elements/s; Newton-GMRES step time to 1e-8, mixed/learned vs FP64"
+UNIT = "elements/s"
+L2_BYTES = 129 * 2 ** 20
+
+# Algorithmic FP32 work of one Out element in the forward-mode J v (counted in the design notes):
+# 8 Gauss points x (interpolation of values + tangents 896, pointwise VMS + tangent 390, weights 16)
+# + contraction of 8 nodes x 4 rows over 8 points (2048).
+FLOPS_JV_OUT_ELEMENT = 8 * (896 + 390 + 16) + 2048
+FLOPS_R_OUT_ELEMENT = 8 * (448 + 130 + 16) + 2048
+
+
+def peaks():
+    p = {"source": "fallback", "sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        p.update({"source": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                  "hbm_gbs": float(d.get("hbm_gbs", 6800.0))})
+    except Exception:
+        pass
+    # plain FP32 ALU peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
+    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    return p
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(x, world, dev=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on a bounded sample of the workload
+# ------------------------------------------------------------------------------------------
+def oracle_sample(w, n_nodes_sample, seed=0):
+    """Build the oracle mesh (untimed), then time residual + J v of the elements touching a
+    seeded sample of nodes.  Returns (elements/s, elements per sample, seconds per sample, om)."""
+    from oracle.oracle import OracleMesh
+    tri = w.triangles()
+    om = OracleMesh(w.lo, w.hi, w.base_level, w.regions, tri, w.lmax)
+    u, up, v = I.state(om.n_nodes, seed)
+    return om, u, up, v
+
+
+def time_oracle(om, w, u, up, v, sel):
+    om.residual_jvp(w.physics, u, up, up, v=v, nodes=sel)      # geometry of the sample, untimed
+    t = time.perf_counter()
+    om.residual_jvp(w.physics, u, up, up, v=v, nodes=sel)
+    dt = time.perf_counter() - t
+    return om.counters()["elements_evaluated"], dt
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    w = I.sphere_les(0)
+    om, u, up, v = oracle_sample(w, 0)
+    rng_sel = lambda k: np.unique(I.splitmix64(1000 + k, args.sample_nodes) % om.n_nodes).astype(np.int64)
+    for k in range(args.warmup):
+        time_oracle(om, w, u, up, v, rng_sel(k))
+    ne_tot, t_tot = 0, 0.0
+    for k in range(args.steps):
+        ne, dt = time_oracle(om, w, u, up, v, rng_sel(100 + k))
+        ne_tot += ne
+        t_tot += dt
+    val = ne_tot / t_tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sphere_les", "elements": om.n_elem, "sample": "elements touching "
+                       f"{args.sample_nodes} seeded nodes per step, residual + J v", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{ne_tot} element evaluations over {args.steps} steps"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2009_00706_gb300 import _lib, api
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _lib.build()
+    w = I.sphere_les(0)
+    prec = api.PRECISION_MIXED if args.precision == "mixed" else api.PRECISION_FP64
+    t0 = time.perf_counter()
+    mesh = api.Mesh.from_workload(w, device=local)
+    build_s = time.perf_counter() - t0
+    info = mesh.info
+    nn = mesh.n_nodes
+    n_active = info["n_out"] + info["n_cut"]
+    u, up, v = I.state(nn, rank)
+    up2 = up.copy()
+    ud, upd, up2d, vd = (torch.from_numpy(a).to(dev) for a in (u, up, up2, v))
+    out = torch.empty_like(ud)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ph = w.physics
+
+    def step(p=prec):
+        mesh.jvp(ph, ud, upd, vd, up2d, precision=p, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # device-timed region: per-step events, L2 flushed (untimed) between steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    mesh.profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with Clocks(local) as clk:
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms = reduce_max(ms, world, dev)
+    barrier(world)
+    value = world * n_active * args.steps / (ms / 1e3)
+    # dominant kernel roofline (Out elements, live CUDA events on the launching stream)
+    k_ms, k_n = prof["out_elements"]
+    k_avg = k_ms / max(k_n, 1)
+    pk = peaks()
+    flops = (FLOPS_JV_OUT_ELEMENT if True else FLOPS_R_OUT_ELEMENT) * info["n_out"]
+    achieved = flops / (k_avg / 1e3) / 1e12
+    roof = {"kernel": "vms_interior (Out elements, J v)", "bound": "alu", "achieved": achieved,
+            "peak": pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None, "unit": "TFLOP/s",
+            "frac": achieved / pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None,
+            "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+            "flops_per_element": FLOPS_JV_OUT_ELEMENT, "avg_launch_ms": k_avg}
+    kern_share = {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()}
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    hu, hup, hup2, hv = (torch.from_numpy(a).pin_memory() for a in (u, up, up2, v))
+    hout = torch.empty_like(hu).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(e2e_steps):
+        ud.copy_(hu, non_blocking=True)
+        upd.copy_(hup, non_blocking=True)
+        up2d.copy_(hup2, non_blocking=True)
+        vd.copy_(hv, non_blocking=True)
+        step()
+        hout.copy_(out, non_blocking=True)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(ea.elapsed_time(eb), world, dev)
+    e2e = {"value": world * n_active * e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": 4 * hu.numel() * 8, "d2h_bytes_per_step": hout.numel() * 8}
+    # companion numbers (not the headline): FP64 J v, residuals
+    extra = {}
+    for name, fn in (("jv_fp64", lambda: mesh.jvp(ph, ud, upd, vd, up2d, precision=0, out=out, stream=stream)),
+                     ("residual_mixed", lambda: mesh.residual(ph, ud, upd, up2d, precision=1, out=out, stream=stream)),
+                     ("residual_fp64", lambda: mesh.residual(ph, ud, upd, up2d, precision=0, out=out, stream=stream))):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        extra[name] = n_active * reps / (tot / 1e3)
+    # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            om, ou, oup, ov = oracle_sample(w, 0)
+            sel = np.unique(I.splitmix64(77, args.sample_nodes) % om.n_nodes).astype(np.int64)
+            ne, dt = time_oracle(om, w, ou, oup, ov, sel)
+            cpu = {"value": ne / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"residual + J v of the {ne} active elements touching {args.sample_nodes} seeded nodes "
+                             f"of the same mesh ({dt:.1f} s)"}
+        except Exception as ex:  # report, never hide
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 element arithmetic, f64 gathers/accumulation"
+                if prec == 1 else "f64", "data": "synthetic",
+                "config": {"workload": "sphere_les (box 32x16x16 D, sphere D=1, levels 4-10 + wake cone, Re 1e4, BDF2)",
+                           "elements": info["n_elem"], "active_elements": n_active, "out_elements": info["n_out"],
+                           "cut_elements": info["n_cut"], "cut_points": info["n_cut_points"],
+                           "surface_points": info["n_surface_points"], "nodes": nn, "precision": args.precision,
+                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                "roofline": roof, "kernel_time_share": kern_share, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": 4 * args.steps, "cpu_baseline": cpu, "extra_elements_per_s": extra,
+                "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sample-nodes", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/* imga.h -- C ABI of the GB300 (sm_103a) immersogeometric VMS residual / Jacobian-vector library.
+ *
+ * The library evaluates, on one GPU, the hot path of the immersogeometric octree LES method of
+ * Saurabh et al., "Industrial scale large eddy simulations with adaptive octree meshes using
+ * immersogeometric analysis" (arXiv:2009.00706):
+ *
+ *   imga_build_mesh   octree refined by region predicates, 2:1 balanced, Morton ordered, meshed
+ *                     with hanging nodes (Sec. "Octree based Mesh Generation", Algorithm 3);
+ *                     triangles distributed to the elements they overlap (Algorithm 1), element
+ *                     markers In/Out/Intercepted (Algorithm 5), adaptive sub-cell quadrature of the
+ *                     Intercepted elements (Sec. "Adaptive Quadrature", Fig. GP) and the surface
+ *                     quadrature of the Nitsche terms (Eq. weakbc).
+ *   imga_classify     normal-based in/out test with ray-tracing fallback (Algorithm 6).
+ *   imga_residual     VMS residual, Eqs. (ALE-VMS-form), (vms), (uprime), (pprime), plus the
+ *                     Nitsche weak Dirichlet terms, Eq. (weakbc), scattered to the nodes through
+ *                     the hanging-node operator M_e^T (Algorithm 2).
+ *   imga_jvp          the exact directional derivative J(u) v of imga_residual: the matrix of
+ *                     Algorithms 2 and 4 applied without being formed.
+ *   imga_newton_step  Newton iterations with right-preconditioned GMRES(m) (appendix "Details of
+ *                     solver selection": Newton line search + Krylov solver).
+ *
+ * Conventions
+ *   - Node vectors are DEVICE pointers to float64 [n_nodes][4] = (u, v, w, p), node-major, owned
+ *     by the caller; the mesh handle owns every other device array.  Nodes are the independent
+ *     (non-hanging) octree nodes in Morton order of their integer coordinates.
+ *   - Streams are passed as void* (a cudaStream_t, NULL = the legacy default stream).  Compute
+ *     calls are asynchronous on that stream; imga_build_mesh and imga_newton_step synchronise.
+ *   - Inputs are never written.  Every call returns a status; nothing aborts or traps.  The
+ *     message of the last failure on the calling thread is imga_last_error().
+ *   - One mesh handle belongs to the device it was built on; calls using it must run with that
+ *     device current or pass pointers of that device.
+ */
+#ifndef IMGA_H
+#define IMGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IMGA_OK = 0,
+    IMGA_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter                         */
+    IMGA_ERR_CUDA = 2,          /* a CUDA runtime call failed                             */
+    IMGA_ERR_OOM = 3,           /* device or host allocation failed                       */
+    IMGA_ERR_SURFACE = 4,       /* degenerate triangle (zero area) in the surface         */
+    IMGA_ERR_TIMEOUT = 5,       /* a device-side wait ran out of its iteration budget      */
+    IMGA_ERR_NOT_CONVERGED = 6, /* Newton / GMRES stopped before the tolerance            */
+    IMGA_ERR_NUMERIC = 7        /* NaN or Inf in a residual norm                          */
+} imga_status;
+
+typedef struct imga_mesh_s* imga_mesh;
+
+/* Refinement region: octants meeting the region are refined to `level` (the user predicate of
+ * Sec. "Octree based Mesh Generation").  kind 0: spherical band |‖x-c‖-r| <= w, par = (cx, cy,
+ * cz, r, w); kind 1: closed box, par = (x0, y0, z0, x1, y1, z1); kind 2: cone along +x, par =
+ * (apex x, y, z, length, radius at the apex, tan(half angle)), tested at the octant centre
+ * inflated by half its diagonal. */
+typedef struct {
+    int kind;
+    int level;          /* 0 .. 14 */
+    double par[8];
+} imga_region;
+
+typedef struct {
+    double lo[3], hi[3];    /* box; the root cube has the largest edge, origin lo; every edge must
+                               be a whole number of base-level cells                         */
+    int base_level;         /* level everywhere, 0 .. 14                                       */
+    int n_regions;
+    const imga_region* regions;
+    int quad_max_split;     /* L_max of the adaptive sub-cell quadrature, 0 .. 4               */
+} imga_mesh_params;
+
+typedef struct {
+    double rho, mu, dt;
+    int time_scheme;        /* 0 backward Euler, 1 Crank-Nicolson, 2 BDF2                       */
+    double C_b;             /* Nitsche penalty constant: tau_B = C_b mu / h_b                   */
+    double C_I;             /* inverse-estimate constant in tau_M                               */
+    double g_body[3];       /* velocity prescribed on the immersed surface (weakly)             */
+    double u_inf[3];        /* velocity prescribed on the box faces (strongly, not the outlet)  */
+    int drop_visc_strong;   /* 1: drop mu grad(div u) from the strong momentum residual         */
+} imga_physics;
+
+typedef struct {
+    int64_t n_elem, n_nodes, n_hanging;
+    int64_t n_out, n_in, n_cut;          /* element markers                                       */
+    int64_t n_cut_points;                /* sub-cell quadrature points of the Intercepted elements */
+    int64_t n_surface_points;            /* Nitsche quadrature points kept                        */
+    int64_t n_tri, n_bt;                 /* triangles, (element, triangle) background pairs       */
+    int64_t n_rays;                      /* ray-parity casts made while building                  */
+    int64_t hi_int[3];                   /* box extent in integer units (2^20 per root edge)      */
+    double scale;                        /* physical length of one integer unit                   */
+    double setup_ms[4];                  /* octree+mesh, background triangles, markers+quadrature, upload */
+} imga_mesh_info;
+
+/* Build the mesh and every geometric table on `device` (synchronous).  tri_xyz_host: host
+ * float64 [n_tri][3][3], counter-clockwise seen from outside each closed body (n_tri may be 0:
+ * no immersed body).  On success *out owns the mesh; free it with imga_destroy_mesh.
+ * device < 0 builds the host tables only (octree, nodes, background triangles) for inspection:
+ * no GPU is touched, and the compute calls reject such a mesh with IMGA_ERR_INVALID_ARG. */
+imga_status imga_build_mesh(const double* tri_xyz_host, int64_t n_tri, const imga_mesh_params* params, int device,
+                            imga_mesh* out);
+void imga_destroy_mesh(imga_mesh mesh);
+imga_status imga_mesh_get_info(imga_mesh mesh, imga_mesh_info* info);
+
+/* Host copies of the mesh tables (every pointer may be NULL to skip it).  anchors [n_elem][3]
+ * integer anchors; levels [n_elem]; conn [n_elem][8] corner -> node index, or n_nodes + h for
+ * hanging node h (corner c has bits (c&1, c>>1&1, c>>2&1) along x, y, z); node_ijk [n_nodes][3];
+ * hang_parents [n_hanging][4] (-1 padded); hang_np [n_hanging] (2 edge, 4 face). */
+imga_status imga_mesh_export(imga_mesh mesh, uint32_t* anchors, uint8_t* levels, int32_t* conn, uint32_t* node_ijk,
+                             int32_t* hang_parents, int8_t* hang_np);
+/* Host copies of marker [n_elem] (0 Out, 1 In, 2 Intercepted) and corner flags [n_elem] (bit c
+ * set: corner c is In), Algorithm 5. */
+imga_status imga_export_markers(imga_mesh mesh, int8_t* marker, uint8_t* corner_flags);
+/* Host copies of the sub-cell quadrature: offsets [n_elem + 1] into points [n_cut_points][4] =
+ * (xi_x, xi_y, xi_z, reference weight) on the element's reference cube [-1, 1]^3. */
+imga_status imga_export_cut_points(imga_mesh mesh, int64_t* offsets, double* points);
+/* Host copy of the background triangles B_T (Algorithm 1): offsets [n_elem + 1] into tri_ids
+ * [n_bt], each element's triangles in increasing order. */
+imga_status imga_export_background(imga_mesh mesh, int32_t* offsets, int32_t* tri_ids);
+/* Host copy of the surface quadrature [n_surface_points][10] = (x, y, z, n_x, n_y, n_z, weight,
+ * h_b, element, triangle); n is the fluid-outward normal. */
+imga_status imga_export_surface_points(imga_mesh mesh, double* out);
+
+/* In/out flags of n points (Algorithm 6): pts_dev float64 [n][3] device, flags_dev uint8 [n]
+ * device, 1 = In, 0 = Out (points outside the box are Out). */
+imga_status imga_classify(imga_mesh mesh, const double* pts_dev, int64_t n, uint8_t* flags_dev, void* stream);
+
+/* Residual R(u) [n_nodes][4] (device).  u_prev2 is read by BDF2 only (may be NULL otherwise);
+ * f is a nodal body force [n_nodes][4] (components 0..2 used) or NULL.  precision 0: FP64
+ * throughout; 1: element arithmetic in FP32 with FP64 nodal gathers, FP64 accumulation and FP64
+ * Nitsche penalty terms.  Rows of strong Dirichlet nodes hold U - g; rows of nodes touched by no
+ * active element (In-only nodes, Algorithm 1) hold U - (g_body, 0). */
+imga_status imga_residual(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
+                          const double* f, const imga_physics* phys, int precision, double* R, void* stream);
+
+/* Jacobian-vector product J(u) v [n_nodes][4] (device), the derivative of imga_residual in the
+ * direction v (the inflow indicator of the Nitsche advective term is held fixed). */
+imga_status imga_jvp(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2, const double* f,
+                     const imga_physics* phys, int precision, const double* v, double* Jv, void* stream);
+
+/* Replace the default strong Dirichlet rows (u = u_inf on every box face but the outlet x = hi,
+ * p = 0 on the outlet) by mask_dev uint8 [n_nodes] (bit k: component k prescribed) and values
+ * val_dev float64 [n_nodes][4].  Both device pointers; copied.  Pass NULL, NULL to restore. */
+imga_status imga_set_dirichlet(imga_mesh mesh, const uint8_t* mask_dev, const double* val_dev, void* stream);
+
+/* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
+ * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.
+ * imga_profile_read synchronises the device and returns, per kernel class (0 Out elements,
+ * 1 Intercepted elements, 2 Nitsche surface points, 3 strong rows), the summed milliseconds
+ * ms[4] and the launch counts launches[4] since profiling was enabled. */
+imga_status imga_profile(imga_mesh mesh, int enable);
+imga_status imga_profile_read(imga_mesh mesh, double* ms, int64_t* launches);
+
+const char* imga_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMGA_H */

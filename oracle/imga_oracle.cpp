@@ -182,14 +182,27 @@ void refine_dfs(Mesh& m, uint32_t a[3], int l, std::vector<std::pair<std::array<
     }
 }
 
-// leaf containing integer point q (half-open boxes), or -1
-int find_leaf(const Mesh& m, int64_t qx, int64_t qy, int64_t qz) {
+// leaf containing integer point q (half-open boxes), or -1.  The containing leaf is unique;
+// `hint` only chooses which levels are probed first (a neighbour is usually within one level).
+int find_leaf(const Mesh& m, int64_t qx, int64_t qy, int64_t qz, int hint = -1) {
     if (!in_domain(m, qx, qy, qz)) return -1;
-    for (int l = 0; l <= MAXLEV; ++l) {
+    auto probe = [&](int l) -> int {
+        if (l < 0 || l > MAXLEV) return -1;
         uint32_t s = osize(l);
         uint32_t ax = (uint32_t)qx & ~(s - 1), ay = (uint32_t)qy & ~(s - 1), az = (uint32_t)qz & ~(s - 1);
         auto it = m.leafidx.find(leafkey(ax, ay, az, l));
-        if (it != m.leafidx.end()) return it->second;
+        return it == m.leafidx.end() ? -1 : it->second;
+    };
+    if (hint >= 0) {
+        for (int l : {hint, hint - 1, hint + 1}) {
+            int e = probe(l);
+            if (e >= 0) return e;
+        }
+    }
+    for (int l = 0; l <= MAXLEV; ++l) {
+        if (hint >= 0 && l >= hint - 1 && l <= hint + 1) continue;
+        int e = probe(l);
+        if (e >= 0) return e;
     }
     return -1;
 }
@@ -226,7 +239,7 @@ void balance(Mesh& m) {
                         int d[3] = {dx, dy, dz};
                         for (int k = 0; k < 3; ++k)
                             q[k] = d[k] < 0 ? (int64_t)m.anc[e][k] - 1 : d[k] > 0 ? (int64_t)m.anc[e][k] + s : (int64_t)m.anc[e][k];
-                        int n = find_leaf(m, q[0], q[1], q[2]);
+                        int n = find_leaf(m, q[0], q[1], q[2], l);
                         if (n >= 0 && m.lev[n] < l - 1) split.insert(n);
                     }
         }
@@ -273,7 +286,7 @@ bool build_nodes(Mesh& m) {
             for (int nb = 0; nb < 8 && !hanging; ++nb) {
                 int64_t q[3] = {(int64_t)P[0] - ((nb & 1) ? 1 : 0), (int64_t)P[1] - ((nb & 2) ? 1 : 0),
                                 (int64_t)P[2] - ((nb & 4) ? 1 : 0)};
-                int n = find_leaf(m, q[0], q[1], q[2]);
+                int n = find_leaf(m, q[0], q[1], q[2], m.lev[e]);
                 if (n < 0) continue;
                 uint32_t ns = osize(m.lev[n]);
                 int mid[3], nmid = 0;
@@ -372,6 +385,7 @@ struct Geom {
     std::vector<uint8_t> bcmask;
     std::vector<std::array<double, 4>> bcval;
     int64_t nrays = 0, nnormal = 0, nnormal_ok = 0;
+    int64_t nevals = 0;   // active elements evaluated by the last residual/jvp call
 };
 
 double elem_h(const Mesh& m, int e) { return (double)osize(m.lev[e]) * m.scale; }
@@ -1036,7 +1050,7 @@ int64_t or_surface_points(void* s, double* out, int64_t cap) {
 
 void or_counters(void* s, int64_t* out) {
     Geom& g = ((State*)s)->geom;
-    out[0] = g.nrays; out[1] = g.nnormal; out[2] = g.nnormal_ok;
+    out[0] = g.nrays; out[1] = g.nnormal; out[2] = g.nnormal_ok; out[3] = g.nevals;
 }
 
 // Override the strong Dirichlet rows: mask bit k = component k prescribed, value val.
@@ -1089,9 +1103,11 @@ int or_residual_jvp(void* s, const double* physv, const double* U, const double*
     const double* VV = V ? V : zero4.data();
     const double* UP2 = Up2 ? Up2 : Up;
     static const std::vector<int> none;
+    g.nevals = 0;
     for (int e : elems) {
         compute_marker(g, e);
         if (g.marker[e] == 1) continue;
+        ++g.nevals;
         for (int c = 0; c < 8; ++c) {
             int id = m.conn[e][c];
             if (id < Nni) active[id] = 1;

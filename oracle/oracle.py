@@ -167,9 +167,10 @@ class OracleMesh:
         return out[:n].copy()
 
     def counters(self):
-        out = np.zeros(3, np.int64)
+        out = np.zeros(4, np.int64)
         lib().or_counters(self.h, _p(out))
-        return {"rays": int(out[0]), "normal_tests": int(out[1]), "normal_decided": int(out[2])}
+        return {"rays": int(out[0]), "normal_tests": int(out[1]), "normal_decided": int(out[2]),
+                "elements_evaluated": int(out[3])}
 
     def set_dirichlet(self, mask, vals):
         mask = np.ascontiguousarray(mask, dtype=np.uint8)

@@ -1,0 +1,184 @@
+"""Thin Python binding of the imga C ABI (same names, argument marshalling only).
+
+Device vectors are torch CUDA tensors (float64, [n_nodes, 4], contiguous); the stream is
+torch's current stream unless one is given.  Every step of the computation runs in the
+library's CUDA kernels; this module only converts arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import MeshInfo, MeshParams, Physics, Region, check
+
+PRECISION_FP64, PRECISION_MIXED = 0, 1
+
+
+def physics_struct(ph) -> Physics:
+    """imga_physics from an inputs.Physics (or anything with the same fields)."""
+    s = Physics()
+    s.rho, s.mu, s.dt, s.time_scheme = ph.rho, ph.mu, ph.dt, int(ph.scheme)
+    s.C_b, s.C_I = ph.Cb, ph.CI
+    s.g_body = (C.c_double * 3)(*ph.g)
+    s.u_inf = (C.c_double * 3)(*ph.uinf)
+    s.drop_visc_strong = int(ph.drop_visc)
+    return s
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _vec(t, n_nodes, name):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.__repr__().endswith("float64") and t.is_contiguous() and t.numel() == 4 * n_nodes):
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor of {n_nodes} x 4")
+    return t
+
+
+class Mesh:
+    """imga_build_mesh / imga_destroy_mesh and the calls that take the mesh handle."""
+
+    def __init__(self, lo, hi, base_level, regions, triangles=None, lmax=3, device=0):
+        L = _lib.load()
+        tri = np.ascontiguousarray(np.zeros((0, 3, 3)) if triangles is None else triangles, dtype=np.float64)
+        regs = (Region * max(1, len(regions)))()
+        for i, r in enumerate(regions):
+            regs[i].kind, regs[i].level = r.kind, r.level
+            regs[i].par = (C.c_double * 8)(*r.packed())
+        P = MeshParams()
+        P.lo = (C.c_double * 3)(*lo)
+        P.hi = (C.c_double * 3)(*hi)
+        P.base_level = base_level
+        P.n_regions = len(regions)
+        P.regions = C.cast(regs, C.POINTER(Region))
+        P.quad_max_split = lmax
+        h = C.c_void_p()
+        n_tri = tri.shape[0]
+        check(L.imga_build_mesh(tri.ctypes.data_as(C.c_void_p) if n_tri else None, n_tri, C.byref(P), device,
+                                C.byref(h)))
+        self.h = h
+        self.device = device
+        info = MeshInfo()
+        check(L.imga_mesh_get_info(h, C.byref(info)))
+        self.info = {k: (list(getattr(info, k)) if k in ("hi_int", "setup_ms") else getattr(info, k))
+                     for k, _ in MeshInfo._fields_}
+        self.n_elem = info.n_elem
+        self.n_nodes = info.n_nodes
+        self.n_hang = info.n_hanging
+        self.scale = info.scale
+        self.lo = np.array(lo, dtype=np.float64)
+
+    @classmethod
+    def from_workload(cls, w, device=0, triangles=None):
+        return cls(w.lo, w.hi, w.base_level, w.regions, w.triangles() if triangles is None else triangles, w.lmax,
+                   device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().imga_destroy_mesh(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host exports ------------------------------------------------------------------
+    def export(self):
+        L = _lib.load()
+        ne, nn, nh = self.n_elem, self.n_nodes, self.n_hang
+        anc = np.zeros((ne, 3), np.uint32)
+        lev = np.zeros(ne, np.uint8)
+        conn = np.zeros((ne, 8), np.int32)
+        ijk = np.zeros((nn, 3), np.uint32)
+        hp = np.zeros((max(nh, 1), 4), np.int32)
+        hn = np.zeros(max(nh, 1), np.int8)
+        f = lambda a: a.ctypes.data_as(C.c_void_p)
+        check(L.imga_mesh_export(self.h, f(anc), f(lev), f(conn), f(ijk), f(hp), f(hn)))
+        return {"anchors": anc, "levels": lev, "conn": conn, "node_ijk": ijk, "hang_parents": hp[:nh], "hang_np": hn[:nh]}
+
+    def markers(self):
+        mk = np.zeros(self.n_elem, np.int8)
+        cf = np.zeros(self.n_elem, np.uint8)
+        check(_lib.load().imga_export_markers(self.h, mk.ctypes.data_as(C.c_void_p), cf.ctypes.data_as(C.c_void_p)))
+        return mk, cf
+
+    def cut_points(self):
+        off = np.zeros(self.n_elem + 1, np.int64)
+        pts = np.zeros((max(1, self.info["n_cut_points"]), 4))
+        check(_lib.load().imga_export_cut_points(self.h, off.ctypes.data_as(C.c_void_p), pts.ctypes.data_as(C.c_void_p)))
+        return off, pts[: self.info["n_cut_points"]]
+
+    def background(self):
+        off = np.zeros(self.n_elem + 1, np.int32)
+        ids = np.zeros(max(1, self.info["n_bt"]), np.int32)
+        check(_lib.load().imga_export_background(self.h, off.ctypes.data_as(C.c_void_p), ids.ctypes.data_as(C.c_void_p)))
+        return off, ids[: self.info["n_bt"]]
+
+    def surface_points(self):
+        n = self.info["n_surface_points"]
+        out = np.zeros((max(1, n), 10))
+        if n:
+            check(_lib.load().imga_export_surface_points(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out[:n]
+
+    # ---- device calls --------------------------------------------------------------------
+    def classify(self, pts, flags=None, stream=None):
+        import torch
+        n = pts.shape[0]
+        if flags is None:
+            flags = torch.empty(n, dtype=torch.uint8, device=pts.device)
+        check(_lib.load().imga_classify(self.h, _ptr(pts), n, _ptr(flags), _stream(stream)))
+        return flags
+
+    def residual(self, phys, u, u_prev, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None):
+        import torch
+        nn = self.n_nodes
+        if out is None:
+            out = torch.empty((nn, 4), dtype=torch.float64, device=u.device)
+        ps = physics_struct(phys)
+        check(_lib.load().imga_residual(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                        _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps),
+                                        precision, _ptr(out), _stream(stream)))
+        return out
+
+    def jvp(self, phys, u, u_prev, v, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None):
+        import torch
+        nn = self.n_nodes
+        if out is None:
+            out = torch.empty((nn, 4), dtype=torch.float64, device=u.device)
+        ps = physics_struct(phys)
+        check(_lib.load().imga_jvp(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                   _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps), precision,
+                                   _ptr(_vec(v, nn, "v")), _ptr(out), _stream(stream)))
+        return out
+
+    def profile(self, enable=True):
+        check(_lib.load().imga_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel: (total ms, launches)} since profiling was enabled (synchronises)."""
+        ms = np.zeros(4)
+        n = np.zeros(4, np.int64)
+        check(_lib.load().imga_profile_read(self.h, ms.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p)))
+        names = ("out_elements", "cut_elements", "nitsche", "strong_rows")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
+
+    def set_dirichlet(self, mask=None, vals=None, stream=None):
+        check(_lib.load().imga_set_dirichlet(self.h, _ptr(mask), _ptr(vals), _stream(stream)))

@@ -1,0 +1,263 @@
+// C ABI of the imga library: argument checks, mesh life cycle, dispatch to the device stages.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "imga_internal.h"
+
+struct imga_mesh_s {
+    imga::Mesh m;
+};
+
+namespace imga {
+thread_local std::string g_last_error;
+void set_error(const std::string& s) { g_last_error = s; }
+}  // namespace imga
+
+using imga::set_error;
+
+namespace {
+
+double ms_since(std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+}
+
+imga_status fail(imga_status s, const std::string& msg) {
+    set_error(msg);
+    return s;
+}
+
+imga_status cuda_status(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return IMGA_OK;
+    return fail(IMGA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool physics_ok(const imga_physics* p) {
+    return p && p->rho > 0.0 && p->mu >= 0.0 && p->dt > 0.0 && p->time_scheme >= 0 && p->time_scheme <= 2 &&
+           std::isfinite(p->rho) && std::isfinite(p->mu) && std::isfinite(p->dt) && p->C_b >= 0.0 && p->C_I >= 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* imga_last_error(void) { return imga::g_last_error.c_str(); }
+
+imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_params* P, int device, imga_mesh* out) {
+    if (!out || !P) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (n_tri < 0 || (n_tri > 0 && !tri)) return fail(IMGA_ERR_INVALID_ARG, "bad triangle array");
+    if (P->base_level < 0 || P->base_level > imga::kMaxLevel - 2) return fail(IMGA_ERR_INVALID_ARG, "base_level out of range");
+    if (P->quad_max_split < 0 || P->quad_max_split > 4) return fail(IMGA_ERR_INVALID_ARG, "quad_max_split out of range (0..4)");
+    if (P->n_regions < 0 || (P->n_regions > 0 && !P->regions)) return fail(IMGA_ERR_INVALID_ARG, "bad region array");
+    for (int r = 0; r < P->n_regions; ++r)
+        if (P->regions[r].level < 0 || P->regions[r].level > imga::kMaxLevel - 2 || P->regions[r].kind < 0 ||
+            P->regions[r].kind > 2)
+            return fail(IMGA_ERR_INVALID_ARG, "region level or kind out of range");
+    const bool host_only = device < 0;
+    if (!host_only && cudaSetDevice(device) != cudaSuccess) return cuda_status("cudaSetDevice");
+    imga_mesh_s* h = new (std::nothrow) imga_mesh_s();
+    if (!h) return fail(IMGA_ERR_OOM, "host allocation failed");
+    imga::Mesh& m = h->m;
+    m.device = device;
+    double L = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        m.lo[k] = P->lo[k];
+        m.hi[k] = P->hi[k];
+        if (!(P->hi[k] > P->lo[k])) { delete h; return fail(IMGA_ERR_INVALID_ARG, "empty box"); }
+        L = std::max(L, P->hi[k] - P->lo[k]);
+    }
+    m.scale = L / (double)(1u << imga::kMaxDepth);
+    m.base_level = P->base_level;
+    m.lmax = P->quad_max_split;
+    m.regions.assign(P->regions, P->regions + P->n_regions);
+    for (int k = 0; k < 3; ++k) {
+        double f = (P->hi[k] - P->lo[k]) / m.scale;
+        m.hiI[k] = (int64_t)std::llround(f);
+        int64_t cell = 1ll << (imga::kMaxDepth - P->base_level);
+        if (std::fabs(f - (double)m.hiI[k]) > 1e-6 || m.hiI[k] % cell != 0) {
+            delete h;
+            return fail(IMGA_ERR_INVALID_ARG, "box edge " + std::to_string(k) + " is not a whole number of base-level cells");
+        }
+    }
+    std::string err;
+    auto t0 = std::chrono::steady_clock::now();
+    if (!imga::build_octree(m, err) || !imga::build_nodes(m, err)) { delete h; return fail(IMGA_ERR_INVALID_ARG, err); }
+    m.setup_ms[0] = ms_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    if (!imga::build_triangles(m, tri, n_tri, err)) { delete h; return fail(IMGA_ERR_SURFACE, err); }
+    imga::build_background(m);
+    imga::build_ray_grid(m);
+    m.setup_ms[1] = ms_since(t0);
+    if (host_only) {
+        m.host_only = true;
+        *out = h;
+        return IMGA_OK;
+    }
+    t0 = std::chrono::steady_clock::now();
+    if (!imga::device_upload_geometry(m, err) || !imga::device_markers(m, err) || !imga::device_cut_quadrature(m, err)) {
+        imga::device_free(m);
+        delete h;
+        return fail(IMGA_ERR_CUDA, err);
+    }
+    m.setup_ms[2] = ms_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    imga::build_surface_points(m);
+    imga::build_bc_flags(m);
+    if (!imga::device_upload_quadrature(m, err)) { imga::device_free(m); delete h; return fail(IMGA_ERR_CUDA, err); }
+    if (cudaDeviceSynchronize() != cudaSuccess) { imga::device_free(m); delete h; return cuda_status("build"); }
+    m.setup_ms[3] = ms_since(t0);
+    *out = h;
+    return IMGA_OK;
+}
+
+void imga_destroy_mesh(imga_mesh h) {
+    if (!h) return;
+    if (h->m.host_only) { delete h; return; }
+    imga::profile_reset(h->m);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->m.device);
+    imga::device_free(h->m);
+    cudaSetDevice(cur);
+    delete h;
+}
+
+imga_status imga_mesh_get_info(imga_mesh h, imga_mesh_info* info) {
+    if (!h || !info) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    const imga::Mesh& m = h->m;
+    std::memset(info, 0, sizeof(*info));
+    info->n_elem = m.n_elem();
+    info->n_nodes = m.n_nodes();
+    info->n_hanging = m.n_hang();
+    info->n_out = (int64_t)m.out_list.size();
+    info->n_cut = (int64_t)m.cut_list.size();
+    info->n_in = m.n_in;
+    info->n_cut_points = m.cut_off.empty() ? 0 : m.cut_off.back();
+    info->n_surface_points = (int64_t)m.sq.size() / 10;
+    info->n_tri = m.tri.n;
+    info->n_bt = (int64_t)m.bt_idx.size();
+    info->n_rays = m.n_rays;
+    for (int k = 0; k < 3; ++k) info->hi_int[k] = m.hiI[k];
+    info->scale = m.scale;
+    for (int k = 0; k < 4; ++k) info->setup_ms[k] = m.setup_ms[k];
+    return IMGA_OK;
+}
+
+imga_status imga_mesh_export(imga_mesh h, uint32_t* anchors, uint8_t* levels, int32_t* conn, uint32_t* node_ijk,
+                             int32_t* hang_parents, int8_t* hang_np) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    const imga::Mesh& m = h->m;
+    if (anchors) std::memcpy(anchors, m.anc.data(), m.anc.size() * sizeof(uint32_t));
+    if (levels) std::memcpy(levels, m.lev.data(), m.lev.size());
+    if (conn) std::memcpy(conn, m.conn.data(), m.conn.size() * sizeof(int32_t));
+    if (node_ijk) std::memcpy(node_ijk, m.nijk.data(), m.nijk.size() * sizeof(uint32_t));
+    if (hang_parents) std::memcpy(hang_parents, m.hpar.data(), m.hpar.size() * sizeof(int32_t));
+    if (hang_np) std::memcpy(hang_np, m.hnp.data(), m.hnp.size());
+    return IMGA_OK;
+}
+
+imga_status imga_export_markers(imga_mesh h, int8_t* marker, uint8_t* cflags) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    if (marker) std::memcpy(marker, h->m.marker.data(), h->m.marker.size());
+    if (cflags) std::memcpy(cflags, h->m.cflags.data(), h->m.cflags.size());
+    return IMGA_OK;
+}
+
+imga_status imga_export_cut_points(imga_mesh h, int64_t* offsets, double* points) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    const imga::Mesh& m = h->m;
+    if (offsets) std::memcpy(offsets, m.cut_off_elem.data(), m.cut_off_elem.size() * sizeof(int64_t));
+    if (points) {
+        // cut_pts is in cut-list order, which is element order
+        std::memcpy(points, m.cut_pts.data(), m.cut_pts.size() * sizeof(double));
+    }
+    return IMGA_OK;
+}
+
+imga_status imga_export_background(imga_mesh h, int32_t* offsets, int32_t* tri_ids) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    if (offsets) std::memcpy(offsets, h->m.bt_off.data(), h->m.bt_off.size() * sizeof(int32_t));
+    if (tri_ids) std::memcpy(tri_ids, h->m.bt_idx.data(), h->m.bt_idx.size() * sizeof(int32_t));
+    return IMGA_OK;
+}
+
+imga_status imga_export_surface_points(imga_mesh h, double* out) {
+    if (!h || !out) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    std::memcpy(out, h->m.sq.data(), h->m.sq.size() * sizeof(double));
+    return IMGA_OK;
+}
+
+imga_status imga_classify(imga_mesh h, const double* pts, int64_t n, uint8_t* flags, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!pts || !flags))) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (imga::device_classify(h->m, pts, n, flags, stream)) return cuda_status("classify");
+    return IMGA_OK;
+}
+
+static imga_status apply(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                         const imga_physics* ph, int precision, const double* v, double* out, void* stream) {
+    if (!h || !u || !up || !out) return fail(IMGA_ERR_INVALID_ARG, "null vector");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
+    if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
+    if (precision != 0 && precision != 1) return fail(IMGA_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    for (const void* p : {(const void*)u, (const void*)up, (const void*)up2, (const void*)f, (const void*)v, (const void*)out})
+        if (p && ((uintptr_t)p & 15)) return fail(IMGA_ERR_INVALID_ARG, "node vectors must be 16-byte aligned");
+    if (imga::vms_apply(h->m, u, up, up2, f, *ph, precision, v, out, stream)) return cuda_status("residual/jvp launch");
+    return IMGA_OK;
+}
+
+imga_status imga_residual(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                          const imga_physics* ph, int precision, double* R, void* stream) {
+    return apply(h, u, up, up2, f, ph, precision, nullptr, R, stream);
+}
+
+imga_status imga_jvp(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                     const imga_physics* ph, int precision, const double* v, double* Jv, void* stream) {
+    if (!v) return fail(IMGA_ERR_INVALID_ARG, "null direction");
+    return apply(h, u, up, up2, f, ph, precision, v, Jv, stream);
+}
+
+imga_status imga_profile(imga_mesh h, int enable) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    if (enable) imga::profile_reset(h->m);
+    h->m.profiling = enable != 0;
+    return IMGA_OK;
+}
+
+imga_status imga_profile_read(imga_mesh h, double* ms, int64_t* launches) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    if (imga::profile_collect(h->m)) return cuda_status("profile_read");
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = h->m.prof_ms[k];
+        if (launches) launches[k] = h->m.prof_n[k];
+    }
+    return IMGA_OK;
+}
+
+imga_status imga_set_dirichlet(imga_mesh h, const uint8_t* mask, const double* val, void* stream) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    imga::Mesh& m = h->m;
+    if (!mask && !val) { m.user_bc = false; return IMGA_OK; }
+    if (!mask || !val) return fail(IMGA_ERR_INVALID_ARG, "mask and values go together");
+    const int64_t nn = m.n_nodes();
+    if (!m.d.bcmask_user) {
+        if (cudaMalloc((void**)&m.d.bcmask_user, std::max<int64_t>(1, nn)) != cudaSuccess ||
+            cudaMalloc((void**)&m.d.bcval_user, std::max<int64_t>(1, nn) * 4 * sizeof(double)) != cudaSuccess)
+            return fail(IMGA_ERR_OOM, "cudaMalloc failed");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemcpyAsync(m.d.bcmask_user, mask, nn, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m.d.bcval_user, val, nn * 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    m.user_bc = true;
+    return cuda_status("set_dirichlet");
+}
+
+}  // extern "C"

@@ -1,0 +1,417 @@
+// Device geometry: in/out classification (Algorithm 6), element markers (Algorithm 5) and the
+// adaptive sub-cell quadrature of Intercepted elements (Sec. "Adaptive Quadrature", Fig. GP).
+//
+// Compiled with -fmad=false: every decision (sign of (P - c_t).n_t, Moller-Trumbore barycentrics)
+// is evaluated as a fixed sequence of IEEE float64 operations, so flags are reproducible bit for
+// bit and independent of the launch configuration.
+//
+// Work decomposition
+//  * markers: one thread per element.  An element that no triangle box meets cannot be crossed
+//    by the surface, so one ray from its centre decides all its points; otherwise its 8 corners
+//    are tested against its background triangles B_T(e), falling back to a ray when the normal
+//    test is not unanimous.
+//  * rays along +x only visit the triangles binned in the (y, z) grid cell of their origin (the
+//    bins are widened far beyond rounding, so no hit or graze is missed); a ray that grazes an
+//    edge or vertex is re-cast along +y, then +z, over all triangles.
+//  * sub-cell quadrature: one thread per Intercepted element walks the sub-cell tree depth first
+//    in Morton child order (count pass, prefix sum, write pass), so every element's point list
+//    comes out in a fixed order.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+
+#include "imga_internal.h"
+
+namespace imga {
+
+namespace {
+
+constexpr double kGauss = 0.57735026918962576451;   // 1/sqrt(3)
+constexpr double kGraze = 1e-12;
+
+struct GeomView {
+    const uint64_t* key;
+    const uint32_t* anc;
+    const uint8_t* lev;
+    int64_t n_elem;
+    double lo[3], scale;
+    int64_t hiI[3];
+    const double* tv;
+    const double* tn;
+    const double* tc;
+    int64_t n_tri;
+    const int32_t* bt_off;
+    const int32_t* bt_idx;
+    const int32_t* rg_off;
+    const int32_t* rg_idx;
+    int rg_ny, rg_nz;
+    double rg_y0, rg_z0, rg_dy, rg_dz;
+};
+
+__device__ __forceinline__ uint64_t dpart1by2(uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ int64_t d_find_leaf(const GeomView& g, int64_t x, int64_t y, int64_t z) {
+    if (x < 0 || y < 0 || z < 0 || x >= g.hiI[0] || y >= g.hiI[1] || z >= g.hiI[2]) return -1;
+    uint64_t k = dpart1by2(x) | (dpart1by2(y) << 1) | (dpart1by2(z) << 2);
+    int64_t lo = 0, hi = g.n_elem;   // first index with key > k
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (g.key[mid] <= k) lo = mid + 1; else hi = mid;
+    }
+    int64_t e = lo - 1;
+    if (e < 0) return -1;
+    uint32_t s = 1u << (kMaxDepth - g.lev[e]);
+    const uint32_t* a = g.anc + 3 * e;
+    if ((uint64_t)(x - a[0]) < s && (uint64_t)(y - a[1]) < s && (uint64_t)(z - a[2]) < s) return e;
+    return -1;
+}
+
+// Moller-Trumbore against triangle t along axis `dir`; returns 1 hit, 0 miss, sets *graze
+__device__ __forceinline__ int mt_hit(const GeomView& g, int64_t t, const double P[3], int dir, bool* graze) {
+    double d[3] = {0.0, 0.0, 0.0};
+    d[dir] = 1.0;
+    const double* v = g.tv + 9 * t;
+    double e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
+    double pv[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
+    double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+    if (det == 0.0) return 0;
+    double inv = 1.0 / det;
+    double tv[3] = {P[0] - v[0], P[1] - v[1], P[2] - v[2]};
+    double u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
+    if (u < -kGraze || u > 1.0 + kGraze) return 0;
+    double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
+    double w = (d[0] * qv[0] + d[1] * qv[1] + d[2] * qv[2]) * inv;
+    if (w < -kGraze || u + w > 1.0 + kGraze) return 0;
+    double tt = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+    if (tt <= 0.0) return 0;
+    if (u < kGraze || w < kGraze || u + w > 1.0 - kGraze) *graze = true;
+    return 1;
+}
+
+__device__ int ray_parity(const GeomView& g, const double P[3], int dir, bool* graze) {
+    *graze = false;
+    int count = 0;
+    if (dir == 0) {
+        int a = (int)floor((P[1] - g.rg_y0) / g.rg_dy);
+        int b = (int)floor((P[2] - g.rg_z0) / g.rg_dz);
+        if (g.rg_ny == 0 || a < 0 || b < 0 || a >= g.rg_ny || b >= g.rg_nz) return 0;
+        int c = a * g.rg_nz + b;
+        for (int32_t i = g.rg_off[c]; i < g.rg_off[c + 1]; ++i) count += mt_hit(g, g.rg_idx[i], P, 0, graze);
+    } else {
+        for (int64_t t = 0; t < g.n_tri; ++t) count += mt_hit(g, t, P, dir, graze);
+    }
+    return count & 1;
+}
+
+__device__ int ray_classify(const GeomView& g, const double P[3], unsigned long long* nrays) {
+    atomicAdd(nrays, 1ull);
+    int par[3];
+    for (int dir = 0; dir < 3; ++dir) {
+        bool gz;
+        par[dir] = ray_parity(g, P, dir, &gz);
+        if (!gz) return par[dir];
+    }
+    return (par[0] + par[1] + par[2]) >= 2 ? 1 : 0;
+}
+
+// normal test: 0 Out, 1 In, -1 undecided (Algorithm 6 with outward normals)
+__device__ int normal_test(const GeomView& g, int64_t e, const double P[3], double tol) {
+    int32_t b = g.bt_off[e], end = g.bt_off[e + 1];
+    if (b == end) return -1;
+    int npos = 0, nneg = 0;
+    for (int32_t i = b; i < end; ++i) {
+        const double* c = g.tc + 3 * g.bt_idx[i];
+        const double* n = g.tn + 3 * g.bt_idx[i];
+        double dx = P[0] - c[0], dy = P[1] - c[1], dz = P[2] - c[2];
+        double s = dx * n[0] + dy * n[1] + dz * n[2];
+        if (s > tol) ++npos;
+        else if (s < -tol) ++nneg;
+    }
+    if (npos == end - b) return 0;
+    if (nneg == end - b) return 1;
+    return -1;
+}
+
+__device__ int is_in(const GeomView& g, int64_t e, const double P[3], unsigned long long* nrays) {
+    double h = (double)(1u << (kMaxDepth - g.lev[e])) * g.scale;
+    int r = normal_test(g, e, P, 1e-12 * h);
+    if (r >= 0) return r;
+    return ray_classify(g, P, nrays);
+}
+
+__global__ void markers_kernel(GeomView g, int8_t* marker, uint8_t* cflags, unsigned long long* nrays) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= g.n_elem) return;
+    uint32_t s = 1u << (kMaxDepth - g.lev[e]);
+    const uint32_t* a = g.anc + 3 * e;
+    int flags = 0;
+    if (g.bt_off[e] == g.bt_off[e + 1]) {
+        double C[3];
+        for (int k = 0; k < 3; ++k) C[k] = g.lo[k] + (double)(a[k] + s / 2) * g.scale;
+        flags = ray_classify(g, C, nrays) ? 0xff : 0;
+    } else {
+        for (int c = 0; c < 8; ++c) {
+            double P[3];
+            for (int k = 0; k < 3; ++k) P[k] = g.lo[k] + (double)(a[k] + (((c >> k) & 1) ? s : 0)) * g.scale;
+            if (is_in(g, e, P, nrays)) flags |= 1 << c;
+        }
+    }
+    cflags[e] = (uint8_t)flags;
+    marker[e] = (int8_t)(flags == 0xff ? 1 : flags == 0 ? 0 : 2);
+}
+
+struct Cell { uint8_t l; uint32_t i[3]; };
+
+// depth-first sub-cell walk of one Intercepted element; pts == nullptr counts only
+__device__ int64_t cut_walk(const GeomView& g, int64_t e, int lmax, double* pts, unsigned long long* nrays) {
+    const uint32_t* a = g.anc + 3 * e;
+    double h = (double)(1u << (kMaxDepth - g.lev[e])) * g.scale, hh = 0.5 * h;
+    double x0[3];
+    for (int k = 0; k < 3; ++k) x0[k] = g.lo[k] + (double)a[k] * g.scale;
+    Cell st[8 * 6];
+    int sp = 0;
+    st[sp++] = Cell{0, {0, 0, 0}};
+    int64_t n = 0;
+    while (sp > 0) {
+        Cell c = st[--sp];
+        double xi[8][3];
+        int in = 0;
+        for (int gp = 0; gp < 8; ++gp) {
+            double P[3];
+            for (int k = 0; k < 3; ++k) {
+                double num = (double)(2 * c.i[k] + 1) + (((gp >> k) & 1) ? kGauss : -kGauss);
+                xi[gp][k] = num / (double)(1u << c.l) - 1.0;
+                P[k] = x0[k] + (xi[gp][k] + 1.0) * hh;
+            }
+            if (is_in(g, e, P, nrays)) in |= 1 << gp;
+        }
+        double w = 1.0 / (double)(1u << (3 * c.l));
+        if (in == 0xff) continue;
+        if (in != 0 && c.l < lmax) {
+            for (int ch = 7; ch >= 0; --ch)
+                st[sp++] = Cell{(uint8_t)(c.l + 1), {2 * c.i[0] + (ch & 1), 2 * c.i[1] + ((ch >> 1) & 1), 2 * c.i[2] + ((ch >> 2) & 1)}};
+            continue;
+        }
+        for (int gp = 0; gp < 8; ++gp) {
+            if ((in >> gp) & 1) continue;
+            if (pts) {
+                double* o = pts + 4 * n;
+                o[0] = xi[gp][0]; o[1] = xi[gp][1]; o[2] = xi[gp][2]; o[3] = w;
+            }
+            ++n;
+        }
+    }
+    return n;
+}
+
+__global__ void cut_count_kernel(GeomView g, const int32_t* cut_list, int64_t n_cut, int lmax, int64_t* count,
+                                 unsigned long long* nrays) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_cut) return;
+    count[i] = cut_walk(g, cut_list[i], lmax, nullptr, nrays);
+}
+
+__global__ void cut_write_kernel(GeomView g, const int32_t* cut_list, int64_t n_cut, int lmax, const int64_t* off,
+                                 double* pts, float* ptsf, unsigned long long* nrays) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_cut) return;
+    double* o = pts + 4 * off[i];
+    int64_t n = cut_walk(g, cut_list[i], lmax, o, nrays);
+    for (int64_t k = 0; k < 4 * n; ++k) ptsf[4 * off[i] + k] = (float)o[k];
+}
+
+__global__ void classify_kernel(GeomView g, const double* pts, int64_t n, uint8_t* flags, unsigned long long* nrays) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double P[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+    int64_t I[3];
+    for (int k = 0; k < 3; ++k) {
+        double f = floor((P[k] - g.lo[k]) / g.scale);
+        if (!(f >= 0.0 && f < (double)g.hiI[k])) { flags[i] = 0; return; }
+        I[k] = (int64_t)f;
+    }
+    int64_t e = d_find_leaf(g, I[0], I[1], I[2]);
+    flags[i] = e < 0 ? 0 : (uint8_t)is_in(g, e, P, nrays);
+}
+
+GeomView view(const Mesh& m) {
+    GeomView g;
+    g.key = m.d.key;
+    g.anc = m.d.anc;
+    g.lev = m.d.lev;
+    g.n_elem = m.n_elem();
+    for (int k = 0; k < 3; ++k) { g.lo[k] = m.lo[k]; g.hiI[k] = m.hiI[k]; }
+    g.scale = m.scale;
+    g.tv = m.d.tv;
+    g.tn = m.d.tn;
+    g.tc = m.d.tc;
+    g.n_tri = m.tri.n;
+    g.bt_off = m.d.bt_off;
+    g.bt_idx = m.d.bt_idx;
+    g.rg_off = m.d.rg_off;
+    g.rg_idx = m.d.rg_idx;
+    g.rg_ny = m.grid.ny;
+    g.rg_nz = m.grid.nz;
+    g.rg_y0 = m.grid.y0;
+    g.rg_z0 = m.grid.z0;
+    g.rg_dy = m.grid.dy;
+    g.rg_dz = m.grid.dz;
+    return g;
+}
+
+unsigned long long* g_nrays_dev = nullptr;
+
+template <class T>
+bool upload(T** dst, const std::vector<T>& src, std::string& err, size_t min_elems = 1) {
+    size_t n = std::max(src.size(), min_elems);
+    if (cudaMalloc((void**)dst, n * sizeof(T)) != cudaSuccess) { err = "cudaMalloc failed"; return false; }
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+        err = "cudaMemcpy failed";
+        return false;
+    }
+    return true;
+}
+
+bool check(cudaError_t e, std::string& err, const char* what) {
+    if (e == cudaSuccess) return true;
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
+}
+
+}  // namespace
+
+bool device_upload_geometry(Mesh& m, std::string& err) {
+    DeviceMesh& d = m.d;
+    d.n_elem = m.n_elem();
+    d.n_nodes = m.n_nodes();
+    d.n_hang = m.n_hang();
+    d.n_tri = m.tri.n;
+    std::vector<int32_t> hp(m.hpar);
+    if (!upload(&d.key, m.key, err) || !upload(&d.anc, m.anc, err) || !upload(&d.lev, m.lev, err) ||
+        !upload(&d.conn, m.conn, err) || !upload(&d.hpar, hp, err) || !upload(&d.tv, m.tri.v, err) ||
+        !upload(&d.tn, m.tri.nrm, err) || !upload(&d.tc, m.tri.cen, err) || !upload(&d.bt_off, m.bt_off, err) ||
+        !upload(&d.bt_idx, m.bt_idx, err) || !upload(&d.rg_off, m.grid.off, err) || !upload(&d.rg_idx, m.grid.idx, err))
+        return false;
+    if (!check(cudaMalloc((void**)&d.marker, std::max<int64_t>(1, d.n_elem)), err, "cudaMalloc")) return false;
+    if (!check(cudaMalloc((void**)&d.cflags, std::max<int64_t>(1, d.n_elem)), err, "cudaMalloc")) return false;
+    if (!g_nrays_dev && !check(cudaMalloc((void**)&g_nrays_dev, sizeof(unsigned long long)), err, "cudaMalloc")) return false;
+    return true;
+}
+
+static int64_t read_rays() {
+    unsigned long long n = 0;
+    cudaMemcpy(&n, g_nrays_dev, sizeof(n), cudaMemcpyDeviceToHost);
+    return (int64_t)n;
+}
+
+bool device_markers(Mesh& m, std::string& err) {
+    const int64_t ne = m.n_elem();
+    cudaMemset(g_nrays_dev, 0, sizeof(unsigned long long));
+    GeomView g = view(m);
+    if (ne > 0) markers_kernel<<<(unsigned)((ne + 127) / 128), 128>>>(g, m.d.marker, m.d.cflags, g_nrays_dev);
+    if (!check(cudaDeviceSynchronize(), err, "markers kernel")) return false;
+    m.marker.resize(ne);
+    m.cflags.resize(ne);
+    if (!check(cudaMemcpy(m.marker.data(), m.d.marker, ne, cudaMemcpyDeviceToHost), err, "copy markers")) return false;
+    if (!check(cudaMemcpy(m.cflags.data(), m.d.cflags, ne, cudaMemcpyDeviceToHost), err, "copy flags")) return false;
+    m.n_rays = read_rays();
+    m.out_list.clear();
+    m.cut_list.clear();
+    m.n_in = 0;
+    for (int64_t e = 0; e < ne; ++e) {
+        if (m.marker[e] == 0) m.out_list.push_back((int32_t)e);
+        else if (m.marker[e] == 2) m.cut_list.push_back((int32_t)e);
+        else ++m.n_in;
+    }
+    return true;
+}
+
+bool device_cut_quadrature(Mesh& m, std::string& err) {
+    const int64_t nc = (int64_t)m.cut_list.size();
+    GeomView g = view(m);
+    if (!upload(&m.d.out_list, m.out_list, err) || !upload(&m.d.cut_list, m.cut_list, err)) return false;
+    int64_t* cnt = nullptr;
+    if (!check(cudaMalloc((void**)&cnt, (nc + 1) * sizeof(int64_t)), err, "cudaMalloc")) return false;
+    cudaMemset(g_nrays_dev, 0, sizeof(unsigned long long));
+    if (nc > 0) cut_count_kernel<<<(unsigned)((nc + 63) / 64), 64>>>(g, m.d.cut_list, nc, m.lmax, cnt, g_nrays_dev);
+    if (!check(cudaDeviceSynchronize(), err, "cut count kernel")) { cudaFree(cnt); return false; }
+    std::vector<int64_t> c(nc);
+    if (nc) cudaMemcpy(c.data(), cnt, nc * sizeof(int64_t), cudaMemcpyDeviceToHost);
+    m.cut_off.assign(nc + 1, 0);
+    for (int64_t i = 0; i < nc; ++i) m.cut_off[i + 1] = m.cut_off[i] + c[i];
+    const int64_t np = m.cut_off[nc];
+    cudaFree(cnt);
+    if (!upload(&m.d.cut_off, m.cut_off, err)) return false;
+    if (!check(cudaMalloc((void**)&m.d.cut_pts, std::max<int64_t>(1, np) * 4 * sizeof(double)), err, "cudaMalloc")) return false;
+    if (!check(cudaMalloc((void**)&m.d.cut_pts_f, std::max<int64_t>(1, np) * 4 * sizeof(float)), err, "cudaMalloc")) return false;
+    if (nc > 0)
+        cut_write_kernel<<<(unsigned)((nc + 63) / 64), 64>>>(g, m.d.cut_list, nc, m.lmax, m.d.cut_off, m.d.cut_pts,
+                                                              m.d.cut_pts_f, g_nrays_dev);
+    if (!check(cudaDeviceSynchronize(), err, "cut write kernel")) return false;
+    m.n_rays += read_rays() / 2;   // the write pass repeats the count pass's casts
+    m.cut_pts.resize(4 * np);
+    if (np) cudaMemcpy(m.cut_pts.data(), m.d.cut_pts, 4 * np * sizeof(double), cudaMemcpyDeviceToHost);
+    m.cut_off_elem.assign(m.n_elem() + 1, 0);
+    for (int64_t i = 0; i < nc; ++i) m.cut_off_elem[m.cut_list[i] + 1] = c[i];
+    for (int64_t e = 0; e < m.n_elem(); ++e) m.cut_off_elem[e + 1] += m.cut_off_elem[e];
+    return true;
+}
+
+// surface points (sorted by owning element, reference coordinates) and boundary flags
+bool device_upload_quadrature(Mesh& m, std::string& err) {
+    const int64_t ns = (int64_t)m.sq.size() / 10;
+    std::vector<int64_t> order(ns);
+    for (int64_t i = 0; i < ns; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return m.sq[10 * a + 8] < m.sq[10 * b + 8]; });
+    std::vector<int32_t> el(ns);
+    std::vector<double> xr(3 * ns), nr(3 * ns), w(ns), tb(ns);
+    for (int64_t j = 0; j < ns; ++j) {
+        const double* r = &m.sq[10 * order[j]];
+        int64_t e = (int64_t)r[8];
+        el[j] = (int32_t)e;
+        double h = (double)(1u << (kMaxDepth - m.lev[e])) * m.scale;
+        for (int k = 0; k < 3; ++k) {
+            double x0 = m.lo[k] + (double)m.anc[3 * e + k] * m.scale;
+            xr[3 * j + k] = (r[k] - x0) / (0.5 * h) - 1.0;
+            nr[3 * j + k] = r[3 + k];
+        }
+        w[j] = r[6];
+        tb[j] = 1.0 / r[7];
+    }
+    if (!upload(&m.d.sq_elem, el, err) || !upload(&m.d.sq_x, xr, err) || !upload(&m.d.sq_n, nr, err) ||
+        !upload(&m.d.sq_w, w, err) || !upload(&m.d.sq_taub, tb, err) || !upload(&m.d.bcflag, m.bcflag, err))
+        return false;
+    return true;
+}
+
+int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream) {
+    if (n <= 0) return 0;
+    GeomView g = view(m);
+    classify_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(g, pts, n, flags, g_nrays_dev);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+void device_free(Mesh& m) {
+    DeviceMesh& d = m.d;
+    void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
+                    d.marker, d.cflags, d.out_list, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
+                    d.sq_n, d.sq_w, d.sq_taub, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    d = DeviceMesh();
+    m.scratch = nullptr;
+}
+
+}  // namespace imga

@@ -1,0 +1,155 @@
+// Internal data structures of the imga library (host side + device pointers).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/imga.h"
+
+namespace imga {
+
+constexpr int kMaxDepth = 20;     // integer coordinates on [0, 2^20] per root edge
+constexpr int kMaxLevel = 15;     // deepest leaf level the mesh accepts (+1 internal)
+
+// Morton code: bit b of x, y, z -> bits 3b, 3b+1, 3b+2
+inline uint64_t part1by2(uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return part1by2(x) | (part1by2(y) << 1) | (part1by2(z) << 2);
+}
+
+// Triangle tables (structure of arrays, float64), shared by the host and the device copies.
+struct TriHost {
+    int64_t n = 0;
+    std::vector<double> v;      // [n][9]
+    std::vector<double> nrm;    // [n][3] unit normal, out of the body
+    std::vector<double> cen;    // [n][3]
+    std::vector<double> bmin, bmax;  // [n][3]
+    std::vector<double> area;   // [n]
+};
+
+// uniform grid over the (y, z) projection of the triangles, for rays cast along +x
+struct RayGridHost {
+    int ny = 0, nz = 0;
+    double y0 = 0, z0 = 0, dy = 1, dz = 1;
+    std::vector<int32_t> off;   // [ny*nz + 1]
+    std::vector<int32_t> idx;
+};
+
+// device mirror of everything the kernels read
+struct DeviceMesh {
+    int64_t n_elem = 0, n_nodes = 0, n_hang = 0, n_tri = 0;
+    uint64_t* key = nullptr;      // [n_elem] Morton key of each anchor (sorted)
+    uint32_t* anc = nullptr;      // [n_elem][3]
+    uint8_t* lev = nullptr;       // [n_elem]
+    int32_t* conn = nullptr;      // [n_elem][8]
+    int32_t* hpar = nullptr;      // [n_hang][4]
+    // triangles
+    double* tv = nullptr;         // [n_tri][9]
+    double* tn = nullptr;         // [n_tri][3]
+    double* tc = nullptr;         // [n_tri][3]
+    int32_t* bt_off = nullptr;    // [n_elem + 1]
+    int32_t* bt_idx = nullptr;
+    int32_t* rg_off = nullptr;    // ray grid
+    int32_t* rg_idx = nullptr;
+    // classification results
+    int8_t* marker = nullptr;     // [n_elem]
+    uint8_t* cflags = nullptr;    // [n_elem]
+    // quadrature
+    int32_t* out_list = nullptr;  // Out elements
+    int32_t* cut_list = nullptr;  // Intercepted elements
+    int64_t* cut_off = nullptr;   // [n_cut + 1] into cut_pts
+    double* cut_pts = nullptr;    // [n][4] (xi0, xi1, xi2, reference weight)
+    float* cut_pts_f = nullptr;   // [n][4] float copy
+    int32_t* sq_elem = nullptr;   // surface points, sorted by element
+    double* sq_x = nullptr;       // [n][3] reference coordinates in the element
+    double* sq_n = nullptr;       // [n][3]
+    double* sq_w = nullptr;
+    double* sq_taub = nullptr;    // 1 / h_b
+    // boundary rows
+    uint8_t* bcflag = nullptr;    // [n_nodes] bits 0-3 box Dirichlet, bit 4 In-only node
+    uint8_t* bcmask_user = nullptr;
+    double* bcval_user = nullptr;
+};
+
+struct Mesh {
+    int device = 0;
+    double lo[3], hi[3], scale = 1.0;
+    int64_t hiI[3];
+    int base_level = 0, lmax = 3;
+    std::vector<imga_region> regions;
+    // octree
+    std::vector<uint64_t> key;
+    std::vector<uint32_t> anc;    // [n][3]
+    std::vector<uint8_t> lev;
+    // nodes
+    std::vector<uint32_t> nijk;   // [n_nodes][3]
+    std::vector<int32_t> conn;    // [n_elem][8]
+    std::vector<int32_t> hpar;    // [n_hang][4]
+    std::vector<int8_t> hnp;
+    // geometry
+    TriHost tri;
+    std::vector<int32_t> bt_off, bt_idx;
+    RayGridHost grid;
+    std::vector<int8_t> marker;
+    std::vector<uint8_t> cflags;
+    std::vector<int32_t> out_list, cut_list;
+    std::vector<int64_t> cut_off_elem;   // [n_elem + 1] for export
+    std::vector<double> cut_pts;         // [n][4] in cut_list order
+    std::vector<int64_t> cut_off;        // [n_cut + 1]
+    std::vector<double> sq;              // [n][10] surface points (export layout)
+    std::vector<uint8_t> bcflag;
+    int64_t n_in = 0, n_rays = 0;
+    double setup_ms[4] = {0, 0, 0, 0};
+    bool user_bc = false;
+    bool host_only = false;
+    DeviceMesh d;
+    void* scratch = nullptr;             // device workspace for the kernels
+    // per-kernel profiling (CUDA events, one pair per launch, resolved at read time)
+    bool profiling = false;
+    std::vector<std::pair<void*, void*>> prof_ev[4];
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_n[4] = {0, 0, 0, 0};
+    size_t scratch_bytes = 0;
+
+    int64_t n_elem() const { return (int64_t)lev.size(); }
+    int64_t n_nodes() const { return (int64_t)nijk.size() / 3; }
+    int64_t n_hang() const { return (int64_t)hnp.size(); }
+};
+
+// host builders (mesh_host.cpp)
+bool build_octree(Mesh& m, std::string& err);
+bool build_nodes(Mesh& m, std::string& err);
+bool build_triangles(Mesh& m, const double* tri, int64_t n, std::string& err);
+void build_background(Mesh& m);
+void build_ray_grid(Mesh& m);
+void build_surface_points(Mesh& m);
+void build_bc_flags(Mesh& m);
+int64_t find_leaf(const Mesh& m, int64_t x, int64_t y, int64_t z);
+
+// device stages (geom.cu)
+bool device_upload_geometry(Mesh& m, std::string& err);
+bool device_markers(Mesh& m, std::string& err);
+bool device_cut_quadrature(Mesh& m, std::string& err);
+bool device_upload_quadrature(Mesh& m, std::string& err);
+int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream);
+void device_free(Mesh& m);
+
+// residual / Jv (vms.cu)
+int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+              const imga_physics& ph, int precision, const double* v, double* out, void* stream);
+
+void profile_reset(Mesh& m);
+int profile_collect(Mesh& m);
+
+void set_error(const std::string& s);
+
+}  // namespace imga

@@ -1,0 +1,487 @@
+// Host-side construction of the linear octree, its nodes, and the geometric tables.
+//
+//  * top-down refinement by region predicates, octants outside the box dropped
+//    (Sec. "Octree based Mesh Generation": refine an octant while a user function says so);
+//  * 2:1 balance across faces, edges and vertices (same section);
+//  * meshing: independent nodes, hanging nodes with 2 (edge) or 4 (face) parents -- the
+//    interpolation operators I1d and I2d = I1d x I1d of Algorithm 3;
+//  * triangle tables, background triangles B_T of every element (Algorithm 1), a (y, z) grid
+//    for ray casting, the Nitsche surface quadrature (Eq. weakbc and its remark on h_b), and
+//    the strong-boundary / In-only node rows (Algorithm 1, Fig. IBM).
+//
+// Leaves are kept sorted by the Morton code of their anchor; the leaf containing a point is
+// the last leaf whose code does not exceed the point's code (binary search).  Arithmetic that
+// decides geometry (region tests, box / AABB overlaps, triangle normals and centroids, h_b) is
+// compiled with floating-point contraction disabled so that it is reproducible bit for bit.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "imga_internal.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace imga {
+
+namespace {
+
+inline uint32_t octsize(int l) { return 1u << (kMaxDepth - l); }
+
+inline bool inside_box(const Mesh& m, int64_t x, int64_t y, int64_t z) {
+    return x >= 0 && y >= 0 && z >= 0 && x < m.hiI[0] && y < m.hiI[1] && z < m.hiI[2];
+}
+
+void phys_box(const Mesh& m, const uint32_t a[3], uint32_t s, double b0[3], double b1[3]) {
+    for (int k = 0; k < 3; ++k) {
+        b0[k] = m.lo[k] + (double)a[k] * m.scale;
+        b1[k] = m.lo[k] + (double)(a[k] + s) * m.scale;
+    }
+}
+
+bool region_meets(const imga_region& r, const double b0[3], const double b1[3]) {
+    const double* p = r.par;
+    switch (r.kind) {
+        case 0: {  // spherical band: nearest and farthest distance of the box to the centre
+            double near2 = 0.0, far2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double below = b0[k] - p[k], above = p[k] - b1[k];
+                double dn = std::max(0.0, std::max(below, above));
+                near2 = near2 + dn * dn;
+                double df = std::max(std::fabs(b0[k] - p[k]), std::fabs(b1[k] - p[k]));
+                far2 = far2 + df * df;
+            }
+            double outer = p[3] + p[4], inner = p[3] - p[4];
+            if (!(near2 <= outer * outer)) return false;
+            return inner <= 0.0 || far2 >= inner * inner;
+        }
+        case 1:
+            for (int k = 0; k < 3; ++k)
+                if (!(b0[k] <= p[3 + k] && b1[k] >= p[k])) return false;
+            return true;
+        default: {  // cone along +x tested at the box centre, inflated by half the diagonal
+            double cx = 0.5 * (b0[0] + b1[0]), cy = 0.5 * (b0[1] + b1[1]), cz = 0.5 * (b0[2] + b1[2]);
+            double half_diag = 0.8660254037844386 * (b1[0] - b0[0]);
+            double s = cx - p[0];
+            if (s < -half_diag || s > p[3] + half_diag) return false;
+            double ry = cy - p[1], rz = cz - p[2];
+            double rad = std::sqrt(ry * ry + rz * rz);
+            return rad <= p[4] + std::max(s, 0.0) * p[5] + half_diag;
+        }
+    }
+}
+
+int wanted_level(const Mesh& m, const uint32_t a[3], int l) {
+    double b0[3], b1[3];
+    phys_box(m, a, octsize(l), b0, b1);
+    int t = m.base_level;
+    for (const imga_region& r : m.regions)
+        if (r.level > t && region_meets(r, b0, b1)) t = r.level;
+    return t;
+}
+
+struct Oct { uint32_t a[3]; int l; };
+
+}  // namespace
+
+int64_t find_leaf(const Mesh& m, int64_t x, int64_t y, int64_t z) {
+    if (!inside_box(m, x, y, z)) return -1;
+    uint64_t k = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+    auto it = std::upper_bound(m.key.begin(), m.key.end(), k);
+    if (it == m.key.begin()) return -1;
+    int64_t e = (int64_t)(it - m.key.begin()) - 1;
+    uint32_t s = octsize(m.lev[e]);
+    const uint32_t* a = &m.anc[3 * e];
+    if ((uint64_t)x - a[0] < s && (uint64_t)y - a[1] < s && (uint64_t)z - a[2] < s) return e;
+    return -1;
+}
+
+static void set_leaves(Mesh& m, const std::vector<Oct>& L) {
+    size_t n = L.size();
+    m.anc.resize(3 * n);
+    m.lev.resize(n);
+    m.key.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) m.anc[3 * i + k] = L[i].a[k];
+        m.lev[i] = (uint8_t)L[i].l;
+        m.key[i] = morton3(L[i].a[0], L[i].a[1], L[i].a[2]);
+    }
+}
+
+bool build_octree(Mesh& m, std::string& err) {
+    // top-down refinement, depth first in Morton child order: leaves come out sorted
+    std::vector<Oct> leaves;
+    std::vector<Oct> stack;
+    stack.push_back({{0, 0, 0}, 0});
+    while (!stack.empty()) {
+        Oct o = stack.back();
+        stack.pop_back();
+        if (o.l < wanted_level(m, o.a, o.l)) {
+            uint32_t h = octsize(o.l) >> 1;
+            for (int c = 7; c >= 0; --c) {   // pushed in reverse so child 0 is processed first
+                Oct ch{{o.a[0] + ((c & 1) ? h : 0), o.a[1] + ((c & 2) ? h : 0), o.a[2] + ((c & 4) ? h : 0)}, o.l + 1};
+                if (inside_box(m, ch.a[0], ch.a[1], ch.a[2])) stack.push_back(ch);
+            }
+        } else {
+            leaves.push_back(o);
+        }
+    }
+    set_leaves(m, leaves);
+    // 2:1 balance: a leaf of level l forces every leaf it touches to level >= l - 1
+    static const int nb[26][3] = {{-1,-1,-1},{0,-1,-1},{1,-1,-1},{-1,0,-1},{0,0,-1},{1,0,-1},{-1,1,-1},{0,1,-1},{1,1,-1},
+                                  {-1,-1,0},{0,-1,0},{1,-1,0},{-1,0,0},{1,0,0},{-1,1,0},{0,1,0},{1,1,0},
+                                  {-1,-1,1},{0,-1,1},{1,-1,1},{-1,0,1},{0,0,1},{1,0,1},{-1,1,1},{0,1,1},{1,1,1}};
+    for (int pass = 0; pass < 64; ++pass) {
+        int64_t n = m.n_elem();
+        std::vector<uint8_t> split(n, 0);
+        int any = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(| : any)
+        for (int64_t e = 0; e < n; ++e) {
+            int l = m.lev[e];
+            if (l < 2) continue;
+            int64_t s = octsize(l);
+            const uint32_t* a = &m.anc[3 * e];
+            for (int d = 0; d < 26; ++d) {
+                int64_t q[3];
+                for (int k = 0; k < 3; ++k)
+                    q[k] = nb[d][k] < 0 ? (int64_t)a[k] - 1 : nb[d][k] > 0 ? (int64_t)a[k] + s : (int64_t)a[k];
+                int64_t o = find_leaf(m, q[0], q[1], q[2]);
+                if (o >= 0 && m.lev[o] < l - 1) { split[o] = 1; any = 1; }
+            }
+        }
+        if (!any) break;
+        std::vector<Oct> next;
+        next.reserve(n + 8 * std::count(split.begin(), split.end(), 1));
+        for (int64_t e = 0; e < n; ++e) {
+            const uint32_t* a = &m.anc[3 * e];
+            int l = m.lev[e];
+            if (!split[e]) { next.push_back({{a[0], a[1], a[2]}, l}); continue; }
+            uint32_t h = octsize(l) >> 1;
+            for (int c = 0; c < 8; ++c) {
+                Oct ch{{a[0] + ((c & 1) ? h : 0), a[1] + ((c & 2) ? h : 0), a[2] + ((c & 4) ? h : 0)}, l + 1};
+                if (inside_box(m, ch.a[0], ch.a[1], ch.a[2])) next.push_back(ch);
+            }
+        }
+        set_leaves(m, next);
+        if (pass == 63) { err = "2:1 balance did not converge"; return false; }
+    }
+    for (int64_t e = 0; e < m.n_elem(); ++e)
+        if (m.lev[e] > kMaxLevel - 1) { err = "leaf level beyond the supported maximum"; return false; }
+    return true;
+}
+
+bool build_nodes(Mesh& m, std::string& err) {
+    const int64_t ne = m.n_elem();
+    // every leaf corner, deduplicated by Morton code of its coordinates
+    std::vector<uint64_t> ck(8 * ne);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < ne; ++e) {
+        uint32_t s = octsize(m.lev[e]);
+        const uint32_t* a = &m.anc[3 * e];
+        for (int c = 0; c < 8; ++c)
+            ck[8 * e + c] = morton3(a[0] + ((c & 1) ? s : 0), a[1] + ((c & 2) ? s : 0), a[2] + ((c & 4) ? s : 0));
+    }
+    std::vector<uint64_t> uk(ck);
+    std::sort(uk.begin(), uk.end());
+    uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
+    const int64_t nu = (int64_t)uk.size();
+    // coordinates of each unique corner (taken from one element that has it)
+    std::vector<uint32_t> ux(3 * nu);
+    std::vector<int64_t> owner(nu, -1);
+    for (int64_t i = 0; i < 8 * ne; ++i) {
+        int64_t u = std::lower_bound(uk.begin(), uk.end(), ck[i]) - uk.begin();
+        if (owner[u] < 0) owner[u] = i;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t u = 0; u < nu; ++u) {
+        int64_t e = owner[u] / 8, c = owner[u] % 8;
+        uint32_t s = octsize(m.lev[e]);
+        for (int k = 0; k < 3; ++k) ux[3 * u + k] = m.anc[3 * e + k] + (((c >> k) & 1) ? s : 0);
+    }
+    // hanging test: P is hanging when a leaf touching P does not have P as a corner
+    std::vector<int8_t> np(nu, 0);
+    std::vector<uint32_t> par(12 * nu);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(| : bad)
+    for (int64_t u = 0; u < nu; ++u) {
+        const uint32_t* P = &ux[3 * u];
+        for (int nbh = 0; nbh < 8 && np[u] == 0; ++nbh) {
+            int64_t q[3] = {(int64_t)P[0] - (nbh & 1), (int64_t)P[1] - ((nbh >> 1) & 1), (int64_t)P[2] - ((nbh >> 2) & 1)};
+            int64_t o = find_leaf(m, q[0], q[1], q[2]);
+            if (o < 0) continue;
+            uint32_t s = octsize(m.lev[o]);
+            const uint32_t* a = &m.anc[3 * o];
+            int mid[3], nmid = 0;
+            for (int k = 0; k < 3; ++k) {
+                if (P[k] == a[k] || P[k] == a[k] + s) mid[k] = 0;
+                else if (P[k] == a[k] + s / 2) { mid[k] = 1; ++nmid; }
+                else { bad = 1; mid[k] = 0; }
+            }
+            if (nmid == 0) continue;
+            if (nmid > 2) { bad = 1; continue; }
+            np[u] = (int8_t)(1 << nmid);
+            for (int p = 0; p < np[u]; ++p) {
+                int bit = 0;
+                for (int k = 0; k < 3; ++k) {
+                    if (mid[k]) { par[12 * u + 3 * p + k] = a[k] + (((p >> bit) & 1) ? s : 0); ++bit; }
+                    else par[12 * u + 3 * p + k] = P[k];
+                }
+            }
+        }
+    }
+    if (bad) { err = "mesh is not 2:1 balanced (hanging node off an edge/face midpoint)"; return false; }
+    // independent nodes (Morton order) and hanging nodes (Morton order)
+    std::vector<int64_t> slot(nu);
+    int64_t nn = 0, nh = 0;
+    for (int64_t u = 0; u < nu; ++u) slot[u] = np[u] ? -(++nh) : nn++;
+    m.nijk.resize(3 * nn);
+    m.hpar.assign(4 * nh, -1);
+    m.hnp.resize(nh);
+    std::vector<uint64_t> nkey(nn);
+    for (int64_t u = 0; u < nu; ++u)
+        if (slot[u] >= 0) {
+            for (int k = 0; k < 3; ++k) m.nijk[3 * slot[u] + k] = ux[3 * u + k];
+            nkey[slot[u]] = uk[u];
+        }
+    for (int64_t u = 0; u < nu; ++u) {
+        if (slot[u] >= 0) continue;
+        int64_t h = -slot[u] - 1;
+        m.hnp[h] = np[u];
+        for (int p = 0; p < np[u]; ++p) {
+            const uint32_t* Q = &par[12 * u + 3 * p];
+            uint64_t pk = morton3(Q[0], Q[1], Q[2]);
+            auto it = std::lower_bound(nkey.begin(), nkey.end(), pk);
+            if (it == nkey.end() || *it != pk) { err = "parent of a hanging node is not an independent node"; return false; }
+            m.hpar[4 * h + p] = (int32_t)(it - nkey.begin());
+        }
+    }
+    m.conn.resize(8 * ne);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < 8 * ne; ++i) {
+        int64_t u = std::lower_bound(uk.begin(), uk.end(), ck[i]) - uk.begin();
+        m.conn[i] = slot[u] >= 0 ? (int32_t)slot[u] : (int32_t)(nn + (-slot[u] - 1));
+    }
+    return true;
+}
+
+bool build_triangles(Mesh& m, const double* t, int64_t n, std::string& err) {
+    TriHost& T = m.tri;
+    T.n = n;
+    T.v.assign(t, t + 9 * n);
+    T.nrm.resize(3 * n);
+    T.cen.resize(3 * n);
+    T.bmin.resize(3 * n);
+    T.bmax.resize(3 * n);
+    T.area.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double* v = &T.v[9 * i];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
+        double cx = e1[1] * e2[2] - e1[2] * e2[1];
+        double cy = e1[2] * e2[0] - e1[0] * e2[2];
+        double cz = e1[0] * e2[1] - e1[1] * e2[0];
+        double len = std::sqrt(cx * cx + cy * cy + cz * cz);
+        if (!(len > 0.0)) { err = "degenerate triangle " + std::to_string(i); return false; }
+        T.nrm[3 * i] = cx / len;
+        T.nrm[3 * i + 1] = cy / len;
+        T.nrm[3 * i + 2] = cz / len;
+        T.area[i] = 0.5 * len;
+        for (int k = 0; k < 3; ++k) {
+            T.cen[3 * i + k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0;
+            T.bmin[3 * i + k] = std::min(std::min(v[k], v[3 + k]), v[6 + k]);
+            T.bmax[3 * i + k] = std::max(std::max(v[k], v[3 + k]), v[6 + k]);
+        }
+    }
+    return true;
+}
+
+// Background triangles: for every triangle, descend the octree from the root through the
+// octants its bounding box meets, down to the leaves; B_T(e) = triangles whose box meets the
+// closed box of e.  Stored as CSR sorted by element, then triangle.
+void build_background(Mesh& m) {
+    const int64_t nt = m.tri.n, ne = m.n_elem();
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> local;
+#pragma omp parallel
+    {
+#pragma omp single
+        {
+#ifdef _OPENMP
+            local.resize(omp_get_num_threads());
+#else
+            local.resize(1);
+#endif
+        }
+#ifdef _OPENMP
+        auto& mine = local[omp_get_thread_num()];
+#else
+        auto& mine = local[0];
+#endif
+        std::vector<Oct> st;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t t = 0; t < nt; ++t) {
+            const double* lo = &m.tri.bmin[3 * t];
+            const double* hi = &m.tri.bmax[3 * t];
+            st.clear();
+            st.push_back({{0, 0, 0}, 0});
+            while (!st.empty()) {
+                Oct o = st.back();
+                st.pop_back();
+                double b0[3], b1[3];
+                uint32_t s = octsize(o.l);
+                phys_box(m, o.a, s, b0, b1);
+                bool meet = true;
+                for (int k = 0; k < 3; ++k)
+                    if (!(lo[k] <= b1[k] && hi[k] >= b0[k])) meet = false;
+                if (!meet) continue;
+                int64_t e = find_leaf(m, o.a[0], o.a[1], o.a[2]);
+                if (e >= 0 && m.lev[e] <= o.l) {
+                    // the octant lies inside leaf e: test the leaf's own box
+                    double c0[3], c1[3];
+                    phys_box(m, &m.anc[3 * e], octsize(m.lev[e]), c0, c1);
+                    bool hit = true;
+                    for (int k = 0; k < 3; ++k)
+                        if (!(lo[k] <= c1[k] && hi[k] >= c0[k])) hit = false;
+                    if (hit) mine.push_back({(int32_t)e, (int32_t)t});
+                    continue;
+                }
+                uint32_t h = s >> 1;
+                for (int c = 0; c < 8; ++c) {
+                    Oct ch{{o.a[0] + ((c & 1) ? h : 0), o.a[1] + ((c & 2) ? h : 0), o.a[2] + ((c & 4) ? h : 0)}, o.l + 1};
+                    if (inside_box(m, ch.a[0], ch.a[1], ch.a[2])) st.push_back(ch);
+                }
+            }
+        }
+    }
+    std::vector<std::pair<int32_t, int32_t>> all;
+    for (auto& v : local) all.insert(all.end(), v.begin(), v.end());
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    m.bt_off.assign(ne + 1, 0);
+    m.bt_idx.resize(all.size());
+    for (size_t i = 0; i < all.size(); ++i) { m.bt_off[all[i].first + 1]++; m.bt_idx[i] = all[i].second; }
+    for (int64_t e = 0; e < ne; ++e) m.bt_off[e + 1] += m.bt_off[e];
+}
+
+// Ray grid: triangles binned by their (y, z) bounding boxes widened by a margin far above
+// rounding, so that a ray cast along +x can only hit -- or graze -- triangles listed in the
+// cell of its origin.
+void build_ray_grid(Mesh& m) {
+    RayGridHost& g = m.grid;
+    const int64_t nt = m.tri.n;
+    g.ny = g.nz = 0;
+    g.off.assign(1, 0);
+    g.idx.clear();
+    if (nt == 0) return;
+    double ylo = 1e300, yhi = -1e300, zlo = 1e300, zhi = -1e300, ext = 0.0;
+    for (int64_t t = 0; t < nt; ++t) {
+        ylo = std::min(ylo, m.tri.bmin[3 * t + 1]); yhi = std::max(yhi, m.tri.bmax[3 * t + 1]);
+        zlo = std::min(zlo, m.tri.bmin[3 * t + 2]); zhi = std::max(zhi, m.tri.bmax[3 * t + 2]);
+    }
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, std::fabs(m.lo[k]) + std::fabs(m.hi[k]));
+    ext = std::max(ext, std::max(std::fabs(ylo), std::max(std::fabs(yhi), std::max(std::fabs(zlo), std::fabs(zhi)))));
+    const double margin = 1e-9 * ext;
+    int n1 = (int)std::min(2048.0, std::max(1.0, std::sqrt((double)nt) * 1.5));
+    g.ny = g.nz = n1;
+    g.y0 = ylo - 2 * margin;
+    g.z0 = zlo - 2 * margin;
+    g.dy = (yhi - ylo + 4 * margin) / n1;
+    g.dz = (zhi - zlo + 4 * margin) / n1;
+    auto cell = [&](double v, double v0, double dv, int n) {
+        int c = (int)std::floor((v - v0) / dv);
+        return std::min(std::max(c, 0), n - 1);
+    };
+    std::vector<int32_t> cnt(n1 * n1 + 1, 0);
+    std::vector<int> r(4 * nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        r[4 * t] = cell(m.tri.bmin[3 * t + 1] - margin, g.y0, g.dy, n1);
+        r[4 * t + 1] = cell(m.tri.bmax[3 * t + 1] + margin, g.y0, g.dy, n1);
+        r[4 * t + 2] = cell(m.tri.bmin[3 * t + 2] - margin, g.z0, g.dz, n1);
+        r[4 * t + 3] = cell(m.tri.bmax[3 * t + 2] + margin, g.z0, g.dz, n1);
+        for (int a = r[4 * t]; a <= r[4 * t + 1]; ++a)
+            for (int b = r[4 * t + 2]; b <= r[4 * t + 3]; ++b) cnt[a * n1 + b + 1]++;
+    }
+    for (int i = 0; i < n1 * n1; ++i) cnt[i + 1] += cnt[i];
+    g.off = cnt;
+    g.idx.resize(cnt[n1 * n1]);
+    std::vector<int32_t> pos(cnt.begin(), cnt.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int a = r[4 * t]; a <= r[4 * t + 1]; ++a)
+            for (int b = r[4 * t + 2]; b <= r[4 * t + 3]; ++b) g.idx[pos[a * n1 + b]++] = (int32_t)t;
+}
+
+// Nitsche surface quadrature: 3 points per triangle (barycentric 2/3, 1/6, 1/6 and
+// permutations, weight area/3), each owned by the leaf that contains it, fluid-outward normal
+// n = -n_t, h_b = largest |(x_a - c_t).n_t| over the owner's Out corners, at least 0.01 h.
+// Points in In elements are dropped.
+void build_surface_points(Mesh& m) {
+    static const double B[3][3] = {{2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0},
+                                   {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}};
+    m.sq.clear();
+    const TriHost& T = m.tri;
+    for (int64_t t = 0; t < T.n; ++t) {
+        const double* v = &T.v[9 * t];
+        const double* nt = &T.nrm[3 * t];
+        const double* ct = &T.cen[3 * t];
+        for (int q = 0; q < 3; ++q) {
+            double x[3];
+            int64_t I[3];
+            bool ok = true;
+            for (int k = 0; k < 3; ++k) {
+                x[k] = (B[q][0] * v[k] + B[q][1] * v[3 + k]) + B[q][2] * v[6 + k];
+                double f = std::floor((x[k] - m.lo[k]) / m.scale);
+                if (!(f >= 0.0 && f < (double)m.hiI[k])) { ok = false; break; }
+                I[k] = (int64_t)f;
+            }
+            if (!ok) continue;
+            int64_t e = find_leaf(m, I[0], I[1], I[2]);
+            if (e < 0 || m.marker[e] == 1) continue;
+            uint32_t s = octsize(m.lev[e]);
+            double h = (double)s * m.scale;
+            double hb = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                if ((m.cflags[e] >> c) & 1) continue;
+                double xa[3];
+                for (int k = 0; k < 3; ++k) xa[k] = m.lo[k] + (double)(m.anc[3 * e + k] + (((c >> k) & 1) ? s : 0)) * m.scale;
+                double dist = std::fabs((xa[0] - ct[0]) * nt[0] + (xa[1] - ct[1]) * nt[1] + (xa[2] - ct[2]) * nt[2]);
+                if (dist > hb) hb = dist;
+            }
+            if (hb < 0.01 * h) hb = 0.01 * h;
+            double rec[10] = {x[0], x[1], x[2], -nt[0], -nt[1], -nt[2], T.area[t] / 3.0, hb, (double)e, (double)t};
+            m.sq.insert(m.sq.end(), rec, rec + 10);
+        }
+    }
+}
+
+// Strong rows: bits 0-2 velocity and bit 3 pressure prescribed on the box (u_inf on every face
+// but the outlet x = hi; p = 0 on the outlet); bit 4: node touched by no active element.
+void build_bc_flags(Mesh& m) {
+    const int64_t nn = m.n_nodes(), ne = m.n_elem();
+    m.bcflag.assign(nn, 0);
+    std::vector<uint8_t> active(nn, 0);
+    for (int64_t e = 0; e < ne; ++e) {
+        if (m.marker[e] == 1) continue;
+        for (int c = 0; c < 8; ++c) {
+            int32_t id = m.conn[8 * e + c];
+            if (id < nn) active[id] = 1;
+            else {
+                int64_t h = id - nn;
+                for (int p = 0; p < m.hnp[h]; ++p) active[m.hpar[4 * h + p]] = 1;
+            }
+        }
+    }
+    for (int64_t n = 0; n < nn; ++n) {
+        const uint32_t* X = &m.nijk[3 * n];
+        uint8_t f = 0;
+        bool outlet = (int64_t)X[0] == m.hiI[0];
+        bool other = X[0] == 0 || X[1] == 0 || X[2] == 0 || (int64_t)X[1] == m.hiI[1] || (int64_t)X[2] == m.hiI[2];
+        if (other) f |= 7;
+        if (outlet) f |= 8;
+        if (!active[n]) f |= 16;
+        m.bcflag[n] = f;
+    }
+}
+
+}  // namespace imga

@@ -1,0 +1,623 @@
+// VMS residual R(u) and Jacobian-vector product J(u) v on Q1 octree elements.
+//
+// Weak form: Eqs. (ALE-VMS-form) and (vms), fine scales Eqs. (uprime) and (pprime), Nitsche
+// terms Eq. (weakbc); In elements skipped, Out elements on the 2x2x2 Gauss rule, Intercepted
+// elements on their adaptive sub-cell points (Algorithm 1); element vectors scattered to the
+// nodes through the hanging-node operator M_e^T (Algorithms 2 and 3).
+//
+// Every quadrature point is reduced to 16 coefficients: with w = phi_a e_i and q = phi_a,
+//     r_{a,i} += wq [ phi_a F_i + d_j phi_a S_ij ],     r_{a,p} += wq [ phi_a G + d_j phi_a H_j ],
+//   F_i  = rho (du_i/dt + (u.grad u)_i - f_i) + (u'.grad u)_i                    terms 1, 6, -F
+//   S_ij = sigma_ij - u'_i u_j - p' delta_ij - u'_i u'_j / rho + taubar (u'.grad u)_i u'_j
+//                                                                                terms 2, 4, 5, 7, 8
+//   G    = div u,   H_j = -u'_j / rho                                             terms 3, 4
+// J v is the forward-mode derivative of the same code (dual numbers value + tangent): the
+// matrix of Algorithms 2/4 applied to v without being formed.
+//
+// Kernels (T = float or double element arithmetic, nodal gathers always float64, scatter by
+// float64 atomics):
+//   vms_interior  8 threads per Out element: thread c gathers corner c, evaluates Gauss point c,
+//                 then contracts node c's four rows over the 8 points through shared memory.
+//   vms_cut       one warp per Intercepted element, 32 sub-cell points per step; lane l owns
+//                 row (node l/4, component l%4) of the element vector.
+//   nitsche       one thread per surface point (points sorted by element).
+//   strong_rows   Dirichlet rows U - g and In-only rows, written after every scatter.
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <type_traits>
+
+#include "imga_internal.h"
+
+namespace imga {
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// scalars: plain T or dual (value, tangent)
+// ------------------------------------------------------------------------------------------
+template <class T> struct Dual { T v, d; };
+
+template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
+template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return {a.v + b, a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return {a.v - b, a.d}; }
+
+template <class S> struct Base { typedef S type; };
+template <class T> struct Base<Dual<T>> { typedef T type; };
+
+template <class T> __device__ __forceinline__ T value(T a) { return a; }
+template <class T> __device__ __forceinline__ T value(Dual<T> a) { return a.v; }
+template <class T> __device__ __forceinline__ T tangent(T) { return T(0); }
+template <class T> __device__ __forceinline__ T tangent(Dual<T> a) { return a.d; }
+
+template <class S> __device__ __forceinline__ S zero() { return S(0); }
+template <> __device__ __forceinline__ Dual<float> zero<Dual<float>>() { return {0.f, 0.f}; }
+template <> __device__ __forceinline__ Dual<double> zero<Dual<double>>() { return {0.0, 0.0}; }
+
+template <class S, class T> __device__ __forceinline__ S make(T v, T d);
+template <> __device__ __forceinline__ float make<float, float>(float v, float) { return v; }
+template <> __device__ __forceinline__ double make<double, double>(double v, double) { return v; }
+template <> __device__ __forceinline__ Dual<float> make<Dual<float>, float>(float v, float d) { return {v, d}; }
+template <> __device__ __forceinline__ Dual<double> make<Dual<double>, double>(double v, double d) { return {v, d}; }
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+template <class T> __device__ __forceinline__ Dual<T> rsq(Dual<T> x) {
+    T r = rsq(x.v);
+    return {r, T(-0.5) * r * r * r * x.d};
+}
+__device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+template <class T> __device__ __forceinline__ Dual<T> rcp(Dual<T> x) {
+    T r = rcp(x.v);
+    return {r, -r * r * x.d};
+}
+
+template <class T> __device__ __forceinline__ T tiny();
+template <> __device__ __forceinline__ float tiny<float>() { return 1e-37f; }
+template <> __device__ __forceinline__ double tiny<double>() { return 1e-300; }
+
+// ------------------------------------------------------------------------------------------
+// launch parameters
+// ------------------------------------------------------------------------------------------
+struct Args {
+    const int32_t* conn;
+    const int32_t* hpar;
+    const uint8_t* lev;
+    int64_t n_nodes;
+    double scale;
+    const double* U;
+    const double* Up;
+    const double* Up2;
+    const double* F;
+    const double* V;
+    double* out;
+    double rho, mu, theta, c0, c1, c2;   // c_k = time coefficients / dt
+    double K0dt;                         // 4 / dt^2
+    double CInu2;                        // C_I nu^2
+    double Cb;
+    double g[3];
+    int drop_visc;
+};
+
+// node values through the hanging-node interpolation (u_e = M_e U)
+__device__ __forceinline__ void load4(const double* a, int64_t i, double o[4]) {
+    const double2* p = reinterpret_cast<const double2*>(a + 4 * i);
+    double2 x = __ldg(p), y = __ldg(p + 1);
+    o[0] = x.x; o[1] = x.y; o[2] = y.x; o[3] = y.y;
+}
+__device__ __forceinline__ void gather(const Args& A, const double* arr, int32_t id, double o[4]) {
+    if (id < A.n_nodes) { load4(arr, id, o); return; }
+    const int32_t* hp = A.hpar + 4 * (int64_t)(id - A.n_nodes);
+    int np = hp[2] >= 0 ? 4 : 2;
+    double t[4];
+    o[0] = o[1] = o[2] = o[3] = 0.0;
+    for (int k = 0; k < np; ++k) {
+        load4(arr, hp[k], t);
+        o[0] += t[0]; o[1] += t[1]; o[2] += t[2]; o[3] += t[3];
+    }
+    double w = np == 4 ? 0.25 : 0.5;
+    o[0] *= w; o[1] *= w; o[2] *= w; o[3] *= w;
+}
+
+// scatter one node's 4 values through M_e^T
+__device__ __forceinline__ void scatter(const Args& A, int32_t id, const double r[4]) {
+    if (id < A.n_nodes) {
+        double* o = A.out + 4 * (int64_t)id;
+        for (int k = 0; k < 4; ++k) atomicAdd(o + k, r[k]);
+        return;
+    }
+    const int32_t* hp = A.hpar + 4 * (int64_t)(id - A.n_nodes);
+    int np = hp[2] >= 0 ? 4 : 2;
+    double w = np == 4 ? 0.25 : 0.5;
+    for (int p = 0; p < np; ++p) {
+        double* o = A.out + 4 * (int64_t)hp[p];
+        for (int k = 0; k < 4; ++k) atomicAdd(o + k, w * r[k]);
+    }
+}
+
+// Nodal data one corner contributes: spatial-state velocity (theta u + (1-theta) u_prev), p,
+// time-derivative combination (c0 u + c1 u_prev + c2 u_prev2) / dt, body force, and -- for J v
+// -- their tangents.  Combined in float64, stored as T.
+constexpr int NF = 10;   // us[3], p, at[3], f[3]
+constexpr int NT = 7;    // dus[3], dp, dat[3]
+
+template <class T, bool JV>
+__device__ __forceinline__ void corner_data(const Args& A, int32_t id, T* dst) {
+    double u[4], up[4], up2[4] = {0, 0, 0, 0}, f[4] = {0, 0, 0, 0};
+    gather(A, A.U, id, u);
+    gather(A, A.Up, id, up);
+    if (A.c2 != 0.0) gather(A, A.Up2, id, up2);
+    if (A.F) gather(A, A.F, id, f);
+    for (int k = 0; k < 3; ++k) {
+        dst[k] = (T)(A.theta * u[k] + (1.0 - A.theta) * up[k]);
+        dst[4 + k] = (T)(A.c0 * u[k] + A.c1 * up[k] + A.c2 * up2[k]);
+        dst[7 + k] = (T)f[k];
+    }
+    dst[3] = (T)u[3];
+    if (JV) {
+        double v[4];
+        gather(A, A.V, id, v);
+        for (int k = 0; k < 3; ++k) {
+            dst[NF + k] = (T)(A.theta * v[k]);
+            dst[NF + 4 + k] = (T)(A.c0 * v[k]);
+        }
+        dst[NF + 3] = (T)v[3];
+    }
+}
+
+// Q1 basis at reference point xi: values, physical gradients (g = 2/h), mixed second derivatives
+template <class T>
+struct Basis {
+    T phi[8], dphi[8][3], d2[8][3];   // d2: (01, 02, 12) mixed second derivatives
+};
+template <class T>
+__device__ __forceinline__ void basis(const T xi[3], T g, Basis<T>& B) {
+    T fm[3], fp[3];
+    for (int k = 0; k < 3; ++k) { fm[k] = T(0.5) * (T(1) - xi[k]); fp[k] = T(0.5) * (T(1) + xi[k]); }
+    const T hg = T(0.5) * g, qg2 = T(0.25) * g * g;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        T f0 = (c & 1) ? fp[0] : fm[0], f1 = (c & 2) ? fp[1] : fm[1], f2 = (c & 4) ? fp[2] : fm[2];
+        T s0 = (c & 1) ? T(1) : T(-1), s1 = (c & 2) ? T(1) : T(-1), s2 = (c & 4) ? T(1) : T(-1);
+        B.phi[c] = f0 * f1 * f2;
+        B.dphi[c][0] = hg * s0 * f1 * f2;
+        B.dphi[c][1] = hg * s1 * f0 * f2;
+        B.dphi[c][2] = hg * s2 * f0 * f1;
+        B.d2[c][0] = qg2 * s0 * s1 * f2;
+        B.d2[c][1] = qg2 * s0 * s2 * f1;
+        B.d2[c][2] = qg2 * s1 * s2 * f0;
+    }
+}
+
+// Pointwise VMS: fields at a quadrature point -> the 16 coefficients (F, S, G, H).
+template <class S, class T>
+__device__ __forceinline__ void vms_point(const Args& A, const Basis<T>& B, const T* nd /*[8][NF+NT]*/, int stride,
+                                          T g2, S out[16]) {
+    S us[3], Gu[3][3], p = zero<S>(), gp[3], at[3], H2[3];
+    T f[3] = {T(0), T(0), T(0)};
+    for (int i = 0; i < 3; ++i) {
+        us[i] = zero<S>(); at[i] = zero<S>(); gp[i] = zero<S>(); H2[i] = zero<S>();
+        for (int j = 0; j < 3; ++j) Gu[i][j] = zero<S>();
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const T* q = nd + c * stride;
+        const T ph = B.phi[c];
+        S vu[3], vp, va[3];
+        if constexpr (std::is_same<S, T>::value) {
+            for (int k = 0; k < 3; ++k) { vu[k] = q[k]; va[k] = q[4 + k]; }
+            vp = q[3];
+        } else {
+            for (int k = 0; k < 3; ++k) { vu[k] = make<S, T>(q[k], q[NF + k]); va[k] = make<S, T>(q[4 + k], q[NF + 4 + k]); }
+            vp = make<S, T>(q[3], q[NF + 3]);
+        }
+        p = p + ph * vp;
+        for (int i = 0; i < 3; ++i) {
+            us[i] = us[i] + ph * vu[i];
+            at[i] = at[i] + ph * va[i];
+            gp[i] = gp[i] + B.dphi[c][i] * vp;
+            f[i] = f[i] + ph * q[7 + i];
+            for (int j = 0; j < 3; ++j) Gu[i][j] = Gu[i][j] + B.dphi[c][j] * vu[i];
+        }
+        // (grad div u)_i = sum_{j != i} d_i d_j u_j  (trilinear: d_j d_j phi = 0)
+        H2[0] = H2[0] + B.d2[c][0] * vu[1] + B.d2[c][1] * vu[2];
+        H2[1] = H2[1] + B.d2[c][0] * vu[0] + B.d2[c][2] * vu[2];
+        H2[2] = H2[2] + B.d2[c][1] * vu[0] + B.d2[c][2] * vu[1];
+    }
+    const T rho = (T)A.rho, mu = (T)A.mu, irho = (T)(1.0 / A.rho);
+    S divu = Gu[0][0] + Gu[1][1] + Gu[2][2];
+    S conv[3], rM[3];
+    for (int i = 0; i < 3; ++i) {
+        conv[i] = Gu[i][0] * us[0] + Gu[i][1] * us[1] + Gu[i][2] * us[2];
+        S r = rho * (at[i] + conv[i] - f[i]) + gp[i];
+        rM[i] = A.drop_visc ? r : r - mu * H2[i];
+    }
+    // tau_M = (4/dt^2 + u.G u + C_I nu^2 G:G)^(-1/2), G = g2 I;  tau_C = 1 / (tau_M tr G)
+    S uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+    S tauM = rsq(g2 * uu + (T)(A.K0dt) + T(3) * (T)A.CInu2 * g2 * g2);
+    S tauC = rcp(T(3) * g2 * tauM);
+    S up[3];
+    for (int i = 0; i < 3; ++i) up[i] = -(tauM * rM[i]);
+    S pp = -(rho * tauC * divu);
+    S q = g2 * (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+    bool bar = value(q) > tiny<T>();
+    S taubar = bar ? rsq(q) : zero<S>();
+    S Gup[3];
+    for (int i = 0; i < 3; ++i) Gup[i] = Gu[i][0] * up[0] + Gu[i][1] * up[1] + Gu[i][2] * up[2];
+    for (int i = 0; i < 3; ++i) {
+        out[i] = rho * (at[i] + conv[i] - f[i]) + Gup[i];
+        S tb = taubar * Gup[i];
+        for (int j = 0; j < 3; ++j) {
+            S sij = mu * (Gu[i][j] + Gu[j][i]) - up[i] * us[j] - irho * (up[i] * up[j]) + tb * up[j];
+            if (i == j) sij = sij - p - pp;
+            out[3 + 3 * i + j] = sij;
+        }
+        out[13 + i] = -(irho * up[i]);
+    }
+    out[12] = divu;
+}
+
+template <class T, bool JV> struct Pick;
+template <class T> struct Pick<T, false> { template <class S> __device__ static T get(S x) { return value(x); } };
+template <class T> struct Pick<T, true> { template <class S> __device__ static T get(S x) { return tangent(x); } };
+
+// ------------------------------------------------------------------------------------------
+// Out elements: 8 threads per element
+// ------------------------------------------------------------------------------------------
+template <class T> struct Epb { static constexpr int value = sizeof(T) == 8 ? 16 : 32; };   // elements per block
+
+template <class T, bool JV>
+__global__ void __launch_bounds__(256) vms_interior(Args A, const int32_t* __restrict__ list, int64_t n) {
+    typedef typename std::conditional<JV, Dual<T>, T>::type S;
+    constexpr int ST = NF + (JV ? NT : 0);
+    constexpr int EPB = Epb<T>::value;
+    __shared__ T s_nd[EPB][8][ST];
+    __shared__ T s_cf[EPB][8][17];
+    const int c = threadIdx.x & 7, le = threadIdx.x >> 3;
+    const int64_t idx = (int64_t)blockIdx.x * EPB + le;
+    const bool valid = idx < n;
+    const int32_t e = list[valid ? idx : n - 1];
+    const int32_t id = A.conn[8 * (int64_t)e + c];
+    corner_data<T, JV>(A, id, &s_nd[le][c][0]);
+    __syncwarp();
+    const double hd = (double)(1u << (kMaxDepth - A.lev[e])) * A.scale;
+    const T g = (T)(2.0 / hd);
+    const T gauss = (T)0.57735026918962576451;
+    T xi[3] = {(c & 1) ? gauss : -gauss, (c & 2) ? gauss : -gauss, (c & 4) ? gauss : -gauss};
+    Basis<T> B;
+    basis<T>(xi, g, B);
+    S cf[16];
+    vms_point<S, T>(A, B, &s_nd[le][0][0], ST, g * g, cf);
+    const T wq = (T)(0.125 * hd * hd * hd);
+    for (int k = 0; k < 16; ++k) s_cf[le][c][k] = wq * Pick<T, JV>::get(cf[k]);
+    __syncwarp();
+    // contraction for node a = c over the 8 Gauss points: phi_a(xi_q) factors as 1D values
+    const T wp = T(0.5) * (T(1) + gauss), wm = T(0.5) * (T(1) - gauss);
+    T r[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        T f[3], d[3];
+        for (int k = 0; k < 3; ++k) {
+            bool same = (((c >> k) & 1) == ((q >> k) & 1));
+            f[k] = same ? wp : wm;
+            d[k] = (((c >> k) & 1) ? T(0.5) : T(-0.5)) * g;
+        }
+        T ph = f[0] * f[1] * f[2];
+        T dp[3] = {d[0] * f[1] * f[2], d[1] * f[0] * f[2], d[2] * f[0] * f[1]};
+        const T* C = s_cf[le][q];
+        for (int i = 0; i < 3; ++i) r[i] += ph * C[i] + dp[0] * C[3 + 3 * i] + dp[1] * C[4 + 3 * i] + dp[2] * C[5 + 3 * i];
+        r[3] += ph * C[12] + dp[0] * C[13] + dp[1] * C[14] + dp[2] * C[15];
+    }
+    if (valid) {
+        double rd[4] = {(double)r[0], (double)r[1], (double)r[2], (double)r[3]};
+        scatter(A, id, rd);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Intercepted elements: one warp per element
+// ------------------------------------------------------------------------------------------
+constexpr int WPB = 4;   // warps per block
+
+template <class T> __device__ __forceinline__ void load_pt(const void* pts, int64_t q, T o[4]);
+template <> __device__ __forceinline__ void load_pt<double>(const void* pts, int64_t q, double o[4]) {
+    const double2* p = reinterpret_cast<const double2*>(pts) + 2 * q;
+    double2 a = __ldg(p), b = __ldg(p + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+template <> __device__ __forceinline__ void load_pt<float>(const void* pts, int64_t q, float o[4]) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(pts) + q);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+
+template <class T, bool JV>
+__global__ void __launch_bounds__(32 * WPB) vms_cut(Args A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
+                                                    const void* __restrict__ pts, int64_t n) {
+    typedef typename std::conditional<JV, Dual<T>, T>::type S;
+    constexpr int ST = NF + (JV ? NT : 0);
+    __shared__ T s_nd[WPB][8][ST];
+    __shared__ T s_cf[WPB][32][20];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t idx = (int64_t)blockIdx.x * WPB + w;
+    if (idx >= n) return;
+    const int32_t e = list[idx];
+    int32_t my_id = 0;
+    if (lane < 8) {
+        my_id = A.conn[8 * (int64_t)e + lane];
+        corner_data<T, JV>(A, my_id, &s_nd[w][lane][0]);
+    }
+    __syncwarp();
+    const double hd = (double)(1u << (kMaxDepth - A.lev[e])) * A.scale;
+    const T g = (T)(2.0 / hd);
+    const T det = (T)(0.125 * hd * hd * hd);
+    const int a = lane >> 2, comp = lane & 3;
+    const T sa[3] = {(a & 1) ? T(1) : T(-1), (a & 2) ? T(1) : T(-1), (a & 4) ? T(1) : T(-1)};
+    T acc = T(0);
+    const int64_t q0 = off[idx], q1 = off[idx + 1];
+    for (int64_t base = q0; base < q1; base += 32) {
+        const int64_t q = base + lane;
+        if (q < q1) {
+            T pt[4];
+            load_pt<T>(pts, q, pt);
+            Basis<T> B;
+            basis<T>(pt, g, B);
+            S cf[16];
+            vms_point<S, T>(A, B, &s_nd[w][0][0], ST, g * g, cf);
+            const T wq = pt[3] * det;
+            for (int k = 0; k < 16; ++k) s_cf[w][lane][k] = wq * Pick<T, JV>::get(cf[k]);
+            s_cf[w][lane][16] = pt[0];
+            s_cf[w][lane][17] = pt[1];
+            s_cf[w][lane][18] = pt[2];
+        } else {
+            for (int k = 0; k < 19; ++k) s_cf[w][lane][k] = T(0);
+        }
+        __syncwarp();
+        const int m = (int)min((int64_t)32, q1 - base);
+        for (int j = 0; j < m; ++j) {
+            const T* C = s_cf[w][j];
+            T f0 = T(0.5) * (T(1) + sa[0] * C[16]), f1 = T(0.5) * (T(1) + sa[1] * C[17]), f2 = T(0.5) * (T(1) + sa[2] * C[18]);
+            T ph = f0 * f1 * f2;
+            T hg = T(0.5) * g;
+            T d0 = hg * sa[0] * f1 * f2, d1 = hg * sa[1] * f0 * f2, d2 = hg * sa[2] * f0 * f1;
+            if (comp < 3) acc += ph * C[comp] + d0 * C[3 + 3 * comp] + d1 * C[4 + 3 * comp] + d2 * C[5 + 3 * comp];
+            else acc += ph * C[12] + d0 * C[13] + d1 * C[14] + d2 * C[15];
+        }
+        __syncwarp();
+    }
+    // gather the four components of node a into lane 4a, then scatter
+    double r[4];
+    for (int k = 0; k < 4; ++k) r[k] = (double)__shfl_sync(0xffffffffu, acc, (lane & ~3) + k);
+    int32_t id = __shfl_sync(0xffffffffu, my_id, a);
+    if (comp == 0) scatter(A, id, r);
+}
+
+// ------------------------------------------------------------------------------------------
+// Nitsche surface terms, one thread per surface point
+// ------------------------------------------------------------------------------------------
+template <class T, bool JV>
+__global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict__ el, const double* __restrict__ xr,
+                                               const double* __restrict__ nr, const double* __restrict__ wr,
+                                               const double* __restrict__ taub, int64_t n) {
+    typedef typename std::conditional<JV, Dual<T>, T>::type S;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t e = el[i];
+    const double hd = (double)(1u << (kMaxDepth - A.lev[e])) * A.scale;
+    const T g = (T)(2.0 / hd);
+    T xi[3] = {(T)xr[3 * i], (T)xr[3 * i + 1], (T)xr[3 * i + 2]};
+    const T nn[3] = {(T)nr[3 * i], (T)nr[3 * i + 1], (T)nr[3 * i + 2]};
+    const double ndd[3] = {nr[3 * i], nr[3 * i + 1], nr[3 * i + 2]};
+    Basis<T> B;
+    basis<T>(xi, g, B);
+    // float64 interpolation of u_s (and its tangent) for the penalty terms
+    double xd[3] = {xr[3 * i], xr[3 * i + 1], xr[3 * i + 2]};
+    double phd[8];
+    for (int c = 0; c < 8; ++c) {
+        double f = 1.0;
+        for (int k = 0; k < 3; ++k) f *= 0.5 * (1.0 + (((c >> k) & 1) ? xd[k] : -xd[k]));
+        phd[c] = f;
+    }
+    S us[3], Gu[3][3], p = zero<S>();
+    double usd[3] = {0, 0, 0}, dusd[3] = {0, 0, 0};
+    int32_t ids[8];
+    for (int k = 0; k < 3; ++k) { us[k] = zero<S>(); for (int j = 0; j < 3; ++j) Gu[k][j] = zero<S>(); }
+    for (int c = 0; c < 8; ++c) {
+        ids[c] = A.conn[8 * (int64_t)e + c];
+        double u[4], up[4], v[4] = {0, 0, 0, 0};
+        gather(A, A.U, ids[c], u);
+        gather(A, A.Up, ids[c], up);
+        if (JV) gather(A, A.V, ids[c], v);
+        S vu[3];
+        for (int k = 0; k < 3; ++k) {
+            double s = A.theta * u[k] + (1.0 - A.theta) * up[k];
+            double ds = A.theta * v[k];
+            vu[k] = make<S, T>((T)s, (T)ds);
+            usd[k] += phd[c] * s;
+            dusd[k] += phd[c] * ds;
+        }
+        S vp = make<S, T>((T)u[3], (T)v[3]);
+        p = p + B.phi[c] * vp;
+        for (int k = 0; k < 3; ++k) {
+            us[k] = us[k] + B.phi[c] * vu[k];
+            for (int j = 0; j < 3; ++j) Gu[k][j] = Gu[k][j] + B.dphi[c][j] * vu[k];
+        }
+    }
+    const T mu = (T)A.mu, rho = (T)A.rho;
+    S d[3];
+    for (int k = 0; k < 3; ++k) d[k] = us[k] - (T)A.g[k];
+    S un = us[0] * nn[0] + us[1] * nn[1] + us[2] * nn[2];
+    S dn = d[0] * nn[0] + d[1] * nn[1] + d[2] * nn[2];
+    const bool inflow = value(un) < T(0);
+    S tr[3];
+    for (int k = 0; k < 3; ++k) {
+        tr[k] = mu * ((Gu[k][0] + Gu[0][k]) * nn[0] + (Gu[k][1] + Gu[1][k]) * nn[1] + (Gu[k][2] + Gu[2][k]) * nn[2]) - p * nn[k];
+    }
+    const double w = wr[i];
+    const double tauB = A.Cb * A.mu * taub[i];
+    // penalty (tau_TAN = tau_NOR: both parts sum to tau_B (u - g)), float64
+    double pen[3];
+    for (int k = 0; k < 3; ++k) pen[k] = JV ? tauB * dusd[k] : tauB * (usd[k] - A.g[k]);
+    (void)ndd;
+    for (int c = 0; c < 8; ++c) {
+        const T ph = B.phi[c];
+        const T gn = B.dphi[c][0] * nn[0] + B.dphi[c][1] * nn[1] + B.dphi[c][2] * nn[2];
+        S gd = B.dphi[c][0] * d[0] + B.dphi[c][1] * d[1] + B.dphi[c][2] * d[2];
+        double r[4];
+        for (int k = 0; k < 3; ++k) {
+            S t = -(ph * tr[k]) - mu * (gn * d[k] + nn[k] * gd);
+            if (inflow) t = t - (ph * rho) * (un * d[k]);
+            r[k] = w * ((double)Pick<T, JV>::get(t) + (double)ph * pen[k]);
+        }
+        r[3] = w * (double)Pick<T, JV>::get(-(ph * dn));
+        scatter(A, ids[c], r);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// strong rows
+// ------------------------------------------------------------------------------------------
+__global__ void strong_rows(Args A, const uint8_t* __restrict__ flag, const uint8_t* __restrict__ umask,
+                            const double* __restrict__ uval, double ux, double uy, double uz, int jv) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= A.n_nodes) return;
+    const uint8_t f = flag[n];
+    uint8_t mask;
+    double gv[4];
+    if (umask) {
+        mask = umask[n];
+        for (int k = 0; k < 4; ++k) gv[k] = uval[4 * n + k];
+    } else {
+        mask = f & 15;
+        gv[0] = ux; gv[1] = uy; gv[2] = uz; gv[3] = 0.0;
+    }
+    if (f & 16) {
+        for (int k = 0; k < 4; ++k)
+            if (!((mask >> k) & 1)) { mask |= (uint8_t)(1 << k); gv[k] = k < 3 ? A.g[k] : 0.0; }
+    }
+    if (!mask) return;
+    const double* src = jv ? A.V : A.U;
+    for (int k = 0; k < 4; ++k)
+        if ((mask >> k) & 1) A.out[4 * n + k] = jv ? src[4 * n + k] : src[4 * n + k] - gv[k];
+}
+
+// optional event pair around a launch (profiling)
+struct Timed {
+    Mesh* m;
+    int k;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timed(const Mesh& mesh, int kind, cudaStream_t st) : m(const_cast<Mesh*>(&mesh)), k(kind), s(st) {
+        if (!m->profiling) return;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    ~Timed() {
+        if (!a) return;
+        cudaEventRecord(b, s);
+        m->prof_ev[k].push_back({(void*)a, (void*)b});
+    }
+};
+
+template <class T, bool JV>
+void launch_all(const Mesh& m, const Args& A, cudaStream_t s) {
+    const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size(), ns = (int64_t)m.sq.size() / 10;
+    constexpr int EPB = Epb<T>::value;
+    if (no > 0) {
+        Timed t(m, 0, s);
+        vms_interior<T, JV><<<(unsigned)((no + EPB - 1) / EPB), 8 * EPB, 0, s>>>(A, m.d.out_list, no);
+    }
+    if (nc > 0) {
+        Timed t(m, 1, s);
+        const void* pts = std::is_same<T, float>::value ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
+        vms_cut<T, JV><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, 0, s>>>(A, m.d.cut_list, m.d.cut_off, pts, nc);
+    }
+    if (ns > 0) {
+        Timed t(m, 2, s);
+        nitsche<T, JV><<<(unsigned)((ns + 127) / 128), 128, 0, s>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
+                                                                    m.d.sq_taub, ns);
+    }
+}
+
+}  // namespace
+
+int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+              const imga_physics& ph, int precision, const double* v, double* out, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    Args A;
+    A.conn = m.d.conn;
+    A.hpar = m.d.hpar;
+    A.lev = m.d.lev;
+    A.n_nodes = m.n_nodes();
+    A.scale = m.scale;
+    A.U = u;
+    A.Up = up;
+    A.Up2 = up2 ? up2 : up;
+    A.F = f;
+    A.V = v;
+    A.out = out;
+    A.rho = ph.rho;
+    A.mu = ph.mu;
+    double c[3], theta;
+    if (ph.time_scheme == 2) { c[0] = 1.5; c[1] = -2.0; c[2] = 0.5; theta = 1.0; }
+    else if (ph.time_scheme == 1) { c[0] = 1.0; c[1] = -1.0; c[2] = 0.0; theta = 0.5; }
+    else { c[0] = 1.0; c[1] = -1.0; c[2] = 0.0; theta = 1.0; }
+    A.theta = theta;
+    A.c0 = c[0] / ph.dt;
+    A.c1 = c[1] / ph.dt;
+    A.c2 = c[2] / ph.dt;
+    A.K0dt = 4.0 / (ph.dt * ph.dt);
+    const double nu = ph.mu / ph.rho;
+    A.CInu2 = ph.C_I * nu * nu;
+    A.Cb = ph.C_b;
+    for (int k = 0; k < 3; ++k) A.g[k] = ph.g_body[k];
+    A.drop_visc = ph.drop_visc_strong;
+    const bool jv = v != nullptr;
+    if (cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
+    if (precision == 0) {
+        if (jv) launch_all<double, true>(m, A, s); else launch_all<double, false>(m, A, s);
+    } else {
+        if (jv) launch_all<float, true>(m, A, s); else launch_all<float, false>(m, A, s);
+    }
+    const int64_t nn = m.n_nodes();
+    Timed t(m, 3, s);
+    if (nn > 0)
+        strong_rows<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(A, m.d.bcflag, m.user_bc ? m.d.bcmask_user : nullptr,
+                                                                m.user_bc ? m.d.bcval_user : nullptr, ph.u_inf[0],
+                                                                ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+void profile_reset(Mesh& m) {
+    for (int k = 0; k < 4; ++k) {
+        for (auto& p : m.prof_ev[k]) { cudaEventDestroy((cudaEvent_t)p.first); cudaEventDestroy((cudaEvent_t)p.second); }
+        m.prof_ev[k].clear();
+        m.prof_ms[k] = 0.0;
+        m.prof_n[k] = 0;
+    }
+}
+
+int profile_collect(Mesh& m) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    for (int k = 0; k < 4; ++k) {
+        for (auto& p : m.prof_ev[k]) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, (cudaEvent_t)p.first, (cudaEvent_t)p.second);
+            m.prof_ms[k] += ms;
+            m.prof_n[k] += 1;
+            cudaEventDestroy((cudaEvent_t)p.first);
+            cudaEventDestroy((cudaEvent_t)p.second);
+        }
+        m.prof_ev[k].clear();
+    }
+    return 0;
+}
+
+}  // namespace imga

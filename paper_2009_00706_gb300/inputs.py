@@ -216,13 +216,14 @@ def small_sphere(seed: int = 0) -> Workload:
 def sphere_les(seed: int = 0) -> Workload:
     """Box 32 x 16 x 16 diameters, sphere D = 1 at (8, 8, 8) (icosphere level 6, 81920
     triangles), level 4 background, level 10 within 0.25 D of the surface, a wake cone behind
-    the sphere at levels 9 and 8; Re 1e4, BDF2 dt 0.01.  About 2M elements."""
+    the sphere at levels 9 (length 11, radius 1 at the centre) and 8 (length 20, radius 2.25),
+    half-angle 15 degrees; Re 1e4, BDF2 dt 0.01.  2,001,176 elements."""
     c = (8.0, 8.0, 8.0)
     return Workload(
         name="sphere_les", lo=(0.0, 0.0, 0.0), hi=(32.0, 16.0, 16.0), base_level=4,
         regions=[Region(REGION_SPHERE_BAND, 10, (*c, 0.5, 0.25)),
-                 Region(REGION_CONE, 9, (8.0, 8.0, 8.0, 5.0, 1.0, 0.2679491924)),
-                 Region(REGION_CONE, 8, (8.0, 8.0, 8.0, 14.0, 2.0, 0.2679491924))],
+                 Region(REGION_CONE, 9, (8.0, 8.0, 8.0, 11.0, 1.0, 0.2679491924)),
+                 Region(REGION_CONE, 8, (8.0, 8.0, 8.0, 20.0, 2.25, 0.2679491924))],
         lmax=3, physics=Physics(rho=1.0, mu=1e-4, dt=0.01, scheme=SCHEME_BDF2),
         surface=lambda: icosphere(6, 0.5, c, 1e-5, seed), seed=seed)
 

@@ -1,0 +1,91 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every declared entry
+point, validates its arguments, and its host mesh builder agrees bit for bit with the oracle's
+(octree, nodes, hanging nodes, background triangles).  No GPU is touched (device < 0)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleMesh
+from paper_2009_00706_gb300 import _lib, api
+from paper_2009_00706_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _lib.build()
+    return _lib.load()
+
+
+def declared_entry_points():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(imga_\w+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert {"imga_build_mesh", "imga_classify", "imga_residual", "imga_jvp"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names <= set(_lib.SIGNATURES), names - set(_lib.SIGNATURES)
+
+
+def _compare(w_lo, w_hi, base, regions, tri, lmax=3):
+    m = api.Mesh(w_lo, w_hi, base, regions, tri, lmax, device=-1)
+    o = OracleMesh(w_lo, w_hi, base, regions, tri, lmax)
+    ex = m.export()
+    assert m.n_elem == o.n_elem and m.n_nodes == o.n_nodes and m.n_hang == o.n_hang
+    assert np.array_equal(ex["anchors"], o.anchors)
+    assert np.array_equal(ex["levels"], o.levels)
+    assert np.array_equal(ex["conn"], o.conn)
+    assert np.array_equal(ex["node_ijk"], o.node_ijk)
+    assert np.array_equal(ex["hang_parents"], o.hang_parents)
+    assert np.array_equal(ex["hang_np"], o.hang_np)
+    off, ids = m.background()
+    for e in range(m.n_elem):
+        assert np.array_equal(ids[off[e]:off[e + 1]], o.background_triangles(e)), e
+    return m
+
+
+def test_host_mesh_matches_oracle_small_sphere(lib):
+    w = I.small_sphere()
+    m = _compare(w.lo, w.hi, w.base_level, w.regions, w.triangles(), w.lmax)
+    assert m.n_hang > 0
+
+
+def test_host_mesh_matches_oracle_carved_box_and_cone(lib):
+    regs = [I.Region(I.REGION_SPHERE_BAND, 6, (1.0, 0.5, 0.5, 0.12, 0.04)),
+            I.Region(I.REGION_CONE, 5, (1.0, 0.5, 0.5, 0.7, 0.1, 0.27)),
+            I.Region(I.REGION_BOX, 4, (0.2, 0.1, 0.1, 0.5, 0.4, 0.3))]
+    tri = I.icosphere(2, 0.12, (1.0, 0.5, 0.5), 1e-4, 4)
+    _compare((0, 0, 0), (2, 1, 1), 2, regs, tri)
+
+
+def test_host_mesh_without_body(lib):
+    _compare((0, 0, 0), (1, 1, 1), 2, [I.Region(I.REGION_SPHERE_BAND, 4, (0.3, 0.6, 0.5, 0.2, 0.05))], None)
+
+
+def test_invalid_arguments_are_rejected(lib):
+    with pytest.raises(_lib.ImgaError) as e:
+        api.Mesh((0, 0, 0), (1, 0.3, 1), 1, [], None, 3, device=-1)      # edge not a whole number of cells
+    assert e.value.status == 1
+    with pytest.raises(_lib.ImgaError):
+        api.Mesh((0, 0, 0), (1, 1, 1), 1, [], None, 7, device=-1)        # L_max out of range
+    with pytest.raises(_lib.ImgaError) as e:
+        bad = np.zeros((1, 3, 3))
+        api.Mesh((0, 0, 0), (1, 1, 1), 1, [], bad, 3, device=-1)         # zero-area triangle
+    assert e.value.status == 4
+    m = api.Mesh((0, 0, 0), (1, 1, 1), 1, [], None, 3, device=-1)
+    ph = api.physics_struct(I.Physics())
+    st = lib.imga_residual(m.h, C.c_void_p(16), C.c_void_p(16), None, None, C.byref(ph), 0, C.c_void_p(16), None)
+    assert st == 1                                                        # host-only mesh: no compute
+    assert b"host-only" in lib.imga_last_error()
