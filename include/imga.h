@@ -28,7 +28,9 @@
  *   - Inputs are never written.  Every call returns a status; nothing aborts or traps.  The
  *     message of the last failure on the calling thread is imga_last_error().
  *   - One mesh handle belongs to the device it was built on; calls using it must run with that
- *     device current or pass pointers of that device.
+ *     device current or pass pointers of that device.  A mesh owns one per-call node workspace,
+ *     so residual / J v calls on the same mesh must not overlap on the GPU (issue them on one
+ *     stream, or order the streams).
  */
 #ifndef IMGA_H
 #define IMGA_H
@@ -149,8 +151,8 @@ imga_status imga_set_dirichlet(imga_mesh mesh, const uint8_t* mask_dev, const do
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.
  * imga_profile_read synchronises the device and returns, per kernel class (0 Out elements,
- * 1 Intercepted elements, 2 Nitsche surface points, 3 strong rows), the summed milliseconds
- * ms[4] and the launch counts launches[4] since profiling was enabled. */
+ * 1 Intercepted elements, 2 Nitsche surface points, 3 strong rows, 4 node preparation), the
+ * summed milliseconds ms[5] and the launch counts launches[5] since profiling was enabled. */
 imga_status imga_profile(imga_mesh mesh, int enable);
 imga_status imga_profile_read(imga_mesh mesh, double* ms, int64_t* launches);
 

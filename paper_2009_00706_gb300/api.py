@@ -174,10 +174,10 @@ class Mesh:
 
     def profile_read(self):
         """{kernel: (total ms, launches)} since profiling was enabled (synchronises)."""
-        ms = np.zeros(4)
-        n = np.zeros(4, np.int64)
+        ms = np.zeros(5)
+        n = np.zeros(5, np.int64)
         check(_lib.load().imga_profile_read(self.h, ms.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p)))
-        names = ("out_elements", "cut_elements", "nitsche", "strong_rows")
+        names = ("out_elements", "cut_elements", "nitsche", "strong_rows", "node_prep")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
 
     def set_dirichlet(self, mask=None, vals=None, stream=None):

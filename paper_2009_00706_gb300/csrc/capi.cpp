@@ -234,7 +234,7 @@ imga_status imga_profile(imga_mesh h, int enable) {
 imga_status imga_profile_read(imga_mesh h, double* ms, int64_t* launches) {
     if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
     if (imga::profile_collect(h->m)) return cuda_status("profile_read");
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         if (ms) ms[k] = h->m.prof_ms[k];
         if (launches) launches[k] = h->m.prof_n[k];
     }

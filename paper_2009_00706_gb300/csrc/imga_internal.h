@@ -74,6 +74,10 @@ struct DeviceMesh {
     double* sq_n = nullptr;       // [n][3]
     double* sq_w = nullptr;
     double* sq_taub = nullptr;    // 1 / h_b
+    // per-call node workspace (node_prep): value, tangent and force data of every independent and
+    // hanging node, one float and one double copy
+    float* nd_f = nullptr;        // [3][n_nodes + n_hang][8]
+    double* nd_d = nullptr;
     // boundary rows
     uint8_t* bcflag = nullptr;    // [n_nodes] bits 0-3 box Dirichlet, bit 4 In-only node
     uint8_t* bcmask_user = nullptr;
@@ -115,9 +119,9 @@ struct Mesh {
     void* scratch = nullptr;             // device workspace for the kernels
     // per-kernel profiling (CUDA events, one pair per launch, resolved at read time)
     bool profiling = false;
-    std::vector<std::pair<void*, void*>> prof_ev[4];
-    double prof_ms[4] = {0, 0, 0, 0};
-    int64_t prof_n[4] = {0, 0, 0, 0};
+    std::vector<std::pair<void*, void*>> prof_ev[5];
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    int64_t prof_n[5] = {0, 0, 0, 0, 0};
     size_t scratch_bytes = 0;
 
     int64_t n_elem() const { return (int64_t)lev.size(); }

@@ -90,8 +90,13 @@ struct Args {
     const int32_t* conn;
     const int32_t* hpar;
     const uint8_t* lev;
-    int64_t n_nodes;
+    int64_t n_nodes, n_hang;
     double scale;
+    float gf[16], wf[16];                // per level: 2/h and h^3/8 (Jacobian of the cube map)
+    double gd[16], wd[16];
+    const void* ndv;                     // node data [n_nodes + n_hang][8] of T: us(3), p, at(3), 0
+    const void* ndt;                     // tangents  [n_nodes + n_hang][8] of T: dus(3), dp, dat(3), 0
+    const void* ndf;                     // body force [n_nodes + n_hang][4] of T, or null
     const double* U;
     const double* Up;
     const double* Up2;
@@ -142,35 +147,106 @@ __device__ __forceinline__ void scatter(const Args& A, int32_t id, const double 
     }
 }
 
-// Nodal data one corner contributes: spatial-state velocity (theta u + (1-theta) u_prev), p,
-// time-derivative combination (c0 u + c1 u_prev + c2 u_prev2) / dt, body force, and -- for J v
-// -- their tangents.  Combined in float64, stored as T.
+// Node data, prepared once per call by node_prep for every independent node and every hanging
+// node (the latter interpolated from its parents, u_e = M_e U), so the element kernels gather
+// with plain loads and no float64 arithmetic:
+//   us = theta u + (1-theta) u_prev (spatial state; theta = 1/2 is Crank-Nicolson), p,
+//   at = (c0 u + c1 u_prev + c2 u_prev2)/dt = c0 (u - u_prev) + c2 (u_prev2 - u_prev)
+//        (c0 + c1 + c2 = 0), the differences taken in float64 before rounding to T,
+//   and for J v the tangents dus = theta v, dp = v_p, dat = c0 v.
 constexpr int NF = 10;   // us[3], p, at[3], f[3]
 constexpr int NT = 7;    // dus[3], dp, dat[3]
 
+template <class T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { typedef double4 type; };
+
+template <class T>
+__device__ __forceinline__ void ld8(const void* base, int64_t i, T o[8]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4* p = reinterpret_cast<const float4*>(base) + 2 * i;
+        float4 a = __ldg(p), b = __ldg(p + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    } else {
+        const double2* p = reinterpret_cast<const double2*>(base) + 4 * i;
+        double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
+    }
+}
+template <class T>
+__device__ __forceinline__ void ld4(const void* base, int64_t i, T o[4]) {
+    if constexpr (sizeof(T) == 4) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(base) + i);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else {
+        const double2* p = reinterpret_cast<const double2*>(base) + 2 * i;
+        double2 a = __ldg(p), b = __ldg(p + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+}
+
 template <class T, bool JV>
 __device__ __forceinline__ void corner_data(const Args& A, int32_t id, T* dst) {
-    double u[4], up[4], up2[4] = {0, 0, 0, 0}, f[4] = {0, 0, 0, 0};
+    T a[8];
+    ld8<T>(A.ndv, id, a);
+    for (int k = 0; k < 7; ++k) dst[k] = a[k];
+    if (A.ndf) {
+        T f[4];
+        ld4<T>(A.ndf, id, f);
+        dst[7] = f[0]; dst[8] = f[1]; dst[9] = f[2];
+    } else {
+        dst[7] = dst[8] = dst[9] = T(0);
+    }
+    if (JV) {
+        T t[8];
+        ld8<T>(A.ndt, id, t);
+        for (int k = 0; k < 7; ++k) dst[NF + k] = t[k];
+    }
+}
+
+template <class T, bool JV>
+__global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T* __restrict__ ndt, T* __restrict__ ndf) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= A.n_nodes + A.n_hang) return;
+    const int32_t id = (int32_t)n;
+    double u[4], up[4], up2[4] = {0, 0, 0, 0};
     gather(A, A.U, id, u);
     gather(A, A.Up, id, up);
     if (A.c2 != 0.0) gather(A, A.Up2, id, up2);
-    if (A.F) gather(A, A.F, id, f);
+    T v8[8];
     for (int k = 0; k < 3; ++k) {
-        dst[k] = (T)(A.theta * u[k] + (1.0 - A.theta) * up[k]);
-        dst[4 + k] = (T)(A.c0 * u[k] + A.c1 * up[k] + A.c2 * up2[k]);
-        dst[7 + k] = (T)f[k];
+        v8[k] = A.theta == 1.0 ? (T)u[k] : (T)(A.theta * u[k] + (1.0 - A.theta) * up[k]);
+        T d1 = (T)(u[k] - up[k]);
+        T d2 = A.c2 != 0.0 ? (T)(up2[k] - up[k]) : T(0);
+        v8[4 + k] = (T)A.c0 * d1 + (T)A.c2 * d2;
     }
-    dst[3] = (T)u[3];
+    v8[3] = (T)u[3];
+    v8[7] = T(0);
+    for (int k = 0; k < 8; ++k) ndv[8 * n + k] = v8[k];
+    if (ndf) {
+        double f[4];
+        gather(A, A.F, id, f);
+        for (int k = 0; k < 3; ++k) ndf[4 * n + k] = (T)f[k];
+        ndf[4 * n + 3] = T(0);
+    }
     if (JV) {
         double v[4];
         gather(A, A.V, id, v);
-        for (int k = 0; k < 3; ++k) {
-            dst[NF + k] = (T)(A.theta * v[k]);
-            dst[NF + 4 + k] = (T)(A.c0 * v[k]);
-        }
-        dst[NF + 3] = (T)v[3];
+        T vt[4] = {(T)v[0], (T)v[1], (T)v[2], (T)v[3]};
+        T t8[8];
+        for (int k = 0; k < 3; ++k) { t8[k] = (T)A.theta * vt[k]; t8[4 + k] = (T)A.c0 * vt[k]; }
+        t8[3] = vt[3];
+        t8[7] = T(0);
+        for (int k = 0; k < 8; ++k) ndt[8 * n + k] = t8[k];
     }
 }
+
+template <class T> __device__ __forceinline__ T lvl_g(const Args& A, int l);
+template <> __device__ __forceinline__ float lvl_g<float>(const Args& A, int l) { return A.gf[l]; }
+template <> __device__ __forceinline__ double lvl_g<double>(const Args& A, int l) { return A.gd[l]; }
+template <class T> __device__ __forceinline__ T lvl_w(const Args& A, int l);
+template <> __device__ __forceinline__ float lvl_w<float>(const Args& A, int l) { return A.wf[l]; }
+template <> __device__ __forceinline__ double lvl_w<double>(const Args& A, int l) { return A.wd[l]; }
 
 // Q1 basis at reference point xi: values, physical gradients (g = 2/h), mixed second derivatives
 template <class T>
@@ -287,15 +363,15 @@ __global__ void __launch_bounds__(256) vms_interior(Args A, const int32_t* __res
     const int32_t id = A.conn[8 * (int64_t)e + c];
     corner_data<T, JV>(A, id, &s_nd[le][c][0]);
     __syncwarp();
-    const double hd = (double)(1u << (kMaxDepth - A.lev[e])) * A.scale;
-    const T g = (T)(2.0 / hd);
+    const int lv = A.lev[e];
+    const T g = lvl_g<T>(A, lv);
     const T gauss = (T)0.57735026918962576451;
     T xi[3] = {(c & 1) ? gauss : -gauss, (c & 2) ? gauss : -gauss, (c & 4) ? gauss : -gauss};
     Basis<T> B;
     basis<T>(xi, g, B);
     S cf[16];
     vms_point<S, T>(A, B, &s_nd[le][0][0], ST, g * g, cf);
-    const T wq = (T)(0.125 * hd * hd * hd);
+    const T wq = lvl_w<T>(A, lv);
     for (int k = 0; k < 16; ++k) s_cf[le][c][k] = wq * Pick<T, JV>::get(cf[k]);
     __syncwarp();
     // contraction for node a = c over the 8 Gauss points: phi_a(xi_q) factors as 1D values
@@ -354,9 +430,8 @@ __global__ void __launch_bounds__(32 * WPB) vms_cut(Args A, const int32_t* __res
         corner_data<T, JV>(A, my_id, &s_nd[w][lane][0]);
     }
     __syncwarp();
-    const double hd = (double)(1u << (kMaxDepth - A.lev[e])) * A.scale;
-    const T g = (T)(2.0 / hd);
-    const T det = (T)(0.125 * hd * hd * hd);
+    const T g = lvl_g<T>(A, A.lev[e]);
+    const T det = lvl_w<T>(A, A.lev[e]);
     const int a = lane >> 2, comp = lane & 3;
     const T sa[3] = {(a & 1) ? T(1) : T(-1), (a & 2) ? T(1) : T(-1), (a & 4) ? T(1) : T(-1)};
     T acc = T(0);
@@ -527,7 +602,18 @@ struct Timed {
 };
 
 template <class T, bool JV>
-void launch_all(const Mesh& m, const Args& A, cudaStream_t s) {
+void launch_all(const Mesh& m, Args A, cudaStream_t s) {
+    const int64_t next = m.n_nodes() + m.n_hang();
+    T* ndv = sizeof(T) == 4 ? (T*)(void*)m.d.nd_f : (T*)(void*)m.d.nd_d;
+    T* ndt = ndv + 8 * next;
+    T* ndf = A.F ? ndt + 8 * next : nullptr;
+    A.ndv = ndv;
+    A.ndt = ndt;
+    A.ndf = ndf;
+    if (next > 0) {
+        Timed t(m, 4, s);
+        node_prep<T, JV><<<(unsigned)((next + 255) / 256), 256, 0, s>>>(A, ndv, ndt, ndf);
+    }
     const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size(), ns = (int64_t)m.sq.size() / 10;
     constexpr int EPB = Epb<T>::value;
     if (no > 0) {
@@ -557,6 +643,15 @@ int vms_apply(const Mesh& m, const double* u, const double* up, const double* up
     A.lev = m.d.lev;
     A.n_nodes = m.n_nodes();
     A.scale = m.scale;
+    A.n_hang = m.n_hang();
+    for (int l = 0; l < 16; ++l) {
+        double h = (double)(1u << (kMaxDepth - l)) * m.scale;
+        A.gd[l] = 2.0 / h;
+        A.wd[l] = 0.125 * h * h * h;
+        A.gf[l] = (float)A.gd[l];
+        A.wf[l] = (float)A.wd[l];
+    }
+    A.ndv = A.ndt = A.ndf = nullptr;
     A.U = u;
     A.Up = up;
     A.Up2 = up2 ? up2 : up;
@@ -596,7 +691,7 @@ int vms_apply(const Mesh& m, const double* u, const double* up, const double* up
 }
 
 void profile_reset(Mesh& m) {
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         for (auto& p : m.prof_ev[k]) { cudaEventDestroy((cudaEvent_t)p.first); cudaEventDestroy((cudaEvent_t)p.second); }
         m.prof_ev[k].clear();
         m.prof_ms[k] = 0.0;
@@ -606,7 +701,7 @@ void profile_reset(Mesh& m) {
 
 int profile_collect(Mesh& m) {
     if (cudaDeviceSynchronize() != cudaSuccess) return 1;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         for (auto& p : m.prof_ev[k]) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, (cudaEvent_t)p.first, (cudaEvent_t)p.second);
