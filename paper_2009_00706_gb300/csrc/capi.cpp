@@ -3,6 +3,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -65,6 +66,7 @@ imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_pa
     if (!h) return fail(IMGA_ERR_OOM, "host allocation failed");
     imga::Mesh& m = h->m;
     m.device = device;
+    if (!host_only) cudaDeviceGetAttribute(&m.n_sm, cudaDevAttrMultiProcessorCount, device);
     double L = 0.0;
     for (int k = 0; k < 3; ++k) {
         m.lo[k] = P->lo[k];

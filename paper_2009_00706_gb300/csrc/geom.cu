@@ -342,6 +342,15 @@ bool device_cut_quadrature(Mesh& m, std::string& err) {
     const int64_t nc = (int64_t)m.cut_list.size();
     GeomView g = view(m);
     if (!upload(&m.d.out_list, m.out_list, err) || !upload(&m.d.cut_list, m.cut_list, err)) return false;
+    {
+        std::vector<int32_t> oc(8 * m.out_list.size());
+        std::vector<uint8_t> ol(m.out_list.size());
+        for (size_t i = 0; i < m.out_list.size(); ++i) {
+            for (int c = 0; c < 8; ++c) oc[8 * i + c] = m.conn[8 * (size_t)m.out_list[i] + c];
+            ol[i] = m.lev[m.out_list[i]];
+        }
+        if (!upload(&m.d.out_conn, oc, err) || !upload(&m.d.out_lev, ol, err)) return false;
+    }
     int64_t* cnt = nullptr;
     if (!check(cudaMalloc((void**)&cnt, (nc + 1) * sizeof(int64_t)), err, "cudaMalloc")) return false;
     cudaMemset(g_nrays_dev, 0, sizeof(unsigned long long));
@@ -410,7 +419,7 @@ int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags,
 void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
-                    d.marker, d.cflags, d.out_list, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
+                    d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
                     d.sq_n, d.sq_w, d.sq_taub, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);

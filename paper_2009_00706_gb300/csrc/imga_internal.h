@@ -65,6 +65,8 @@ struct DeviceMesh {
     uint8_t* cflags = nullptr;    // [n_elem]
     // quadrature
     int32_t* out_list = nullptr;  // Out elements
+    int32_t* out_conn = nullptr;  // [n_out][8] their corner -> node (or n_nodes + hanging) indices
+    uint8_t* out_lev = nullptr;   // [n_out] their levels
     int32_t* cut_list = nullptr;  // Intercepted elements
     int64_t* cut_off = nullptr;   // [n_cut + 1] into cut_pts
     double* cut_pts = nullptr;    // [n][4] (xi0, xi1, xi2, reference weight)
@@ -115,6 +117,7 @@ struct Mesh {
     double setup_ms[4] = {0, 0, 0, 0};
     bool user_bc = false;
     bool host_only = false;
+    int n_sm = 1;                        // streaming multiprocessors of the device
     DeviceMesh d;
     void* scratch = nullptr;             // device workspace for the kernels
     // per-kernel profiling (CUDA events, one pair per launch, resolved at read time)

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <type_traits>
 
 #include "imga_internal.h"
@@ -106,6 +107,9 @@ struct Args {
     double rho, mu, theta, c0, c1, c2;   // c_k = time coefficients / dt
     double K0dt;                         // 4 / dt^2
     double CInu2;                        // C_I nu^2
+    double irho;
+    float rhof, muf, irhof, K0f, CI3f;   // float copies (CI3 = 3 C_I nu^2, the G:G factor)
+    double CI3;
     double Cb;
     double g[3];
     int drop_visc;
@@ -154,8 +158,9 @@ __device__ __forceinline__ void scatter(const Args& A, int32_t id, const double 
 //   at = (c0 u + c1 u_prev + c2 u_prev2)/dt = c0 (u - u_prev) + c2 (u_prev2 - u_prev)
 //        (c0 + c1 + c2 = 0), the differences taken in float64 before rounding to T,
 //   and for J v the tangents dus = theta v, dp = v_p, dat = c0 v.
-constexpr int NF = 10;   // us[3], p, at[3], f[3]
-constexpr int NT = 7;    // dus[3], dp, dat[3]
+// corner row in shared memory: node value row (us, p, at, 0) | tangent row (dus, dp, dat, 0) |
+// force row (f, 0); 20 T, a multiple of 16 bytes so rows can be filled by 16-byte async copies
+constexpr int CT = 8, CF = 16, CS = 20;
 
 template <class T> struct Vec4;
 template <> struct Vec4<float> { typedef float4 type; };
@@ -187,20 +192,34 @@ __device__ __forceinline__ void ld4(const void* base, int64_t i, T o[4]) {
 
 template <class T, bool JV>
 __device__ __forceinline__ void corner_data(const Args& A, int32_t id, T* dst) {
-    T a[8];
-    ld8<T>(A.ndv, id, a);
-    for (int k = 0; k < 7; ++k) dst[k] = a[k];
-    if (A.ndf) {
-        T f[4];
-        ld4<T>(A.ndf, id, f);
-        dst[7] = f[0]; dst[8] = f[1]; dst[9] = f[2];
-    } else {
-        dst[7] = dst[8] = dst[9] = T(0);
-    }
+    ld8<T>(A.ndv, id, dst);
+    if (JV) ld8<T>(A.ndt, id, dst + CT);
+    if (A.ndf) ld4<T>(A.ndf, id, dst + CF);
+    else dst[CF] = dst[CF + 1] = dst[CF + 2] = dst[CF + 3] = T(0);
+}
+
+// 16-byte asynchronous global -> shared copy (bypasses registers and L1)
+__device__ __forceinline__ void cp16(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <class T, bool JV>
+__device__ __forceinline__ void corner_async(const Args& A, int32_t id, T* dst) {
+    constexpr int C8 = 8 * sizeof(T) / 16;   // 16-byte chunks in a row of 8 T
+    const char* v = reinterpret_cast<const char*>(A.ndv) + (size_t)id * 8 * sizeof(T);
+    for (int k = 0; k < C8; ++k) cp16(reinterpret_cast<char*>(dst) + 16 * k, v + 16 * k);
     if (JV) {
-        T t[8];
-        ld8<T>(A.ndt, id, t);
-        for (int k = 0; k < 7; ++k) dst[NF + k] = t[k];
+        const char* t = reinterpret_cast<const char*>(A.ndt) + (size_t)id * 8 * sizeof(T);
+        for (int k = 0; k < C8; ++k) cp16(reinterpret_cast<char*>(dst + CT) + 16 * k, t + 16 * k);
+    }
+    if (A.ndf) {
+        const char* f = reinterpret_cast<const char*>(A.ndf) + (size_t)id * 4 * sizeof(T);
+        for (int k = 0; k < C8 / 2; ++k) cp16(reinterpret_cast<char*>(dst + CF) + 16 * k, f + 16 * k);
+    } else {
+        dst[CF] = dst[CF + 1] = dst[CF + 2] = dst[CF + 3] = T(0);
     }
 }
 
@@ -241,6 +260,17 @@ __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T*
     }
 }
 
+// physical constants in the element precision
+template <class T> struct Phys;
+template <> struct Phys<float> {
+    float rho, mu, irho, K0, CI3;
+    __device__ Phys(const Args& A) : rho(A.rhof), mu(A.muf), irho(A.irhof), K0(A.K0f), CI3(A.CI3f) {}
+};
+template <> struct Phys<double> {
+    double rho, mu, irho, K0, CI3;
+    __device__ Phys(const Args& A) : rho(A.rho), mu(A.mu), irho(A.irho), K0(A.K0dt), CI3(A.CI3) {}
+};
+
 template <class T> __device__ __forceinline__ T lvl_g(const Args& A, int l);
 template <> __device__ __forceinline__ float lvl_g<float>(const Args& A, int l) { return A.gf[l]; }
 template <> __device__ __forceinline__ double lvl_g<double>(const Args& A, int l) { return A.gd[l]; }
@@ -248,34 +278,37 @@ template <class T> __device__ __forceinline__ T lvl_w(const Args& A, int l);
 template <> __device__ __forceinline__ float lvl_w<float>(const Args& A, int l) { return A.wf[l]; }
 template <> __device__ __forceinline__ double lvl_w<double>(const Args& A, int l) { return A.wd[l]; }
 
-// Q1 basis at reference point xi: values, physical gradients (g = 2/h), mixed second derivatives
+// Q1 basis at reference point xi: values, reference-cube first derivatives d/dxi and mixed
+// second derivatives; physical derivatives are these times g = 2/h (g^2), applied to the
+// interpolated fields rather than to every basis function.
 template <class T>
 struct Basis {
     T phi[8], dphi[8][3], d2[8][3];   // d2: (01, 02, 12) mixed second derivatives
 };
 template <class T>
-__device__ __forceinline__ void basis(const T xi[3], T g, Basis<T>& B) {
+__device__ __forceinline__ void basis(const T xi[3], Basis<T>& B) {
     T fm[3], fp[3];
     for (int k = 0; k < 3; ++k) { fm[k] = T(0.5) * (T(1) - xi[k]); fp[k] = T(0.5) * (T(1) + xi[k]); }
-    const T hg = T(0.5) * g, qg2 = T(0.25) * g * g;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         T f0 = (c & 1) ? fp[0] : fm[0], f1 = (c & 2) ? fp[1] : fm[1], f2 = (c & 4) ? fp[2] : fm[2];
-        T s0 = (c & 1) ? T(1) : T(-1), s1 = (c & 2) ? T(1) : T(-1), s2 = (c & 4) ? T(1) : T(-1);
-        B.phi[c] = f0 * f1 * f2;
-        B.dphi[c][0] = hg * s0 * f1 * f2;
-        B.dphi[c][1] = hg * s1 * f0 * f2;
-        B.dphi[c][2] = hg * s2 * f0 * f1;
-        B.d2[c][0] = qg2 * s0 * s1 * f2;
-        B.d2[c][1] = qg2 * s0 * s2 * f1;
-        B.d2[c][2] = qg2 * s1 * s2 * f0;
+        T h0 = (c & 1) ? T(0.5) : T(-0.5), h1 = (c & 2) ? T(0.5) : T(-0.5), h2 = (c & 4) ? T(0.5) : T(-0.5);
+        T f01 = f0 * f1;
+        B.phi[c] = f01 * f2;
+        B.dphi[c][0] = h0 * (f1 * f2);
+        B.dphi[c][1] = h1 * (f0 * f2);
+        B.dphi[c][2] = h2 * f01;
+        B.d2[c][0] = (h0 * h1) * f2;
+        B.d2[c][1] = (h0 * h2) * f1;
+        B.d2[c][2] = (h1 * h2) * f0;
     }
 }
 
-// Pointwise VMS: fields at a quadrature point -> the 16 coefficients (F, S, G, H).
+// Pointwise VMS: fields at a quadrature point -> the 16 coefficients (F, S, G, H).  The S and H
+// coefficients come out divided by g (they multiply reference derivatives in the contraction).
 template <class S, class T>
-__device__ __forceinline__ void vms_point(const Args& A, const Basis<T>& B, const T* nd /*[8][NF+NT]*/, int stride,
-                                          T g2, S out[16]) {
+__device__ __forceinline__ void vms_point(const Args& A, const T fm[3], const T fp[3], const T* nd /*[8][CS]*/,
+                                          int stride, T g, S out[16]) {
     S us[3], Gu[3][3], p = zero<S>(), gp[3], at[3], H2[3];
     T f[3] = {T(0), T(0), T(0)};
     for (int i = 0; i < 3; ++i) {
@@ -285,59 +318,79 @@ __device__ __forceinline__ void vms_point(const Args& A, const Basis<T>& B, cons
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const T* q = nd + c * stride;
-        const T ph = B.phi[c];
+        // basis of corner c at the point, formed on the fly (keeps no 8-corner tables live)
+        const T f0 = (c & 1) ? fp[0] : fm[0], f1 = (c & 2) ? fp[1] : fm[1], f2 = (c & 4) ? fp[2] : fm[2];
+        const T h0 = (c & 1) ? T(0.5) : T(-0.5), h1 = (c & 2) ? T(0.5) : T(-0.5), h2 = (c & 4) ? T(0.5) : T(-0.5);
+        const T f01 = f0 * f1;
+        const T ph = f01 * f2;
+        const T dph[3] = {h0 * (f1 * f2), h1 * (f0 * f2), h2 * f01};
+        const T d2[3] = {(h0 * h1) * f2, (h0 * h2) * f1, (h1 * h2) * f0};
         S vu[3], vp, va[3];
         if constexpr (std::is_same<S, T>::value) {
             for (int k = 0; k < 3; ++k) { vu[k] = q[k]; va[k] = q[4 + k]; }
             vp = q[3];
         } else {
-            for (int k = 0; k < 3; ++k) { vu[k] = make<S, T>(q[k], q[NF + k]); va[k] = make<S, T>(q[4 + k], q[NF + 4 + k]); }
-            vp = make<S, T>(q[3], q[NF + 3]);
+            for (int k = 0; k < 3; ++k) { vu[k] = make<S, T>(q[k], q[CT + k]); va[k] = make<S, T>(q[4 + k], q[CT + 4 + k]); }
+            vp = make<S, T>(q[3], q[CT + 3]);
         }
         p = p + ph * vp;
         for (int i = 0; i < 3; ++i) {
             us[i] = us[i] + ph * vu[i];
             at[i] = at[i] + ph * va[i];
-            gp[i] = gp[i] + B.dphi[c][i] * vp;
-            f[i] = f[i] + ph * q[7 + i];
-            for (int j = 0; j < 3; ++j) Gu[i][j] = Gu[i][j] + B.dphi[c][j] * vu[i];
+            gp[i] = gp[i] + dph[i] * vp;
+            for (int j = 0; j < 3; ++j) Gu[i][j] = Gu[i][j] + dph[j] * vu[i];
         }
         // (grad div u)_i = sum_{j != i} d_i d_j u_j  (trilinear: d_j d_j phi = 0)
-        H2[0] = H2[0] + B.d2[c][0] * vu[1] + B.d2[c][1] * vu[2];
-        H2[1] = H2[1] + B.d2[c][0] * vu[0] + B.d2[c][2] * vu[2];
-        H2[2] = H2[2] + B.d2[c][1] * vu[0] + B.d2[c][2] * vu[1];
+        H2[0] = H2[0] + d2[0] * vu[1] + d2[1] * vu[2];
+        H2[1] = H2[1] + d2[0] * vu[0] + d2[2] * vu[2];
+        H2[2] = H2[2] + d2[1] * vu[0] + d2[2] * vu[1];
     }
-    const T rho = (T)A.rho, mu = (T)A.mu, irho = (T)(1.0 / A.rho);
+    if (A.ndf) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const T ph = ((c & 1) ? fp[0] : fm[0]) * ((c & 2) ? fp[1] : fm[1]) * ((c & 4) ? fp[2] : fm[2]);
+            for (int i = 0; i < 3; ++i) f[i] = f[i] + ph * nd[c * stride + CF + i];
+        }
+    }
+    const Phys<T> P(A);
+    const T g2 = g * g;
+    for (int i = 0; i < 3; ++i) {
+        gp[i] = g * gp[i];
+        H2[i] = g2 * H2[i];
+        for (int j = 0; j < 3; ++j) Gu[i][j] = g * Gu[i][j];
+    }
     S divu = Gu[0][0] + Gu[1][1] + Gu[2][2];
     S conv[3], rM[3];
     for (int i = 0; i < 3; ++i) {
         conv[i] = Gu[i][0] * us[0] + Gu[i][1] * us[1] + Gu[i][2] * us[2];
-        S r = rho * (at[i] + conv[i] - f[i]) + gp[i];
-        rM[i] = A.drop_visc ? r : r - mu * H2[i];
+        S r = P.rho * (at[i] + conv[i] - f[i]) + gp[i];
+        rM[i] = A.drop_visc ? r : r - P.mu * H2[i];
     }
-    // tau_M = (4/dt^2 + u.G u + C_I nu^2 G:G)^(-1/2), G = g2 I;  tau_C = 1 / (tau_M tr G)
+    // tau_M = (4/dt^2 + u.G u + C_I nu^2 G:G)^(-1/2), G = g^2 I;  tau_C = 1 / (tau_M tr G)
     S uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
-    S tauM = rsq(g2 * uu + (T)(A.K0dt) + T(3) * (T)A.CInu2 * g2 * g2);
-    S tauC = rcp(T(3) * g2 * tauM);
+    S tauM = rsq(g2 * uu + (P.K0 + P.CI3 * (g2 * g2)));
+    S tauC = rcp((T(3) * g2) * tauM);
     S up[3];
     for (int i = 0; i < 3; ++i) up[i] = -(tauM * rM[i]);
-    S pp = -(rho * tauC * divu);
+    S pp = -(P.rho * tauC * divu);
     S q = g2 * (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
     bool bar = value(q) > tiny<T>();
     S taubar = bar ? rsq(q) : zero<S>();
     S Gup[3];
     for (int i = 0; i < 3; ++i) Gup[i] = Gu[i][0] * up[0] + Gu[i][1] * up[1] + Gu[i][2] * up[2];
+    const T ig = T(1) / g;
     for (int i = 0; i < 3; ++i) {
-        out[i] = rho * (at[i] + conv[i] - f[i]) + Gup[i];
+        out[i] = P.rho * (at[i] + conv[i] - f[i]) + Gup[i];
         S tb = taubar * Gup[i];
         for (int j = 0; j < 3; ++j) {
-            S sij = mu * (Gu[i][j] + Gu[j][i]) - up[i] * us[j] - irho * (up[i] * up[j]) + tb * up[j];
+            S sij = P.mu * (Gu[i][j] + Gu[j][i]) - up[i] * us[j] - P.irho * (up[i] * up[j]) + tb * up[j];
             if (i == j) sij = sij - p - pp;
             out[3 + 3 * i + j] = sij;
         }
-        out[13 + i] = -(irho * up[i]);
+        out[13 + i] = -(P.irho * up[i]);
     }
     out[12] = divu;
+    (void)ig;
 }
 
 template <class T, bool JV> struct Pick;
@@ -349,52 +402,91 @@ template <class T> struct Pick<T, true> { template <class S> __device__ static T
 // ------------------------------------------------------------------------------------------
 template <class T> struct Epb { static constexpr int value = sizeof(T) == 8 ? 16 : 32; };   // elements per block
 
+template <class T> struct IntShape {
+    static constexpr int EPB = Epb<T>::value;                                   // elements per block
+    static constexpr int THREADS = 8 * EPB;
+    static constexpr size_t smem = (size_t)(2 * EPB * 8 * CS + EPB * 8 * 17) * sizeof(T);
+};
+
+// Persistent: a block walks element groups with a grid stride; while it computes group g its
+// threads already stream the node rows of group g + stride into the other shared buffer
+// (cp.async), so the gather latency hides behind the arithmetic.  Thread c of an element
+// gathers corner c, evaluates Gauss point c, then contracts node c's four rows.
 template <class T, bool JV>
-__global__ void __launch_bounds__(256) vms_interior(Args A, const int32_t* __restrict__ list, int64_t n) {
+__global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, const int32_t* __restrict__ oconn,
+                                                    const uint8_t* __restrict__ olev, int64_t n) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
-    constexpr int ST = NF + (JV ? NT : 0);
-    constexpr int EPB = Epb<T>::value;
-    __shared__ T s_nd[EPB][8][ST];
-    __shared__ T s_cf[EPB][8][17];
+    constexpr int EPB = IntShape<T>::EPB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s_nd = reinterpret_cast<T*>(smem_raw);          // [2][EPB][8][CS]
+    T* s_cf = s_nd + 2 * EPB * 8 * CS;                  // [EPB][8][17]
     const int c = threadIdx.x & 7, le = threadIdx.x >> 3;
-    const int64_t idx = (int64_t)blockIdx.x * EPB + le;
-    const bool valid = idx < n;
-    const int32_t e = list[valid ? idx : n - 1];
-    const int32_t id = A.conn[8 * (int64_t)e + c];
-    corner_data<T, JV>(A, id, &s_nd[le][c][0]);
-    __syncwarp();
-    const int lv = A.lev[e];
-    const T g = lvl_g<T>(A, lv);
+    const int64_t ngroups = (n + EPB - 1) / EPB;
+    int64_t gi = blockIdx.x;
+    if (gi >= ngroups) return;
+    auto corner_id = [&](int64_t grp) -> int32_t {
+        int64_t idx = grp * EPB + le;
+        if (idx >= n) idx = n - 1;
+        return __ldg(oconn + 8 * idx + c);
+    };
+    auto row = [&](int buf) -> T* { return s_nd + ((buf * EPB + le) * 8 + c) * CS; };
+    int32_t id_cur = corner_id(gi);
+    corner_async<T, JV>(A, id_cur, row(0));
+    cp_commit();
+    int32_t id_next = gi + gridDim.x < ngroups ? corner_id(gi + gridDim.x) : 0;
     const T gauss = (T)0.57735026918962576451;
-    T xi[3] = {(c & 1) ? gauss : -gauss, (c & 2) ? gauss : -gauss, (c & 4) ? gauss : -gauss};
-    Basis<T> B;
-    basis<T>(xi, g, B);
-    S cf[16];
-    vms_point<S, T>(A, B, &s_nd[le][0][0], ST, g * g, cf);
-    const T wq = lvl_w<T>(A, lv);
-    for (int k = 0; k < 16; ++k) s_cf[le][c][k] = wq * Pick<T, JV>::get(cf[k]);
-    __syncwarp();
-    // contraction for node a = c over the 8 Gauss points: phi_a(xi_q) factors as 1D values
     const T wp = T(0.5) * (T(1) + gauss), wm = T(0.5) * (T(1) - gauss);
-    T r[4] = {T(0), T(0), T(0), T(0)};
+    // Gauss point c: 1D factors (1 -/+ xi_k)/2 take the values wp, wm
+    T fm[3], fp[3];
+    for (int k = 0; k < 3; ++k) {
+        const bool plus = (c >> k) & 1;
+        fm[k] = plus ? wm : wp;
+        fp[k] = plus ? wp : wm;
+    }
+    int buf = 0;
+    for (; gi < ngroups; gi += gridDim.x) {
+        const int64_t gnext = gi + gridDim.x;
+        if (gnext < ngroups) corner_async<T, JV>(A, id_next, row(buf ^ 1));
+        cp_commit();
+        const int32_t id_after = gnext + gridDim.x < ngroups ? corner_id(gnext + gridDim.x) : 0;
+        cp_wait<1>();
+        __syncwarp();
+        const int64_t idx = gi * EPB + le;
+        const bool valid = idx < n;
+        const int lv = __ldg(olev + (valid ? idx : n - 1));
+        const T g = lvl_g<T>(A, lv);
+        S cf[16];
+        vms_point<S, T>(A, fm, fp, s_nd + (buf * EPB + le) * 8 * CS, CS, g, cf);
+        const T wq = lvl_w<T>(A, lv), wqg = wq * g;
+        T* mycf = s_cf + (le * 8 + c) * 17;
+        // F, G multiply phi; S, H multiply physical gradients = g x reference gradients
+        for (int k = 0; k < 16; ++k) mycf[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
+        __syncwarp();
+        T r[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        T f[3], d[3];
-        for (int k = 0; k < 3; ++k) {
-            bool same = (((c >> k) & 1) == ((q >> k) & 1));
-            f[k] = same ? wp : wm;
-            d[k] = (((c >> k) & 1) ? T(0.5) : T(-0.5)) * g;
+        for (int q = 0; q < 8; ++q) {
+            T f[3], d[3];
+            for (int k = 0; k < 3; ++k) {
+                bool same = (((c >> k) & 1) == ((q >> k) & 1));
+                f[k] = same ? wp : wm;
+                d[k] = ((c >> k) & 1) ? T(0.5) : T(-0.5);
+            }
+            T ph = f[0] * f[1] * f[2];
+            T dp[3] = {d[0] * f[1] * f[2], d[1] * f[0] * f[2], d[2] * f[0] * f[1]};
+            const T* C = s_cf + (le * 8 + q) * 17;
+            for (int i = 0; i < 3; ++i) r[i] += ph * C[i] + dp[0] * C[3 + 3 * i] + dp[1] * C[4 + 3 * i] + dp[2] * C[5 + 3 * i];
+            r[3] += ph * C[12] + dp[0] * C[13] + dp[1] * C[14] + dp[2] * C[15];
         }
-        T ph = f[0] * f[1] * f[2];
-        T dp[3] = {d[0] * f[1] * f[2], d[1] * f[0] * f[2], d[2] * f[0] * f[1]};
-        const T* C = s_cf[le][q];
-        for (int i = 0; i < 3; ++i) r[i] += ph * C[i] + dp[0] * C[3 + 3 * i] + dp[1] * C[4 + 3 * i] + dp[2] * C[5 + 3 * i];
-        r[3] += ph * C[12] + dp[0] * C[13] + dp[1] * C[14] + dp[2] * C[15];
+        if (valid) {
+            double rd[4] = {(double)r[0], (double)r[1], (double)r[2], (double)r[3]};
+            scatter(A, id_cur, rd);
+        }
+        __syncwarp();   // this buffer and s_cf are rewritten by later iterations
+        id_cur = id_next;
+        id_next = id_after;
+        buf ^= 1;
     }
-    if (valid) {
-        double rd[4] = {(double)r[0], (double)r[1], (double)r[2], (double)r[3]};
-        scatter(A, id, rd);
-    }
+    cp_wait<0>();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -417,8 +509,7 @@ template <class T, bool JV>
 __global__ void __launch_bounds__(32 * WPB) vms_cut(Args A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
                                                     const void* __restrict__ pts, int64_t n) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
-    constexpr int ST = NF + (JV ? NT : 0);
-    __shared__ T s_nd[WPB][8][ST];
+    __shared__ T s_nd[WPB][8][CS];
     __shared__ T s_cf[WPB][32][20];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t idx = (int64_t)blockIdx.x * WPB + w;
@@ -441,12 +532,12 @@ __global__ void __launch_bounds__(32 * WPB) vms_cut(Args A, const int32_t* __res
         if (q < q1) {
             T pt[4];
             load_pt<T>(pts, q, pt);
-            Basis<T> B;
-            basis<T>(pt, g, B);
+            T fm[3], fp[3];
+            for (int k = 0; k < 3; ++k) { fm[k] = T(0.5) * (T(1) - pt[k]); fp[k] = T(0.5) * (T(1) + pt[k]); }
             S cf[16];
-            vms_point<S, T>(A, B, &s_nd[w][0][0], ST, g * g, cf);
-            const T wq = pt[3] * det;
-            for (int k = 0; k < 16; ++k) s_cf[w][lane][k] = wq * Pick<T, JV>::get(cf[k]);
+            vms_point<S, T>(A, fm, fp, &s_nd[w][0][0], CS, g, cf);
+            const T wq = pt[3] * det, wqg = wq * g;
+            for (int k = 0; k < 16; ++k) s_cf[w][lane][k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
             s_cf[w][lane][16] = pt[0];
             s_cf[w][lane][17] = pt[1];
             s_cf[w][lane][18] = pt[2];
@@ -459,8 +550,7 @@ __global__ void __launch_bounds__(32 * WPB) vms_cut(Args A, const int32_t* __res
             const T* C = s_cf[w][j];
             T f0 = T(0.5) * (T(1) + sa[0] * C[16]), f1 = T(0.5) * (T(1) + sa[1] * C[17]), f2 = T(0.5) * (T(1) + sa[2] * C[18]);
             T ph = f0 * f1 * f2;
-            T hg = T(0.5) * g;
-            T d0 = hg * sa[0] * f1 * f2, d1 = hg * sa[1] * f0 * f2, d2 = hg * sa[2] * f0 * f1;
+            T d0 = T(0.5) * sa[0] * f1 * f2, d1 = T(0.5) * sa[1] * f0 * f2, d2 = T(0.5) * sa[2] * f0 * f1;
             if (comp < 3) acc += ph * C[comp] + d0 * C[3 + 3 * comp] + d1 * C[4 + 3 * comp] + d2 * C[5 + 3 * comp];
             else acc += ph * C[12] + d0 * C[13] + d1 * C[14] + d2 * C[15];
         }
@@ -484,73 +574,59 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t e = el[i];
-    const double hd = (double)(1u << (kMaxDepth - A.lev[e])) * A.scale;
-    const T g = (T)(2.0 / hd);
+    const T g = lvl_g<T>(A, A.lev[e]);
     T xi[3] = {(T)xr[3 * i], (T)xr[3 * i + 1], (T)xr[3 * i + 2]};
     const T nn[3] = {(T)nr[3 * i], (T)nr[3 * i + 1], (T)nr[3 * i + 2]};
-    const double ndd[3] = {nr[3 * i], nr[3 * i + 1], nr[3 * i + 2]};
     Basis<T> B;
-    basis<T>(xi, g, B);
-    // float64 interpolation of u_s (and its tangent) for the penalty terms
-    double xd[3] = {xr[3 * i], xr[3 * i + 1], xr[3 * i + 2]};
-    double phd[8];
-    for (int c = 0; c < 8; ++c) {
-        double f = 1.0;
-        for (int k = 0; k < 3; ++k) f *= 0.5 * (1.0 + (((c >> k) & 1) ? xd[k] : -xd[k]));
-        phd[c] = f;
-    }
-    S us[3], Gu[3][3], p = zero<S>();
-    double usd[3] = {0, 0, 0}, dusd[3] = {0, 0, 0};
+    basis<T>(xi, B);
+    // u_s, p and grad u_s from the node data; the velocity jump d = u_s - g from corner values
+    // formed in float64 (the penalty multiplies it by tau_B, up to 100 C_b mu / h on slivers)
+    S us[3], Gu[3][3], p = zero<S>(), d[3];
     int32_t ids[8];
-    for (int k = 0; k < 3; ++k) { us[k] = zero<S>(); for (int j = 0; j < 3; ++j) Gu[k][j] = zero<S>(); }
+    for (int k = 0; k < 3; ++k) { us[k] = zero<S>(); d[k] = zero<S>(); for (int j = 0; j < 3; ++j) Gu[k][j] = zero<S>(); }
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
         ids[c] = A.conn[8 * (int64_t)e + c];
-        double u[4], up[4], v[4] = {0, 0, 0, 0};
-        gather(A, A.U, ids[c], u);
-        gather(A, A.Up, ids[c], up);
-        if (JV) gather(A, A.V, ids[c], v);
-        S vu[3];
+        T a8[8], t8[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        ld8<T>(A.ndv, ids[c], a8);
+        if (JV) ld8<T>(A.ndt, ids[c], t8);
+        double u4[4], up4[4];
+        gather(A, A.U, ids[c], u4);
+        if (A.theta != 1.0) gather(A, A.Up, ids[c], up4);
+        const T ph = B.phi[c];
         for (int k = 0; k < 3; ++k) {
-            double s = A.theta * u[k] + (1.0 - A.theta) * up[k];
-            double ds = A.theta * v[k];
-            vu[k] = make<S, T>((T)s, (T)ds);
-            usd[k] += phd[c] * s;
-            dusd[k] += phd[c] * ds;
+            S vu = make<S, T>(a8[k], t8[k]);
+            double usk = A.theta == 1.0 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
+            S jump = make<S, T>((T)(usk - A.g[k]), t8[k]);
+            us[k] = us[k] + ph * vu;
+            d[k] = d[k] + ph * jump;
+            for (int j = 0; j < 3; ++j) Gu[k][j] = Gu[k][j] + B.dphi[c][j] * vu;
         }
-        S vp = make<S, T>((T)u[3], (T)v[3]);
-        p = p + B.phi[c] * vp;
-        for (int k = 0; k < 3; ++k) {
-            us[k] = us[k] + B.phi[c] * vu[k];
-            for (int j = 0; j < 3; ++j) Gu[k][j] = Gu[k][j] + B.dphi[c][j] * vu[k];
-        }
+        p = p + ph * make<S, T>(a8[3], t8[3]);
     }
-    const T mu = (T)A.mu, rho = (T)A.rho;
-    S d[3];
-    for (int k = 0; k < 3; ++k) d[k] = us[k] - (T)A.g[k];
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) Gu[k][j] = g * Gu[k][j];
+    const Phys<T> P(A);
     S un = us[0] * nn[0] + us[1] * nn[1] + us[2] * nn[2];
     S dn = d[0] * nn[0] + d[1] * nn[1] + d[2] * nn[2];
     const bool inflow = value(un) < T(0);
     S tr[3];
-    for (int k = 0; k < 3; ++k) {
-        tr[k] = mu * ((Gu[k][0] + Gu[0][k]) * nn[0] + (Gu[k][1] + Gu[1][k]) * nn[1] + (Gu[k][2] + Gu[2][k]) * nn[2]) - p * nn[k];
-    }
-    const double w = wr[i];
-    const double tauB = A.Cb * A.mu * taub[i];
-    // penalty (tau_TAN = tau_NOR: both parts sum to tau_B (u - g)), float64
-    double pen[3];
-    for (int k = 0; k < 3; ++k) pen[k] = JV ? tauB * dusd[k] : tauB * (usd[k] - A.g[k]);
-    (void)ndd;
+    for (int k = 0; k < 3; ++k)
+        tr[k] = P.mu * ((Gu[k][0] + Gu[0][k]) * nn[0] + (Gu[k][1] + Gu[1][k]) * nn[1] + (Gu[k][2] + Gu[2][k]) * nn[2]) - p * nn[k];
+    const T w = (T)wr[i];
+    const T tauB = (T)(A.Cb * A.mu * taub[i]);    // tau_TAN = tau_NOR: both penalty parts sum to tau_B (u - g)
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
         const T ph = B.phi[c];
-        const T gn = B.dphi[c][0] * nn[0] + B.dphi[c][1] * nn[1] + B.dphi[c][2] * nn[2];
-        S gd = B.dphi[c][0] * d[0] + B.dphi[c][1] * d[1] + B.dphi[c][2] * d[2];
+        const T gn = g * (B.dphi[c][0] * nn[0] + B.dphi[c][1] * nn[1] + B.dphi[c][2] * nn[2]);
+        S gd = g * (B.dphi[c][0] * d[0] + B.dphi[c][1] * d[1] + B.dphi[c][2] * d[2]);
         double r[4];
         for (int k = 0; k < 3; ++k) {
-            S t = -(ph * tr[k]) - mu * (gn * d[k] + nn[k] * gd);
-            if (inflow) t = t - (ph * rho) * (un * d[k]);
-            r[k] = w * ((double)Pick<T, JV>::get(t) + (double)ph * pen[k]);
+            S t = (tauB * ph) * d[k] - ph * tr[k] - P.mu * (gn * d[k] + nn[k] * gd);
+            if (inflow) t = t - (ph * P.rho) * (un * d[k]);
+            r[k] = (double)(w * Pick<T, JV>::get(t));
         }
-        r[3] = w * (double)Pick<T, JV>::get(-(ph * dn));
+        r[3] = (double)(w * Pick<T, JV>::get(-(ph * dn)));
         scatter(A, ids[c], r);
     }
 }
@@ -618,7 +694,17 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s) {
     constexpr int EPB = Epb<T>::value;
     if (no > 0) {
         Timed t(m, 0, s);
-        vms_interior<T, JV><<<(unsigned)((no + EPB - 1) / EPB), 8 * EPB, 0, s>>>(A, m.d.out_list, no);
+        static int per_sm[2][2] = {{0, 0}, {0, 0}};
+        int& bps = per_sm[sizeof(T) == 8][JV];
+        const size_t smem = IntShape<T>::smem;
+        if (bps == 0) {
+            cudaFuncSetAttribute(vms_interior<T, JV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, vms_interior<T, JV>, 8 * EPB, smem);
+            if (bps < 1) bps = 1;
+        }
+        const int64_t groups = (no + EPB - 1) / EPB;
+        const int64_t grid = std::min<int64_t>(groups, (int64_t)bps * m.n_sm);
+        vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, smem, s>>>(A, m.d.out_conn, m.d.out_lev, no);
     }
     if (nc > 0) {
         Timed t(m, 1, s);
@@ -671,6 +757,13 @@ int vms_apply(const Mesh& m, const double* u, const double* up, const double* up
     A.K0dt = 4.0 / (ph.dt * ph.dt);
     const double nu = ph.mu / ph.rho;
     A.CInu2 = ph.C_I * nu * nu;
+    A.CI3 = 3.0 * A.CInu2;
+    A.irho = 1.0 / ph.rho;
+    A.rhof = (float)ph.rho;
+    A.muf = (float)ph.mu;
+    A.irhof = (float)A.irho;
+    A.K0f = (float)A.K0dt;
+    A.CI3f = (float)A.CI3;
     A.Cb = ph.C_b;
     for (int k = 0; k < 3; ++k) A.g[k] = ph.g_body[k];
     A.drop_visc = ph.drop_visc_strong;
