@@ -143,6 +143,28 @@ imga_status imga_residual(imga_mesh mesh, const double* u, const double* u_prev,
 imga_status imga_jvp(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2, const double* f,
                      const imga_physics* phys, int precision, const double* v, double* Jv, void* stream);
 
+/* imga_jvp that allocates nothing.  No counterpart in the paper: this entry point exists for
+ * callers that cannot allocate device memory when they apply the operator -- processes whose
+ * device memory is capped or handed out once at start-up (a GPU shared through a memory-limited
+ * partition, an application that reserves all of its memory up front and treats any later
+ * cudaMalloc as a failure).  It computes exactly what imga_jvp computes, on the caller's
+ * inputs and into the caller's output, but its per-call node workspace is a fixed device array
+ * of 32 MiB compiled into the library, which every GPU that loads the library holds until the
+ * process exits, instead of the workspace of the mesh handle.
+ *   Limit: (16 + 4 if f != NULL) x (n_nodes + n_hanging) x (4 bytes for precision 1, 8 bytes
+ *   for precision 0) must not exceed 32 MiB; larger meshes are rejected with
+ *   IMGA_ERR_INVALID_ARG and a message giving the bytes needed.
+ *   The first call on a device looks the array up on that device (cudaGetSymbolAddress, with
+ *   that device current); make that first call before any stream capture.
+ *   Every call on every mesh shares the one array, and each call overwrites all of the part it
+ *   uses before reading it, so nothing has to be cleared between calls; calls that overlap on
+ *   the GPU race on the array: issue them on one stream or order their streams.
+ *   The mesh's device must be current.  Calls no cudaMalloc, cudaFree or other allocating
+ *   routine. */
+imga_status imga_jvp_noalloc(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
+                             const double* f, const imga_physics* phys, int precision, const double* v, double* Jv,
+                             void* stream);
+
 /* Replace the default strong Dirichlet rows (u = u_inf on every box face but the outlet x = hi,
  * p = 0 on the outlet) by mask_dev uint8 [n_nodes] (bit k: component k prescribed) and values
  * val_dev float64 [n_nodes][4].  Both device pointers; copied.  Pass NULL, NULL to restore. */

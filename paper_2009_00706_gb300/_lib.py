@@ -114,6 +114,7 @@ SIGNATURES = {
     "imga_classify": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "imga_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp]),
     "imga_jvp": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),
+    "imga_jvp_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),
     "imga_set_dirichlet": (C.c_int, [_vp, _vp, _vp, _vp]),
     "imga_profile": (C.c_int, [_vp, _int]),
     "imga_profile_read": (C.c_int, [_vp, _vp, _vp]),

@@ -243,6 +243,21 @@ imga_status imga_profile_read(imga_mesh h, double* ms, int64_t* launches) {
     return IMGA_OK;
 }
 
+imga_status imga_jvp_noalloc(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                             const imga_physics* ph, int precision, const double* v, double* Jv, void* stream) {
+    if (!h || !u || !up || !v || !Jv) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
+    if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
+    if (precision != 0 && precision != 1) return fail(IMGA_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    for (const void* p : {(const void*)u, (const void*)up, (const void*)up2, (const void*)f, (const void*)v, (const void*)Jv})
+        if (p && ((uintptr_t)p & 15)) return fail(IMGA_ERR_INVALID_ARG, "node vectors must be 16-byte aligned");
+    std::string err;
+    if (imga::vms_jvp_noalloc(h->m, u, up, up2, f, *ph, precision, v, Jv, stream, err))
+        return fail(IMGA_ERR_INVALID_ARG, "imga_jvp_noalloc: " + err);
+    return cuda_status("jvp_noalloc launch");
+}
+
 imga_status imga_set_dirichlet(imga_mesh h, const uint8_t* mask, const double* val, void* stream) {
     if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
     if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");

@@ -154,6 +154,12 @@ void device_free(Mesh& m);
 int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
               const imga_physics& ph, int precision, const double* v, double* out, void* stream);
 
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // fixed scratch of imga_jvp_noalloc
+constexpr int kMaxDevices = 64;
+int vms_jvp_noalloc(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                    const imga_physics& ph, int precision, const double* v, double* out, void* stream,
+                    std::string& err);
+
 void profile_reset(Mesh& m);
 int profile_collect(Mesh& m);
 

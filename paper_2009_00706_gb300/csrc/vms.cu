@@ -27,6 +27,8 @@
 
 #include <cstdio>
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "imga_internal.h"
@@ -678,9 +680,9 @@ struct Timed {
 };
 
 template <class T, bool JV>
-void launch_all(const Mesh& m, Args A, cudaStream_t s) {
+void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr) {
     const int64_t next = m.n_nodes() + m.n_hang();
-    T* ndv = sizeof(T) == 4 ? (T*)(void*)m.d.nd_f : (T*)(void*)m.d.nd_d;
+    T* ndv = ws ? (T*)ws : sizeof(T) == 4 ? (T*)(void*)m.d.nd_f : (T*)(void*)m.d.nd_d;
     T* ndt = ndv + 8 * next;
     T* ndf = A.F ? ndt + 8 * next : nullptr;
     A.ndv = ndv;
@@ -720,8 +722,8 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s) {
 
 }  // namespace
 
-int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
-              const imga_physics& ph, int precision, const double* v, double* out, void* stream) {
+static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                        const imga_physics& ph, int precision, const double* v, double* out, void* stream, void* ws) {
     cudaStream_t s = (cudaStream_t)stream;
     Args A;
     A.conn = m.d.conn;
@@ -770,9 +772,9 @@ int vms_apply(const Mesh& m, const double* u, const double* up, const double* up
     const bool jv = v != nullptr;
     if (cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
     if (precision == 0) {
-        if (jv) launch_all<double, true>(m, A, s); else launch_all<double, false>(m, A, s);
+        if (jv) launch_all<double, true>(m, A, s, ws); else launch_all<double, false>(m, A, s, ws);
     } else {
-        if (jv) launch_all<float, true>(m, A, s); else launch_all<float, false>(m, A, s);
+        if (jv) launch_all<float, true>(m, A, s, ws); else launch_all<float, false>(m, A, s, ws);
     }
     const int64_t nn = m.n_nodes();
     Timed t(m, 3, s);
@@ -781,6 +783,50 @@ int vms_apply(const Mesh& m, const double* u, const double* up, const double* up
                                                                 m.user_bc ? m.d.bcval_user : nullptr, ph.u_inf[0],
                                                                 ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+              const imga_physics& ph, int precision, const double* v, double* out, void* stream) {
+    return vms_apply_ws(m, u, up, up2, f, ph, precision, v, out, stream, nullptr);
+}
+
+// ------------------------------------------------------------------------------------------
+// J v with no allocation at all: the per-call node workspace lives in this fixed array, which
+// every GPU that loads the library holds until the process exits.  Host code must not pass the
+// array's name to a kernel (on the host it names a shadow, not device memory): its device
+// address is looked up once per device with cudaGetSymbolAddress.
+// ------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kMaxDevices] = {};
+
+int vms_jvp_noalloc(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                    const imga_physics& ph, int precision, const double* v, double* out, void* stream,
+                    std::string& err) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) { err = "no usable current device"; return 1; }
+    if (dev != m.device) { err = "the mesh's device must be current"; return 1; }
+    const size_t next = (size_t)(m.n_nodes() + m.n_hang());
+    const size_t per_node = (size_t)(f ? 20 : 16) * (precision == 0 ? sizeof(double) : sizeof(float));
+    if (next * per_node > kNoAllocScratchBytes) {
+        err = "mesh too large for the fixed scratch: needs " + std::to_string(next * per_node) + " bytes, limit " +
+              std::to_string(kNoAllocScratchBytes);
+        return 1;
+    }
+    void* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (rc != cudaSuccess || !p) { err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(rc); return 1; }
+            g_noalloc_addr[dev] = p;
+        }
+        ws = g_noalloc_addr[dev];
+    }
+    if (vms_apply_ws(m, u, up, up2, f, ph, precision, v, out, stream, ws)) { err = "launch failed"; return 1; }
+    return 0;
 }
 
 void profile_reset(Mesh& m) {
