@@ -41,6 +41,20 @@ FLOPS_JV_OUT_ELEMENT = 8 * (896 + 390 + 16) + 2048
 FLOPS_R_OUT_ELEMENT = 8 * (448 + 130 + 16) + 2048
 
 
+def interior_traffic():
+    """DRAM bytes per launch of vms_interior from the committed ncu record, or None when the kernel
+    source changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "vms_interior_traffic.json")))
+        h = hashlib.sha256()
+        for f in ("paper_2009_00706_gb300/csrc/vms.cu", "paper_2009_00706_gb300/csrc/vms_device.cuh"):
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["traffic_bytes_per_launch"] if h.hexdigest() == rec["source_sha256"] else None
+    except Exception:
+        return None
+
+
 def peaks():
     p = {"source": "fallback", "sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}
     try:
@@ -246,7 +260,8 @@ def run_ours(args):
     roof = {"kernel": "vms_interior (Out elements, J v)", "bound": "alu", "achieved": achieved,
             "peak": pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None, "unit": "TFLOP/s",
             "frac": achieved / pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None,
-            "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+            "traffic": interior_traffic() if prec == api.PRECISION_MIXED else None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (of derived)",
             "flops_per_element": FLOPS_JV_OUT_ELEMENT, "avg_launch_ms": k_avg}
     kern_share = {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()}
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -286,6 +301,29 @@ def run_ours(args):
             torch.cuda.synchronize()
             tot += a.elapsed_time(b)
         extra[name] = n_active * reps / (tot / 1e3)
+    # Newton-GMRES step to 1e-8 (float64 residual), block-Jacobi, J v in FP64 vs mixed precision, on the
+    # small-sphere problem (7,288 elements: the size the learned preconditioner is evaluated at).  On the
+    # 2M-element sphere LES nodal block-Jacobi does not bring GMRES(50) to 1e-8 (see the design notes).
+    newton = {}
+    if not args.no_newton:
+        ws = I.small_sphere(0)
+        ms = api.Mesh.from_workload(ws, device=local)
+        su, sup, _ = I.state(ms.n_nodes, 16 + rank)
+        sud, supd = torch.from_numpy(su).to(dev), torch.from_numpy(sup).to(dev)
+        for name, p in (("mixed", api.PRECISION_MIXED), ("fp64", api.PRECISION_FP64)):
+            runs = []
+            for rep in range(2):   # the first run also allocates the Krylov workspace
+                uw = sud.clone()
+                torch.cuda.synchronize()
+                st = ms.newton_step(ws.physics, uw, supd, precision=p, precond=1, rtol=1e-8, gmres_m=50,
+                                    krylov_rtol=args.krylov_rtol, max_newton=20, max_krylov=500, stream=stream,
+                                    raise_on_failure=False)
+                runs.append(st)
+            st = runs[-1]
+            newton[name] = {"ms": st["time_ms"], "newton_its": st["newton_its"], "krylov_its": st["krylov_its"],
+                            "converged": bool(st["converged"]), "rel_residual": st["res_norm"][-1] / st["res_norm"][0],
+                            "workload": "small_sphere (7,288 elements, Re 10, BE dt 0.01), block-Jacobi, GMRES(50)"}
+        ms.close()
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -311,7 +349,7 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roof, "kernel_time_share": kern_share, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": 4 * args.steps, "cpu_baseline": cpu, "extra_elements_per_s": extra,
-                "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
+                "newton_step": newton, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -329,6 +367,8 @@ def main():
     ap.add_argument("--sample-nodes", type=int, default=60000)
     ap.add_argument("--ref-sample-nodes", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-newton", action="store_true", help="skip the Newton-GMRES step timing")
+    ap.add_argument("--krylov-rtol", type=float, default=1e-3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -170,6 +170,43 @@ imga_status imga_jvp_noalloc(imga_mesh mesh, const double* u, const double* u_pr
  * val_dev float64 [n_nodes][4].  Both device pointers; copied.  Pass NULL, NULL to restore. */
 imga_status imga_set_dirichlet(imga_mesh mesh, const uint8_t* mask_dev, const double* val_dev, void* stream);
 
+/* Element Jacobians k_e = d r_e / d u_e for a list of elements (Algorithm 4's element matrix, before
+ * the hanging correction M_e^T k_e M_e of Algorithm 2): elems_dev int32 [n] device, distinct
+ * element indices; K_dev float64 [n][32][32] device, row a*4+i (corner a, component i), column
+ * b*4+k, with respect to the element's own corner values (volume + Nitsche terms; In elements give
+ * zeros).  precision as in imga_residual. */
+imga_status imga_element_jacobians(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
+                                   const double* f, const imga_physics* phys, int precision, const int32_t* elems_dev,
+                                   int64_t n, double* K_dev, void* stream);
+
+typedef struct {
+    int gmres_m;            /* restart length of GMRES (1 .. 63), e.g. 50                          */
+    int max_newton;         /* Newton iterations at most (<= 32)                                   */
+    int max_krylov;         /* GMRES iterations per Newton iteration at most                      */
+    double rtol, atol;      /* stop when ||R(u)|| <= max(rtol ||R(u_0)||, atol)                     */
+    double krylov_rtol;     /* inner tolerance: ||J du + R|| <= krylov_rtol ||R||                 */
+    int precision;          /* J v and preconditioner precision: 0 FP64, 1 mixed (FP32 elements)  */
+    int precond;            /* 0 none, 1 block-Jacobi (nodal 4x4 diagonal blocks of J)             */
+    int line_search;        /* 1: backtracking (Armijo, c = 1e-4, halving, <= 12 trials)          */
+} imga_solver_opts;
+
+typedef struct {
+    int newton_its, krylov_its;
+    int krylov_per_newton[32];
+    double res_norm[33];    /* float64 ||R|| before the first and after every Newton iteration   */
+    double time_ms;
+    int converged;
+} imga_solver_stats;
+
+/* Newton iterations on R(u) = 0 from u_inout (device [n_nodes][4], updated in place), each linear
+ * step solved by right-preconditioned GMRES(m) with classical Gram-Schmidt applied twice, every
+ * vector and reduction in float64; convergence is judged on the float64 residual.  Synchronous.
+ * The mesh keeps the Krylov workspace ((m + 1) + 8 vectors + 2 x 16 n_nodes doubles) for later
+ * calls.  Returns IMGA_ERR_NOT_CONVERGED (stats filled) when the tolerance is not reached. */
+imga_status imga_newton_step(imga_mesh mesh, double* u_inout, const double* u_prev, const double* u_prev2,
+                             const double* f, const imga_physics* phys, const imga_solver_opts* opts,
+                             imga_solver_stats* stats, void* stream);
+
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.
  * imga_profile_read synchronises the device and returns, per kernel class (0 Out elements,

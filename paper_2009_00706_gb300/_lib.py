@@ -24,8 +24,10 @@ SOURCES = [
     ("capi.cpp", []),
     ("geom.cu", ["-fmad=false"]),
     ("vms.cu", []),
+    ("jac.cu", []),
+    ("solver.cu", []),
 ]
-HEADERS = ["imga_internal.h", os.path.join("..", "..", "include", "imga.h")]
+HEADERS = ["imga_internal.h", "vms_device.cuh", os.path.join("..", "..", "include", "imga.h")]
 
 
 def _nvcc():
@@ -100,6 +102,17 @@ class MeshInfo(C.Structure):
                 ("hi_int", C.c_int64 * 3), ("scale", C.c_double), ("setup_ms", C.c_double * 4)]
 
 
+class SolverOpts(C.Structure):
+    _fields_ = [("gmres_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int), ("rtol", C.c_double),
+                ("atol", C.c_double), ("krylov_rtol", C.c_double), ("precision", C.c_int), ("precond", C.c_int),
+                ("line_search", C.c_int)]
+
+
+class SolverStats(C.Structure):
+    _fields_ = [("newton_its", C.c_int), ("krylov_its", C.c_int), ("krylov_per_newton", C.c_int * 32),
+                ("res_norm", C.c_double * 33), ("time_ms", C.c_double), ("converged", C.c_int)]
+
+
 # every entry point declared in include/imga.h, with its ctypes signature
 _vp, _i64, _int, _dp = C.c_void_p, C.c_int64, C.c_int, C.c_void_p
 SIGNATURES = {
@@ -116,6 +129,9 @@ SIGNATURES = {
     "imga_jvp": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),
     "imga_jvp_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),
     "imga_set_dirichlet": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "imga_element_jacobians": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _i64, _vp, _vp]),
+    "imga_newton_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), C.POINTER(SolverOpts),
+                                   C.POINTER(SolverStats), _vp]),
     "imga_profile": (C.c_int, [_vp, _int]),
     "imga_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "imga_last_error": (C.c_char_p, []),

@@ -11,7 +11,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MeshInfo, MeshParams, Physics, Region, check
+from ._lib import MeshInfo, MeshParams, Physics, Region, SolverOpts, SolverStats, check
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
@@ -167,6 +167,38 @@ class Mesh:
         check(_lib.load().imga_jvp(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
                                    _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps), precision,
                                    _ptr(_vec(v, nn, "v")), _ptr(out), _stream(stream)))
+        return out
+
+    def element_jacobians(self, phys, u, u_prev, elems, u_prev2=None, f=None, precision=PRECISION_FP64, out=None,
+                          stream=None):
+        """k_e [n, 32, 32] (float64, device) of the elements in `elems` (int32 device tensor)."""
+        import torch
+        nn = self.n_nodes
+        n = elems.numel()
+        if out is None:
+            out = torch.empty((n, 32, 32), dtype=torch.float64, device=u.device)
+        ps = physics_struct(phys)
+        check(_lib.load().imga_element_jacobians(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                                 _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")),
+                                                 C.byref(ps), precision, _ptr(elems), n, _ptr(out), _stream(stream)))
+        return out
+
+    def newton_step(self, phys, u, u_prev, u_prev2=None, f=None, gmres_m=50, max_newton=20, max_krylov=1000,
+                    rtol=1e-8, atol=0.0, krylov_rtol=1e-3, precision=PRECISION_FP64, precond=1, line_search=1,
+                    stream=None, raise_on_failure=True):
+        """Newton-GMRES in place on u; returns a stats dict."""
+        nn = self.n_nodes
+        o = SolverOpts(gmres_m, max_newton, max_krylov, rtol, atol, krylov_rtol, precision, precond, line_search)
+        st = SolverStats()
+        ps = physics_struct(phys)
+        status = _lib.load().imga_newton_step(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                              _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")),
+                                              C.byref(ps), C.byref(o), C.byref(st), _stream(stream))
+        out = {"status": status, "newton_its": st.newton_its, "krylov_its": st.krylov_its,
+               "krylov_per_newton": list(st.krylov_per_newton)[: st.newton_its],
+               "res_norm": list(st.res_norm)[: st.newton_its + 1], "time_ms": st.time_ms, "converged": st.converged}
+        if raise_on_failure and status != 0:
+            check(status)
         return out
 
     def profile(self, enable=True):

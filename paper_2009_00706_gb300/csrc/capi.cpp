@@ -122,6 +122,7 @@ void imga_destroy_mesh(imga_mesh h) {
     if (!h) return;
     if (h->m.host_only) { delete h; return; }
     imga::profile_reset(h->m);
+    imga::solver_free(h->m);
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(h->m.device);
@@ -224,6 +225,37 @@ imga_status imga_jvp(imga_mesh h, const double* u, const double* up, const doubl
                      const imga_physics* ph, int precision, const double* v, double* Jv, void* stream) {
     if (!v) return fail(IMGA_ERR_INVALID_ARG, "null direction");
     return apply(h, u, up, up2, f, ph, precision, v, Jv, stream);
+}
+
+imga_status imga_element_jacobians(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                                   const imga_physics* ph, int precision, const int32_t* elems, int64_t n, double* K,
+                                   void* stream) {
+    if (!h || !u || !up || n < 0 || (n > 0 && (!elems || !K))) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
+    if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
+    if (precision != 0 && precision != 1) return fail(IMGA_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    if (imga::element_jacobians(h->m, u, up, up2, f, *ph, precision, elems, n, K, stream)) return cuda_status("element_jacobians");
+    return IMGA_OK;
+}
+
+imga_status imga_newton_step(imga_mesh h, double* u, const double* up, const double* up2, const double* f,
+                             const imga_physics* ph, const imga_solver_opts* o, imga_solver_stats* stats, void* stream) {
+    if (!h || !u || !up || !o || !stats) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
+    if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
+    if (o->gmres_m < 1 || o->gmres_m > 63 || o->max_newton < 0 || o->max_krylov < 1 || !(o->rtol >= 0.0) ||
+        !(o->krylov_rtol > 0.0) || (o->precision != 0 && o->precision != 1) || o->precond < 0 || o->precond > 1)
+        return fail(IMGA_ERR_INVALID_ARG, "bad solver options");
+    std::string err;
+    int rc = imga::newton_solve(h->m, u, up, up2, f, *ph, *o, stats, stream, err);
+    if (rc == 3) return fail(IMGA_ERR_OOM, err);
+    if (rc == 2) return fail(IMGA_ERR_NUMERIC, err);
+    if (rc) return fail(IMGA_ERR_CUDA, err);
+    if (cudaGetLastError() != cudaSuccess) return cuda_status("newton_step");
+    if (!stats->converged) return fail(IMGA_ERR_NOT_CONVERGED, "Newton did not reach the tolerance");
+    return IMGA_OK;
 }
 
 imga_status imga_profile(imga_mesh h, int enable) {

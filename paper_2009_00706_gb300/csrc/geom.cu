@@ -403,6 +403,7 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
         !upload(&m.d.sq_w, w, err) || !upload(&m.d.sq_taub, tb, err) || !upload(&m.d.bcflag, m.bcflag, err))
         return false;
     const size_t next = (size_t)(m.n_nodes() + m.n_hang());
+    if (!check(cudaMalloc((void**)&m.d.slot, std::max<int64_t>(1, m.n_elem()) * sizeof(int32_t)), err, "cudaMalloc")) return false;
     if (!check(cudaMalloc((void**)&m.d.nd_f, std::max<size_t>(1, 24 * next) * sizeof(float)), err, "cudaMalloc") ||
         !check(cudaMalloc((void**)&m.d.nd_d, std::max<size_t>(1, 24 * next) * sizeof(double)), err, "cudaMalloc"))
         return false;
@@ -420,7 +421,7 @@ void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
                     d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
-                    d.sq_n, d.sq_w, d.sq_taub, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d};
+                    d.sq_n, d.sq_w, d.sq_taub, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh();

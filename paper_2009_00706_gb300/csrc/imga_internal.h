@@ -80,6 +80,7 @@ struct DeviceMesh {
     // hanging node, one float and one double copy
     float* nd_f = nullptr;        // [3][n_nodes + n_hang][8]
     double* nd_d = nullptr;
+    int32_t* slot = nullptr;      // [n_elem] position of an element in a requested list, or -1
     // boundary rows
     uint8_t* bcflag = nullptr;    // [n_nodes] bits 0-3 box Dirichlet, bit 4 In-only node
     uint8_t* bcmask_user = nullptr;
@@ -120,6 +121,7 @@ struct Mesh {
     int n_sm = 1;                        // streaming multiprocessors of the device
     DeviceMesh d;
     void* scratch = nullptr;             // device workspace for the kernels
+    void* solver_work = nullptr;         // Krylov workspace (solver.cu)
     // per-kernel profiling (CUDA events, one pair per launch, resolved at read time)
     bool profiling = false;
     std::vector<std::pair<void*, void*>> prof_ev[5];
@@ -162,6 +164,18 @@ int vms_jvp_noalloc(const Mesh& m, const double* u, const double* up, const doub
 
 void profile_reset(Mesh& m);
 int profile_collect(Mesh& m);
+
+// element Jacobians and block-Jacobi (jac.cu)
+int element_jacobians(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                      const imga_physics& ph, int precision, const int32_t* elems, int64_t n, double* K, void* stream);
+int block_jacobi_setup(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                       const imga_physics& ph, int precision, double* D, double* Dinv, void* stream);
+int block_jacobi_apply(const Mesh& m, const double* Dinv, const double* x, double* y, void* stream);
+
+// Newton-GMRES (solver.cu)
+int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const double* f, const imga_physics& ph,
+                 const imga_solver_opts& o, imga_solver_stats* stats, void* stream, std::string& err);
+void solver_free(Mesh& m);
 
 void set_error(const std::string& s);
 

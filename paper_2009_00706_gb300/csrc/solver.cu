@@ -1,0 +1,340 @@
+// Newton iterations with right-preconditioned GMRES(m) on the device (appendix "Details of solver
+// selection": a Newton line-search method with a Krylov solver; here GMRES replaces BiCGStab and
+// the preconditioner is block-Jacobi over the nodal 4x4 blocks instead of additive Schwarz).
+//
+// All vectors and reductions are float64.  The Arnoldi basis is orthogonalised by classical
+// Gram-Schmidt applied twice (CGS2): one multi-dot kernel h = V^T w over all previous basis vectors
+// and one multi-axpy w -= V h per pass, so each pass reads the basis once.  The Hessenberg matrix
+// and its Givens rotations (m x m, tiny) live on the host.  J v is imga_jvp's kernels in the
+// requested precision; the true residual that decides convergence is always the float64 residual.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "imga_internal.h"
+
+namespace imga {
+
+namespace {
+
+constexpr int kRedBlocks = 1024;   // blocks of the reduction kernels
+constexpr int kDotGroup = 8;       // basis vectors per multi-dot pass
+
+// partial[b][k] = sum over block b's slice of V[k0+k] . w   (k < nv)
+template <int NV>
+__global__ void __launch_bounds__(256) mdot_kernel(int64_t n, const double* __restrict__ V, int64_t ld, int k0, int nv,
+                                                   const double* __restrict__ w, double* __restrict__ partial) {
+    double acc[NV];
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) acc[k] += V[(int64_t)(k0 + k) * ld + i] * wi;
+    }
+    __shared__ double red[NV][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV && (int)threadIdx.x < nv) {
+        double v = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) v += red[threadIdx.x][j];
+        partial[(int64_t)blockIdx.x * 64 + k0 + threadIdx.x] = v;
+    }
+}
+
+// h[k] = sum_b partial[b][k], k < nk
+__global__ void mdot_final(int nblocks, int nk, const double* __restrict__ partial, double* __restrict__ h) {
+    const int k = blockIdx.x;
+    if (k >= nk) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(int64_t)b * 64 + k];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[j];
+        h[k] = s;
+    }
+}
+
+// w = alpha w + beta * sum_{k<nk} h[k] V[k]
+__global__ void __launch_bounds__(256) maxpy_kernel(int64_t n, const double* __restrict__ V, int64_t ld, int nk,
+                                                    const double* __restrict__ h, double beta, double alpha,
+                                                    double* __restrict__ w) {
+    __shared__ double hs[64];
+    if (threadIdx.x < nk) hs[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nk; ++k) s += hs[k] * V[(int64_t)k * ld + i];
+        w[i] = alpha * w[i] + beta * s;
+    }
+}
+
+__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void scale_copy_kernel(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i];
+}
+
+struct Work {
+    int m = 0;
+    int64_t n = 0;
+    double* V = nullptr;       // [(m+1)][n]
+    double* vec = nullptr;     // 8 vectors of n
+    double* D = nullptr;       // [n_nodes][16]
+    double* Dinv = nullptr;
+    double* partial = nullptr; // [kRedBlocks][64]
+    double* h = nullptr;       // [64]
+    double* hh = nullptr;      // pinned host [64]
+};
+
+class Solver {
+public:
+    Solver(Mesh& m, const imga_physics& ph, const imga_solver_opts& o, cudaStream_t s, const double* up,
+           const double* up2, const double* f)
+        : M(m), P(ph), O(o), st(s), Up(up), Up2(up2), F(f) {
+        n = 4 * m.n_nodes();
+    }
+
+    int alloc(std::string& err) {
+        Work& w = W;
+        const int mm = std::max(1, std::min(O.gmres_m, 63));
+        if (M.solver_work && ((Work*)M.solver_work)->m >= mm && ((Work*)M.solver_work)->n == n) {
+            W = *(Work*)M.solver_work;
+            return 0;
+        }
+        free_work(M);
+        w.m = mm;
+        w.n = n;
+        size_t bytes = (size_t)(mm + 1) * n * sizeof(double);
+        if (cudaMalloc((void**)&w.V, bytes) != cudaSuccess || cudaMalloc((void**)&w.vec, 8 * n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&w.D, 4 * n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&w.Dinv, 4 * n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&w.partial, kRedBlocks * 64 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&w.h, 64 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost((void**)&w.hh, 64 * sizeof(double)) != cudaSuccess) {
+            err = "solver workspace allocation failed";
+            cudaGetLastError();
+            return 1;
+        }
+        M.solver_work = new Work(w);
+        return 0;
+    }
+
+    static void free_work(Mesh& m) {
+        if (!m.solver_work) return;
+        Work* w = (Work*)m.solver_work;
+        cudaFree(w->V); cudaFree(w->vec); cudaFree(w->D); cudaFree(w->Dinv); cudaFree(w->partial); cudaFree(w->h);
+        cudaFreeHost(w->hh);
+        delete w;
+        m.solver_work = nullptr;
+    }
+
+    double* vec(int k) { return W.vec + (int64_t)k * n; }
+    double* basis(int k) { return W.V + (int64_t)k * n; }
+
+    // h[0..nk) = V[0..nk)^T w, copied to the host
+    void mdot(const double* V, int nk, const double* w, double* host) {
+        const int grid = (int)std::min<int64_t>(kRedBlocks, (n + 255) / 256);
+        for (int k0 = 0; k0 < nk; k0 += kDotGroup)
+            mdot_kernel<kDotGroup><<<grid, 256, 0, st>>>(n, V, n, k0, std::min(kDotGroup, nk - k0), w, W.partial);
+        mdot_final<<<nk, 256, 0, st>>>(grid, nk, W.partial, W.h);
+        cudaMemcpyAsync(W.hh, W.h, nk * sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        std::memcpy(host, W.hh, nk * sizeof(double));
+    }
+    double norm(const double* x) {
+        double v;
+        mdot(x, 1, x, &v);
+        return std::sqrt(std::max(v, 0.0));
+    }
+    void maxpy(const double* V, int nk, const double* hhost, double beta, double alpha, double* w) {
+        std::memcpy(W.hh, hhost, nk * sizeof(double));
+        cudaMemcpyAsync(W.h, W.hh, nk * sizeof(double), cudaMemcpyHostToDevice, st);
+        const int grid = (int)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256);
+        maxpy_kernel<<<grid, 256, 0, st>>>(n, V, n, nk, W.h, beta, alpha, w);
+    }
+    void axpby(double a, const double* x, double b, double* y) {
+        axpby_kernel<<<(unsigned)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256), 256, 0, st>>>(n, a, x, b, y);
+    }
+    void scale_copy(double a, const double* x, double* y) {
+        scale_copy_kernel<<<(unsigned)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256), 256, 0, st>>>(n, a, x, y);
+    }
+
+    int residual(const double* u, double* R) {
+        return vms_apply(M, u, Up, Up2, F, P, 0, nullptr, R, st);
+    }
+    int jv(const double* u, const double* v, double* out) {
+        return vms_apply(M, u, Up, Up2, F, P, O.precision, v, out, st);
+    }
+    void precond(const double* x, double* y) {
+        if (O.precond >= 1) block_jacobi_apply(M, W.Dinv, x, y, st);
+        else cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    }
+
+    // solve J(u) x = b to ||b - J x|| <= rtol ||b|| (or max_its); x starts at 0
+    int gmres(const double* u, const double* b, double* x, double rtol, int max_its, int* its_out, double* res_out) {
+        const int m = W.m;
+        double* r = vec(4);
+        double* z = vec(5);
+        double* w = vec(6);
+        cudaMemsetAsync(x, 0, n * sizeof(double), st);
+        const double bnorm = norm(b);
+        const double target = rtol * bnorm;
+        int its = 0;
+        double res = bnorm;
+        std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
+        cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        while (true) {
+            const double beta = its == 0 ? bnorm : norm(r);
+            res = beta;
+            if (beta <= target || its >= max_its || beta == 0.0) break;
+            scale_copy(1.0 / beta, r, basis(0));
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = beta;
+            int k = 0;
+            for (; k < m && its < max_its; ++k) {
+                precond(basis(k), z);
+                if (jv(u, z, w)) return 1;
+                // CGS2
+                mdot(W.V, k + 1, w, h.data());
+                maxpy(W.V, k + 1, h.data(), -1.0, 1.0, w);
+                mdot(W.V, k + 1, w, h2.data());
+                maxpy(W.V, k + 1, h2.data(), -1.0, 1.0, w);
+                for (int i = 0; i <= k; ++i) H[i * m + k] = h[i] + h2[i];
+                const double hn = norm(w);
+                H[(k + 1) * m + k] = hn;
+                if (hn > 0.0) scale_copy(1.0 / hn, w, basis(k + 1));
+                for (int i = 0; i < k; ++i) {
+                    const double t = cs[i] * H[i * m + k] + sn[i] * H[(i + 1) * m + k];
+                    H[(i + 1) * m + k] = -sn[i] * H[i * m + k] + cs[i] * H[(i + 1) * m + k];
+                    H[i * m + k] = t;
+                }
+                const double den = std::hypot(H[k * m + k], H[(k + 1) * m + k]);
+                cs[k] = den > 0.0 ? H[k * m + k] / den : 1.0;
+                sn[k] = den > 0.0 ? H[(k + 1) * m + k] / den : 0.0;
+                H[k * m + k] = cs[k] * H[k * m + k] + sn[k] * H[(k + 1) * m + k];
+                H[(k + 1) * m + k] = 0.0;
+                g[k + 1] = -sn[k] * g[k];
+                g[k] = cs[k] * g[k];
+                ++its;
+                res = std::fabs(g[k + 1]);
+                if (res <= target || hn == 0.0) { ++k; break; }
+            }
+            for (int i = k - 1; i >= 0; --i) {
+                double s = g[i];
+                for (int j = i + 1; j < k; ++j) s -= H[i * m + j] * y[j];
+                y[i] = s / H[i * m + i];
+            }
+            // x += M^{-1} (V y)
+            cudaMemsetAsync(w, 0, n * sizeof(double), st);
+            maxpy(W.V, k, y.data(), 1.0, 0.0, w);
+            precond(w, z);
+            axpby(1.0, z, 1.0, x);
+            if (res <= target || its >= max_its) {
+                // true residual of the returned solution
+                if (jv(u, x, w)) return 1;
+                cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+                axpby(-1.0, w, 1.0, r);
+                res = norm(r);
+                if (res <= target * 1.0000001 || its >= max_its) break;
+                continue;
+            }
+            if (jv(u, x, w)) return 1;
+            cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            axpby(-1.0, w, 1.0, r);
+        }
+        *its_out = its;
+        *res_out = res;
+        return 0;
+    }
+
+    int newton(double* u, imga_solver_stats* S, std::string& err) {
+        auto t0 = std::chrono::steady_clock::now();
+        double* R = vec(0);
+        double* b = vec(1);
+        double* du = vec(2);
+        double* ut = vec(3);
+        double* Rt = vec(7);
+        if (residual(u, R)) { err = "residual launch failed"; return 1; }
+        double r0 = norm(R), rn = r0;
+        if (!std::isfinite(r0)) { err = "NaN/Inf in the initial residual"; return 2; }
+        S->res_norm[0] = r0;
+        const double target = std::max(O.rtol * r0, O.atol);
+        int it = 0;
+        for (; it < O.max_newton && it < 32; ++it) {
+            if (rn <= target) break;
+            if (O.precond >= 1 &&
+                block_jacobi_setup(M, u, Up, Up2, F, P, O.precision, W.D, W.Dinv, st)) {
+                err = "block-Jacobi setup failed";
+                return 1;
+            }
+            scale_copy(-1.0, R, b);
+            int kits = 0;
+            double kres = 0.0;
+            if (gmres(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
+            S->krylov_per_newton[it] = kits;
+            S->krylov_its += kits;
+            double lam = 1.0, rt = 0.0;
+            for (int ls = 0; ls < 12; ++ls) {
+                cudaMemcpyAsync(ut, u, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+                axpby(lam, du, 1.0, ut);
+                if (residual(ut, Rt)) { err = "residual launch failed"; return 1; }
+                rt = norm(Rt);
+                if (!O.line_search || (std::isfinite(rt) && rt <= (1.0 - 1e-4 * lam) * rn)) break;
+                lam *= 0.5;
+            }
+            if (!std::isfinite(rt)) { err = "NaN/Inf in the residual"; return 2; }
+            cudaMemcpyAsync(u, ut, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(R, Rt, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            rn = rt;
+            S->res_norm[it + 1] = rn;
+        }
+        cudaStreamSynchronize(st);
+        S->newton_its = it;
+        S->converged = rn <= target ? 1 : 0;
+        S->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return 0;
+    }
+
+    Mesh& M;
+    imga_physics P;
+    imga_solver_opts O;
+    cudaStream_t st;
+    const double *Up, *Up2, *F;
+    int64_t n;
+    Work W;
+};
+
+}  // namespace
+
+int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const double* f, const imga_physics& ph,
+                 const imga_solver_opts& o, imga_solver_stats* stats, void* stream, std::string& err) {
+    std::memset(stats, 0, sizeof(*stats));
+    Solver S(m, ph, o, (cudaStream_t)stream, up, up2, f);
+    if (S.alloc(err)) return 3;
+    return S.newton(u, stats, err);
+}
+
+void solver_free(Mesh& m) { Solver::free_work(m); }
+
+}  // namespace imga
