@@ -186,8 +186,15 @@ typedef struct {
     double rtol, atol;      /* stop when ||R(u)|| <= max(rtol ||R(u_0)||, atol)                     */
     double krylov_rtol;     /* inner tolerance: ||J du + R|| <= krylov_rtol ||R||                 */
     int precision;          /* J v and preconditioner precision: 0 FP64, 1 mixed (FP32 elements)  */
-    int precond;            /* 0 none, 1 block-Jacobi (nodal 4x4 diagonal blocks of J)             */
+    int precond;            /* 0 none, 1 block-Jacobi (nodal 4x4 diagonal blocks of J), 2 block-Jacobi
+                               plus the learned element-block correction of `learned`, 3 block-
+                               Jacobi plus the exact element-block correction the network is
+                               trained to reproduce.  With 2 or 3, a linear solve that does not
+                               reach krylov_rtol is redone with block-Jacobi alone (counted in
+                               imga_solver_stats.fallbacks)                                     */
     int line_search;        /* 1: backtracking (Armijo, c = 1e-4, halving, <= 12 trials)          */
+    const void* learned;    /* imga_mlp for precond 2 (n_in 1027, n_out 1024), else NULL         */
+    double learned_omega;   /* weight of the learned correction, e.g. 0.5                          */
 } imga_solver_opts;
 
 typedef struct {
@@ -196,6 +203,7 @@ typedef struct {
     double res_norm[33];    /* float64 ||R|| before the first and after every Newton iteration   */
     double time_ms;
     int converged;
+    int fallbacks;          /* linear solves redone with block-Jacobi (precond 2, 3)              */
 } imga_solver_stats;
 
 /* Newton iterations on R(u) = 0 from u_inout (device [n_nodes][4], updated in place), each linear
@@ -206,6 +214,42 @@ typedef struct {
 imga_status imga_newton_step(imga_mesh mesh, double* u_inout, const double* u_prev, const double* u_prev2,
                              const double* f, const imga_physics* phys, const imga_solver_opts* opts,
                              imga_solver_stats* stats, void* stream);
+
+/* ---- learned block preconditioner -------------------------------------------------------------
+ * A 3-layer MLP (ReLU, widths n_in -> width -> width -> n_out) with BF16 weights and activations on
+ * the tensor cores, FP32 accumulation and FP32 master weights, trained by Adam on the mean squared
+ * error sum (y - t)^2 / (2 n).  As a preconditioner (imga_solver_opts.precond = 2) it maps each active
+ * element's Jacobian block, scaled by its mean |diagonal| s_e, plus (log h, Intercepted flag,
+ * log10(1 + local Re)) to a 32 x 32 correction C_e, and GMRES uses
+ *     P^-1 v = D^-1 v + omega sum_e M_e^T (C_e / s_e) M_e v      (free rows only),
+ * D the nodal block-Jacobi diagonal.  The paper has no learned component: its conclusion asks for
+ * preconditioners tailored to the method for matrix-free solvers.  Device pointers unless named host. */
+typedef struct imga_mlp_s* imga_mlp;
+imga_status imga_mlp_create(int n_in, int width, int n_out, uint64_t seed, int device, imga_mlp* out);
+void imga_mlp_destroy(imga_mlp mlp);
+/* number of parameters and the padded input width the layout uses (W1 is width x n_in_pad) */
+imga_status imga_mlp_shape(imga_mlp mlp, int64_t* n_params, int* n_in_pad);
+/* FP32 master weights in the order W1 [width][n_in_pad], b1, W2 [width][width], b2, W3 [n_out][width],
+ * b3 (host array of n_params floats); set = 1 writes them (and resets Adam), set = 0 reads. */
+imga_status imga_mlp_params(imga_mlp mlp, float* host, int set);
+/* Y [n][n_out] = MLP(X [n][ldx], first n_in columns), float32 device arrays */
+imga_status imga_mlp_forward(imga_mlp mlp, const float* X, int64_t ldx, int64_t n, float* Y, void* stream);
+/* loss and gradient (host, n_params floats, same order as the weights) over all n samples */
+imga_status imga_mlp_gradient(imga_mlp mlp, const float* X, int64_t ldx, const float* T, int64_t n, double* loss,
+                              float* grad_host, void* stream);
+/* `epochs` passes of Adam (lr, beta 0.9 / 0.999) over mini-batches of `batch` rows in order;
+ * loss_hist (host, may be NULL) receives the mean training loss of each epoch. */
+imga_status imga_mlp_train(imga_mlp mlp, const float* X, int64_t ldx, const float* T, int64_t n, int epochs, int batch,
+                           float lr, double* loss_hist, void* stream);
+/* Network inputs X [n][ldx] (ldx >= 1027) and, when T != NULL, targets T [n][1024] =
+ * (K_e/s_e + 0.1 I)^-1 - blockdiag4(K_e/s_e + 0.1 I)^-1 of the listed elements, plus their scales
+ * s_e [n]; float32 device arrays.  Allocates a temporary float64 [n][32][32] buffer.  (The shift of
+ * the target is 0.1, not 1e-3: an element's constant-pressure mode is nearly singular.) */
+imga_status imga_precond_dataset(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
+                                 const double* f, const imga_physics* phys, int precision, const int32_t* elems_dev,
+                                 int64_t n, int ldx, float* X, float* T, float* scale, void* stream);
+/* C [M][N] = A [M][K] B[N][K]^T with A, B rounded to BF16, FP32 accumulation (the GEMM of the network) */
+imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, float* C, void* stream);
 
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.

@@ -26,6 +26,7 @@ SOURCES = [
     ("vms.cu", []),
     ("jac.cu", []),
     ("solver.cu", []),
+    ("mlp.cu", []),
 ]
 HEADERS = ["imga_internal.h", "vms_device.cuh", os.path.join("..", "..", "include", "imga.h")]
 
@@ -105,12 +106,12 @@ class MeshInfo(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("gmres_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int), ("rtol", C.c_double),
                 ("atol", C.c_double), ("krylov_rtol", C.c_double), ("precision", C.c_int), ("precond", C.c_int),
-                ("line_search", C.c_int)]
+                ("line_search", C.c_int), ("learned", C.c_void_p), ("learned_omega", C.c_double)]
 
 
 class SolverStats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("krylov_its", C.c_int), ("krylov_per_newton", C.c_int * 32),
-                ("res_norm", C.c_double * 33), ("time_ms", C.c_double), ("converged", C.c_int)]
+                ("res_norm", C.c_double * 33), ("time_ms", C.c_double), ("converged", C.c_int), ("fallbacks", C.c_int)]
 
 
 # every entry point declared in include/imga.h, with its ctypes signature
@@ -132,6 +133,16 @@ SIGNATURES = {
     "imga_element_jacobians": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _i64, _vp, _vp]),
     "imga_newton_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), C.POINTER(SolverOpts),
                                    C.POINTER(SolverStats), _vp]),
+    "imga_mlp_create": (C.c_int, [_int, _int, _int, C.c_uint64, _int, C.POINTER(_vp)]),
+    "imga_mlp_destroy": (None, [_vp]),
+    "imga_mlp_shape": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "imga_mlp_params": (C.c_int, [_vp, _vp, _int]),
+    "imga_mlp_forward": (C.c_int, [_vp, _vp, _i64, _i64, _vp, _vp]),
+    "imga_mlp_gradient": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.POINTER(C.c_double), _vp, _vp]),
+    "imga_mlp_train": (C.c_int, [_vp, _vp, _i64, _vp, _i64, _int, _int, C.c_float, _vp, _vp]),
+    "imga_precond_dataset": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _i64, _int, _vp, _vp,
+                                       _vp, _vp]),
+    "imga_gemm_bf16": (C.c_int, [_int, _int, _int, _vp, _vp, _vp, _vp]),
     "imga_profile": (C.c_int, [_vp, _int]),
     "imga_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "imga_last_error": (C.c_char_p, []),

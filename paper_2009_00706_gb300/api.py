@@ -185,10 +185,11 @@ class Mesh:
 
     def newton_step(self, phys, u, u_prev, u_prev2=None, f=None, gmres_m=50, max_newton=20, max_krylov=1000,
                     rtol=1e-8, atol=0.0, krylov_rtol=1e-3, precision=PRECISION_FP64, precond=1, line_search=1,
-                    stream=None, raise_on_failure=True):
-        """Newton-GMRES in place on u; returns a stats dict."""
+                    stream=None, raise_on_failure=True, learned=None, learned_omega=0.5):
+        """Newton-GMRES in place on u; returns a stats dict.  precond 2 needs learned = an Mlp."""
         nn = self.n_nodes
-        o = SolverOpts(gmres_m, max_newton, max_krylov, rtol, atol, krylov_rtol, precision, precond, line_search)
+        o = SolverOpts(gmres_m, max_newton, max_krylov, rtol, atol, krylov_rtol, precision, precond, line_search,
+                       learned.h if learned is not None else None, learned_omega)
         st = SolverStats()
         ps = physics_struct(phys)
         status = _lib.load().imga_newton_step(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
@@ -196,10 +197,27 @@ class Mesh:
                                               C.byref(ps), C.byref(o), C.byref(st), _stream(stream))
         out = {"status": status, "newton_its": st.newton_its, "krylov_its": st.krylov_its,
                "krylov_per_newton": list(st.krylov_per_newton)[: st.newton_its],
-               "res_norm": list(st.res_norm)[: st.newton_its + 1], "time_ms": st.time_ms, "converged": st.converged}
+               "res_norm": list(st.res_norm)[: st.newton_its + 1], "time_ms": st.time_ms, "converged": st.converged,
+               "fallbacks": st.fallbacks}
         if raise_on_failure and status != 0:
             check(status)
         return out
+
+    def precond_dataset(self, phys, u, u_prev, elems, u_prev2=None, f=None, precision=PRECISION_MIXED, targets=True,
+                        ldx=1040, stream=None):
+        """(X [n, ldx], T [n, 1024] or None, scale [n]) float32 device tensors of the listed elements."""
+        import torch
+        n = elems.numel()
+        X = torch.empty((n, ldx), dtype=torch.float32, device=u.device)
+        T = torch.empty((n, 1024), dtype=torch.float32, device=u.device) if targets else None
+        sc = torch.empty(n, dtype=torch.float32, device=u.device)
+        ps = physics_struct(phys)
+        nn = self.n_nodes
+        check(_lib.load().imga_precond_dataset(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                               _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps),
+                                               precision, _ptr(elems), n, ldx, _ptr(X), _ptr(T), _ptr(sc),
+                                               _stream(stream)))
+        return X, T, sc
 
     def profile(self, enable=True):
         check(_lib.load().imga_profile(self.h, 1 if enable else 0))
@@ -214,3 +232,78 @@ class Mesh:
 
     def set_dirichlet(self, mask=None, vals=None, stream=None):
         check(_lib.load().imga_set_dirichlet(self.h, _ptr(mask), _ptr(vals), _stream(stream)))
+
+
+class Mlp:
+    """imga_mlp: the learned block preconditioner's network (3 layers, BF16 tensor cores)."""
+
+    def __init__(self, n_in=1027, width=128, n_out=1024, seed=0, device=0):
+        h = C.c_void_p()
+        check(_lib.load().imga_mlp_create(n_in, width, n_out, seed, device, C.byref(h)))
+        self.h = h
+        npar, pad = C.c_int64(), C.c_int()
+        check(_lib.load().imga_mlp_shape(h, C.byref(npar), C.byref(pad)))
+        self.n_params, self.n_in_pad = npar.value, pad.value
+        self.n_in, self.width, self.n_out = n_in, width, n_out
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().imga_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        check(_lib.load().imga_mlp_params(self.h, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(_lib.load().imga_mlp_params(self.h, p.ctypes.data_as(C.c_void_p), 1))
+
+    def unpack(self, p):
+        """(W1 [w, n_in], b1, W2, b2, W3, b3) float64 views of a flat parameter vector."""
+        w, pad, nin, no = self.width, self.n_in_pad, self.n_in, self.n_out
+        o = 0
+        W1 = p[o:o + w * pad].reshape(w, pad)[:, :nin].astype(np.float64); o += w * pad
+        b1 = p[o:o + w].astype(np.float64); o += w
+        W2 = p[o:o + w * w].reshape(w, w).astype(np.float64); o += w * w
+        b2 = p[o:o + w].astype(np.float64); o += w
+        W3 = p[o:o + no * w].reshape(no, w).astype(np.float64); o += no * w
+        b3 = p[o:o + no].astype(np.float64)
+        return [W1, b1, W2, b2, W3, b3]
+
+    def forward(self, X, stream=None):
+        import torch
+        n = X.shape[0]
+        Y = torch.empty((n, self.n_out), dtype=torch.float32, device=X.device)
+        check(_lib.load().imga_mlp_forward(self.h, _ptr(X), X.shape[1], n, _ptr(Y), _stream(stream)))
+        return Y
+
+    def gradient(self, X, T, stream=None):
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_double()
+        check(_lib.load().imga_mlp_gradient(self.h, _ptr(X), X.shape[1], _ptr(T), X.shape[0], C.byref(loss),
+                                            g.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return loss.value, g
+
+    def train(self, X, T, epochs=10, batch=1024, lr=1e-3, stream=None):
+        hist = np.zeros(max(1, epochs))
+        check(_lib.load().imga_mlp_train(self.h, _ptr(X), X.shape[1], _ptr(T), X.shape[0], epochs, batch, lr,
+                                         hist.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return hist[:epochs]
+
+
+def gemm_bf16(A, B, stream=None):
+    """C = A B^T with A, B rounded to BF16, FP32 accumulate (float32 CUDA tensors)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    Cm = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    check(_lib.load().imga_gemm_bf16(M, N, K, _ptr(A), _ptr(B), _ptr(Cm), _stream(stream)))
+    return Cm

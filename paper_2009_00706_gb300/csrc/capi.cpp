@@ -13,6 +13,10 @@
 struct imga_mesh_s {
     imga::Mesh m;
 };
+struct imga_mlp_s {
+    imga::Mlp* M = nullptr;
+    int nin = 0, nout = 0, device = 0;
+};
 
 namespace imga {
 thread_local std::string g_last_error;
@@ -246,15 +250,97 @@ imga_status imga_newton_step(imga_mesh h, double* u, const double* up, const dou
     if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
     if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
     if (o->gmres_m < 1 || o->gmres_m > 63 || o->max_newton < 0 || o->max_krylov < 1 || !(o->rtol >= 0.0) ||
-        !(o->krylov_rtol > 0.0) || (o->precision != 0 && o->precision != 1) || o->precond < 0 || o->precond > 1)
+        !(o->krylov_rtol > 0.0) || (o->precision != 0 && o->precision != 1) || o->precond < 0 || o->precond > 3 ||
+        (o->precond == 2 && !o->learned))
         return fail(IMGA_ERR_INVALID_ARG, "bad solver options");
+    imga_solver_opts oo = *o;
+    if (oo.precond == 2) oo.learned = ((const imga_mlp_s*)o->learned)->M;
     std::string err;
-    int rc = imga::newton_solve(h->m, u, up, up2, f, *ph, *o, stats, stream, err);
+    int rc = imga::newton_solve(h->m, u, up, up2, f, *ph, oo, stats, stream, err);
     if (rc == 3) return fail(IMGA_ERR_OOM, err);
     if (rc == 2) return fail(IMGA_ERR_NUMERIC, err);
     if (rc) return fail(IMGA_ERR_CUDA, err);
     if (cudaGetLastError() != cudaSuccess) return cuda_status("newton_step");
     if (!stats->converged) return fail(IMGA_ERR_NOT_CONVERGED, "Newton did not reach the tolerance");
+    return IMGA_OK;
+}
+
+imga_status imga_mlp_create(int n_in, int width, int n_out, uint64_t seed, int device, imga_mlp* out) {
+    if (!out || n_in < 1 || width < 1 || n_out < 1 || width > 4096 || n_in > 1 << 16 || n_out > 1 << 16)
+        return fail(IMGA_ERR_INVALID_ARG, "bad MLP shape");
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return cuda_status("cudaSetDevice");
+    imga_mlp_s* h = new imga_mlp_s();
+    std::string err;
+    if (imga::mlp_create(n_in, width, n_out, seed, &h->M, err)) { delete h; return fail(IMGA_ERR_OOM, err); }
+    h->nin = n_in;
+    h->nout = n_out;
+    h->device = device;
+    *out = h;
+    return IMGA_OK;
+}
+
+void imga_mlp_destroy(imga_mlp h) {
+    if (!h) return;
+    imga::mlp_destroy(h->M);
+    delete h;
+}
+
+imga_status imga_mlp_shape(imga_mlp h, int64_t* n_params, int* n_in_pad) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null MLP");
+    if (n_params) *n_params = imga::mlp_nparam(h->M);
+    if (n_in_pad) *n_in_pad = imga::mlp_nin_pad(h->M);
+    return IMGA_OK;
+}
+
+imga_status imga_mlp_params(imga_mlp h, float* host, int set) {
+    if (!h || !host) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (imga::mlp_params(h->M, host, set)) return cuda_status("mlp_params");
+    return IMGA_OK;
+}
+
+imga_status imga_mlp_forward(imga_mlp h, const float* X, int64_t ldx, int64_t n, float* Y, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!X || !Y)) || ldx < h->nin) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    if (imga::mlp_forward(h->M, X, ldx, n, Y, (cudaStream_t)stream)) return cuda_status("mlp_forward");
+    return IMGA_OK;
+}
+
+imga_status imga_mlp_gradient(imga_mlp h, const float* X, int64_t ldx, const float* T, int64_t n, double* loss,
+                              float* grad_host, void* stream) {
+    if (!h || n < 1 || !X || !T || !loss || ldx < h->nin) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    if (imga::mlp_gradient(h->M, X, ldx, T, n, loss, (cudaStream_t)stream)) return cuda_status("mlp_gradient");
+    if (grad_host && imga::mlp_grads(h->M, grad_host)) return cuda_status("mlp_gradient copy");
+    return IMGA_OK;
+}
+
+imga_status imga_mlp_train(imga_mlp h, const float* X, int64_t ldx, const float* T, int64_t n, int epochs, int batch,
+                           float lr, double* loss_hist, void* stream) {
+    if (!h || n < 1 || !X || !T || epochs < 0 || batch < 1 || ldx < h->nin || !(lr > 0.f))
+        return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    if (imga::mlp_train(h->M, X, ldx, T, n, epochs, batch, lr, loss_hist, (cudaStream_t)stream)) return cuda_status("mlp_train");
+    return IMGA_OK;
+}
+
+imga_status imga_precond_dataset(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                                 const imga_physics* ph, int precision, const int32_t* elems, int64_t n, int ldx,
+                                 float* X, float* T, float* scale, void* stream) {
+    if (!h || !u || !up || n < 0 || (n > 0 && (!elems || !X || !scale)) || ldx < 1027)
+        return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (!physics_ok(ph) || (ph->time_scheme == 2 && !up2)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
+    if (n == 0) return IMGA_OK;
+    double* K = nullptr;
+    if (cudaMalloc((void**)&K, (size_t)n * 1024 * sizeof(double)) != cudaSuccess) return fail(IMGA_ERR_OOM, "cudaMalloc failed");
+    int rc = imga::precond_dataset(h->m, u, up, up2, f, *ph, precision, elems, n, ldx, X, T, scale, K, (cudaStream_t)stream);
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(K);
+    if (rc) return cuda_status("precond_dataset");
+    return IMGA_OK;
+}
+
+imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, float* C, void* stream) {
+    if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    if (imga::gemm_bf16_test(M, N, K, A, B, C, (cudaStream_t)stream)) return cuda_status("gemm_bf16");
     return IMGA_OK;
 }
 

@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/imga.h"
 
 namespace imga {
@@ -171,6 +173,25 @@ int element_jacobians(const Mesh& m, const double* u, const double* up, const do
 int block_jacobi_setup(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
                        const imga_physics& ph, int precision, double* D, double* Dinv, void* stream);
 int block_jacobi_apply(const Mesh& m, const double* Dinv, const double* x, double* y, void* stream);
+
+// learned block preconditioner (mlp.cu)
+struct Mlp;
+int mlp_create(int nin, int width, int nout, uint64_t seed, Mlp** out, std::string& err);
+void mlp_destroy(Mlp* M);
+int64_t mlp_nparam(const Mlp* M);
+int mlp_nin_pad(const Mlp* M);
+int mlp_params(Mlp* M, float* host, int set);
+int mlp_grads(Mlp* M, float* host);
+int mlp_forward(Mlp* M, const float* X, int64_t ldx, int64_t n, float* Y, cudaStream_t s);
+int mlp_gradient(Mlp* M, const float* X, int64_t ldx, const float* T, int64_t n, double* loss, cudaStream_t s);
+int mlp_train(Mlp* M, const float* X, int64_t ldx, const float* T, int64_t n, int epochs, int batch, float lr,
+              double* loss_hist, cudaStream_t s);
+int precond_dataset(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                    const imga_physics& ph, int precision, const int32_t* elems, int64_t n, int ldx, float* X,
+                    float* T, float* scale, double* Kbuf, cudaStream_t s);
+int precond_correction(const Mesh& m, const imga_physics& ph, const int32_t* elems, int64_t n, const float* C,
+                       const float* scale, float omega, const double* v, double* zc, double* z, cudaStream_t s);
+int gemm_bf16_test(int M, int N, int K, const float* A, const float* B, float* C, cudaStream_t s);
 
 // Newton-GMRES (solver.cu)
 int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const double* f, const imga_physics& ph,

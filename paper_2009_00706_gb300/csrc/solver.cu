@@ -104,7 +104,7 @@ struct Work {
     double* Dinv = nullptr;
     double* partial = nullptr; // [kRedBlocks][64]
     double* h = nullptr;       // [64]
-    double* hh = nullptr;      // pinned host [64]
+    double* hh = nullptr;      // pinned host [128]: dot products in, coefficients out
 };
 
 class Solver {
@@ -131,7 +131,7 @@ public:
             cudaMalloc((void**)&w.Dinv, 4 * n * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.partial, kRedBlocks * 64 * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.h, 64 * sizeof(double)) != cudaSuccess ||
-            cudaMallocHost((void**)&w.hh, 64 * sizeof(double)) != cudaSuccess) {
+            cudaMallocHost((void**)&w.hh, 128 * sizeof(double)) != cudaSuccess) {
             err = "solver workspace allocation failed";
             cudaGetLastError();
             return 1;
@@ -168,8 +168,9 @@ public:
         return std::sqrt(std::max(v, 0.0));
     }
     void maxpy(const double* V, int nk, const double* hhost, double beta, double alpha, double* w) {
-        std::memcpy(W.hh, hhost, nk * sizeof(double));
-        cudaMemcpyAsync(W.h, W.hh, nk * sizeof(double), cudaMemcpyHostToDevice, st);
+        // upload half of the pinned buffer (the other half receives the dot products)
+        std::memcpy(W.hh + 64, hhost, nk * sizeof(double));
+        cudaMemcpyAsync(W.h, W.hh + 64, nk * sizeof(double), cudaMemcpyHostToDevice, st);
         const int grid = (int)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256);
         maxpy_kernel<<<grid, 256, 0, st>>>(n, V, n, nk, W.h, beta, alpha, w);
     }
@@ -186,9 +187,49 @@ public:
     int jv(const double* u, const double* v, double* out) {
         return vms_apply(M, u, Up, Up2, F, P, O.precision, v, out, st);
     }
+    int pmode = 0;   // preconditioner in use for the current linear solve (block-Jacobi fallback)
     void precond(const double* x, double* y) {
-        if (O.precond >= 1) block_jacobi_apply(M, W.Dinv, x, y, st);
+        if (pmode >= 1) block_jacobi_apply(M, W.Dinv, x, y, st);
         else cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (pmode >= 2)
+            precond_correction(M, P, L.elems, L.n, L.C, L.scale, (float)O.learned_omega, x, L.zc, y, st);
+    }
+
+    // learned correction: network inputs of every active element, one inference per Newton iteration
+    struct Learned {
+        int64_t n = 0;
+        int ldx = 0;
+        int32_t* elems = nullptr;
+        float *X = nullptr, *C = nullptr, *scale = nullptr;
+        double *K = nullptr, *zc = nullptr;
+    } L;
+
+    int learned_alloc(std::string& err) {
+        std::vector<int32_t> act(M.out_list);
+        act.insert(act.end(), M.cut_list.begin(), M.cut_list.end());
+        L.n = (int64_t)act.size();
+        L.ldx = O.precond == 2 ? mlp_nin_pad((const Mlp*)O.learned) : 1040;
+        if (L.ldx < 1027) { err = "learned preconditioner: the network must take 1027 inputs"; return 1; }
+        bool ok = cudaMalloc((void**)&L.elems, std::max<int64_t>(1, L.n) * 4) == cudaSuccess &&
+                  cudaMalloc((void**)&L.X, std::max<int64_t>(1, L.n) * L.ldx * 4) == cudaSuccess &&
+                  cudaMalloc((void**)&L.C, std::max<int64_t>(1, L.n) * 1024 * 4) == cudaSuccess &&
+                  cudaMalloc((void**)&L.scale, std::max<int64_t>(1, L.n) * 4) == cudaSuccess &&
+                  cudaMalloc((void**)&L.K, std::max<int64_t>(1, L.n) * 1024 * 8) == cudaSuccess &&
+                  cudaMalloc((void**)&L.zc, n * 8) == cudaSuccess;
+        if (!ok) { err = "learned preconditioner allocation failed"; cudaGetLastError(); return 1; }
+        cudaMemcpyAsync(L.elems, act.data(), L.n * 4, cudaMemcpyHostToDevice, st);
+        return 0;
+    }
+    void learned_free() {
+        cudaFree(L.elems); cudaFree(L.X); cudaFree(L.C); cudaFree(L.scale); cudaFree(L.K); cudaFree(L.zc);
+        L = Learned();
+    }
+    int learned_setup(const double* u) {
+        // precond 2: the network's correction; precond 3: the exact element-block correction it is trained on
+        float* T = O.precond == 3 ? L.C : nullptr;
+        if (precond_dataset(M, u, Up, Up2, F, P, O.precision, L.elems, L.n, L.ldx, L.X, T, L.scale, L.K, st)) return 1;
+        if (O.precond == 3) return 0;
+        return mlp_forward((Mlp*)O.learned, L.X, L.ldx, L.n, L.C, st);
     }
 
     // solve J(u) x = b to ||b - J x|| <= rtol ||b|| (or max_its); x starts at 0
@@ -288,10 +329,19 @@ public:
                 err = "block-Jacobi setup failed";
                 return 1;
             }
+            if (O.precond >= 2 && learned_setup(u)) { err = "learned preconditioner setup failed"; return 1; }
             scale_copy(-1.0, R, b);
             int kits = 0;
             double kres = 0.0;
+            pmode = O.precond;
             if (gmres(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
+            if (pmode >= 2 && !(kres <= O.krylov_rtol * rn * 1.0000001)) {
+                // the correction did not bring GMRES to its tolerance: redo the solve with block-Jacobi
+                S->fallbacks += 1;
+                S->krylov_its += kits;
+                pmode = 1;
+                if (gmres(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
+            }
             S->krylov_per_newton[it] = kits;
             S->krylov_its += kits;
             double lam = 1.0, rt = 0.0;
@@ -332,7 +382,10 @@ int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const 
     std::memset(stats, 0, sizeof(*stats));
     Solver S(m, ph, o, (cudaStream_t)stream, up, up2, f);
     if (S.alloc(err)) return 3;
-    return S.newton(u, stats, err);
+    if (o.precond >= 2 && S.learned_alloc(err)) return 3;
+    int rc = S.newton(u, stats, err);
+    if (o.precond >= 2) { cudaStreamSynchronize((cudaStream_t)stream); S.learned_free(); }
+    return rc;
 }
 
 void solver_free(Mesh& m) { Solver::free_work(m); }

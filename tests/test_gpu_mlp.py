@@ -1,0 +1,106 @@
+"""GPU network of the learned block preconditioner against the FP64 oracle MLP, and its effect.
+
+* BF16 tensor-core GEMM (mma.sync m16n8k16, FP32 accumulate) against the float64 product of the
+  BF16-rounded operands, ragged sizes: <= 1e-5 relative.
+* Loss and gradient of the device MLP (BF16 weights/activations) against the oracle's exact FP64
+  backward pass at the same BF16-rounded weights and inputs.  What remains is the rounding of the
+  intermediates to BF16 (2^-8 relative each: two activations forward, three back-propagated
+  errors on the way to W1) inside batch sums that cancel; bound 5e-2 relative per parameter block.
+* Adam training lowers the loss.
+* Learned correction inside GMRES on held-out seeds: converges to the same 1e-8 float64 residual;
+  the GMRES iteration counts with and without it are reported.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mlp as omlp
+from paper_2009_00706_gb300 import _lib, api
+from paper_2009_00706_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _lib.build()
+    return torch.device("cuda:0")
+
+
+def test_bf16_gemm_ragged(dev):
+    for M, N, K in ((100, 70, 45), (130, 9, 200), (1, 64, 16)):
+        A = torch.from_numpy(I.normal(1, M * K).reshape(M, K).astype(np.float32)).to(dev)
+        B = torch.from_numpy(I.normal(2, N * K).reshape(N, K).astype(np.float32)).to(dev)
+        Cg = api.gemm_bf16(A, B).cpu().numpy().astype(np.float64)
+        Ab = A.to(torch.bfloat16).to(torch.float64).cpu().numpy()
+        Bb = B.to(torch.bfloat16).to(torch.float64).cpu().numpy()
+        ref = Ab @ Bb.T
+        assert np.linalg.norm(Cg - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_mlp_gradient_matches_oracle(dev):
+    net = api.Mlp(n_in=37, width=32, n_out=24, seed=3)
+    n = 300
+    X = I.normal(4, n * 48).reshape(n, 48).astype(np.float32)
+    T = I.normal(5, n * 24).reshape(n, 24).astype(np.float32)
+    loss, g = net.gradient(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev))
+    bf = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    p = net.unpack(net.params())
+    p = [bf(q) if k in (0, 2, 4) else q for k, q in enumerate(p)]      # weights enter the GEMMs in BF16
+    Xb = bf(X[:, :37])
+    lo = omlp.loss(p, Xb, T.astype(np.float64))
+    go = omlp.grad(p, Xb, T.astype(np.float64))
+    gd = net.unpack(g)
+    assert abs(loss - lo) <= 1e-2 * lo
+    for k in range(6):
+        err = np.linalg.norm(gd[k] - go[k]) / np.linalg.norm(go[k])
+        assert err <= 5e-2, (k, err)
+
+
+def test_training_lowers_the_loss(dev):
+    net = api.Mlp(n_in=37, width=64, n_out=24, seed=4)
+    n = 4096
+    X = I.normal(6, n * 48).reshape(n, 48).astype(np.float32)
+    W = I.normal(7, 37 * 24).reshape(37, 24).astype(np.float32) / 6.0
+    T = np.tanh(X[:, :37] @ W).astype(np.float32)
+    hist = net.train(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), epochs=30, batch=512, lr=2e-3)
+    assert hist[-1] < 0.3 * hist[0], hist
+
+
+def _elements(mesh):
+    mk, _ = mesh.markers()
+    return np.where(mk != 1)[0].astype(np.int32)
+
+
+def test_learned_preconditioner_in_gmres(dev):
+    w = I.small_sphere(0)
+    mesh = api.Mesh.from_workload(w, device=0)
+    elems = torch.from_numpy(_elements(mesh)).to(dev)
+    Xs, Ts = [], []
+    for seed in range(4):
+        u, up, _ = I.state(mesh.n_nodes, seed)
+        X, Tt, _ = mesh.precond_dataset(w.physics, torch.from_numpy(u).to(dev), torch.from_numpy(up).to(dev), elems)
+        Xs.append(X)
+        Ts.append(Tt)
+    X, Tt = torch.cat(Xs), torch.cat(Ts)
+    net = api.Mlp(seed=11)
+    hist = net.train(X, Tt, epochs=20, batch=1024, lr=1e-3)
+    assert hist[-1] < hist[0]
+    out = {}
+    from oracle.oracle import OracleMesh
+    o = OracleMesh(w.lo, w.hi, w.base_level, w.regions, w.triangles(), w.lmax)
+    for seed in (16, 17):
+        u, up, _ = I.state(mesh.n_nodes, seed)
+        R0 = np.linalg.norm(o.residual(w.physics, u, up))
+        for name, kw in (("block_jacobi", dict(precond=1)), ("exact_correction", dict(precond=3, learned_omega=0.5)),
+                         ("learned", dict(precond=2, learned=net, learned_omega=0.5))):
+            ud = torch.from_numpy(u).to(dev)
+            st = mesh.newton_step(w.physics, ud, torch.from_numpy(up).to(dev), precision=api.PRECISION_FP64,
+                                  rtol=1e-8, gmres_m=50, raise_on_failure=False, **kw)
+            out.setdefault(name, []).append((st["krylov_its"], st["fallbacks"], st["converged"]))
+            # the float64 residual is the judge: the oracle's residual at the result
+            assert st["converged"], (name, st)
+            assert np.linalg.norm(o.residual(w.physics, ud.cpu().numpy(), up)) <= 1.5e-8 * R0
+    print("GMRES iterations (its, fallbacks, converged):", out, "training loss", hist[0], hist[-1])
