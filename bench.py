@@ -301,21 +301,40 @@ def run_ours(args):
             torch.cuda.synchronize()
             tot += a.elapsed_time(b)
         extra[name] = n_active * reps / (tot / 1e3)
+    # J v replayed as a CUDA graph (parallel branches for the Out / Intercepted / surface kernels)
+    mesh.use_graphs(True)
+    step()
+    torch.cuda.synchronize()
+    gms = 0.0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(20):
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        gms += a.elapsed_time(b)
+    extra["jv_mixed_graph"] = n_active * 20 / (gms / 1e3)
+    mesh.use_graphs(False)
+    batched = run_batched(args, dev, stream) if not args.no_batched else None
+
     # Newton-GMRES step to 1e-8 (float64 residual), block-Jacobi, J v in FP64 vs mixed precision, on the
     # small-sphere problem (7,288 elements: the size the learned preconditioner is evaluated at).  On the
     # 2M-element sphere LES nodal block-Jacobi does not bring GMRES(50) to 1e-8 (see the design notes).
     newton = {}
     if not args.no_newton:
         ws = I.small_sphere(0)
-        ms = api.Mesh.from_workload(ws, device=local)
-        su, sup, _ = I.state(ms.n_nodes, 16 + rank)
+        smesh = api.Mesh.from_workload(ws, device=local)
+        su, sup, _ = I.state(smesh.n_nodes, 16 + rank)
         sud, supd = torch.from_numpy(su).to(dev), torch.from_numpy(sup).to(dev)
-        for name, p in (("mixed", api.PRECISION_MIXED), ("fp64", api.PRECISION_FP64)):
+        for name, p, gr in (("mixed", api.PRECISION_MIXED, False), ("fp64", api.PRECISION_FP64, False),
+                            ("mixed_graphs", api.PRECISION_MIXED, True)):
+            smesh.use_graphs(gr)
             runs = []
             for rep in range(2):   # the first run also allocates the Krylov workspace
                 uw = sud.clone()
                 torch.cuda.synchronize()
-                st = ms.newton_step(ws.physics, uw, supd, precision=p, precond=1, rtol=1e-8, gmres_m=50,
+                st = smesh.newton_step(ws.physics, uw, supd, precision=p, precond=1, rtol=1e-8, gmres_m=50,
                                     krylov_rtol=args.krylov_rtol, max_newton=20, max_krylov=500, stream=stream,
                                     raise_on_failure=False)
                 runs.append(st)
@@ -323,7 +342,7 @@ def run_ours(args):
             newton[name] = {"ms": st["time_ms"], "newton_its": st["newton_its"], "krylov_its": st["krylov_its"],
                             "converged": bool(st["converged"]), "rel_residual": st["res_norm"][-1] / st["res_norm"][0],
                             "workload": "small_sphere (7,288 elements, Re 10, BE dt 0.01), block-Jacobi, GMRES(50)"}
-        ms.close()
+        smesh.close()
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -349,12 +368,68 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roof, "kernel_time_share": kern_share, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": 4 * args.steps, "cpu_baseline": cpu, "extra_elements_per_s": extra,
-                "newton_step": newton, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
+                "newton_step": newton, "batched": batched, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(args, dev, stream):
+    """64 independent sphere problems (5k-200k elements, Re 1-1e6): J v of all of them through one
+    batched mesh (one launch of each kernel) vs 64 meshes called one after the other."""
+    import torch
+
+    from paper_2009_00706_gb300 import api
+    probs = [wl for wl, _, _ in I.batched_spheres(64)]
+    t0 = time.perf_counter()
+    B = api.Mesh.batch(probs, device=dev.index)
+    tb = time.perf_counter() - t0
+    sep = [api.Mesh.from_workload(w, device=dev.index) for w in probs]
+    n_act = B.info["n_out"] + B.info["n_cut"]
+    states = [I.state(m.n_nodes, 100 + k) for k, m in enumerate(sep)]
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ub, upb, vb = (T(np.concatenate([s[i] for s in states])) for i in range(3))
+    outb = torch.empty_like(ub)
+    per = [(T(s[0]), T(s[1]), T(s[2]), torch.empty_like(T(s[0]))) for s in states]
+    ph = probs[0].physics
+    prec = api.PRECISION_MIXED
+
+    def batched_step():
+        B.jvp(ph, ub, upb, vb, precision=prec, out=outb, stream=stream)
+
+    def sequential_step():
+        for m, w, (u, up, v, o) in zip(sep, probs, per):
+            m.jvp(w.physics, u, up, v, precision=prec, out=o, stream=stream)
+
+    res = {"problems": 64, "elements": int(B.n_elem), "active_elements": int(n_act), "batch_build_s": tb}
+    for name, fn in (("one_batched_launch", batched_step), ("sequential_64_meshes", sequential_step)):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        res[name] = {"ms_per_jv": ms, "elements_per_s": n_act / (ms / 1e3)}
+    B.use_graphs(True)
+    batched_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(10):
+        batched_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 10
+    res["one_batched_graph"] = {"ms_per_jv": ms, "elements_per_s": n_act / (ms / 1e3)}
+    for m in sep:
+        m.close()
+    B.close()
+    return res
 
 
 def main():
@@ -368,6 +443,7 @@ def main():
     ap.add_argument("--ref-sample-nodes", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-GMRES step timing")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--krylov-rtol", type=float, default=1e-3)
     args = ap.parse_args()
     if args.impl == "reference":

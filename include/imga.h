@@ -105,6 +105,23 @@ typedef struct {
 imga_status imga_build_mesh(const double* tri_xyz_host, int64_t n_tri, const imga_mesh_params* params, int device,
                             imga_mesh* out);
 void imga_destroy_mesh(imga_mesh mesh);
+
+/* Several independent problems in one mesh, so that one launch of each residual / J v / Jacobian
+ * kernel covers all of them.  Problem p has its own surface, octree parameters and viscosity mu
+ * (the mu of the imga_physics passed to later calls is ignored; rho, dt, the time scheme, C_b, C_I,
+ * g_body and u_inf are shared).  Every problem must use the same box origin and root size.  Its
+ * nodes and elements come in problem order: imga_mesh_problems gives the offsets.  Node vectors
+ * of the batched mesh are the concatenation of the problems' vectors.  imga_classify is refused
+ * (classify against a problem's own mesh). */
+typedef struct {
+    const double* tri_xyz_host;
+    int64_t n_tri;
+    imga_mesh_params params;
+    double mu;
+} imga_problem;
+imga_status imga_build_mesh_batch(const imga_problem* problems, int n_problems, int device, imga_mesh* out);
+/* number of problems (1 for an ordinary mesh) and elem_off / node_off [n_problems + 1] (host) */
+imga_status imga_mesh_problems(imga_mesh mesh, int* n_problems, int64_t* elem_off, int64_t* node_off);
 imga_status imga_mesh_get_info(imga_mesh mesh, imga_mesh_info* info);
 
 /* Host copies of the mesh tables (every pointer may be NULL to skip it).  anchors [n_elem][3]
@@ -250,6 +267,15 @@ imga_status imga_precond_dataset(imga_mesh mesh, const double* u, const double* 
                                  int64_t n, int ldx, float* X, float* T, float* scale, void* stream);
 /* C [M][N] = A [M][K] B[N][K]^T with A, B rounded to BF16, FP32 accumulation (the GEMM of the network) */
 imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, float* C, void* stream);
+
+/* Options of a mesh.  IMGA_OPT_GRAPHS (value 1 on, 0 off, default off): imga_residual and imga_jvp
+ * run as CUDA graphs -- the first call with a given set of pointers, stream, precision and physics
+ * captures node preparation, the Out-element, Intercepted-element and surface kernels (the last
+ * three on parallel branches) and the strong rows; later identical calls replay that graph (up to
+ * 32 graphs are kept per mesh).  The first call for a key must not itself run inside a stream
+ * capture.  imga_set_dirichlet drops the cached graphs.  Profiling (imga_profile) bypasses them. */
+enum { IMGA_OPT_GRAPHS = 1 };
+imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
 
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.

@@ -22,6 +22,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = [
     ("mesh_host.cpp", ["-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fopenmp"]),
     ("capi.cpp", []),
+    ("batch.cpp", []),
     ("geom.cu", ["-fmad=false"]),
     ("vms.cu", []),
     ("jac.cu", []),
@@ -96,6 +97,10 @@ class Physics(C.Structure):
                 ("drop_visc_strong", C.c_int)]
 
 
+class Problem(C.Structure):
+    _fields_ = [("tri_xyz_host", C.c_void_p), ("n_tri", C.c_int64), ("params", MeshParams), ("mu", C.c_double)]
+
+
 class MeshInfo(C.Structure):
     _fields_ = [("n_elem", C.c_int64), ("n_nodes", C.c_int64), ("n_hanging", C.c_int64), ("n_out", C.c_int64),
                 ("n_in", C.c_int64), ("n_cut", C.c_int64), ("n_cut_points", C.c_int64),
@@ -119,6 +124,8 @@ _vp, _i64, _int, _dp = C.c_void_p, C.c_int64, C.c_int, C.c_void_p
 SIGNATURES = {
     "imga_build_mesh": (C.c_int, [_dp, _i64, C.POINTER(MeshParams), _int, C.POINTER(_vp)]),
     "imga_destroy_mesh": (None, [_vp]),
+    "imga_build_mesh_batch": (C.c_int, [C.POINTER(Problem), _int, _int, C.POINTER(_vp)]),
+    "imga_mesh_problems": (C.c_int, [_vp, C.POINTER(C.c_int), _vp, _vp]),
     "imga_mesh_get_info": (C.c_int, [_vp, C.POINTER(MeshInfo)]),
     "imga_mesh_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "imga_export_markers": (C.c_int, [_vp, _vp, _vp]),
@@ -143,6 +150,7 @@ SIGNATURES = {
     "imga_precond_dataset": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _i64, _int, _vp, _vp,
                                        _vp, _vp]),
     "imga_gemm_bf16": (C.c_int, [_int, _int, _int, _vp, _vp, _vp, _vp]),
+    "imga_set_option": (C.c_int, [_vp, _int, _i64]),
     "imga_profile": (C.c_int, [_vp, _int]),
     "imga_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "imga_last_error": (C.c_char_p, []),

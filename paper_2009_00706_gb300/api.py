@@ -11,7 +11,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MeshInfo, MeshParams, Physics, Region, SolverOpts, SolverStats, check
+from ._lib import MeshInfo, MeshParams, Physics, Problem, Region, SolverOpts, SolverStats, check
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
@@ -53,8 +53,11 @@ def _vec(t, n_nodes, name):
 class Mesh:
     """imga_build_mesh / imga_destroy_mesh and the calls that take the mesh handle."""
 
-    def __init__(self, lo, hi, base_level, regions, triangles=None, lmax=3, device=0):
+    def __init__(self, lo=None, hi=None, base_level=None, regions=None, triangles=None, lmax=3, device=0, _handle=None):
         L = _lib.load()
+        if _handle is not None:
+            self._adopt(_handle, device)
+            return
         tri = np.ascontiguousarray(np.zeros((0, 3, 3)) if triangles is None else triangles, dtype=np.float64)
         regs = (Region * max(1, len(regions)))()
         for i, r in enumerate(regions):
@@ -71,6 +74,11 @@ class Mesh:
         n_tri = tri.shape[0]
         check(L.imga_build_mesh(tri.ctypes.data_as(C.c_void_p) if n_tri else None, n_tri, C.byref(P), device,
                                 C.byref(h)))
+        self._adopt(h, device)
+        self.lo = np.array(lo, dtype=np.float64)
+
+    def _adopt(self, h, device):
+        L = _lib.load()
         self.h = h
         self.device = device
         info = MeshInfo()
@@ -81,7 +89,41 @@ class Mesh:
         self.n_nodes = info.n_nodes
         self.n_hang = info.n_hanging
         self.scale = info.scale
-        self.lo = np.array(lo, dtype=np.float64)
+        np_ = C.c_int()
+        L.imga_mesh_problems(h, C.byref(np_), None, None)
+        self.n_problems = np_.value
+        eo = np.zeros(self.n_problems + 1, np.int64)
+        no = np.zeros(self.n_problems + 1, np.int64)
+        L.imga_mesh_problems(h, C.byref(np_), eo.ctypes.data_as(C.c_void_p), no.ctypes.data_as(C.c_void_p))
+        self.elem_off, self.node_off = eo, no
+
+    @classmethod
+    def batch(cls, workloads, mus=None, device=0):
+        """imga_build_mesh_batch over a list of inputs.Workload (viscosity: each workload's physics.mu)."""
+        L = _lib.load()
+        n = len(workloads)
+        probs = (Problem * n)()
+        keep = []
+        for i, w in enumerate(workloads):
+            tri = np.ascontiguousarray(w.triangles(), dtype=np.float64)
+            regs = (Region * max(1, len(w.regions)))()
+            for j, r in enumerate(w.regions):
+                regs[j].kind, regs[j].level = r.kind, r.level
+                regs[j].par = (C.c_double * 8)(*r.packed())
+            keep += [tri, regs]
+            probs[i].tri_xyz_host = tri.ctypes.data_as(C.c_void_p) if tri.shape[0] else None
+            probs[i].n_tri = tri.shape[0]
+            P = probs[i].params
+            P.lo = (C.c_double * 3)(*w.lo)
+            P.hi = (C.c_double * 3)(*w.hi)
+            P.base_level = w.base_level
+            P.n_regions = len(w.regions)
+            P.regions = C.cast(regs, C.POINTER(Region))
+            P.quad_max_split = w.lmax
+            probs[i].mu = w.physics.mu if mus is None else mus[i]
+        h = C.c_void_p()
+        check(L.imga_build_mesh_batch(probs, n, device, C.byref(h)))
+        return cls(_handle=h, device=device)
 
     @classmethod
     def from_workload(cls, w, device=0, triangles=None):
@@ -221,6 +263,10 @@ class Mesh:
 
     def profile(self, enable=True):
         check(_lib.load().imga_profile(self.h, 1 if enable else 0))
+
+    def use_graphs(self, on=True):
+        """imga_set_option(IMGA_OPT_GRAPHS): replay residual / J v calls as CUDA graphs."""
+        check(_lib.load().imga_set_option(self.h, 1, 1 if on else 0))
 
     def profile_read(self):
         """{kernel: (total ms, launches)} since profiling was enabled (synchronises)."""

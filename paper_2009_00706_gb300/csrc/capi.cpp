@@ -122,11 +122,55 @@ imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_pa
     return IMGA_OK;
 }
 
+imga_status imga_build_mesh_batch(const imga_problem* probs, int n, int device, imga_mesh* out) {
+    if (!out || !probs || n < 1 || n > 65535) return fail(IMGA_ERR_INVALID_ARG, "bad problem list");
+    *out = nullptr;
+    if (device < 0) return fail(IMGA_ERR_INVALID_ARG, "batched meshes need a device");
+    std::vector<imga_mesh> parts(n, nullptr);
+    std::vector<double> mu(n);
+    auto cleanup = [&]() { for (imga_mesh q : parts) imga_destroy_mesh(q); };
+    for (int p = 0; p < n; ++p) {
+        if (!(probs[p].mu >= 0.0)) { cleanup(); return fail(IMGA_ERR_INVALID_ARG, "bad problem viscosity"); }
+        imga_status st = imga_build_mesh(probs[p].tri_xyz_host, probs[p].n_tri, &probs[p].params, device, &parts[p]);
+        if (st != IMGA_OK) { std::string e = imga::g_last_error; cleanup(); return fail(st, "problem " + std::to_string(p) + ": " + e); }
+        mu[p] = probs[p].mu;
+    }
+    imga_mesh_s* h = new (std::nothrow) imga_mesh_s();
+    if (!h) { cleanup(); return fail(IMGA_ERR_OOM, "host allocation failed"); }
+    imga::Mesh& m = h->m;
+    m.device = device;
+    m.batched = true;
+    m.n_sm = parts[0]->m.n_sm;
+    std::vector<const imga::Mesh*> pm;
+    for (imga_mesh q : parts) pm.push_back(&q->m);
+    std::string err;
+    bool ok = imga::merge_meshes(m, pm, mu, err);
+    for (int k = 0; k < 4; ++k)
+        for (imga_mesh q : parts) m.setup_ms[k] += q->m.setup_ms[k];
+    cleanup();
+    if (!ok || cudaDeviceSynchronize() != cudaSuccess) { imga::device_free(m); delete h; return fail(IMGA_ERR_CUDA, err.empty() ? "batch upload" : err); }
+    *out = h;
+    return IMGA_OK;
+}
+
+imga_status imga_mesh_problems(imga_mesh h, int* n_problems, int64_t* elem_off, int64_t* node_off) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    const imga::Mesh& m = h->m;
+    const int np = m.batched ? (int)m.prob_elem_off.size() : 1;
+    if (n_problems) *n_problems = np;
+    for (int p = 0; p <= np; ++p) {
+        if (elem_off) elem_off[p] = !m.batched ? (p ? m.n_elem() : 0) : (p < np ? m.prob_elem_off[p] : m.n_elem());
+        if (node_off) node_off[p] = !m.batched ? (p ? m.n_nodes() : 0) : (p < np ? m.prob_node_off[p] : m.n_nodes());
+    }
+    return IMGA_OK;
+}
+
 void imga_destroy_mesh(imga_mesh h) {
     if (!h) return;
     if (h->m.host_only) { delete h; return; }
     imga::profile_reset(h->m);
     imga::solver_free(h->m);
+    imga::graphs_free(h->m);
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(h->m.device);
@@ -203,6 +247,7 @@ imga_status imga_export_surface_points(imga_mesh h, double* out) {
 imga_status imga_classify(imga_mesh h, const double* pts, int64_t n, uint8_t* flags, void* stream) {
     if (!h || n < 0 || (n > 0 && (!pts || !flags))) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
     if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (h->m.batched) return fail(IMGA_ERR_INVALID_ARG, "classify a point against one of the problems' own meshes");
     if (imga::device_classify(h->m, pts, n, flags, stream)) return cuda_status("classify");
     return IMGA_OK;
 }
@@ -344,6 +389,19 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
     return IMGA_OK;
 }
 
+imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
+    if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    switch (option) {
+        case IMGA_OPT_GRAPHS:
+            if (!value) imga::graphs_free(h->m);
+            h->m.use_graphs = value != 0;
+            return IMGA_OK;
+        default:
+            return fail(IMGA_ERR_INVALID_ARG, "unknown option");
+    }
+}
+
 imga_status imga_profile(imga_mesh h, int enable) {
     if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
     if (enable) imga::profile_reset(h->m);
@@ -380,6 +438,7 @@ imga_status imga_set_dirichlet(imga_mesh h, const uint8_t* mask, const double* v
     if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
     if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
     imga::Mesh& m = h->m;
+    imga::graphs_free(m);   // graphs bake the boundary rows in
     if (!mask && !val) { m.user_bc = false; return IMGA_OK; }
     if (!mask || !val) return fail(IMGA_ERR_INVALID_ARG, "mask and values go together");
     const int64_t nn = m.n_nodes();

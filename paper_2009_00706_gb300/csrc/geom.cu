@@ -410,6 +410,34 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
     return true;
 }
 
+// the arrays a batched mesh (several problems merged) needs for residual / J v / Jacobians
+bool device_upload_batch(Mesh& m, std::string& err) {
+    DeviceMesh& d = m.d;
+    d.n_elem = m.n_elem();
+    d.n_nodes = m.n_nodes();
+    d.n_hang = m.n_hang();
+    d.n_tri = 0;
+    std::vector<int32_t> hp(m.hpar);
+    std::vector<int32_t> oc(8 * m.out_list.size());
+    std::vector<uint8_t> ol(m.out_list.size());
+    std::vector<uint16_t> op(m.out_list.size());
+    for (size_t i = 0; i < m.out_list.size(); ++i) {
+        for (int c = 0; c < 8; ++c) oc[8 * i + c] = m.conn[8 * (size_t)m.out_list[i] + c];
+        ol[i] = m.lev[m.out_list[i]];
+        op[i] = m.eprob[m.out_list[i]];
+    }
+    std::vector<float> ptsf(m.cut_pts.begin(), m.cut_pts.end());
+    std::vector<float> muf(m.pmu.begin(), m.pmu.end());
+    if (!upload(&d.lev, m.lev, err) || !upload(&d.conn, m.conn, err) || !upload(&d.hpar, hp, err) ||
+        !upload(&d.marker, m.marker, err) || !upload(&d.cflags, m.cflags, err) || !upload(&d.out_list, m.out_list, err) ||
+        !upload(&d.out_conn, oc, err) || !upload(&d.out_lev, ol, err) || !upload(&d.out_prob, op, err) ||
+        !upload(&d.cut_list, m.cut_list, err) || !upload(&d.cut_off, m.cut_off, err) ||
+        !upload(&d.cut_pts, m.cut_pts, err) || !upload(&d.cut_pts_f, ptsf, err) || !upload(&d.eprob, m.eprob, err) ||
+        !upload(&d.pmu, m.pmu, err) || !upload(&d.pmuf, muf, err))
+        return false;
+    return device_upload_quadrature(m, err);
+}
+
 int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream) {
     if (n <= 0) return 0;
     GeomView g = view(m);
@@ -420,7 +448,7 @@ int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags,
 void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
-                    d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
+                    d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
                     d.sq_n, d.sq_w, d.sq_taub, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot};
     for (void* p : ptrs)
         if (p) cudaFree(p);

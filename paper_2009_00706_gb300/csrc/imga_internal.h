@@ -69,6 +69,10 @@ struct DeviceMesh {
     int32_t* out_list = nullptr;  // Out elements
     int32_t* out_conn = nullptr;  // [n_out][8] their corner -> node (or n_nodes + hanging) indices
     uint8_t* out_lev = nullptr;   // [n_out] their levels
+    uint16_t* out_prob = nullptr; // [n_out] their problem (batched meshes), else null
+    uint16_t* eprob = nullptr;    // [n_elem] problem of every element (batched meshes), else null
+    double* pmu = nullptr;        // [n_prob] viscosity of every problem (batched meshes)
+    float* pmuf = nullptr;
     int32_t* cut_list = nullptr;  // Intercepted elements
     int64_t* cut_off = nullptr;   // [n_cut + 1] into cut_pts
     double* cut_pts = nullptr;    // [n][4] (xi0, xi1, xi2, reference weight)
@@ -87,6 +91,14 @@ struct DeviceMesh {
     uint8_t* bcflag = nullptr;    // [n_nodes] bits 0-3 box Dirichlet, bit 4 In-only node
     uint8_t* bcmask_user = nullptr;
     double* bcval_user = nullptr;
+};
+
+struct GraphKey {
+    const double *u, *up, *up2, *f, *v;
+    double* out;
+    int precision;
+    int user_bc;
+    imga_physics ph;
 };
 
 struct Mesh {
@@ -117,9 +129,20 @@ struct Mesh {
     std::vector<double> sq;              // [n][10] surface points (export layout)
     std::vector<uint8_t> bcflag;
     int64_t n_in = 0, n_rays = 0;
+    // batched meshes: element -> problem, per-problem viscosity and element/node offsets
+    std::vector<uint16_t> eprob;
+    std::vector<double> pmu;
+    std::vector<int64_t> prob_elem_off, prob_node_off;
     double setup_ms[4] = {0, 0, 0, 0};
     bool user_bc = false;
     bool host_only = false;
+    bool batched = false;
+    // CUDA-graph execution of residual / J v (imga_set_option): cached executable graphs keyed by the
+    // call's pointers and parameters, and two side streams + fork/join events for parallel branches
+    bool use_graphs = false;
+    std::vector<std::pair<GraphKey, void*>> graphs;
+    void* side[3] = {nullptr, nullptr, nullptr};   // two branch streams + the private capture stream
+    void* fork_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // fork, 2 joins, caller->graph, graph->caller
     int n_sm = 1;                        // streaming multiprocessors of the device
     DeviceMesh d;
     void* scratch = nullptr;             // device workspace for the kernels
@@ -151,6 +174,7 @@ bool device_upload_geometry(Mesh& m, std::string& err);
 bool device_markers(Mesh& m, std::string& err);
 bool device_cut_quadrature(Mesh& m, std::string& err);
 bool device_upload_quadrature(Mesh& m, std::string& err);
+bool device_upload_batch(Mesh& m, std::string& err);
 int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream);
 void device_free(Mesh& m);
 
@@ -166,6 +190,7 @@ int vms_jvp_noalloc(const Mesh& m, const double* u, const double* up, const doub
 
 void profile_reset(Mesh& m);
 int profile_collect(Mesh& m);
+void graphs_free(Mesh& m);
 
 // element Jacobians and block-Jacobi (jac.cu)
 int element_jacobians(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
@@ -197,6 +222,8 @@ int gemm_bf16_test(int M, int N, int K, const float* A, const float* B, float* C
 int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const double* f, const imga_physics& ph,
                  const imga_solver_opts& o, imga_solver_stats* stats, void* stream, std::string& err);
 void solver_free(Mesh& m);
+
+bool merge_meshes(Mesh& m, const std::vector<const Mesh*>& parts, const std::vector<double>& mu, std::string& err);
 
 void set_error(const std::string& s);
 

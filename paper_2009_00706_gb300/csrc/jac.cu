@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(8 * JacShape<T>::EPB) jac_out(Args A, const in
             Fields<Dual<T>, T> F;
             seed_fields<T>(A, V, g, phb, dphb, d2b, k, F);
             Dual<T> cf[16];
-            pointwise<Dual<T>, T>(A, F, g, cf);
+            pointwise<Dual<T>, T>(A, Phys<T>(A, prob_of(A, e)), F, g, cf);
             for (int q = 0; q < 16; ++q) s_cf[le][c][q] = ((q < 3 || q == 12) ? wq : wqg) * cf[q].d;
             __syncwarp();
             T r[4] = {T(0), T(0), T(0), T(0)};
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(32 * JWPB) jac_cut(Args A, const int32_t* __re
             Fields<Dual<T>, T> F;
             seed_fields<T>(A, V, g, phb, dphb, d2b, k, F);
             Dual<T> cf[16];
-            pointwise<Dual<T>, T>(A, F, g, cf);
+            pointwise<Dual<T>, T>(A, Phys<T>(A, prob_of(A, e)), F, g, cf);
             for (int qq = 0; qq < 16; ++qq) s_cf[w][lane][qq] = ((qq < 3 || qq == 12) ? wq : wqg) * cf[qq].d;
             s_cf[w][lane][16] = pt[0];
             s_cf[w][lane][17] = pt[1];
@@ -242,12 +242,14 @@ __global__ void __launch_bounds__(128) jac_nitsche(Args A, const int32_t* __rest
     NitschePoint<T, T> V;
     nitsche_fields<T, T, false>(A, e, xr + 3 * i, nr + 3 * i, V);
     const T w = (T)wr[i];
-    const T tauB = (T)(A.Cb * A.mu * taub[i]);
+    const T tauB = (T)(A.Cb * (double)V.mu * taub[i]);
     for (int b = 0; b < 8; ++b) {
         for (int k = 0; k < 4; ++k) {
             // tangent point data of the seed (corner b, component k)
             NitschePoint<Dual<T>, T> P;
             P.g = V.g;
+            P.mu = V.mu;
+            P.rho = V.rho;
             P.B = V.B;
             for (int c = 0; c < 8; ++c) P.ids[c] = V.ids[c];
             for (int j = 0; j < 3; ++j) P.nn[j] = V.nn[j];

@@ -227,7 +227,7 @@ __global__ void dataset_kernel(Args A, int64_t n, const int32_t* __restrict__ el
             gather(A, A.U, A.conn[8 * (int64_t)e + c], u4);
             uu += sqrt(u4[0] * u4[0] + u4[1] * u4[1] + u4[2] * u4[2]) / 8.0;
         }
-        const double nu = A.mu / A.rho;
+        const double nu = (A.eprob ? A.pmu[A.eprob[e]] : A.mu) / A.rho;
         xo[1024] = (float)log(h);
         xo[1025] = marker[e] == 2 ? 1.f : 0.f;
         xo[1026] = (float)log10(1.0 + uu * h / (nu > 0.0 ? nu : 1e-300));

@@ -27,6 +27,7 @@
 
 #include <cstdio>
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -55,7 +56,8 @@ template <class T> struct IntShape {
 // gathers corner c, evaluates Gauss point c, then contracts node c's four rows.
 template <class T, bool JV>
 __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, const int32_t* __restrict__ oconn,
-                                                    const uint8_t* __restrict__ olev, int64_t n) {
+                                                    const uint8_t* __restrict__ olev,
+                                                    const uint16_t* __restrict__ oprob, int64_t n) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
     constexpr int EPB = IntShape<T>::EPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -96,8 +98,9 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
         const bool valid = idx < n;
         const int lv = __ldg(olev + (valid ? idx : n - 1));
         const T g = lvl_g<T>(A, lv);
+        const Phys<T> P(A, oprob ? (int)oprob[valid ? idx : n - 1] : -1);
         S cf[16];
-        vms_point<S, T>(A, fm, fp, s_nd + (buf * EPB + le) * 8 * CS, CS, g, cf);
+        vms_point<S, T>(A, P, fm, fp, s_nd + (buf * EPB + le) * 8 * CS, CS, g, cf);
         const T wq = lvl_w<T>(A, lv), wqg = wq * g;
         T* mycf = s_cf + (le * 8 + c) * 17;
         // F, G multiply phi; S, H multiply physical gradients = g x reference gradients
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(32 * WPB) vms_cut(Args A, const int32_t* __res
             T fm[3], fp[3];
             for (int k = 0; k < 3; ++k) { fm[k] = T(0.5) * (T(1) - pt[k]); fp[k] = T(0.5) * (T(1) + pt[k]); }
             S cf[16];
-            vms_point<S, T>(A, fm, fp, &s_nd[w][0][0], CS, g, cf);
+            vms_point<S, T>(A, Phys<T>(A, prob_of(A, e)), fm, fp, &s_nd[w][0][0], CS, g, cf);
             const T wq = pt[3] * det, wqg = wq * g;
             for (int k = 0; k < 16; ++k) s_cf[w][lane][k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
             s_cf[w][lane][16] = pt[0];
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
     NitschePoint<S, T> P;
     nitsche_fields<S, T, JV>(A, el[i], xr + 3 * i, nr + 3 * i, P);
     const T w = (T)wr[i];
-    const T tauB = (T)(A.Cb * A.mu * taub[i]);
+    const T tauB = (T)(A.Cb * (double)P.mu * taub[i]);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         S t[4];
@@ -263,8 +266,23 @@ struct Timed {
     }
 };
 
+// Resident CTAs of the persistent interior kernel per SM (queried once; also sets its dynamic smem opt-in).
 template <class T, bool JV>
-void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr) {
+int interior_blocks_per_sm() {
+    static int bps = 0;
+    if (bps == 0) {
+        const size_t smem = IntShape<T>::smem;
+        int b = 0;
+        cudaFuncSetAttribute(vms_interior<T, JV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, vms_interior<T, JV>, 8 * Epb<T>::value, smem);
+        bps = b < 1 ? 1 : b;
+    }
+    return bps;
+}
+
+template <class T, bool JV>
+void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaStream_t s_cut = nullptr,
+                cudaStream_t s_sur = nullptr, cudaEvent_t* ev = nullptr) {
     const int64_t next = m.n_nodes() + m.n_hang();
     T* ndv = node_workspace<T>(m, ws);
     T* ndt = ndv + 8 * next;
@@ -276,53 +294,121 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr) {
         Timed t(m, 4, s);
         node_prep<T, JV><<<(unsigned)((next + 255) / 256), 256, 0, s>>>(A, ndv, ndt, ndf);
     }
+    // fork: the Intercepted-element and surface kernels run beside the Out-element kernel
+    const cudaStream_t sc = s_cut ? s_cut : s, ss = s_sur ? s_sur : s;
+    if (ev) {
+        cudaEventRecord(ev[0], s);
+        cudaStreamWaitEvent(sc, ev[0], 0);
+        cudaStreamWaitEvent(ss, ev[0], 0);
+    }
     const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size(), ns = (int64_t)m.sq.size() / 10;
     constexpr int EPB = Epb<T>::value;
     if (no > 0) {
         Timed t(m, 0, s);
-        static int per_sm[2][2] = {{0, 0}, {0, 0}};
-        int& bps = per_sm[sizeof(T) == 8][JV];
+        const int bps = interior_blocks_per_sm<T, JV>();
         const size_t smem = IntShape<T>::smem;
-        if (bps == 0) {
-            cudaFuncSetAttribute(vms_interior<T, JV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, vms_interior<T, JV>, 8 * EPB, smem);
-            if (bps < 1) bps = 1;
-        }
         const int64_t groups = (no + EPB - 1) / EPB;
         const int64_t grid = std::min<int64_t>(groups, (int64_t)bps * m.n_sm);
-        vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, smem, s>>>(A, m.d.out_conn, m.d.out_lev, no);
+        vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, smem, s>>>(A, m.d.out_conn, m.d.out_lev, m.d.out_prob, no);
     }
     if (nc > 0) {
-        Timed t(m, 1, s);
+        Timed t(m, 1, sc);
         const void* pts = std::is_same<T, float>::value ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
-        vms_cut<T, JV><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, 0, s>>>(A, m.d.cut_list, m.d.cut_off, pts, nc);
+        vms_cut<T, JV><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, 0, sc>>>(A, m.d.cut_list, m.d.cut_off, pts, nc);
     }
     if (ns > 0) {
-        Timed t(m, 2, s);
-        nitsche<T, JV><<<(unsigned)((ns + 127) / 128), 128, 0, s>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
-                                                                    m.d.sq_taub, ns);
+        Timed t(m, 2, ss);
+        nitsche<T, JV><<<(unsigned)((ns + 127) / 128), 128, 0, ss>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
+                                                                     m.d.sq_taub, ns);
+    }
+    if (ev) {   // join
+        cudaEventRecord(ev[1], sc);
+        cudaEventRecord(ev[2], ss);
+        cudaStreamWaitEvent(s, ev[1], 0);
+        cudaStreamWaitEvent(s, ev[2], 0);
     }
 }
 
-}  // namespace
-
-static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
-                        const imga_physics& ph, int precision, const double* v, double* out, void* stream, void* ws) {
-    cudaStream_t s = (cudaStream_t)stream;
-    Args A = make_args(m, u, up, up2, f, ph, v, out);
-    const bool jv = v != nullptr;
-    if (cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
-    if (precision == 0) {
-        if (jv) launch_all<double, true>(m, A, s, ws); else launch_all<double, false>(m, A, s, ws);
-    } else {
-        if (jv) launch_all<float, true>(m, A, s, ws); else launch_all<float, false>(m, A, s, ws);
-    }
+void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bool jv, cudaStream_t s) {
     const int64_t nn = m.n_nodes();
     Timed t(m, 3, s);
     if (nn > 0)
         strong_rows<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(A, m.d.bcflag, m.user_bc ? m.d.bcmask_user : nullptr,
                                                                 m.user_bc ? m.d.bcval_user : nullptr, ph.u_inf[0],
                                                                 ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
+}
+
+}  // namespace
+
+void graphs_free(Mesh& m) {
+    for (auto& g : m.graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
+    m.graphs.clear();
+    for (int k = 0; k < 3; ++k) if (m.side[k]) { cudaStreamDestroy((cudaStream_t)m.side[k]); m.side[k] = nullptr; }
+    for (int k = 0; k < 5; ++k) if (m.fork_ev[k]) { cudaEventDestroy((cudaEvent_t)m.fork_ev[k]); m.fork_ev[k] = nullptr; }
+}
+
+static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                        const imga_physics& ph, int precision, const double* v, double* out, void* stream, void* ws) {
+    cudaStream_t s = (cudaStream_t)stream;
+    Args A = make_args(m, u, up, up2, f, ph, v, out);
+    const bool jv = v != nullptr;
+    if (m.use_graphs && !ws && !m.profiling) {
+        // Replay (or capture once) the whole call as a CUDA graph with parallel branches.  Capture runs on
+        // a private stream (the legacy default stream cannot be captured); the graph is launched on a
+        // private stream too, ordered after the caller's stream by events and joined back into it.
+        Mesh& mm = const_cast<Mesh&>(m);
+        GraphKey key;
+        std::memset(&key, 0, sizeof(key));
+        key.u = u; key.up = up; key.up2 = up2; key.f = f; key.v = v; key.out = out;
+        key.precision = precision;
+        key.ph = ph;
+        key.user_bc = m.user_bc;
+        if (!mm.side[0]) {
+            for (int k = 0; k < 3; ++k)
+                if (cudaStreamCreateWithFlags((cudaStream_t*)&mm.side[k], cudaStreamNonBlocking) != cudaSuccess) return 1;
+            for (int k = 0; k < 5; ++k)
+                if (cudaEventCreateWithFlags((cudaEvent_t*)&mm.fork_ev[k], cudaEventDisableTiming) != cudaSuccess) return 1;
+        }
+        cudaStream_t s1 = (cudaStream_t)mm.side[0], s2 = (cudaStream_t)mm.side[1], cs = (cudaStream_t)mm.side[2];
+        cudaEvent_t* ev = (cudaEvent_t*)mm.fork_ev;
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : mm.graphs)
+            if (std::memcmp(&g.first, &key, sizeof(key)) == 0) { exec = (cudaGraphExec_t)g.second; break; }
+        if (!exec) {
+            if (precision == 0) { interior_blocks_per_sm<double, true>(); interior_blocks_per_sm<double, false>(); }
+            else { interior_blocks_per_sm<float, true>(); interior_blocks_per_sm<float, false>(); }
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return 1;
+            cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), cs);
+            if (precision == 0) {
+                if (jv) launch_all<double, true>(m, A, cs, nullptr, s1, s2, ev); else launch_all<double, false>(m, A, cs, nullptr, s1, s2, ev);
+            } else {
+                if (jv) launch_all<float, true>(m, A, cs, nullptr, s1, s2, ev); else launch_all<float, false>(m, A, cs, nullptr, s1, s2, ev);
+            }
+            launch_strong_rows(m, A, ph, jv, cs);
+            const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+            if (ec != cudaSuccess || !graph) return 1;
+            const cudaError_t rc = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (rc != cudaSuccess) return 1;
+            if (mm.graphs.size() >= 32) {   // bounded cache: drop the oldest
+                cudaGraphExecDestroy((cudaGraphExec_t)mm.graphs.front().second);
+                mm.graphs.erase(mm.graphs.begin());
+            }
+            mm.graphs.push_back({key, (void*)exec});
+        }
+        if (cudaEventRecord(ev[3], s) != cudaSuccess || cudaStreamWaitEvent(cs, ev[3], 0) != cudaSuccess) return 1;
+        if (cudaGraphLaunch(exec, cs) != cudaSuccess) return 1;
+        if (cudaEventRecord(ev[4], cs) != cudaSuccess || cudaStreamWaitEvent(s, ev[4], 0) != cudaSuccess) return 1;
+        return 0;
+    }
+    if (cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
+    if (precision == 0) {
+        if (jv) launch_all<double, true>(m, A, s, ws); else launch_all<double, false>(m, A, s, ws);
+    } else {
+        if (jv) launch_all<float, true>(m, A, s, ws); else launch_all<float, false>(m, A, s, ws);
+    }
+    launch_strong_rows(m, A, ph, jv, s);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

@@ -92,6 +92,12 @@ struct Args {
     double Cb;
     double g[3];
     int drop_visc;
+    // batched meshes: element -> problem and the viscosity of every problem (null: the scalars)
+    const uint16_t* eprob;
+    const double* pmu;
+    const float* pmuf;
+    double CI;
+    float CIf;
 };
 
 // node values through the hanging-node interpolation (u_e = M_e U)
@@ -243,12 +249,20 @@ __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T*
 template <class T> struct Phys;
 template <> struct Phys<float> {
     float rho, mu, irho, K0, CI3;
-    __device__ Phys(const Args& A) : rho(A.rhof), mu(A.muf), irho(A.irhof), K0(A.K0f), CI3(A.CI3f) {}
+    // p: problem of the element in a batched mesh, or -1
+    __device__ Phys(const Args& A, int p) : rho(A.rhof), mu(A.muf), irho(A.irhof), K0(A.K0f), CI3(A.CI3f) {
+        if (p >= 0) { mu = A.pmuf[p]; const float nu = mu * irho; CI3 = 3.f * A.CIf * nu * nu; }
+    }
 };
 template <> struct Phys<double> {
     double rho, mu, irho, K0, CI3;
-    __device__ Phys(const Args& A) : rho(A.rho), mu(A.mu), irho(A.irho), K0(A.K0dt), CI3(A.CI3) {}
+    __device__ Phys(const Args& A, int p) : rho(A.rho), mu(A.mu), irho(A.irho), K0(A.K0dt), CI3(A.CI3) {
+        if (p >= 0) { mu = A.pmu[p]; const double nu = mu * irho; CI3 = 3.0 * A.CI * nu * nu; }
+    }
 };
+
+// problem of element e in a batched mesh, -1 otherwise
+__device__ __forceinline__ int prob_of(const Args& A, int32_t e) { return A.eprob ? (int)A.eprob[e] : -1; }
 
 template <class T> __device__ __forceinline__ T lvl_g(const Args& A, int l);
 template <> __device__ __forceinline__ float lvl_g<float>(const Args& A, int l) { return A.gf[l]; }
@@ -348,8 +362,7 @@ __device__ __forceinline__ void interp(const Args& A, const T fm[3], const T fp[
 
 // Pointwise VMS: fields -> the 16 coefficients (F, S, G, H) of Eq. (vms).
 template <class S, class T>
-__device__ __forceinline__ void pointwise(const Args& A, const Fields<S, T>& F, T g, S out[16]) {
-    const Phys<T> P(A);
+__device__ __forceinline__ void pointwise(const Args& A, const Phys<T>& P, const Fields<S, T>& F, T g, S out[16]) {
     const T g2 = g * g;
     S divu = F.Gu[0][0] + F.Gu[1][1] + F.Gu[2][2];
     S conv[3], rM[3];
@@ -384,11 +397,11 @@ __device__ __forceinline__ void pointwise(const Args& A, const Fields<S, T>& F, 
 }
 
 template <class S, class T>
-__device__ __forceinline__ void vms_point(const Args& A, const T fm[3], const T fp[3], const T* nd, int stride, T g,
-                                          S out[16]) {
+__device__ __forceinline__ void vms_point(const Args& A, const Phys<T>& P, const T fm[3], const T fp[3], const T* nd,
+                                          int stride, T g, S out[16]) {
     Fields<S, T> F;
     interp<S, T>(A, fm, fp, nd, stride, g, F);
-    pointwise<S, T>(A, F, g, out);
+    pointwise<S, T>(A, P, F, g, out);
 }
 
 template <class T, bool JV> struct Pick;
@@ -414,6 +427,7 @@ template <> __device__ __forceinline__ void load_pt<float>(const void* pts, int6
 template <class S, class T>
 struct NitschePoint {
     T g, nn[3];
+    T mu, rho;
     Basis<T> B;
     int32_t ids[8];
     S us[3], Gu[3][3], p, d[3], un, dn, tr[3];
@@ -424,13 +438,12 @@ template <class S, class T>
 __device__ __forceinline__ void finish_nitsche(const Args& A, NitschePoint<S, T>& P) {
     for (int k = 0; k < 3; ++k)
         for (int j = 0; j < 3; ++j) P.Gu[k][j] = P.g * P.Gu[k][j];
-    const Phys<T> Ph(A);
     const T* nn = P.nn;
     P.un = P.us[0] * nn[0] + P.us[1] * nn[1] + P.us[2] * nn[2];
     P.dn = P.d[0] * nn[0] + P.d[1] * nn[1] + P.d[2] * nn[2];
     P.inflow = value(P.un) < T(0);
     for (int k = 0; k < 3; ++k)
-        P.tr[k] = Ph.mu * ((P.Gu[k][0] + P.Gu[0][k]) * nn[0] + (P.Gu[k][1] + P.Gu[1][k]) * nn[1] +
+        P.tr[k] = P.mu * ((P.Gu[k][0] + P.Gu[0][k]) * nn[0] + (P.Gu[k][1] + P.Gu[1][k]) * nn[1] +
                            (P.Gu[k][2] + P.Gu[2][k]) * nn[2]) - P.p * nn[k];
 }
 
@@ -440,6 +453,11 @@ template <class S, class T, bool JV>
 __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, const double* xr, const double* nr,
                                                NitschePoint<S, T>& P) {
     P.g = lvl_g<T>(A, A.lev[e]);
+    {
+        const Phys<T> Ph(A, prob_of(A, e));
+        P.mu = Ph.mu;
+        P.rho = Ph.rho;
+    }
     T xi[3] = {(T)xr[0], (T)xr[1], (T)xr[2]};
     for (int k = 0; k < 3; ++k) P.nn[k] = (T)nr[k];
     basis<T>(xi, P.B);
@@ -472,14 +490,13 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, const d
 // tau_TAN = tau_NOR: both penalty parts sum to tau_B (u - g)
 template <class S, class T>
 __device__ __forceinline__ void nitsche_rows(const Args& A, const NitschePoint<S, T>& P, int c, T tauB, S t[4]) {
-    const Phys<T> Ph(A);
     const T ph = P.B.phi[c];
     const T* nn = P.nn;
     const T gn = P.g * (P.B.dphi[c][0] * nn[0] + P.B.dphi[c][1] * nn[1] + P.B.dphi[c][2] * nn[2]);
     S gd = P.g * (P.B.dphi[c][0] * P.d[0] + P.B.dphi[c][1] * P.d[1] + P.B.dphi[c][2] * P.d[2]);
     for (int k = 0; k < 3; ++k) {
-        S v = (tauB * ph) * P.d[k] - ph * P.tr[k] - Ph.mu * (gn * P.d[k] + nn[k] * gd);
-        if (P.inflow) v = v - (ph * Ph.rho) * (P.un * P.d[k]);
+        S v = (tauB * ph) * P.d[k] - ph * P.tr[k] - P.mu * (gn * P.d[k] + nn[k] * gd);
+        if (P.inflow) v = v - (ph * P.rho) * (P.un * P.d[k]);
         t[k] = v;
     }
     t[3] = -(ph * P.dn);
@@ -532,6 +549,11 @@ inline Args make_args(const Mesh& m, const double* u, const double* up, const do
     A.Cb = ph.C_b;
     for (int k = 0; k < 3; ++k) A.g[k] = ph.g_body[k];
     A.drop_visc = ph.drop_visc_strong;
+    A.eprob = m.d.eprob;
+    A.pmu = m.d.pmu;
+    A.pmuf = m.d.pmuf;
+    A.CI = ph.C_I;
+    A.CIf = (float)ph.C_I;
     return A;
 }
 

@@ -237,3 +237,45 @@ def state(n_nodes: int, seed: int = 0, sigma: float = 0.01):
     u[:, :3] += normal(seed * 4 + 1, n_nodes * 3, sigma).reshape(n_nodes, 3)
     v = normal(seed * 4 + 2, n_nodes * 4).reshape(n_nodes, 4)
     return u, up, v
+
+
+def _sphere_band_model(level: int, w: float, r: float = 0.1) -> float:
+    """Element-count model of a unit-cube sphere mesh (level 3 far field, `level` within w of the
+    sphere): 512 base elements plus ~1.9 x the band volume over the fine element volume (the factor
+    accounts for the 2:1 transition layers; 1.9 reproduces the small-sphere workload)."""
+    shell = 4.0 / 3.0 * math.pi * ((r + w) ** 3 - max(r - w, 0.0) ** 3)
+    return 512.0 + 1.9 * shell * 8.0 ** level
+
+
+def batched_spheres(n: int = 64, seed0: int = 0):
+    """n independent unit-cube sphere problems (seeds seed0 .. seed0+n-1): target element counts
+    log-uniform in [5k, 200k], Reynolds numbers log-uniform in [1, 1e6] on the diameter 0.2 (mu = 0.2 /
+    Re), BE dt 0.01.  For each problem the finest level (5..8) and the band width are chosen by
+    bisection on the element-count model so that the model meets the target.
+    Returns a list of (Workload, target elements, Re)."""
+    out = []
+    for k in range(n):
+        s = seed0 + k
+        u = uniform(1000 + s, 2)
+        target = math.exp(math.log(5e3) + u[0] * (math.log(2e5) - math.log(5e3)))
+        Re = 10.0 ** (6.0 * u[1])
+        level, w = 8, 0.01
+        for L in (5, 6, 7, 8):
+            if _sphere_band_model(L, 0.09) >= target:
+                level = L
+                break
+        lo, hi = 1e-4, 0.09
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if _sphere_band_model(level, mid) < target:
+                lo = mid
+            else:
+                hi = mid
+        w = 0.5 * (lo + hi)
+        c = (0.5, 0.5, 0.5)
+        wl = Workload(name=f"sphere_{s}", lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), base_level=3,
+                      regions=[Region(REGION_SPHERE_BAND, level, (*c, 0.1, w))], lmax=3,
+                      physics=Physics(rho=1.0, mu=0.2 / Re, dt=0.01, scheme=SCHEME_BE),
+                      surface=(lambda s=s: icosphere(3, 0.1, (0.5, 0.5, 0.5), 1e-4, s)), seed=s)
+        out.append((wl, target, Re))
+    return out
