@@ -17,9 +17,10 @@
 // Kernels (T = float or double element arithmetic, nodal gathers always float64, scatter by
 // float64 atomics):
 //   vms_interior  8 threads per Out element: thread c gathers corner c, evaluates Gauss point c,
-//                 then contracts node c's four rows over the 8 points through shared memory.
-//   vms_cut       one warp per Intercepted element, 32 sub-cell points per step; lane l owns
-//                 row (node l/4, component l%4) of the element vector.
+//                 then contracts node c's four rows over the 8 points; interpolation and test
+//                 functions both run in the monomial form of the trilinear basis.
+//   vms_cut       one warp per Intercepted element; lane l evaluates sub-cell points l, l + 32, ...
+//                 and accumulates their monomial moments, summed over the lanes at the end.
 //   nitsche       one thread per surface point (points sorted by element).
 //   strong_rows   Dirichlet rows U - g and In-only rows, written after every scatter.
 
@@ -47,22 +48,28 @@ template <class T> struct Epb { static constexpr int value = sizeof(T) == 8 ? 16
 template <class T> struct IntShape {
     static constexpr int EPB = Epb<T>::value;                                   // elements per block
     static constexpr int THREADS = 8 * EPB;
-    static constexpr size_t smem = (size_t)(2 * EPB * 8 * CS + EPB * 8 * 17) * sizeof(T);
+    // element stride of the corner rows: 8 rows of CS plus 8 T, so the elements of a warp start 8
+    // (float) or 16 (double) banks apart and column and broadcast row reads are conflict-free
+    static constexpr int ESTR = 8 * CS + 8;
+    static constexpr int MSTR = 32 + 16 / (int)sizeof(T);   // row stride of the per-point moments
+    static constexpr size_t smem = (size_t)(2 * EPB * ESTR + EPB * 8 * MSTR) * sizeof(T);
 };
 
 // Persistent: a block walks element groups with a grid stride; while it computes group g its
 // threads already stream the node rows of group g + stride into the other shared buffer
 // (cp.async), so the gather latency hides behind the arithmetic.  Thread c of an element
-// gathers corner c, evaluates Gauss point c, then contracts node c's four rows.
+// gathers corner c, transforms column c of the element's rows into monomial coefficients,
+// evaluates Gauss point c, writes the point's 32 monomial moments,
+// then sums moment column S = c over the 8 points and runs the backward butterfly: node c's rows.
 template <class T, bool JV>
 __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, const int32_t* __restrict__ oconn,
                                                     const uint8_t* __restrict__ olev,
                                                     const uint16_t* __restrict__ oprob, int64_t n) {
-    typedef typename std::conditional<JV, Dual<T>, T>::type S;
-    constexpr int EPB = IntShape<T>::EPB;
+    typedef typename std::conditional<JV, Dual<T, sizeof(T) == 4>, T>::type S;
+    constexpr int EPB = IntShape<T>::EPB, ESTR = IntShape<T>::ESTR, MSTR = IntShape<T>::MSTR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* s_nd = reinterpret_cast<T*>(smem_raw);          // [2][EPB][8][CS]
-    T* s_cf = s_nd + 2 * EPB * 8 * CS;                  // [EPB][8][17]
+    T* s_nd = reinterpret_cast<T*>(smem_raw);          // [2][EPB][ESTR]: 8 rows of CS per element
+    T* s_m = s_nd + 2 * EPB * ESTR;                     // [EPB][8][MSTR]
     const int c = threadIdx.x & 7, le = threadIdx.x >> 3;
     const int64_t ngroups = (n + EPB - 1) / EPB;
     int64_t gi = blockIdx.x;
@@ -72,20 +79,21 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
         if (idx >= n) idx = n - 1;
         return __ldg(oconn + 8 * idx + c);
     };
-    auto row = [&](int buf) -> T* { return s_nd + ((buf * EPB + le) * 8 + c) * CS; };
+    auto row = [&](int buf) -> T* { return s_nd + (buf * EPB + le) * ESTR + c * CS; };
     int32_t id_cur = corner_id(gi);
     corner_async<T, JV>(A, id_cur, row(0));
     cp_commit();
     int32_t id_next = gi + gridDim.x < ngroups ? corner_id(gi + gridDim.x) : 0;
-    const T gauss = (T)0.57735026918962576451;
-    const T wp = T(0.5) * (T(1) + gauss), wm = T(0.5) * (T(1) - gauss);
-    // Gauss point c: 1D factors (1 -/+ xi_k)/2 take the values wp, wm
-    T fm[3], fp[3];
-    for (int k = 0; k < 3; ++k) {
-        const bool plus = (c >> k) & 1;
-        fm[k] = plus ? wm : wp;
-        fp[k] = plus ? wp : wm;
+    // Gauss point c: xi_k = +-1/sqrt(3) by bit k of c
+    T m[8];
+    {
+        const T gauss = (T)0.57735026918962576451;
+        T xi[3];
+        for (int k = 0; k < 3; ++k) xi[k] = ((c >> k) & 1) ? gauss : -gauss;
+        monomials<T>(xi, m);
     }
+    T* mrow = s_m + (le * 8 + c) * MSTR;
+    const T* mcol = s_m + le * 8 * MSTR + 4 * c;
     int buf = 0;
     for (; gi < ngroups; gi += gridDim.x) {
         const int64_t gnext = gi + gridDim.x;
@@ -94,38 +102,44 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
         const int32_t id_after = gnext + gridDim.x < ngroups ? corner_id(gnext + gridDim.x) : 0;
         cp_wait<1>();
         __syncwarp();
+        {   // corner values -> monomial coefficients: thread c transforms column c of the element's rows
+            T* nd = s_nd + (buf * EPB + le) * ESTR;
+            if (c < 7) {
+                column_to_monomial<T>(nd + c);
+                if (JV) column_to_monomial<T>(nd + CT + c);
+            }
+            if (A.ndf && c < 3) column_to_monomial<T>(nd + CF + c);
+        }
+        __syncwarp();
         const int64_t idx = gi * EPB + le;
         const bool valid = idx < n;
         const int lv = __ldg(olev + (valid ? idx : n - 1));
         const T g = lvl_g<T>(A, lv);
         const Phys<T> P(A, oprob ? (int)oprob[valid ? idx : n - 1] : -1);
         S cf[16];
-        vms_point<S, T>(A, P, fm, fp, s_nd + (buf * EPB + le) * 8 * CS, CS, g, cf);
+        vms_point_modal<S, T>(A, P, m, s_nd + (buf * EPB + le) * ESTR, CS, g, cf);
         const T wq = lvl_w<T>(A, lv), wqg = wq * g;
-        T* mycf = s_cf + (le * 8 + c) * 17;
         // F, G multiply phi; S, H multiply physical gradients = g x reference gradients
-        for (int k = 0; k < 16; ++k) mycf[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
+        T w16[16];
+        for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
+        T M[32];
+        for (int k = 0; k < 32; ++k) M[k] = T(0);
+        add_moments<T, true>(m, w16, M);
+        for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
         __syncwarp();
         T r[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            T f[3], d[3];
-            for (int k = 0; k < 3; ++k) {
-                bool same = (((c >> k) & 1) == ((q >> k) & 1));
-                f[k] = same ? wp : wm;
-                d[k] = ((c >> k) & 1) ? T(0.5) : T(-0.5);
-            }
-            T ph = f[0] * f[1] * f[2];
-            T dp[3] = {d[0] * f[1] * f[2], d[1] * f[0] * f[2], d[2] * f[0] * f[1]};
-            const T* C = s_cf + (le * 8 + q) * 17;
-            for (int i = 0; i < 3; ++i) r[i] += ph * C[i] + dp[0] * C[3 + 3 * i] + dp[1] * C[4 + 3 * i] + dp[2] * C[5 + 3 * i];
-            r[3] += ph * C[12] + dp[0] * C[13] + dp[1] * C[14] + dp[2] * C[15];
+            T v[4];
+            ld4s<T>(mcol + q * MSTR, v);
+            r[0] += v[0]; r[1] += v[1]; r[2] += v[2]; r[3] += v[3];
         }
+        for (int k = 0; k < 4; ++k) r[k] = hadamard_bwd<1>(r[k], c);
         if (valid) {
             double rd[4] = {(double)r[0], (double)r[1], (double)r[2], (double)r[3]};
             scatter(A, id_cur, rd);
         }
-        __syncwarp();   // this buffer and s_cf are rewritten by later iterations
+        __syncwarp();   // this buffer and the moments are rewritten by later iterations
         id_cur = id_next;
         id_next = id_after;
         buf ^= 1;
@@ -139,61 +153,64 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
 constexpr int WPB = 4;   // warps per block
 
 template <class T, bool JV>
-__global__ void __launch_bounds__(32 * WPB) vms_cut(Args A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 4 : 2) vms_cut(Args A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
                                                     const void* __restrict__ pts, int64_t n) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
-    __shared__ T s_nd[WPB][8][CS];
-    __shared__ T s_cf[WPB][32][20];
+    constexpr int PAD = 16 / (int)sizeof(T), MSTR = 32 + PAD;
+    __shared__ __align__(16) T s_nd[WPB][8 * CS];
+    __shared__ __align__(16) T s_m[WPB][32 * MSTR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t idx = (int64_t)blockIdx.x * WPB + w;
     if (idx >= n) return;
     const int32_t e = list[idx];
-    int32_t my_id = 0;
-    if (lane < 8) {
-        my_id = A.conn[8 * (int64_t)e + lane];
-        corner_data<T, JV>(A, my_id, &s_nd[w][lane][0]);
+    // every 8-lane group gathers the 8 corner rows and forms their monomial coefficients; lanes 0-7 store them
+    const int c8 = lane & 7;
+    const int32_t my_id = A.conn[8 * (int64_t)e + c8];
+    {
+        T rw[CS];
+        corner_data<T, JV>(A, my_id, rw);
+        for (int j = 0; j < 7; ++j) rw[j] = hadamard_fwd(rw[j], c8);
+        if (JV)
+            for (int j = 0; j < 7; ++j) rw[CT + j] = hadamard_fwd(rw[CT + j], c8);
+        if (A.ndf)
+            for (int j = 0; j < 3; ++j) rw[CF + j] = hadamard_fwd(rw[CF + j], c8);
+        if (lane < 8)
+            for (int j = 0; j < CS; ++j) s_nd[w][lane * CS + j] = rw[j];
     }
     __syncwarp();
     const T g = lvl_g<T>(A, A.lev[e]);
     const T det = lvl_w<T>(A, A.lev[e]);
-    const int a = lane >> 2, comp = lane & 3;
-    const T sa[3] = {(a & 1) ? T(1) : T(-1), (a & 2) ? T(1) : T(-1), (a & 4) ? T(1) : T(-1)};
-    T acc = T(0);
+    const Phys<T> P(A, prob_of(A, e));
+    // lane l evaluates points q0 + l, q0 + l + 32, ... and accumulates their monomial moments
+    T M[32];
+    for (int k = 0; k < 32; ++k) M[k] = T(0);
     const int64_t q0 = off[idx], q1 = off[idx + 1];
-    for (int64_t base = q0; base < q1; base += 32) {
-        const int64_t q = base + lane;
-        if (q < q1) {
-            T pt[4];
-            load_pt<T>(pts, q, pt);
-            T fm[3], fp[3];
-            for (int k = 0; k < 3; ++k) { fm[k] = T(0.5) * (T(1) - pt[k]); fp[k] = T(0.5) * (T(1) + pt[k]); }
-            S cf[16];
-            vms_point<S, T>(A, Phys<T>(A, prob_of(A, e)), fm, fp, &s_nd[w][0][0], CS, g, cf);
-            const T wq = pt[3] * det, wqg = wq * g;
-            for (int k = 0; k < 16; ++k) s_cf[w][lane][k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
-            s_cf[w][lane][16] = pt[0];
-            s_cf[w][lane][17] = pt[1];
-            s_cf[w][lane][18] = pt[2];
-        } else {
-            for (int k = 0; k < 19; ++k) s_cf[w][lane][k] = T(0);
-        }
-        __syncwarp();
-        const int m = (int)min((int64_t)32, q1 - base);
-        for (int j = 0; j < m; ++j) {
-            const T* C = s_cf[w][j];
-            T f0 = T(0.5) * (T(1) + sa[0] * C[16]), f1 = T(0.5) * (T(1) + sa[1] * C[17]), f2 = T(0.5) * (T(1) + sa[2] * C[18]);
-            T ph = f0 * f1 * f2;
-            T d0 = T(0.5) * sa[0] * f1 * f2, d1 = T(0.5) * sa[1] * f0 * f2, d2 = T(0.5) * sa[2] * f0 * f1;
-            if (comp < 3) acc += ph * C[comp] + d0 * C[3 + 3 * comp] + d1 * C[4 + 3 * comp] + d2 * C[5 + 3 * comp];
-            else acc += ph * C[12] + d0 * C[13] + d1 * C[14] + d2 * C[15];
-        }
-        __syncwarp();
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+        T pt[4];
+        load_pt<T>(pts, q, pt);
+        T m[8];
+        monomials<T>(pt, m);
+        S cf[16];
+        vms_point_modal<S, T>(A, P, m, &s_nd[w][0], CS, g, cf);
+        const T wq = pt[3] * det, wqg = wq * g;
+        T w16[16];
+        for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
+        add_moments<T, false>(m, w16, M);
     }
-    // gather the four components of node a into lane 4a, then scatter
+    // sum the moments over the lanes (transpose through shared memory): lane l gets moment l = 4 S + k
+    T* mrow = &s_m[w][lane * MSTR];
+    for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
+    __syncwarp();
+    T acc = T(0);
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) acc += s_m[w][t * MSTR + lane];
+    // backward butterfly over S = lane >> 2: lane 4 a + k now holds row (node a, component k)
+    acc = hadamard_bwd<4>(acc, lane >> 2);
+    const int a = lane >> 2;
     double r[4];
     for (int k = 0; k < 4; ++k) r[k] = (double)__shfl_sync(0xffffffffu, acc, (lane & ~3) + k);
-    int32_t id = __shfl_sync(0xffffffffu, my_id, a);
-    if (comp == 0) scatter(A, id, r);
+    const int32_t id = __shfl_sync(0xffffffffu, my_id, a);
+    if ((lane & 3) == 0) scatter(A, id, r);
 }
 
 // ------------------------------------------------------------------------------------------

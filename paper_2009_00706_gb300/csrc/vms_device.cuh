@@ -17,44 +17,84 @@ namespace {
 // ------------------------------------------------------------------------------------------
 // scalars: plain T or dual (value, tangent)
 // ------------------------------------------------------------------------------------------
-template <class T> struct Dual { T v, d; };
+// K = 1: float duals on the packed FP32x2 pipe (see below); K = 0: plain scalar arithmetic
+template <class T, int K = 0> struct alignas(2 * sizeof(T)) Dual { T v, d; };
 
-template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
-template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return {a.v + b, a.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return {a.v - b, a.d}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator+(Dual<T, K> a, Dual<T, K> b) { return {a.v + b.v, a.d + b.d}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator-(Dual<T, K> a, Dual<T, K> b) { return {a.v - b.v, a.d - b.d}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator-(Dual<T, K> a) { return {-a.v, -a.d}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator*(Dual<T, K> a, Dual<T, K> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator*(T a, Dual<T, K> b) { return {a * b.v, a * b.d}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator*(Dual<T, K> a, T b) { return {a.v * b, a.d * b}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator+(Dual<T, K> a, T b) { return {a.v + b, a.d}; }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> operator-(Dual<T, K> a, T b) { return {a.v - b, a.d}; }
+
+// Packed float duals: (value, tangent) is one register pair, so a sum, a real multiple or a fused
+// real multiply-add of duals is one FP32x2 instruction.  Pays where scalars broadcast into pairs
+// are reused (the Out-element kernel); kernels with higher register pressure keep K = 0.
+typedef Dual<float, 1> PDual;
+__device__ __forceinline__ float2 f2(PDual a) { return make_float2(a.v, a.d); }
+__device__ __forceinline__ PDual df(float2 a) { return {a.x, a.y}; }
+__device__ __forceinline__ PDual operator+(PDual a, PDual b) { return df(__fadd2_rn(f2(a), f2(b))); }
+__device__ __forceinline__ PDual operator-(PDual a, PDual b) { return df(__ffma2_rn(f2(b), make_float2(-1.f, -1.f), f2(a))); }
+__device__ __forceinline__ PDual operator*(float a, PDual b) { return df(__fmul2_rn(make_float2(a, a), f2(b))); }
+__device__ __forceinline__ PDual operator*(PDual a, float b) { return df(__fmul2_rn(f2(a), make_float2(b, b))); }
+__device__ __forceinline__ PDual operator*(PDual a, PDual b) {
+    const float2 t = __fmul2_rn(f2(a), make_float2(b.v, b.v));
+    return {t.x, fmaf(a.v, b.d, t.y)};
+}
+
+// acc + s a (s real) and acc + a b, fused
+template <class T> __device__ __forceinline__ T madd(T s, T a, T acc) { return fma(s, a, acc); }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> madd(T s, Dual<T, K> a, Dual<T, K> acc) {
+    return {fma(s, a.v, acc.v), fma(s, a.d, acc.d)};
+}
+__device__ __forceinline__ PDual madd(float s, PDual a, PDual acc) { return df(__ffma2_rn(make_float2(s, s), f2(a), f2(acc))); }
+template <class T> __device__ __forceinline__ T mmadd(T a, T b, T acc) { return fma(a, b, acc); }
+template <class T, int K> __device__ __forceinline__ Dual<T, K> mmadd(Dual<T, K> a, Dual<T, K> b, Dual<T, K> acc) {
+    return {fma(a.v, b.v, acc.v), fma(a.d, b.v, fma(a.v, b.d, acc.d))};
+}
+__device__ __forceinline__ PDual mmadd(PDual a, PDual b, PDual acc) {
+    const float2 t = __ffma2_rn(f2(a), make_float2(b.v, b.v), f2(acc));
+    return {t.x, fmaf(a.v, b.d, t.y)};
+}
+// (a0, a1) += s (x0, x1); the float form on the packed pipe
+template <class T> __device__ __forceinline__ void fma_pair(T s, T x0, T x1, T& a0, T& a1) {
+    a0 = fma(s, x0, a0);
+    a1 = fma(s, x1, a1);
+}
+__device__ __forceinline__ void fma_pair2(float s, float x0, float x1, float& a0, float& a1) {
+    const float2 r = __ffma2_rn(make_float2(s, s), make_float2(x0, x1), make_float2(a0, a1));
+    a0 = r.x;
+    a1 = r.y;
+}
+__device__ __forceinline__ void fma_pair2(double s, double x0, double x1, double& a0, double& a1) { fma_pair(s, x0, x1, a0, a1); }
 
 template <class S> struct Base { typedef S type; };
-template <class T> struct Base<Dual<T>> { typedef T type; };
+template <class T, int K> struct Base<Dual<T, K>> { typedef T type; };
 
 template <class T> __device__ __forceinline__ T value(T a) { return a; }
-template <class T> __device__ __forceinline__ T value(Dual<T> a) { return a.v; }
+template <class T, int K> __device__ __forceinline__ T value(Dual<T, K> a) { return a.v; }
 template <class T> __device__ __forceinline__ T tangent(T) { return T(0); }
-template <class T> __device__ __forceinline__ T tangent(Dual<T> a) { return a.d; }
+template <class T, int K> __device__ __forceinline__ T tangent(Dual<T, K> a) { return a.d; }
 
-template <class S> __device__ __forceinline__ S zero() { return S(0); }
-template <> __device__ __forceinline__ Dual<float> zero<Dual<float>>() { return {0.f, 0.f}; }
-template <> __device__ __forceinline__ Dual<double> zero<Dual<double>>() { return {0.0, 0.0}; }
+template <class S> struct Zero { __device__ static S get() { return S(0); } };
+template <class T, int K> struct Zero<Dual<T, K>> { __device__ static Dual<T, K> get() { return {T(0), T(0)}; } };
+template <class S> __device__ __forceinline__ S zero() { return Zero<S>::get(); }
 
-template <class S, class T> __device__ __forceinline__ S make(T v, T d);
-template <> __device__ __forceinline__ float make<float, float>(float v, float) { return v; }
-template <> __device__ __forceinline__ double make<double, double>(double v, double) { return v; }
-template <> __device__ __forceinline__ Dual<float> make<Dual<float>, float>(float v, float d) { return {v, d}; }
-template <> __device__ __forceinline__ Dual<double> make<Dual<double>, double>(double v, double d) { return {v, d}; }
+template <class S, class T> struct Make { __device__ static S get(T v, T) { return v; } };
+template <class T, int K> struct Make<Dual<T, K>, T> { __device__ static Dual<T, K> get(T v, T d) { return {v, d}; } };
+template <class S, class T> __device__ __forceinline__ S make(T v, T d) { return Make<S, T>::get(v, d); }
 
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-template <class T> __device__ __forceinline__ Dual<T> rsq(Dual<T> x) {
+template <class T, int K> __device__ __forceinline__ Dual<T, K> rsq(Dual<T, K> x) {
     T r = rsq(x.v);
     return {r, T(-0.5) * r * r * r * x.d};
 }
 __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-template <class T> __device__ __forceinline__ Dual<T> rcp(Dual<T> x) {
+template <class T, int K> __device__ __forceinline__ Dual<T, K> rcp(Dual<T, K> x) {
     T r = rcp(x.v);
     return {r, -r * r * x.d};
 }
@@ -147,9 +187,6 @@ __device__ __forceinline__ void scatter(const Args& A, int32_t id, const double 
 // force row (f, 0); 20 T, a multiple of 16 bytes so rows can be filled by 16-byte async copies
 constexpr int CT = 8, CF = 16, CS = 20;
 
-template <class T> struct Vec4;
-template <> struct Vec4<float> { typedef float4 type; };
-template <> struct Vec4<double> { typedef double4 type; };
 
 template <class T>
 __device__ __forceinline__ void ld8(const void* base, int64_t i, T o[8]) {
@@ -365,33 +402,38 @@ template <class S, class T>
 __device__ __forceinline__ void pointwise(const Args& A, const Phys<T>& P, const Fields<S, T>& F, T g, S out[16]) {
     const T g2 = g * g;
     S divu = F.Gu[0][0] + F.Gu[1][1] + F.Gu[2][2];
-    S conv[3], rM[3];
+    S acc[3], rM[3];   // acc = d_t u + u . grad u - f (per unit density)
     for (int i = 0; i < 3; ++i) {
-        conv[i] = F.Gu[i][0] * F.us[0] + F.Gu[i][1] * F.us[1] + F.Gu[i][2] * F.us[2];
-        S r = P.rho * (F.at[i] + conv[i] - F.f[i]) + F.gp[i];
-        rM[i] = A.drop_visc ? r : r - P.mu * F.H2[i];
+        const S conv = mmadd(F.Gu[i][2], F.us[2], mmadd(F.Gu[i][1], F.us[1], F.Gu[i][0] * F.us[0]));
+        acc[i] = F.at[i] + conv - F.f[i];
+        const S r = madd(P.rho, acc[i], F.gp[i]);
+        rM[i] = A.drop_visc ? r : madd(-P.mu, F.H2[i], r);
     }
     // tau_M = (4/dt^2 + u.G u + C_I nu^2 G:G)^(-1/2), G = g^2 I;  tau_C = 1 / (tau_M tr G)
-    S uu = F.us[0] * F.us[0] + F.us[1] * F.us[1] + F.us[2] * F.us[2];
+    S uu = mmadd(F.us[2], F.us[2], mmadd(F.us[1], F.us[1], F.us[0] * F.us[0]));
     S tauM = rsq(g2 * uu + (P.K0 + P.CI3 * (g2 * g2)));
     S tauC = rcp((T(3) * g2) * tauM);
+    const S ntauM = T(-1) * tauM;
     S up[3];
-    for (int i = 0; i < 3; ++i) up[i] = -(tauM * rM[i]);
-    S pp = -(P.rho * tauC * divu);
-    S q = g2 * (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+    for (int i = 0; i < 3; ++i) up[i] = ntauM * rM[i];
+    S pp = (-P.rho) * (tauC * divu);
+    S q = g2 * mmadd(up[2], up[2], mmadd(up[1], up[1], up[0] * up[0]));
     bool bar = value(q) > tiny<T>();
     S taubar = bar ? rsq(q) : zero<S>();
-    S Gup[3];
-    for (int i = 0; i < 3; ++i) Gup[i] = F.Gu[i][0] * up[0] + F.Gu[i][1] * up[1] + F.Gu[i][2] * up[2];
+    const S ppp = F.p + pp;
     for (int i = 0; i < 3; ++i) {
-        out[i] = P.rho * (F.at[i] + conv[i] - F.f[i]) + Gup[i];
-        S tb = taubar * Gup[i];
+        const S Gup = mmadd(F.Gu[i][2], up[2], mmadd(F.Gu[i][1], up[1], F.Gu[i][0] * up[0]));
+        out[i] = madd(P.rho, acc[i], Gup);
+        const S wi = (-P.irho) * up[i];                 // -(u'_i / rho)
+        const S ci = mmadd(taubar, Gup, wi);           // coefficient of u'_j in S_ij
+        const S nup = T(-1) * up[i];
         for (int j = 0; j < 3; ++j) {
-            S sij = P.mu * (F.Gu[i][j] + F.Gu[j][i]) - up[i] * F.us[j] - P.irho * (up[i] * up[j]) + tb * up[j];
-            if (i == j) sij = sij - F.p - pp;
+            // S_ij = 2 mu eps_ij - u'_i u_j - u'_i u'_j / rho + taubar (u' . grad u)_i u'_j  (- p - p' on i = j)
+            S sij = mmadd(ci, up[j], mmadd(nup, F.us[j], P.mu * (F.Gu[i][j] + F.Gu[j][i])));
+            if (i == j) sij = sij - ppp;
             out[3 + 3 * i + j] = sij;
         }
-        out[13 + i] = -(P.irho * up[i]);
+        out[13 + i] = wi;
     }
     out[12] = divu;
 }
@@ -402,6 +444,195 @@ __device__ __forceinline__ void vms_point(const Args& A, const Phys<T>& P, const
     Fields<S, T> F;
     interp<S, T>(A, fm, fp, nd, stride, g, F);
     pointwise<S, T>(A, P, F, g, out);
+}
+
+// ------------------------------------------------------------------------------------------
+// Monomial (Hadamard) form of the trilinear interpolant on the reference cube [-1,1]^3.
+// With s_{c,k} = +1 where bit k of corner c is set and -1 otherwise,
+//   phi_c(xi) = prod_k (1 + s_{c,k} xi_k) / 2 = sum_S sigma_{c,S} m_S(xi),
+//   sigma_{c,S} = prod_{k in S} s_{c,k},   m_S(xi) = prod_{k in S} xi_k / 8,
+// S a subset of the three axes numbered by bits like the corners.  So a field is
+//   u(xi) = sum_S a_S m_S(xi)  with  a_S = sum_c sigma_{c,S} u_c          (forward butterfly),
+// d m_S / d xi_k = m_{S - k} for k in S, and a test-function sum over points is
+//   sum_q [phi_c r_q + grad phi_c . s_q] = sum_S sigma_{c,S} M_S,
+//   M_S = sum_q [m_S r_q + sum_{k in S} m_{S - k} s_{q,k}]                 (backward butterfly).
+// Each butterfly is three stages of sums and differences, one per axis.
+// ------------------------------------------------------------------------------------------
+// four consecutive T in shared memory, 16-byte aligned (float4, or two double2)
+template <class T>
+__device__ __forceinline__ void st4s(T* p, T a, T b, T c, T d) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+        reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+    }
+}
+template <class T>
+__device__ __forceinline__ void ld4s(const T* p, T o[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        const double2 v = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+        o[0] = v.x; o[1] = v.y; o[2] = w.x; o[3] = w.y;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void monomials(const T xi[3], T m[8]) {
+    const T e = T(0.125);
+    m[0] = e;
+    m[1] = e * xi[0];
+    m[2] = e * xi[1];
+    m[3] = m[1] * xi[1];
+    m[4] = e * xi[2];
+    m[5] = m[1] * xi[2];
+    m[6] = m[2] * xi[2];
+    m[7] = m[3] * xi[2];
+}
+
+// forward butterfly across the lanes (lane & 7) = corner c of an 8-lane group: corner value -> a_c
+template <class T>
+__device__ __forceinline__ T hadamard_fwd(T x, int c) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T o = __shfl_xor_sync(0xffffffffu, x, 1 << k);
+        x = ((c >> k) & 1) ? x - o : x + o;
+    }
+    return x;
+}
+
+// backward butterfly: lane holds M_S with S = (lane / LS) & 7; returns the sum for corner c = S's slot
+template <int LS, class T>
+__device__ __forceinline__ T hadamard_bwd(T x, int c) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T o = __shfl_xor_sync(0xffffffffu, x, LS << k);
+        x = ((c >> k) & 1) ? x + o : x - o;
+    }
+    return x;
+}
+
+// Fields at a point from the monomial coefficients of the 8 corner rows (row S holds a_S of every
+// column; layout as the corner rows: values | tangents at CT | force at CF; rows 16-byte aligned),
+// monomials m of the point.  Rows are read whole and accumulated into every field they enter.
+template <class S, class T>
+__device__ __forceinline__ void interp_modal(const Args& A, const T m[8], const T* nd, int stride, T g,
+                                             Fields<S, T>& F) {
+    constexpr bool JV = !std::is_same<S, T>::value;
+    for (int i = 0; i < 3; ++i) {
+        F.us[i] = zero<S>(); F.at[i] = zero<S>(); F.gp[i] = zero<S>(); F.f[i] = T(0);
+        for (int j = 0; j < 3; ++j) F.Gu[i][j] = zero<S>();
+    }
+    F.p = zero<S>();
+    S d01[2] = {zero<S>(), zero<S>()}, d02[2] = {zero<S>(), zero<S>()}, d12[2] = {zero<S>(), zero<S>()};
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const T* r = nd + t * stride;
+        T v[8], d[8];
+        ld4s<T>(r, v);
+        ld4s<T>(r + 4, v + 4);
+        if constexpr (JV) {
+            ld4s<T>(r + CT, d);
+            ld4s<T>(r + CT + 4, d + 4);
+        }
+        S a[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            if constexpr (JV) a[j] = make<S, T>(v[j], d[j]);
+            else a[j] = v[j];
+        }
+        const T mv = m[t];
+        for (int i = 0; i < 3; ++i) {
+            F.us[i] = madd(mv, a[i], F.us[i]);
+            F.at[i] = madd(mv, a[4 + i], F.at[i]);
+        }
+        F.p = madd(mv, a[3], F.p);
+        // d m_S / d xi_k = m_{S - k}: row t enters the k-derivative with monomial m[t ^ (1 << k)]
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (t & (1 << k)) {
+                const T mk = m[t ^ (1 << k)];
+                for (int i = 0; i < 3; ++i) F.Gu[i][k] = madd(mk, a[i], F.Gu[i][k]);
+                F.gp[k] = madd(mk, a[3], F.gp[k]);
+            }
+        }
+        if ((t & 3) == 3) { const T q = m[t ^ 3]; d01[0] = madd(q, a[0], d01[0]); d01[1] = madd(q, a[1], d01[1]); }
+        if ((t & 5) == 5) { const T q = m[t ^ 5]; d02[0] = madd(q, a[0], d02[0]); d02[1] = madd(q, a[2], d02[1]); }
+        if ((t & 6) == 6) { const T q = m[t ^ 6]; d12[0] = madd(q, a[1], d12[0]); d12[1] = madd(q, a[2], d12[1]); }
+        if (A.ndf) {
+            T f4[4];
+            ld4s<T>(r + CF, f4);
+            for (int i = 0; i < 3; ++i) F.f[i] = F.f[i] + mv * f4[i];
+        }
+    }
+    // (grad div u)_i = sum_{j != i} d_i d_j u_j   (d01 holds u0, u1; d02 u0, u2; d12 u1, u2)
+    F.H2[0] = d01[1] + d02[1];
+    F.H2[1] = d01[0] + d12[1];
+    F.H2[2] = d02[0] + d12[0];
+    const T g2 = g * g;
+    for (int i = 0; i < 3; ++i) {
+        F.gp[i] = g * F.gp[i];
+        F.H2[i] = g2 * F.H2[i];
+        for (int j = 0; j < 3; ++j) F.Gu[i][j] = g * F.Gu[i][j];
+    }
+}
+
+// forward butterfly down one column of an element's 8 corner rows (row stride CS), in place
+template <class T>
+__device__ __forceinline__ void column_to_monomial(T* col) {
+    T x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = col[t * CS];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (!(t & (1 << k))) {
+                const T lo = x[t], hi = x[t | (1 << k)];
+                x[t] = lo + hi;
+                x[t | (1 << k)] = hi - lo;
+            }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) col[t * CS] = x[t];
+}
+
+template <class S, class T>
+__device__ __forceinline__ void vms_point_modal(const Args& A, const Phys<T>& P, const T m[8], const T* nd,
+                                                int stride, T g, S out[16]) {
+    Fields<S, T> F;
+    interp_modal<S, T>(A, m, nd, stride, g, F);
+    pointwise<S, T>(A, P, F, g, out);
+}
+
+// M[4 S + k] += monomial moments of one point's weighted coefficients c (F | S | G | H, the 16 of
+// pointwise() times the quadrature weight, S and H in reference-gradient scaling), k = component.
+template <class T, bool PACKED>
+__device__ __forceinline__ void add_moments(const T m[8], const T c[16], T M[32]) {
+#pragma unroll
+    for (int p = 0; p < 4; p += 2) {   // components (p, p + 1) together
+        T f[2], sx[2], sy[2], sz[2];
+        for (int h = 0; h < 2; ++h) {
+            const int k = p + h;
+            f[h] = k < 3 ? c[k] : c[12];
+            sx[h] = k < 3 ? c[3 + 3 * k] : c[13];
+            sy[h] = k < 3 ? c[4 + 3 * k] : c[14];
+            sz[h] = k < 3 ? c[5 + 3 * k] : c[15];
+        }
+        auto add = [&](int S, T s, const T x[2]) {
+            if constexpr (PACKED) fma_pair2(s, x[0], x[1], M[4 * S + p], M[4 * S + p + 1]);
+            else fma_pair(s, x[0], x[1], M[4 * S + p], M[4 * S + p + 1]);
+        };
+        add(0, m[0], f);
+        add(1, m[1], f); add(1, m[0], sx);
+        add(2, m[2], f); add(2, m[0], sy);
+        add(3, m[3], f); add(3, m[2], sx); add(3, m[1], sy);
+        add(4, m[4], f); add(4, m[0], sz);
+        add(5, m[5], f); add(5, m[4], sx); add(5, m[1], sz);
+        add(6, m[6], f); add(6, m[4], sy); add(6, m[2], sz);
+        add(7, m[7], f); add(7, m[6], sx); add(7, m[5], sy); add(7, m[3], sz);
+    }
 }
 
 template <class T, bool JV> struct Pick;
