@@ -384,6 +384,21 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
     std::vector<int64_t> order(ns);
     for (int64_t i = 0; i < ns; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return m.sq[10 * a + 8] < m.sq[10 * b + 8]; });
+    // two buckets: points of elements hosting fewer than kNitscheDenseMin points first (one thread per
+    // point), then the runs of the other elements (one warp per element)
+    {
+        std::vector<int64_t> sparse, dense;
+        for (int64_t j = 0; j < ns;) {
+            int64_t k = j;
+            while (k < ns && m.sq[10 * order[k] + 8] == m.sq[10 * order[j] + 8]) ++k;
+            auto& dst = (k - j) >= kNitscheDenseMin ? dense : sparse;
+            dst.insert(dst.end(), order.begin() + j, order.begin() + k);
+            j = k;
+        }
+        m.n_sq_sparse = (int64_t)sparse.size();
+        sparse.insert(sparse.end(), dense.begin(), dense.end());
+        order.swap(sparse);
+    }
     std::vector<int32_t> el(ns);
     std::vector<double> xr(3 * ns), nr(3 * ns), w(ns), tb(ns);
     for (int64_t j = 0; j < ns; ++j) {
@@ -399,8 +414,16 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
         w[j] = r[6];
         tb[j] = 1.0 / r[7];
     }
+    // runs of points per host element in the dense bucket
+    std::vector<int32_t> sl;
+    std::vector<int64_t> so;
+    for (int64_t j = m.n_sq_sparse; j < ns; ++j)
+        if (j == m.n_sq_sparse || el[j] != el[j - 1]) { sl.push_back(el[j]); so.push_back(j); }
+    so.push_back(ns);
+    m.n_sq_elem = (int64_t)sl.size();
     if (!upload(&m.d.sq_elem, el, err) || !upload(&m.d.sq_x, xr, err) || !upload(&m.d.sq_n, nr, err) ||
-        !upload(&m.d.sq_w, w, err) || !upload(&m.d.sq_taub, tb, err) || !upload(&m.d.bcflag, m.bcflag, err))
+        !upload(&m.d.sq_w, w, err) || !upload(&m.d.sq_taub, tb, err) || !upload(&m.d.sq_list, sl, err) ||
+        !upload(&m.d.sq_off, so, err) || !upload(&m.d.bcflag, m.bcflag, err))
         return false;
     const size_t next = (size_t)(m.n_nodes() + m.n_hang());
     if (!check(cudaMalloc((void**)&m.d.slot, std::max<int64_t>(1, m.n_elem()) * sizeof(int32_t)), err, "cudaMalloc")) return false;
@@ -449,7 +472,7 @@ void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
                     d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
-                    d.sq_n, d.sq_w, d.sq_taub, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot};
+                    d.sq_n, d.sq_w, d.sq_taub, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh();

@@ -82,6 +82,8 @@ struct DeviceMesh {
     double* sq_n = nullptr;       // [n][3]
     double* sq_w = nullptr;
     double* sq_taub = nullptr;    // 1 / h_b
+    int32_t* sq_list = nullptr;   // elements hosting at least kNitscheDenseMin surface points
+    int64_t* sq_off = nullptr;    // [n_sq_elem + 1] their point ranges in the sorted arrays
     // per-call node workspace (node_prep): value, tangent and force data of every independent and
     // hanging node, one float and one double copy
     float* nd_f = nullptr;        // [3][n_nodes + n_hang][8]
@@ -92,6 +94,9 @@ struct DeviceMesh {
     uint8_t* bcmask_user = nullptr;
     double* bcval_user = nullptr;
 };
+
+// elements hosting at least this many surface points take the warp-per-element surface kernel
+constexpr int kNitscheDenseMin = 8;
 
 struct GraphKey {
     const double *u, *up, *up2, *f, *v;
@@ -127,6 +132,8 @@ struct Mesh {
     std::vector<double> cut_pts;         // [n][4] in cut_list order
     std::vector<int64_t> cut_off;        // [n_cut + 1]
     std::vector<double> sq;              // [n][10] surface points (export layout)
+    int64_t n_sq_sparse = 0;             // surface points of elements hosting < kNitscheDenseMin (stored first)
+    int64_t n_sq_elem = 0;               // elements hosting >= kNitscheDenseMin surface points
     std::vector<uint8_t> bcflag;
     int64_t n_in = 0, n_rays = 0;
     // batched meshes: element -> problem, per-problem viscosity and element/node offsets

@@ -21,7 +21,8 @@
 //                 functions both run in the monomial form of the trilinear basis.
 //   vms_cut       one warp per Intercepted element; lane l evaluates sub-cell points l, l + 32, ...
 //                 and accumulates their monomial moments, summed over the lanes at the end.
-//   nitsche       one thread per surface point (points sorted by element).
+//   nitsche       one thread per surface point, for elements hosting few points;
+//   nitsche_el    one warp per element hosting many, lanes over its points (moments).
 //   strong_rows   Dirichlet rows U - g and In-only rows, written after every scatter.
 
 #include <cuda_runtime.h>
@@ -152,6 +153,27 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
 // ------------------------------------------------------------------------------------------
 constexpr int WPB = 4;   // warps per block
 
+// Warp epilogue of the per-element kernels: lane l holds the monomial moments M of its points;
+// sum them over the lanes (transpose through shared memory s_m [32][32 + pad]), run the backward
+// butterfly so lane 4 a + k holds row (node a, component k), and scatter node a from lane 4 a.
+// my_id: the node id of corner (lane & 7).
+template <class T>
+__device__ __forceinline__ void warp_scatter_moments(const Args& A, const T M[32], T* s_m, int lane, int32_t my_id) {
+    constexpr int MSTR = 32 + 16 / (int)sizeof(T);
+    T* mrow = s_m + lane * MSTR;
+    for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
+    __syncwarp();
+    T acc = T(0);
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) acc += s_m[t * MSTR + lane];
+    acc = hadamard_bwd<4>(acc, lane >> 2);
+    const int a = lane >> 2;
+    double r[4];
+    for (int k = 0; k < 4; ++k) r[k] = (double)__shfl_sync(0xffffffffu, acc, (lane & ~3) + k);
+    const int32_t id = __shfl_sync(0xffffffffu, my_id, a);
+    if ((lane & 3) == 0) scatter(A, id, r);
+}
+
 template <class T, bool JV>
 __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 4 : 2) vms_cut(Args A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
                                                     const void* __restrict__ pts, int64_t n) {
@@ -197,24 +219,11 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 4 : 2) vms_cut(Args
         for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
         add_moments<T, false>(m, w16, M);
     }
-    // sum the moments over the lanes (transpose through shared memory): lane l gets moment l = 4 S + k
-    T* mrow = &s_m[w][lane * MSTR];
-    for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
-    __syncwarp();
-    T acc = T(0);
-#pragma unroll 8
-    for (int t = 0; t < 32; ++t) acc += s_m[w][t * MSTR + lane];
-    // backward butterfly over S = lane >> 2: lane 4 a + k now holds row (node a, component k)
-    acc = hadamard_bwd<4>(acc, lane >> 2);
-    const int a = lane >> 2;
-    double r[4];
-    for (int k = 0; k < 4; ++k) r[k] = (double)__shfl_sync(0xffffffffu, acc, (lane & ~3) + k);
-    const int32_t id = __shfl_sync(0xffffffffu, my_id, a);
-    if ((lane & 3) == 0) scatter(A, id, r);
+    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id);
 }
 
 // ------------------------------------------------------------------------------------------
-// Nitsche surface terms, one thread per surface point
+// Nitsche surface terms (Eq. weakbc), one thread per surface point: elements hosting few points
 // ------------------------------------------------------------------------------------------
 template <class T, bool JV>
 __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict__ el, const double* __restrict__ xr,
@@ -235,6 +244,112 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
         for (int k = 0; k < 4; ++k) r[k] = (double)(w * Pick<T, JV>::get(t[k]));
         scatter(A, P.ids[c], r);
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// Nitsche surface terms (Eq. weakbc), one warp per element hosting many surface points; lane l takes
+// points l, l + 32, ... of the element.  Per point the 4 rows of corner c are
+//   t_k = phi_c [tau_B d_k - tr_k - [u.n < 0] rho (u.n) d_k] - mu g sum_j d_j phi_c (n_j d_k + n_k d_j),
+//   t_p = -phi_c (d.n),   d = u_s - g, tr = -p n + 2 mu eps(u) n,
+// i.e. coefficients of phi_c and of its reference gradient, accumulated as monomial moments.
+// ------------------------------------------------------------------------------------------
+template <class T, bool JV>
+__global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(Args A, const int32_t* __restrict__ list,
+                                                    const int64_t* __restrict__ off, const double* __restrict__ xr,
+                                                    const double* __restrict__ nr, const double* __restrict__ wr,
+                                                    const double* __restrict__ taub, int64_t n) {
+    typedef typename std::conditional<JV, Dual<T>, T>::type S;
+    constexpr int PAD = 16 / (int)sizeof(T), MSTR = 32 + PAD;
+    __shared__ __align__(16) T s_nd[WPB][8 * CS];
+    __shared__ __align__(16) T s_m[WPB][32 * MSTR];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t idx = (int64_t)blockIdx.x * WPB + w;
+    if (idx >= n) return;
+    const int32_t e = list[idx];
+    // corner rows: u_s (0-2), p (3), jump d = u_s - g formed in float64 (4-6), tangents at CT
+    const int c8 = lane & 7;
+    const int32_t my_id = A.conn[8 * (int64_t)e + c8];
+    {
+        T a8[8], t8[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        ld8<T>(A.ndv, my_id, a8);
+        if (JV) ld8<T>(A.ndt, my_id, t8);
+        double u4[4], up4[4];
+        gather(A, A.U, my_id, u4);
+        if (A.theta != 1.0) gather(A, A.Up, my_id, up4);
+        T rw[CS];
+        for (int k = 0; k < 3; ++k) {
+            const double usk = A.theta == 1.0 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
+            rw[k] = a8[k];
+            rw[4 + k] = (T)(usk - A.g[k]);
+            rw[CT + k] = t8[k];
+            rw[CT + 4 + k] = t8[k];
+        }
+        rw[3] = a8[3];
+        rw[CT + 3] = t8[3];
+        for (int j = 0; j < 7; ++j) rw[j] = hadamard_fwd(rw[j], c8);
+        if (JV)
+            for (int j = 0; j < 7; ++j) rw[CT + j] = hadamard_fwd(rw[CT + j], c8);
+        if (lane < 8) {
+            for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + j] = rw[j];
+            if (JV)
+                for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + CT + j] = rw[CT + j];
+        }
+    }
+    __syncwarp();
+    const T g = lvl_g<T>(A, A.lev[e]);
+    T mu, rho;
+    {
+        const Phys<T> Ph(A, prob_of(A, e));
+        mu = Ph.mu;
+        rho = Ph.rho;
+    }
+    const double Cbmu = A.Cb * (double)mu;
+    T M[32];
+    for (int k = 0; k < 32; ++k) M[k] = T(0);
+    const int64_t q0 = off[idx], q1 = off[idx + 1];
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+        T xi[3], nn[3], m[8];
+        for (int k = 0; k < 3; ++k) { xi[k] = (T)xr[3 * q + k]; nn[k] = (T)nr[3 * q + k]; }
+        monomials<T>(xi, m);
+        // u_s, grad u_s, p, d at the point
+        S us[3], Gu[3][3], p, d[3];
+        for (int i = 0; i < 3; ++i) { us[i] = zero<S>(); d[i] = zero<S>(); for (int j = 0; j < 3; ++j) Gu[i][j] = zero<S>(); }
+        p = zero<S>();
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const T* r = &s_nd[w][t * CS];
+            S a[7];
+            for (int j = 0; j < 7; ++j) a[j] = make<S, T>(r[j], JV ? r[CT + j] : T(0));
+            for (int i = 0; i < 3; ++i) {
+                us[i] = madd(m[t], a[i], us[i]);
+                d[i] = madd(m[t], a[4 + i], d[i]);
+            }
+            p = madd(m[t], a[3], p);
+            for (int k = 0; k < 3; ++k)
+                if (t & (1 << k))
+                    for (int i = 0; i < 3; ++i) Gu[i][k] = madd(m[t ^ (1 << k)], a[i], Gu[i][k]);
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Gu[i][j] = g * Gu[i][j];
+        const S un = mmadd(us[2], S(make<S, T>(nn[2], T(0))), mmadd(us[1], S(make<S, T>(nn[1], T(0))), us[0] * nn[0]));
+        const S dn = madd(nn[2], d[2], madd(nn[1], d[1], nn[0] * d[0]));
+        const bool inflow = value(un) < T(0);
+        const T tauB = (T)(Cbmu * taub[q]);
+        const T wq = (T)wr[q], wqg = wq * g;
+        T c[16];
+        for (int k = 0; k < 3; ++k) {
+            S tr = (-nn[k]) * p;
+            for (int j = 0; j < 3; ++j) tr = madd(mu * nn[j], Gu[k][j] + Gu[j][k], tr);
+            S fk = tauB * d[k] - tr;
+            if (inflow) fk = fk - rho * (un * d[k]);
+            c[k] = wq * Pick<T, JV>::get(fk);
+            for (int j = 0; j < 3; ++j) c[3 + 3 * k + j] = (-wqg * mu) * Pick<T, JV>::get(madd(nn[j], d[k], nn[k] * d[j]));
+        }
+        c[12] = -wq * Pick<T, JV>::get(dn);
+        c[13] = c[14] = c[15] = T(0);
+        add_moments<T, false>(m, c, M);
+    }
+    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -318,7 +433,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         cudaStreamWaitEvent(sc, ev[0], 0);
         cudaStreamWaitEvent(ss, ev[0], 0);
     }
-    const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size(), ns = (int64_t)m.sq.size() / 10;
+    const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size();
     constexpr int EPB = Epb<T>::value;
     if (no > 0) {
         Timed t(m, 0, s);
@@ -333,10 +448,16 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         const void* pts = std::is_same<T, float>::value ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
         vms_cut<T, JV><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, 0, sc>>>(A, m.d.cut_list, m.d.cut_off, pts, nc);
     }
-    if (ns > 0) {
+    const int64_t nsp = m.n_sq_sparse, nse = m.n_sq_elem;
+    if (nsp > 0) {
         Timed t(m, 2, ss);
-        nitsche<T, JV><<<(unsigned)((ns + 127) / 128), 128, 0, ss>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
-                                                                     m.d.sq_taub, ns);
+        nitsche<T, JV><<<(unsigned)((nsp + 127) / 128), 128, 0, ss>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
+                                                                      m.d.sq_taub, nsp);
+    }
+    if (nse > 0) {
+        Timed t(m, 2, ss);
+        nitsche_el<T, JV><<<(unsigned)((nse + WPB - 1) / WPB), 32 * WPB, 0, ss>>>(A, m.d.sq_list, m.d.sq_off, m.d.sq_x,
+                                                                                m.d.sq_n, m.d.sq_w, m.d.sq_taub, nse);
     }
     if (ev) {   // join
         cudaEventRecord(ev[1], sc);
