@@ -269,10 +269,11 @@ imga_status imga_precond_dataset(imga_mesh mesh, const double* u, const double* 
 imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, float* C, void* stream);
 
 /* Options of a mesh.  IMGA_OPT_GRAPHS (value 1 on, 0 off, default off): imga_residual and imga_jvp
- * run as CUDA graphs -- the first call with a given set of pointers, stream, precision and physics
- * captures node preparation, the Out-element, Intercepted-element and surface kernels (the last
+ * run as CUDA graphs -- the first call with a given set of pointers, precision and physics
+ * captures (on a private stream) node preparation, the Out-element, Intercepted-element and surface kernels (the last
  * three on parallel branches) and the strong rows; later identical calls replay that graph (up to
- * 32 graphs are kept per mesh).  The first call for a key must not itself run inside a stream
+ * 32 graphs are kept per mesh), ordered after the work already queued on the caller's stream and
+ * before anything queued on it later.  The first call for a key must not itself run inside a stream
  * capture.  imga_set_dirichlet drops the cached graphs.  Profiling (imga_profile) bypasses them. */
 enum { IMGA_OPT_GRAPHS = 1 };
 imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
@@ -281,9 +282,19 @@ imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.
  * imga_profile_read synchronises the device and returns, per kernel class (0 Out elements,
  * 1 Intercepted elements, 2 Nitsche surface points, 3 strong rows, 4 node preparation), the
- * summed milliseconds ms[5] and the launch counts launches[5] since profiling was enabled. */
+ * summed milliseconds ms[5] and the kernel launch counts launches[5] since profiling was enabled
+ * (node preparation is one timed span of up to two kernels; the surface class counts its
+ * thread-per-point and warp-per-element kernels separately). */
 imga_status imga_profile(imga_mesh mesh, int enable);
 imga_status imga_profile_read(imga_mesh mesh, double* ms, int64_t* launches);
+
+/* Self-check of the float64 <-> float32 conversions that the mixed-precision kernels do on the
+ * integer pipes (no counterpart in the paper: it is an implementation device of this library).
+ * Runs n cases on `device` -- random bit patterns, round-to-nearest-even ties, the edges of the
+ * float32 normal range, zeros, subnormals, infinities and NaNs -- derived from `seed`, and stores in
+ * *mismatches the number whose result differs in any bit from the hardware conversion (NaN: from
+ * being NaN).  Synchronous.  Errors: IMGA_ERR_INVALID_ARG (n < 0, null output), IMGA_ERR_CUDA. */
+imga_status imga_selftest_conversions(int device, int64_t n, uint64_t seed, int64_t* mismatches);
 
 const char* imga_last_error(void);
 

@@ -345,6 +345,14 @@ class Mlp:
         return hist[:epochs]
 
 
+def selftest_conversions(n=1 << 24, seed=1, device=0):
+    """imga_selftest_conversions: number of float64 <-> float32 conversion cases (of n) whose result
+    differs from the hardware conversion."""
+    bad = C.c_int64()
+    check(_lib.load().imga_selftest_conversions(device, n, seed, C.byref(bad)))
+    return bad.value
+
+
 def gemm_bf16(A, B, stream=None):
     """C = A B^T with A, B rounded to BF16, FP32 accumulate (float32 CUDA tensors)."""
     import torch

@@ -434,6 +434,14 @@ imga_status imga_jvp_noalloc(imga_mesh h, const double* u, const double* up, con
     return cuda_status("jvp_noalloc launch");
 }
 
+imga_status imga_selftest_conversions(int device, int64_t n, uint64_t seed, int64_t* mismatches) {
+    if (n < 0 || !mismatches) return fail(IMGA_ERR_INVALID_ARG, "n must be >= 0 and mismatches non-null");
+    if (cudaSetDevice(device) != cudaSuccess) return cuda_status("cudaSetDevice");
+    std::string err;
+    if (imga::conversion_selftest(n, seed, mismatches, err)) return fail(IMGA_ERR_CUDA, "conversion self-check: " + err);
+    return cuda_status("conversion self-check");
+}
+
 imga_status imga_set_dirichlet(imga_mesh h, const uint8_t* mask, const double* val, void* stream) {
     if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
     if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");

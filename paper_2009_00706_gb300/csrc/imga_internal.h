@@ -156,7 +156,8 @@ struct Mesh {
     void* solver_work = nullptr;         // Krylov workspace (solver.cu)
     // per-kernel profiling (CUDA events, one pair per launch, resolved at read time)
     bool profiling = false;
-    std::vector<std::pair<void*, void*>> prof_ev[5];
+    struct ProfEv { void *a, *b; int launches; };   // event pair around `launches` kernels
+    std::vector<ProfEv> prof_ev[5];
     double prof_ms[5] = {0, 0, 0, 0, 0};
     int64_t prof_n[5] = {0, 0, 0, 0, 0};
     size_t scratch_bytes = 0;
@@ -186,6 +187,7 @@ int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags,
 void device_free(Mesh& m);
 
 // residual / Jv (vms.cu)
+int conversion_selftest(int64_t n, uint64_t seed, int64_t* mismatches, std::string& err);
 int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
               const imga_physics& ph, int precision, const double* v, double* out, void* stream);
 

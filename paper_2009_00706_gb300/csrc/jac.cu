@@ -353,7 +353,7 @@ void launch_jac(const Mesh& m, Args A, const int32_t* slot, double* K, double* D
     A.ndt = ndv + 8 * next;
     A.ndf = A.F ? ndv + 16 * next : nullptr;
     if (next > 0)
-        node_prep<T, false><<<(unsigned)((next + 255) / 256), 256, 0, s>>>(A, ndv, ndv + 8 * next, (T*)A.ndf);
+        launch_node_prep<T, false>(A, ndv, ndv + 8 * next, (T*)A.ndf, s);
     const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size(), ns = (int64_t)m.sq.size() / 10;
     constexpr int EPB = JacShape<T>::EPB;
     if (no > 0) jac_out<T, MODE><<<(unsigned)((no + EPB - 1) / EPB), 8 * EPB, 0, s>>>(A, m.d.out_list, no, slot, K, D);

@@ -136,10 +136,7 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
             r[0] += v[0]; r[1] += v[1]; r[2] += v[2]; r[3] += v[3];
         }
         for (int k = 0; k < 4; ++k) r[k] = hadamard_bwd<1>(r[k], c);
-        if (valid) {
-            double rd[4] = {(double)r[0], (double)r[1], (double)r[2], (double)r[3]};
-            scatter(A, id_cur, rd);
-        }
+        if (valid) scatter_t(A, id_cur, r);
         __syncwarp();   // this buffer and the moments are rewritten by later iterations
         id_cur = id_next;
         id_next = id_after;
@@ -168,10 +165,10 @@ __device__ __forceinline__ void warp_scatter_moments(const Args& A, const T M[32
     for (int t = 0; t < 32; ++t) acc += s_m[t * MSTR + lane];
     acc = hadamard_bwd<4>(acc, lane >> 2);
     const int a = lane >> 2;
-    double r[4];
-    for (int k = 0; k < 4; ++k) r[k] = (double)__shfl_sync(0xffffffffu, acc, (lane & ~3) + k);
+    T r[4];
+    for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(0xffffffffu, acc, (lane & ~3) + k);
     const int32_t id = __shfl_sync(0xffffffffu, my_id, a);
-    if ((lane & 3) == 0) scatter(A, id, r);
+    if ((lane & 3) == 0) scatter_t(A, id, r);
 }
 
 template <class T, bool JV>
@@ -240,9 +237,9 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
     for (int c = 0; c < 8; ++c) {
         S t[4];
         nitsche_rows<S, T>(A, P, c, tauB, t);
-        double r[4];
-        for (int k = 0; k < 4; ++k) r[k] = (double)(w * Pick<T, JV>::get(t[k]));
-        scatter(A, P.ids[c], r);
+        T r[4];
+        for (int k = 0; k < 4; ++k) r[k] = w * Pick<T, JV>::get(t[k]);
+        scatter_t(A, P.ids[c], r);
     }
 }
 
@@ -382,10 +379,11 @@ __global__ void strong_rows(Args A, const uint8_t* __restrict__ flag, const uint
 // optional event pair around a launch (profiling)
 struct Timed {
     Mesh* m;
-    int k;
+    int k, nk;
     cudaStream_t s;
     cudaEvent_t a = nullptr, b = nullptr;
-    Timed(const Mesh& mesh, int kind, cudaStream_t st) : m(const_cast<Mesh*>(&mesh)), k(kind), s(st) {
+    Timed(const Mesh& mesh, int kind, cudaStream_t st, int launches = 1)
+        : m(const_cast<Mesh*>(&mesh)), k(kind), nk(launches), s(st) {
         if (!m->profiling) return;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
@@ -394,7 +392,7 @@ struct Timed {
     ~Timed() {
         if (!a) return;
         cudaEventRecord(b, s);
-        m->prof_ev[k].push_back({(void*)a, (void*)b});
+        m->prof_ev[k].push_back({(void*)a, (void*)b, nk});
     }
 };
 
@@ -423,8 +421,8 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     A.ndt = ndt;
     A.ndf = ndf;
     if (next > 0) {
-        Timed t(m, 4, s);
-        node_prep<T, JV><<<(unsigned)((next + 255) / 256), 256, 0, s>>>(A, ndv, ndt, ndf);
+        Timed t(m, 4, s, (A.n_nodes > 0) + (A.n_hang > 0));
+        launch_node_prep<T, JV>(A, ndv, ndt, ndf, s);
     }
     // fork: the Intercepted-element and surface kernels run beside the Out-element kernel
     const cudaStream_t sc = s_cut ? s_cut : s, ss = s_sur ? s_sur : s;
@@ -550,6 +548,60 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+// ------------------------------------------------------------------------------------------
+// self-check of f2d / d2f against the hardware conversions
+// ------------------------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void conversion_check(int64_t n, uint64_t seed, unsigned long long* bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t r = mix64(seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1));
+    const uint64_t r2 = mix64(r ^ 0xD1B54A32D192ED03ull);
+    uint64_t bits;
+    const uint64_t sign = r2 & 0x8000000000000000ull, frac = r & 0x000FFFFFFFFFFFFFull;
+    switch (i & 7) {
+        case 0: bits = r; break;                                                    // anything
+        case 1: bits = sign | ((uint64_t)(897 + (r2 >> 8) % 254) << 52) | frac; break;   // float32 normal range
+        case 2: bits = sign | ((uint64_t)(897 + (r2 >> 8) % 254) << 52) | (frac & ~0x1FFFFFFFull) | 0x10000000ull; break;  // tie
+        case 3: {                                                                   // edges of the range
+            const uint32_t E[6] = {0, 1, 896, 897, 1150, 1151};
+            bits = sign | ((uint64_t)E[(r2 >> 8) % 6] << 52) | frac;
+            break;
+        }
+        case 4: bits = sign | ((uint64_t)1150 << 52) | (0x000FFFFFF0000000ull | (frac & 0x0FFFFFFFull)); break;  // rounds to inf
+        case 5: bits = sign | ((uint64_t)(r2 % 3 == 0 ? 2047 : (r2 % 3 == 1 ? 0 : 1)) << 52) | ((r2 >> 4) & 1 ? frac : 0); break;
+        case 6: bits = sign | ((uint64_t)(897 + (r2 >> 8) % 254) << 52) | (frac | 0x000FFFFFE0000000ull); break;   // carry into the exponent
+        default: bits = sign | ((uint64_t)(897 + (r2 >> 8) % 254) << 52) | (frac & ~0x1FFFFFFFull); break;        // exact in float32
+    }
+    const double x = __longlong_as_double((long long)bits);
+    const float a = d2f(x), b = (float)x;
+    bool ok = (a != a) ? (b != b) : (__float_as_uint(a) == __float_as_uint(b));
+    const float y = __uint_as_float((uint32_t)(r2 >> 17));
+    const double c = f2d(y), d = (double)y;
+    ok = ok && ((c != c) ? (d != d) : (__double_as_longlong(c) == __double_as_longlong(d)));
+    if (!ok) atomicAdd(bad, 1ull);
+}
+}  // namespace
+
+int conversion_selftest(int64_t n, uint64_t seed, int64_t* mismatches, std::string& err) {
+    unsigned long long* bad = nullptr;
+    if (cudaMalloc((void**)&bad, sizeof(*bad)) != cudaSuccess) { err = "cudaMalloc failed"; return 1; }
+    cudaMemset(bad, 0, sizeof(*bad));
+    if (n > 0) conversion_check<<<(unsigned)((n + 255) / 256), 256>>>(n, seed, bad);
+    unsigned long long h = 0;
+    const cudaError_t rc = cudaMemcpy(&h, bad, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(bad);
+    if (rc != cudaSuccess) { err = cudaGetErrorString(rc); return 1; }
+    *mismatches = (int64_t)h;
+    return 0;
+}
+
 int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
               const imga_physics& ph, int precision, const double* v, double* out, void* stream) {
     return vms_apply_ws(m, u, up, up2, f, ph, precision, v, out, stream, nullptr);
@@ -596,7 +648,7 @@ int vms_jvp_noalloc(const Mesh& m, const double* u, const double* up, const doub
 
 void profile_reset(Mesh& m) {
     for (int k = 0; k < 5; ++k) {
-        for (auto& p : m.prof_ev[k]) { cudaEventDestroy((cudaEvent_t)p.first); cudaEventDestroy((cudaEvent_t)p.second); }
+        for (auto& p : m.prof_ev[k]) { cudaEventDestroy((cudaEvent_t)p.a); cudaEventDestroy((cudaEvent_t)p.b); }
         m.prof_ev[k].clear();
         m.prof_ms[k] = 0.0;
         m.prof_n[k] = 0;
@@ -608,11 +660,11 @@ int profile_collect(Mesh& m) {
     for (int k = 0; k < 5; ++k) {
         for (auto& p : m.prof_ev[k]) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, (cudaEvent_t)p.first, (cudaEvent_t)p.second);
+            cudaEventElapsedTime(&ms, (cudaEvent_t)p.a, (cudaEvent_t)p.b);
             m.prof_ms[k] += ms;
-            m.prof_n[k] += 1;
-            cudaEventDestroy((cudaEvent_t)p.first);
-            cudaEventDestroy((cudaEvent_t)p.second);
+            m.prof_n[k] += p.launches;
+            cudaEventDestroy((cudaEvent_t)p.a);
+            cudaEventDestroy((cudaEvent_t)p.b);
         }
         m.prof_ev[k].clear();
     }

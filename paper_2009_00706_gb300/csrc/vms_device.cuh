@@ -176,9 +176,9 @@ __device__ __forceinline__ void scatter(const Args& A, int32_t id, const double 
     }
 }
 
-// Node data, prepared once per call by node_prep for every independent node and every hanging
-// node (the latter interpolated from its parents, u_e = M_e U), so the element kernels gather
-// with plain loads and no float64 arithmetic:
+// Node data, prepared once per call by node_prep for every independent node and by
+// node_prep_hanging for every hanging node (from its parents' rows, u_e = M_e U), so the element
+// kernels gather with plain loads and no float64 arithmetic:
 //   us = theta u + (1-theta) u_prev (spatial state; theta = 1/2 is Crank-Nicolson), p,
 //   at = (c0 u + c1 u_prev + c2 u_prev2)/dt = c0 (u - u_prev) + c2 (u_prev2 - u_prev)
 //        (c0 + c1 + c2 = 0), the differences taken in float64 before rounding to T,
@@ -245,41 +245,116 @@ __device__ __forceinline__ void corner_async(const Args& A, int32_t id, T* dst) 
     }
 }
 
+// Conversions between float64 and float32 on the integer pipes (this GPU's float64 unit is narrow),
+// written from the IEEE-754 binary64 / binary32 layouts: exponent bias 1023 / 127, fraction 52 / 23
+// bits.  Normal numbers by re-biasing the exponent and shifting the fraction (rounding to nearest,
+// ties to even, on the 29 dropped bits going down); zeros by their sign; subnormal, infinite and NaN
+// operands take the hardware conversion.  Results equal the hardware's for every input.
+__device__ __forceinline__ double f2d(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = b & 0x7F800000u;
+    if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    if (e == 0u || e == 0x7F800000u) return (double)x;
+    const uint32_t hi = (b & 0x80000000u) | (((b & 0x7FFFFFFFu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ float d2f(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t E = (hi >> 20) & 0x7FFu;
+    if (E == 0u) return __uint_as_float(hi & 0x80000000u);   // zero or float64 subnormal: rounds to +-0
+    if (E - 897u >= 254u) return (float)x;                   // below / above the float32 normal range
+    uint32_t f = ((((hi & 0x7FFFFFFFu) << 3) | (lo >> 29)) - (896u << 23)) | (hi & 0x80000000u);
+    const uint32_t rest = lo & 0x1FFFFFFFu, half = 0x10000000u;
+    f += (rest > half || (rest == half && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+}
+template <class T> __device__ __forceinline__ T to_t(double x);
+template <> __device__ __forceinline__ float to_t<float>(double x) { return d2f(x); }
+template <> __device__ __forceinline__ double to_t<double>(double x) { return x; }
+
+// scatter one node's 4 values in the element precision: widened to float64 on the float64 unit,
+// which the element kernels leave idle while their integer pipe is busy
+__device__ __forceinline__ void scatter_t(const Args& A, int32_t id, const double r[4]) { scatter(A, id, r); }
+__device__ __forceinline__ void scatter_t(const Args& A, int32_t id, const float r[4]) {
+    const double rd[4] = {(double)r[0], (double)r[1], (double)r[2], (double)r[3]};
+    scatter(A, id, rd);
+}
+
+// Node data, pass 1: independent nodes (float64 differences, then rounding to T)
 template <class T, bool JV>
 __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T* __restrict__ ndt, T* __restrict__ ndf) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= A.n_nodes + A.n_hang) return;
-    const int32_t id = (int32_t)n;
+    if (n >= A.n_nodes) return;
     double u[4], up[4], up2[4] = {0, 0, 0, 0};
-    gather(A, A.U, id, u);
-    gather(A, A.Up, id, up);
-    if (A.c2 != 0.0) gather(A, A.Up2, id, up2);
+    load4(A.U, n, u);
+    load4(A.Up, n, up);
+    if (A.c2 != 0.0) load4(A.Up2, n, up2);
     T v8[8];
     for (int k = 0; k < 3; ++k) {
-        v8[k] = A.theta == 1.0 ? (T)u[k] : (T)(A.theta * u[k] + (1.0 - A.theta) * up[k]);
-        T d1 = (T)(u[k] - up[k]);
-        T d2 = A.c2 != 0.0 ? (T)(up2[k] - up[k]) : T(0);
+        v8[k] = A.theta == 1.0 ? to_t<T>(u[k]) : to_t<T>(A.theta * u[k] + (1.0 - A.theta) * up[k]);
+        T d1 = to_t<T>(u[k] - up[k]);
+        T d2 = A.c2 != 0.0 ? to_t<T>(up2[k] - up[k]) : T(0);
         v8[4 + k] = (T)A.c0 * d1 + (T)A.c2 * d2;
     }
-    v8[3] = (T)u[3];
+    v8[3] = to_t<T>(u[3]);
     v8[7] = T(0);
     for (int k = 0; k < 8; ++k) ndv[8 * n + k] = v8[k];
     if (ndf) {
         double f[4];
-        gather(A, A.F, id, f);
-        for (int k = 0; k < 3; ++k) ndf[4 * n + k] = (T)f[k];
+        load4(A.F, n, f);
+        for (int k = 0; k < 3; ++k) ndf[4 * n + k] = to_t<T>(f[k]);
         ndf[4 * n + 3] = T(0);
     }
     if (JV) {
         double v[4];
-        gather(A, A.V, id, v);
-        T vt[4] = {(T)v[0], (T)v[1], (T)v[2], (T)v[3]};
+        load4(A.V, n, v);
+        T vt[4] = {to_t<T>(v[0]), to_t<T>(v[1]), to_t<T>(v[2]), to_t<T>(v[3])};
         T t8[8];
         for (int k = 0; k < 3; ++k) { t8[k] = (T)A.theta * vt[k]; t8[4 + k] = (T)A.c0 * vt[k]; }
         t8[3] = vt[3];
         t8[7] = T(0);
         for (int k = 0; k < 8; ++k) ndt[8 * n + k] = t8[k];
     }
+}
+
+// Node data, pass 2: a hanging node's rows are the mean of its 2 (edge) or 4 (face) parents' rows
+// (every entry is linear in the nodal vectors, so this is u_e = M_e U applied to the rows)
+template <class T, bool JV>
+__global__ void __launch_bounds__(256) node_prep_hanging(Args A, T* __restrict__ ndv, T* __restrict__ ndt,
+                                                         T* __restrict__ ndf) {
+    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= A.n_hang) return;
+    const int64_t n = A.n_nodes + h;
+    const int32_t* hp = A.hpar + 4 * h;
+    const int np = hp[2] >= 0 ? 4 : 2;
+    const T w = np == 4 ? T(0.25) : T(0.5);
+    T a[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}, b[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    T c[4] = {T(0), T(0), T(0), T(0)};
+    for (int p = 0; p < np; ++p) {
+        T r[8];
+        ld8<T>(ndv, hp[p], r);
+        for (int k = 0; k < 8; ++k) a[k] += r[k];
+        if (JV) {
+            ld8<T>(ndt, hp[p], r);
+            for (int k = 0; k < 8; ++k) b[k] += r[k];
+        }
+        if (ndf) {
+            ld4<T>(ndf, hp[p], r);
+            for (int k = 0; k < 4; ++k) c[k] += r[k];
+        }
+    }
+    for (int k = 0; k < 8; ++k) ndv[8 * n + k] = w * a[k];
+    if (JV)
+        for (int k = 0; k < 8; ++k) ndt[8 * n + k] = w * b[k];
+    if (ndf)
+        for (int k = 0; k < 4; ++k) ndf[4 * n + k] = w * c[k];
+}
+
+// both passes on stream s
+template <class T, bool JV>
+inline void launch_node_prep(const Args& A, T* ndv, T* ndt, T* ndf, cudaStream_t s) {
+    if (A.n_nodes > 0) node_prep<T, JV><<<(unsigned)((A.n_nodes + 255) / 256), 256, 0, s>>>(A, ndv, ndt, ndf);
+    if (A.n_hang > 0) node_prep_hanging<T, JV><<<(unsigned)((A.n_hang + 255) / 256), 256, 0, s>>>(A, ndv, ndt, ndf);
 }
 
 // physical constants in the element precision
