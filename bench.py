@@ -159,12 +159,29 @@ def oracle_sample(w, n_nodes_sample, seed=0):
     return om, u, up, v
 
 
-def time_oracle(om, w, u, up, v, sel):
+def time_oracle(om, w, u, up, v, sel, rows=False):
     om.residual_jvp(w.physics, u, up, up, v=v, nodes=sel)      # geometry of the sample, untimed
     t = time.perf_counter()
-    om.residual_jvp(w.physics, u, up, up, v=v, nodes=sel)
+    R, J = om.residual_jvp(w.physics, u, up, up, v=v, nodes=sel)
     dt = time.perf_counter() - t
+    if rows:
+        return om.counters()["elements_evaluated"], dt, R, J
     return om.counters()["elements_evaluated"], dt
+
+
+def parity_on_sample(mesh, ph, ud, upd, up2d, vd, sel, Ro, Jo):
+    """R and J v of the GPU path (float64 and mixed) against the oracle on the sampled rows."""
+    from paper_2009_00706_gb300 import api
+    out = {"nodes": int(sel.size), "bound": {"fp64": 1e-10, "mixed": 2e-5}}
+    for name, p in (("fp64", api.PRECISION_FP64), ("mixed", api.PRECISION_MIXED)):
+        Rg = mesh.residual(ph, ud, upd, up2d, precision=p).cpu().numpy()[sel]
+        Jg = mesh.jvp(ph, ud, upd, vd, up2d, precision=p).cpu().numpy()[sel]
+        r = {}
+        for key, g, o in (("R", Rg, Ro[sel]), ("Jv", Jg, Jo[sel])):
+            r[key + "_rel_l2"] = float(np.linalg.norm(g - o) / max(np.linalg.norm(o), 1e-300))
+            r[key + "_max_abs"] = float(np.abs(g - o).max())
+        out[name] = r
+    return out
 
 
 def run_reference(args):
@@ -318,6 +335,7 @@ def run_ours(args):
     extra["jv_mixed_graph"] = n_active * 20 / (gms / 1e3)
     mesh.use_graphs(False)
     batched = run_batched(args, dev, stream) if not args.no_batched else None
+    bluff = run_bluff(args, dev, stream) if not args.no_bluff else None
 
     # Newton-GMRES step to 1e-8 (float64 residual), block-Jacobi, J v in FP64 vs mixed precision, on the
     # small-sphere problem (7,288 elements: the size the learned preconditioner is evaluated at).  On the
@@ -345,12 +363,13 @@ def run_ours(args):
                             "workload": "small_sphere (7,288 elements, Re 10, BE dt 0.01), block-Jacobi, GMRES(50)"}
         smesh.close()
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             om, ou, oup, ov = oracle_sample(w, 0)
             sel = np.unique(I.splitmix64(77, args.sample_nodes) % om.n_nodes).astype(np.int64)
-            ne, dt = time_oracle(om, w, ou, oup, ov, sel)
+            ne, dt, Ro, Jo = time_oracle(om, w, ou, oup, ov, sel, rows=True)
+            parity = parity_on_sample(mesh, ph, ud, upd, up2d, vd, sel, Ro, Jo)
             cpu = {"value": ne / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"residual + J v of the {ne} active elements touching {args.sample_nodes} seeded nodes "
                              f"of the same mesh ({dt:.1f} s)"}
@@ -368,8 +387,9 @@ def run_ours(args):
                            "surface_points": info["n_surface_points"], "nodes": nn, "precision": args.precision,
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roof, "kernel_time_share": kern_share, "clocks": clocks, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "extra_elements_per_s": extra,
-                "newton_step": newton, "batched": batched, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
+                "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
+                "extra_elements_per_s": extra,
+                "newton_step": newton, "batched": batched, "bluff_pair": bluff, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -433,6 +453,57 @@ def run_batched(args, dev, stream):
     return res
 
 
+def run_bluff(args, dev, stream):
+    """Bluff-body pair (19.8 M elements, 397,488 triangles, Re 1e6, BDF2): mixed J v and residual,
+    direct and as a CUDA graph, with the per-kernel time shares."""
+    import torch
+
+    from paper_2009_00706_gb300 import api
+    w = I.bluff_pair(0)
+    t0 = time.perf_counter()
+    m = api.Mesh.from_workload(w, device=dev.index)
+    build_s = time.perf_counter() - t0
+    info = m.info
+    n_act = info["n_out"] + info["n_cut"]
+    u, up, v = I.state(m.n_nodes, 0)
+    ud, upd, vd = (torch.from_numpy(a).to(dev) for a in (u, up, v))
+    out = torch.empty_like(ud)
+    ph = w.physics
+    prec = api.PRECISION_MIXED
+    res = {"workload": "bluff_pair (two trucks, 16L x 2L x 2L, levels 5-11, Re 1e6, BDF2)", "elements": info["n_elem"],
+           "active_elements": n_act, "cut_elements": info["n_cut"], "cut_points": info["n_cut_points"],
+           "surface_points": info["n_surface_points"], "triangles": info["n_tri"], "build_s": build_s}
+
+    def timed(fn, n=10):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    jv = lambda: m.jvp(ph, ud, upd, vd, upd, precision=prec, out=out, stream=stream)
+    ms = timed(jv)
+    res["jv_mixed"] = {"ms": ms, "elements_per_s": n_act / (ms / 1e3)}
+    ms = timed(lambda: m.residual(ph, ud, upd, upd, precision=prec, out=out, stream=stream))
+    res["residual_mixed"] = {"ms": ms, "elements_per_s": n_act / (ms / 1e3)}
+    m.profile(True)
+    for _ in range(3):
+        jv()
+    prof = m.profile_read()
+    m.profile(False)
+    tot = sum(x[0] for x in prof.values())
+    res["jv_kernel_time_share"] = {k: x[0] / max(tot, 1e-9) for k, x in prof.items()}
+    m.use_graphs(True)
+    ms = timed(jv)
+    res["jv_mixed_graph"] = {"ms": ms, "elements_per_s": n_act / (ms / 1e3)}
+    m.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,6 +516,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-GMRES step timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
+    ap.add_argument("--no-bluff", action="store_true", help="skip the 19.8 M-element bluff-body pair measurement")
     ap.add_argument("--krylov-rtol", type=float, default=1e-3)
     args = ap.parse_args()
     if args.impl == "reference":

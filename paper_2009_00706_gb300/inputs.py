@@ -228,6 +228,47 @@ def sphere_les(seed: int = 0) -> Workload:
         surface=lambda: icosphere(6, 0.5, c, 1e-5, seed), seed=seed)
 
 
+TRUCK_L = 5.05   # truck length: cab 1, gap 0.05, trailer 4
+
+
+def truck(x0: float, yc: float, zb: float, n_per_edge: int, jitter: float, seed: int) -> np.ndarray:
+    """Two disjoint closed filleted boxes (fillet 0.05), bottom-aligned at z = zb and centred on
+    y = yc: a cab 1 x 1 x 0.8 at x in [x0, x0 + 1] in front of a trailer 4 x 1 x 1 at
+    x in [x0 + 1.05, x0 + 5.05].  CCW from outside."""
+    cab = rounded_box((x0, yc - 0.5, zb), (x0 + 1.0, yc + 0.5, zb + 0.8), 0.05, n_per_edge, jitter, seed)
+    trailer = rounded_box((x0 + 1.05, yc - 0.5, zb), (x0 + TRUCK_L, yc + 0.5, zb + 1.0), 0.05, n_per_edge, jitter,
+                          seed + 1)
+    return np.concatenate([cab, trailer])
+
+
+def bluff_pair(seed: int = 0, levels: int = 0, n_per_edge: int = 91) -> Workload:
+    """Two trucks in tandem at a 0.5 L gap (L = 5.05), the first 5 L behind the inlet of a
+    16 L x 2 L x 2 L box, both centred in y and z; each body two rounded boxes of 12 n^2 triangles
+    (n = 91: 198,744 triangles per truck), jitter 1e-5.  Levels 5 (far field) to 11: level 11 in a
+    box around both trucks and the near wake, 10 and 9 in longer wake boxes, 8 around those.
+    `levels` < 0 lowers every refinement level by -levels, not below the far field's 5 (same geometry,
+    smaller mesh).  Re 1e6 on
+    L (mu = L / 1e6), BDF2 dt 0.01.  At full size: 19,791,080 elements, 19,520,852 nodes."""
+    L = TRUCK_L
+    Lx, Ly, Lz = 16 * L, 2 * L, 2 * L
+    yc, zc = 0.5 * Ly, 0.5 * Lz
+    zb = zc - 0.5
+    x1 = 5 * L
+    x2 = x1 + L + 0.5 * L
+    d = levels
+
+    def box(lev, xa, xb, half):
+        return Region(REGION_BOX, max(5, lev + d), (xa, yc - half, zc - half, xb, yc + half, zc + half))
+
+    regions = [box(11, x1 - 0.25, x2 + L + 12.0, 3.1), box(10, x1 - 1.0, x2 + L + 30.0, 3.6),
+               box(9, x1 - 5.0, Lx, 4.5), box(8, 0.0, Lx, 6.0)]
+    return Workload(
+        name="bluff_pair", lo=(0.0, 0.0, 0.0), hi=(Lx, Ly, Lz), base_level=5, regions=regions, lmax=3,
+        physics=Physics(rho=1.0, mu=L / 1e6, dt=0.01, scheme=SCHEME_BDF2),
+        surface=lambda: np.concatenate([truck(x1, yc, zb, n_per_edge, 1e-5, seed),
+                                        truck(x2, yc, zb, n_per_edge, 1e-5, seed + 2)]), seed=seed)
+
+
 def state(n_nodes: int, seed: int = 0, sigma: float = 0.01):
     """u_prev = uniform inflow (1, 0, 0), p = 0; u = u_prev + N(0, sigma^2) on the velocity;
     v ~ N(0, 1) on every dof.  Node-major [n_nodes, 4] float64 (u, v, w, p)."""
