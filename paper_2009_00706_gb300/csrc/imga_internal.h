@@ -188,6 +188,9 @@ void device_free(Mesh& m);
 
 // residual / Jv (vms.cu)
 int conversion_selftest(int64_t n, uint64_t seed, int64_t* mismatches, std::string& err);
+int vms_apply_skip(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                   const imga_physics& ph, int precision, const double* v, double* out, void* stream, const int* skip);
+void vms_prepare();
 int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
               const imga_physics& ph, int precision, const double* v, double* out, void* stream);
 

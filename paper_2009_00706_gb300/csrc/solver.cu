@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -95,6 +96,211 @@ __global__ void scale_copy_kernel(int64_t n, double a, const double* __restrict_
         y[i] = a * x[i];
 }
 
+// ------------------------------------------------------------------------------------------
+// Device-resident GMRES: the Arnoldi step reads the iteration index k and writes the Hessenberg
+// column, the Givens rotations and the residual estimate in device memory, so one captured step
+// graph serves every k.  A step that starts after its cycle ended (stop != 0) does nothing.
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxM = 63;
+
+struct GState {
+    int k;          // Arnoldi index in the current cycle
+    int its;        // iterations of this solve
+    int stop;       // the cycle has ended: converged, breakdown, max iterations or k + 1 = m
+    int kdone;      // Arnoldi vectors of the ended cycle
+    int m, max_its;
+    double target, hn, res;
+    double H[(kMaxM + 1) * kMaxM];
+    double cs[kMaxM], sn[kMaxM], g[kMaxM + 1], y[kMaxM];
+    double h[64], h2[64];
+};
+
+__global__ void dg_start(GState* G, int m, int max_its, double target, double beta, int its) {
+    G->k = 0;
+    G->its = its;
+    G->stop = 0;
+    G->kdone = 0;
+    G->m = m;
+    G->max_its = max_its;
+    G->target = target;
+    G->res = beta;
+    for (int i = 0; i <= m; ++i) G->g[i] = 0.0;
+    G->g[0] = beta;
+}
+
+__global__ void dg_copy_basis(const GState* __restrict__ G, int64_t n, const double* __restrict__ V, double* __restrict__ y) {
+    if (G->stop) return;
+    const double* src = V + (int64_t)G->k * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = src[i];
+}
+
+// partial[b][j] = block b's share of V[j] . w for j <= k; blockIdx.y = group of 8 basis vectors
+__global__ void __launch_bounds__(256) dg_mdot(const GState* __restrict__ G, int64_t n, const double* __restrict__ V,
+                                               const double* __restrict__ w, double* __restrict__ partial) {
+    if (G->stop) return;
+    const int nk = G->k + 1, k0 = kDotGroup * blockIdx.y;
+    if (k0 >= nk) return;
+    const int nv = min(kDotGroup, nk - k0);
+    double acc[kDotGroup];
+    for (int j = 0; j < kDotGroup; ++j) acc[j] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int j = 0; j < kDotGroup; ++j)
+            if (j < nv) acc[j] += V[(int64_t)(k0 + j) * n + i] * wi;
+    }
+    __shared__ double red[kDotGroup][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kDotGroup; ++j) {
+        double v = acc[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[j][wid] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nv) {
+        double v = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[threadIdx.x][q];
+        partial[(int64_t)blockIdx.x * 64 + k0 + threadIdx.x] = v;
+    }
+}
+
+// out[j] = sum_b partial[b][j], j <= k (one block per j)
+__global__ void dg_mdot_final(const GState* __restrict__ G, int nblocks, const double* __restrict__ partial,
+                              double* __restrict__ out) {
+    if (G->stop) return;
+    const int j = blockIdx.x;
+    if (j > G->k) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(int64_t)b * 64 + j];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        out[j] = t;
+    }
+}
+
+// w -= sum_{j <= k} c[j] V[j]
+__global__ void __launch_bounds__(256) dg_maxpy(const GState* __restrict__ G, int64_t n, const double* __restrict__ V,
+                                                const double* __restrict__ c, double* __restrict__ w) {
+    if (G->stop) return;
+    const int nk = G->k + 1;
+    __shared__ double cs[64];
+    if ((int)threadIdx.x < nk) cs[threadIdx.x] = c[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int j = 0; j < nk; ++j) t += cs[j] * V[(int64_t)j * n + i];
+        w[i] -= t;
+    }
+}
+
+// partial[b][0] = block b's share of w . w
+__global__ void __launch_bounds__(256) dg_dot(const GState* __restrict__ G, int64_t n, const double* __restrict__ w,
+                                              double* __restrict__ partial) {
+    if (G->stop) return;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += w[i] * w[i];
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        partial[(int64_t)blockIdx.x * 64] = t;
+    }
+}
+
+// hn = sqrt(sum_b partial[b][0])
+__global__ void dg_norm_final(GState* G, int nblocks, const double* __restrict__ partial) {
+    if (G->stop) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(int64_t)b * 64];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        G->hn = sqrt(fmax(t, 0.0));
+    }
+}
+
+// V[k+1] = w / hn
+__global__ void dg_normalize(const GState* __restrict__ G, int64_t n, const double* __restrict__ w, double* __restrict__ V) {
+    if (G->stop) return;
+    const double hn = G->hn;
+    if (!(hn > 0.0)) return;
+    double* dst = V + (int64_t)(G->k + 1) * n;
+    const double inv = 1.0 / hn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = inv * w[i];
+}
+
+// Hessenberg column k (CGS2 coefficients h + h2, norm hn), previous rotations, the new rotation,
+// the residual estimate |g[k+1]|; ends the cycle or advances k.  One thread.
+__global__ void dg_givens(GState* G) {
+    if (G->stop) return;
+    const int k = G->k, m = G->m;
+    double* H = G->H;
+    for (int i = 0; i <= k; ++i) H[i * m + k] = G->h[i] + G->h2[i];
+    H[(k + 1) * m + k] = G->hn;
+    for (int i = 0; i < k; ++i) {
+        const double t = G->cs[i] * H[i * m + k] + G->sn[i] * H[(i + 1) * m + k];
+        H[(i + 1) * m + k] = -G->sn[i] * H[i * m + k] + G->cs[i] * H[(i + 1) * m + k];
+        H[i * m + k] = t;
+    }
+    const double a = H[k * m + k], b = H[(k + 1) * m + k];
+    const double den = hypot(a, b);
+    const double c = den > 0.0 ? a / den : 1.0, sn = den > 0.0 ? b / den : 0.0;
+    G->cs[k] = c;
+    G->sn[k] = sn;
+    H[k * m + k] = c * a + sn * b;
+    H[(k + 1) * m + k] = 0.0;
+    G->g[k + 1] = -sn * G->g[k];
+    G->g[k] = c * G->g[k];
+    G->its += 1;
+    G->res = fabs(G->g[k + 1]);
+    if (G->res <= G->target || !(G->hn > 0.0) || G->its >= G->max_its || k + 1 >= m) {
+        G->stop = 1;
+        G->kdone = k + 1;
+    } else {
+        G->k = k + 1;
+    }
+}
+
+// y = H^-1 g over the kdone columns of the ended cycle (back substitution).  One thread.
+__global__ void dg_solve_y(GState* G) {
+    const int kk = G->kdone, m = G->m;
+    for (int i = kk - 1; i >= 0; --i) {
+        double t = G->g[i];
+        for (int j = i + 1; j < kk; ++j) t -= G->H[i * m + j] * G->y[j];
+        G->y[i] = t / G->H[i * m + i];
+    }
+}
+
+// w = sum_{j < kdone} y[j] V[j]
+__global__ void __launch_bounds__(256) dg_combine(const GState* __restrict__ G, int64_t n, const double* __restrict__ V,
+                                                  double* __restrict__ w) {
+    const int kk = G->kdone;
+    __shared__ double ys[64];
+    if ((int)threadIdx.x < kk) ys[threadIdx.x] = G->y[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int j = 0; j < kk; ++j) t += ys[j] * V[(int64_t)j * n + i];
+        w[i] = t;
+    }
+}
+
 struct Work {
     int m = 0;
     int64_t n = 0;
@@ -105,6 +311,8 @@ struct Work {
     double* partial = nullptr; // [kRedBlocks][64]
     double* h = nullptr;       // [64]
     double* hh = nullptr;      // pinned host [128]: dot products in, coefficients out
+    GState* G = nullptr;       // device-resident GMRES state
+    double* gh = nullptr;      // pinned host [8]: the head of G read back once per chunk of steps
 };
 
 class Solver {
@@ -131,7 +339,9 @@ public:
             cudaMalloc((void**)&w.Dinv, 4 * n * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.partial, kRedBlocks * 64 * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.h, 64 * sizeof(double)) != cudaSuccess ||
-            cudaMallocHost((void**)&w.hh, 128 * sizeof(double)) != cudaSuccess) {
+            cudaMallocHost((void**)&w.hh, 128 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&w.G, sizeof(GState)) != cudaSuccess ||
+            cudaMallocHost((void**)&w.gh, 8 * sizeof(double)) != cudaSuccess) {
             err = "solver workspace allocation failed";
             cudaGetLastError();
             return 1;
@@ -145,6 +355,8 @@ public:
         Work* w = (Work*)m.solver_work;
         cudaFree(w->V); cudaFree(w->vec); cudaFree(w->D); cudaFree(w->Dinv); cudaFree(w->partial); cudaFree(w->h);
         cudaFreeHost(w->hh);
+        cudaFree(w->G);
+        cudaFreeHost(w->gh);
         delete w;
         m.solver_work = nullptr;
     }
@@ -230,6 +442,125 @@ public:
         if (precond_dataset(M, u, Up, Up2, F, P, O.precision, L.elems, L.n, L.ldx, L.X, T, L.scale, L.K, st)) return 1;
         if (O.precond == 3) return 0;
         return mlp_forward((Mlp*)O.learned, L.X, L.ldx, L.n, L.C, st);
+    }
+
+    ~Solver() {
+        for (auto& g : step_graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap) cudaStreamDestroy(cap);
+    }
+
+    // ---- device-resident GMRES: one Arnoldi step per replay of a captured graph ----
+    static constexpr int kChunk = 8;   // steps launched between two reads of the stop flag
+    cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cap = nullptr;
+
+    double* dev_field(size_t off) { return reinterpret_cast<double*>(reinterpret_cast<char*>(W.G) + off); }
+
+    // precondition V[k], J v, CGS2 against V[0..k], normalise into V[k+1], Givens update
+    int step_launches(const double* u) {
+        GState* G = W.G;
+        double* vk = vec(4);
+        double* z = vec(5);
+        double* w = vec(6);
+        const int grid = (int)std::min<int64_t>(kRedBlocks, (n + 255) / 256);
+        const int grid2 = (int)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256);
+        dg_copy_basis<<<grid2, 256, 0, st>>>(G, n, W.V, vk);
+        precond(vk, z);
+        if (vms_apply_skip(M, u, Up, Up2, F, P, O.precision, z, w, st, &G->stop)) return 1;
+        for (int pass = 0; pass < 2; ++pass) {
+            double* c = dev_field(pass ? offsetof(GState, h2) : offsetof(GState, h));
+            dg_mdot<<<dim3(grid, (kMaxM + 1 + kDotGroup - 1) / kDotGroup), 256, 0, st>>>(G, n, W.V, w, W.partial);
+            dg_mdot_final<<<64, 256, 0, st>>>(G, grid, W.partial, c);
+            dg_maxpy<<<grid2, 256, 0, st>>>(G, n, W.V, c, w);
+        }
+        dg_dot<<<grid, 256, 0, st>>>(G, n, w, W.partial);
+        dg_norm_final<<<1, 256, 0, st>>>(G, grid, W.partial);
+        dg_normalize<<<grid2, 256, 0, st>>>(G, n, w, W.V);
+        dg_givens<<<1, 1, 0, st>>>(G);
+        return cudaGetLastError() == cudaSuccess ? 0 : 1;
+    }
+
+    int capture_step(const double* u) {
+        if (step_graph[pmode]) return 0;
+        if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return 1;
+        vms_prepare();
+        cudaStream_t keep = st;
+        st = cap;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { st = keep; return 1; }
+        const int rc = step_launches(u);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cap, &g);
+        st = keep;
+        if (rc || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return 1;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&step_graph[pmode], g, 0);
+        cudaGraphDestroy(g);
+        return ei == cudaSuccess ? 0 : 1;
+    }
+
+    struct Head { int stop, its; double res; };
+    Head read_head() {
+        cudaMemcpyAsync(W.gh, W.G, offsetof(GState, H), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        GState h;
+        std::memcpy(&h, W.gh, offsetof(GState, H));
+        return {h.stop, h.its, h.res};
+    }
+
+    // the same solve as gmres(), with the Arnoldi steps replayed as a graph and no host round trip
+    // inside a chunk of steps
+    int gmres_dev(const double* u, const double* b, double* x, double rtol, int max_its, int* its_out, double* res_out) {
+        const int m = std::min(W.m, kMaxM);
+        double* r = vec(4);
+        double* z = vec(5);
+        double* w = vec(6);
+        cudaMemsetAsync(x, 0, n * sizeof(double), st);
+        const double bnorm = norm(b);
+        const double target = rtol * bnorm;
+        int its = 0;
+        double res = bnorm, beta = bnorm;
+        if (capture_step(u)) return 1;
+        cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        const int grid2 = (int)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256);
+        while (true) {
+            res = beta;
+            if (beta <= target || its >= max_its || beta == 0.0) break;
+            scale_copy(1.0 / beta, r, basis(0));
+            dg_start<<<1, 1, 0, st>>>(W.G, m, max_its, target, beta, its);
+            Head h{0, its, beta};
+            for (int chunk = 0; !h.stop; ++chunk) {
+                if (chunk > m) return 1;   // every step advances k or ends the cycle
+                for (int c = 0; c < kChunk; ++c)
+                    if (cudaGraphLaunch(step_graph[pmode], st) != cudaSuccess) return 1;
+                h = read_head();
+            }
+            its = h.its;
+            dg_solve_y<<<1, 1, 0, st>>>(W.G);
+            dg_combine<<<grid2, 256, 0, st>>>(W.G, n, W.V, w);
+            precond(w, z);
+            axpby(1.0, z, 1.0, x);
+            // residual of the iterate: the true one decides at the end, the restart starts from it
+            if (jv(u, x, w)) return 1;
+            cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            axpby(-1.0, w, 1.0, r);
+            beta = norm(r);
+            if (h.res <= target || its >= max_its) {
+                res = beta;
+                if (beta <= target * 1.0000001 || its >= max_its) break;
+            }
+        }
+        *its_out = its;
+        *res_out = res;
+        return 0;
+    }
+
+    int solve(const double* u, const double* b, double* x, double rtol, int max_its, int* its_out, double* res_out) {
+        if (M.use_graphs && !M.profiling) return gmres_dev(u, b, x, rtol, max_its, its_out, res_out);
+        return gmres(u, b, x, rtol, max_its, its_out, res_out);
     }
 
     // solve J(u) x = b to ||b - J x|| <= rtol ||b|| (or max_its); x starts at 0
@@ -334,13 +665,13 @@ public:
             int kits = 0;
             double kres = 0.0;
             pmode = O.precond;
-            if (gmres(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
+            if (solve(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
             if (pmode >= 2 && !(kres <= O.krylov_rtol * rn * 1.0000001)) {
                 // the correction did not bring GMRES to its tolerance: redo the solve with block-Jacobi
                 S->fallbacks += 1;
                 S->krylov_its += kits;
                 pmode = 1;
-                if (gmres(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
+                if (solve(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
             }
             S->krylov_per_newton[it] = kits;
             S->krylov_its += kits;

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
     const int c = threadIdx.x & 7, le = threadIdx.x >> 3;
     const int64_t ngroups = (n + EPB - 1) / EPB;
     int64_t gi = blockIdx.x;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     if (gi >= ngroups) return;
     auto corner_id = [&](int64_t grp) -> int32_t {
         int64_t idx = grp * EPB + le;
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 4 : 2) vms_cut(Args
     __shared__ __align__(16) T s_m[WPB][32 * MSTR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t idx = (int64_t)blockIdx.x * WPB + w;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     if (idx >= n) return;
     const int32_t e = list[idx];
     // every 8-lane group gathers the 8 corner rows and forms their monomial coefficients; lanes 0-7 store them
@@ -229,6 +231,7 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     NitschePoint<S, T> P;
     nitsche_fields<S, T, JV>(A, el[i], xr + 3 * i, nr + 3 * i, P);
     const T w = (T)wr[i];
@@ -261,6 +264,7 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
     __shared__ __align__(16) T s_m[WPB][32 * MSTR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t idx = (int64_t)blockIdx.x * WPB + w;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     if (idx >= n) return;
     const int32_t e = list[idx];
     // corner rows: u_s (0-2), p (3), jump d = u_s - g formed in float64 (4-6), tangents at CT
@@ -272,10 +276,10 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         if (JV) ld8<T>(A.ndt, my_id, t8);
         double u4[4], up4[4];
         gather(A, A.U, my_id, u4);
-        if (A.theta != 1.0) gather(A, A.Up, my_id, up4);
+        if (!A.theta1) gather(A, A.Up, my_id, up4);
         T rw[CS];
         for (int k = 0; k < 3; ++k) {
-            const double usk = A.theta == 1.0 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
+            const double usk = A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
             rw[k] = a8[k];
             rw[4 + k] = (T)(usk - A.g[k]);
             rw[CT + k] = t8[k];
@@ -356,6 +360,7 @@ __global__ void strong_rows(Args A, const uint8_t* __restrict__ flag, const uint
                             const double* __restrict__ uval, double ux, double uy, double uz, int jv) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= A.n_nodes) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     const uint8_t f = flag[n];
     uint8_t mask;
     double gv[4];
@@ -600,6 +605,33 @@ int conversion_selftest(int64_t n, uint64_t seed, int64_t* mismatches, std::stri
     if (rc != cudaSuccess) { err = cudaGetErrorString(rc); return 1; }
     *mismatches = (int64_t)h;
     return 0;
+}
+
+// Residual / J v on `stream` without the graph path, every kernel returning at once while *skip is
+// nonzero (steps of a solver loop that is itself captured in a graph).
+int vms_apply_skip(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                   const imga_physics& ph, int precision, const double* v, double* out, void* stream,
+                   const int* skip) {
+    cudaStream_t s = (cudaStream_t)stream;
+    Args A = make_args(m, u, up, up2, f, ph, v, out);
+    A.skip = skip;
+    const bool jv = v != nullptr;
+    if (cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
+    if (precision == 0) {
+        if (jv) launch_all<double, true>(m, A, s); else launch_all<double, false>(m, A, s);
+    } else {
+        if (jv) launch_all<float, true>(m, A, s); else launch_all<float, false>(m, A, s);
+    }
+    launch_strong_rows(m, A, ph, jv, s);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+// one-time launch attributes of the element kernels (call before any stream capture)
+void vms_prepare() {
+    interior_blocks_per_sm<double, true>();
+    interior_blocks_per_sm<double, false>();
+    interior_blocks_per_sm<float, true>();
+    interior_blocks_per_sm<float, false>();
 }
 
 int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,

@@ -124,6 +124,9 @@ struct Args {
     const double* V;
     double* out;
     double rho, mu, theta, c0, c1, c2;   // c_k = time coefficients / dt
+    float thetaf, c0f, c2f;               // the same in float32
+    int theta1, has_c2;                   // theta == 1, c2 != 0 (tests off the float64 unit)
+    const int* skip;                      // non-null and nonzero: return at once (solver steps captured in graphs)
     double K0dt;                         // 4 / dt^2
     double CInu2;                        // C_I nu^2
     double irho;
@@ -268,6 +271,9 @@ __device__ __forceinline__ float d2f(double x) {
     f += (rest > half || (rest == half && (f & 1u))) ? 1u : 0u;
     return __uint_as_float(f);
 }
+template <class T> __device__ __forceinline__ T tcoef(double d, float f);
+template <> __device__ __forceinline__ float tcoef<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double tcoef<double>(double d, float) { return d; }
 template <class T> __device__ __forceinline__ T to_t(double x);
 template <> __device__ __forceinline__ float to_t<float>(double x) { return d2f(x); }
 template <> __device__ __forceinline__ double to_t<double>(double x) { return x; }
@@ -285,16 +291,18 @@ template <class T, bool JV>
 __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T* __restrict__ ndt, T* __restrict__ ndf) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= A.n_nodes) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     double u[4], up[4], up2[4] = {0, 0, 0, 0};
     load4(A.U, n, u);
     load4(A.Up, n, up);
-    if (A.c2 != 0.0) load4(A.Up2, n, up2);
+    if (A.has_c2) load4(A.Up2, n, up2);
+    const T c0 = tcoef<T>(A.c0, A.c0f), c2 = tcoef<T>(A.c2, A.c2f), th = tcoef<T>(A.theta, A.thetaf);
     T v8[8];
     for (int k = 0; k < 3; ++k) {
-        v8[k] = A.theta == 1.0 ? to_t<T>(u[k]) : to_t<T>(A.theta * u[k] + (1.0 - A.theta) * up[k]);
+        v8[k] = A.theta1 ? to_t<T>(u[k]) : to_t<T>(A.theta * u[k] + (1.0 - A.theta) * up[k]);
         T d1 = to_t<T>(u[k] - up[k]);
-        T d2 = A.c2 != 0.0 ? to_t<T>(up2[k] - up[k]) : T(0);
-        v8[4 + k] = (T)A.c0 * d1 + (T)A.c2 * d2;
+        T d2 = A.has_c2 ? to_t<T>(up2[k] - up[k]) : T(0);
+        v8[4 + k] = c0 * d1 + c2 * d2;
     }
     v8[3] = to_t<T>(u[3]);
     v8[7] = T(0);
@@ -310,7 +318,7 @@ __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T*
         load4(A.V, n, v);
         T vt[4] = {to_t<T>(v[0]), to_t<T>(v[1]), to_t<T>(v[2]), to_t<T>(v[3])};
         T t8[8];
-        for (int k = 0; k < 3; ++k) { t8[k] = (T)A.theta * vt[k]; t8[4 + k] = (T)A.c0 * vt[k]; }
+        for (int k = 0; k < 3; ++k) { t8[k] = th * vt[k]; t8[4 + k] = c0 * vt[k]; }
         t8[3] = vt[3];
         t8[7] = T(0);
         for (int k = 0; k < 8; ++k) ndt[8 * n + k] = t8[k];
@@ -324,6 +332,7 @@ __global__ void __launch_bounds__(256) node_prep_hanging(Args A, T* __restrict__
                                                          T* __restrict__ ndf) {
     const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= A.n_hang) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     const int64_t n = A.n_nodes + h;
     const int32_t* hp = A.hpar + 4 * h;
     const int np = hp[2] >= 0 ? 4 : 2;
@@ -777,11 +786,11 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, const d
         if (JV) ld8<T>(A.ndt, P.ids[c], t8);
         double u4[4], up4[4];
         gather(A, A.U, P.ids[c], u4);
-        if (A.theta != 1.0) gather(A, A.Up, P.ids[c], up4);
+        if (!A.theta1) gather(A, A.Up, P.ids[c], up4);
         const T ph = P.B.phi[c];
         for (int k = 0; k < 3; ++k) {
             S vu = make<S, T>(a8[k], t8[k]);
-            double usk = A.theta == 1.0 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
+            double usk = A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
             S jump = make<S, T>((T)(usk - A.g[k]), t8[k]);
             P.us[k] = P.us[k] + ph * vu;
             P.d[k] = P.d[k] + ph * jump;
@@ -826,6 +835,7 @@ inline Args make_args(const Mesh& m, const double* u, const double* up, const do
         A.wf[l] = (float)A.wd[l];
     }
     A.ndv = A.ndt = A.ndf = nullptr;
+    A.skip = nullptr;
     A.U = u;
     A.Up = up;
     A.Up2 = up2 ? up2 : up;
@@ -842,6 +852,11 @@ inline Args make_args(const Mesh& m, const double* u, const double* up, const do
     A.c0 = c[0] / ph.dt;
     A.c1 = c[1] / ph.dt;
     A.c2 = c[2] / ph.dt;
+    A.thetaf = (float)A.theta;
+    A.c0f = (float)A.c0;
+    A.c2f = (float)A.c2;
+    A.theta1 = A.theta == 1.0;
+    A.has_c2 = A.c2 != 0.0;
     A.K0dt = 4.0 / (ph.dt * ph.dt);
     const double nu = ph.mu / ph.rho;
     A.CInu2 = ph.C_I * nu * nu;

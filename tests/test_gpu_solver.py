@@ -116,3 +116,25 @@ def test_newton_matches_oracle_solver(dev):
     assert st["converged"]
     ug = ud.cpu().numpy().ravel()
     assert np.linalg.norm(ug - uo) <= 1e-7 * np.linalg.norm(uo)
+
+
+@pytest.mark.parametrize("prec", [api.PRECISION_FP64, api.PRECISION_MIXED])
+def test_graph_replayed_gmres_matches_host_driven(sphere, dev, prec):
+    """With CUDA graphs on, GMRES keeps its Hessenberg matrix and rotations on the device and replays
+    one captured Arnoldi step; the Newton solve is the same as the host-driven one."""
+    w, g, o = sphere
+    u, up, _ = I.state(g.n_nodes, 14)
+    R0 = np.linalg.norm(o.residual(w.physics, u, up))
+    out = {}
+    try:
+        for graphs in (False, True):
+            g.use_graphs(graphs)
+            ud = T(u, dev)
+            st = g.newton_step(w.physics, ud, T(up, dev), precision=prec, precond=1, rtol=1e-8, gmres_m=50)
+            assert st["converged"], (graphs, st)
+            assert np.linalg.norm(o.residual(w.physics, ud.cpu().numpy(), up)) <= 1.5e-8 * R0
+            out[graphs] = st
+    finally:
+        g.use_graphs(False)
+    assert out[True]["newton_its"] == out[False]["newton_its"]
+    assert abs(out[True]["krylov_its"] - out[False]["krylov_its"]) <= 0.05 * out[False]["krylov_its"] + 5, out
