@@ -245,6 +245,7 @@ def run_ours(args):
     def step(p=prec):
         mesh.jvp(ph, ud, upd, vd, up2d, precision=p, out=out, stream=stream)
 
+    mesh.autotune(True)   # the first warm-up step picks the Intercepted-element tile shape
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -386,7 +387,8 @@ def run_ours(args):
                            "cut_elements": info["n_cut"], "cut_points": info["n_cut_points"],
                            "surface_points": info["n_surface_points"], "nodes": nn, "precision": args.precision,
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "kernel_time_share": kern_share, "clocks": clocks, "e2e": e2e,
+                "roofline": roof, "kernel_time_share": kern_share,
+                "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])), "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
                 "extra_elements_per_s": extra,
                 "newton_step": newton, "batched": batched, "bluff_pair": bluff, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
@@ -425,6 +427,9 @@ def run_batched(args, dev, stream):
             m.jvp(w.physics, u, up, v, precision=prec, out=o, stream=stream)
 
     res = {"problems": 64, "elements": int(B.n_elem), "active_elements": int(n_act), "batch_build_s": tb}
+    B.autotune(True)
+    for m in sep:
+        m.autotune(True)
     for name, fn in (("one_batched_launch", batched_step), ("sequential_64_meshes", sequential_step)):
         fn()
         torch.cuda.synchronize()
@@ -436,6 +441,7 @@ def run_batched(args, dev, stream):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / 10
         res[name] = {"ms_per_jv": ms, "elements_per_s": n_act / (ms / 1e3)}
+    res["cut_tile"] = dict(zip(("warps_per_block", "longest_first", "candidate_ms"), B.tuning()[(prec, "jvp")]))
     B.use_graphs(True)
     batched_step()
     torch.cuda.synchronize()
@@ -486,6 +492,7 @@ def run_bluff(args, dev, stream):
         return a.elapsed_time(b) / n
 
     jv = lambda: m.jvp(ph, ud, upd, vd, upd, precision=prec, out=out, stream=stream)
+    m.autotune(True)
     ms = timed(jv)
     res["jv_mixed"] = {"ms": ms, "elements_per_s": n_act / (ms / 1e3)}
     ms = timed(lambda: m.residual(ph, ud, upd, upd, precision=prec, out=out, stream=stream))

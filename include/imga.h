@@ -275,8 +275,21 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * 32 graphs are kept per mesh), ordered after the work already queued on the caller's stream and
  * before anything queued on it later.  The first call for a key must not itself run inside a stream
  * capture.  imga_set_dirichlet drops the cached graphs.  Profiling (imga_profile) bypasses them. */
-enum { IMGA_OPT_GRAPHS = 1 };
+/* IMGA_OPT_AUTOTUNE (value 1): the next imga_residual / imga_jvp call of each precision and kind
+ * (residual or J v) first times the Intercepted-element kernel in every tile shape -- 2, 4 or 8
+ * warps per block (8 in mixed precision only), elements in Morton order or longest first -- on the
+ * call's own inputs and keeps the fastest for that mesh.  This follows the cost model of
+ * Eq. (Wpart): the bucket of elements with uneven quadrature counts (8 to 4096 points).  Tuning
+ * synchronises the stream and is skipped inside a stream capture.  Value 0 restores the default
+ * shape (4 warps, Morton order).  Both values drop the cached graphs. */
+enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2 };
 imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
+
+/* The tile shapes in use.  shape[8] = {warps per block, longest-first order} for
+ * [float64, mixed] x [residual, J v].  If ms is non-null, ms[24] receives the per-launch milliseconds
+ * of the last tuning for the same 4 cases x 6 candidates (warps 2, 4, 8) x (Morton, longest first);
+ * an entry is 0 where not measured. */
+imga_status imga_tuning(imga_mesh mesh, int32_t* shape, float* ms);
 
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.

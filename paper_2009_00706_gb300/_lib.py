@@ -137,6 +137,7 @@ SIGNATURES = {
     "imga_jvp": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),
     "imga_jvp_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),
     "imga_selftest_conversions": (C.c_int, [_int, _i64, C.c_uint64, C.POINTER(C.c_int64)]),
+    "imga_tuning": (C.c_int, [_vp, _vp, _vp]),
     "imga_set_dirichlet": (C.c_int, [_vp, _vp, _vp, _vp]),
     "imga_element_jacobians": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _i64, _vp, _vp]),
     "imga_newton_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), C.POINTER(SolverOpts),

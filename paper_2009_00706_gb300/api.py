@@ -268,6 +268,22 @@ class Mesh:
         """imga_set_option(IMGA_OPT_GRAPHS): replay residual / J v calls as CUDA graphs."""
         check(_lib.load().imga_set_option(self.h, 1, 1 if on else 0))
 
+    def autotune(self, on=True):
+        """imga_set_option(IMGA_OPT_AUTOTUNE): tune the Intercepted-element tile shape on the next call
+        of each precision and kind."""
+        check(_lib.load().imga_set_option(self.h, 2, 1 if on else 0))
+
+    def tuning(self):
+        """{(precision, 'residual' | 'jvp'): (warps per block, longest first, candidate ms[6])}."""
+        shape = np.zeros(8, np.int32)
+        ms = np.zeros(24, np.float32)
+        check(_lib.load().imga_tuning(self.h, shape.ctypes.data_as(C.c_void_p), ms.ctypes.data_as(C.c_void_p)))
+        out = {}
+        for p in range(2):
+            for j, kind in enumerate(("residual", "jvp")):
+                out[(p, kind)] = (int(shape[4 * p + 2 * j]), int(shape[4 * p + 2 * j + 1]), ms[12 * p + 6 * j:12 * p + 6 * j + 6].tolist())
+        return out
+
     def profile_read(self):
         """{kernel: (total ms, launches)} since profiling was enabled (synchronises)."""
         ms = np.zeros(5)

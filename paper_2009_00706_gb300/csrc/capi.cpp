@@ -397,9 +397,29 @@ imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
             if (!value) imga::graphs_free(h->m);
             h->m.use_graphs = value != 0;
             return IMGA_OK;
+        case IMGA_OPT_AUTOTUNE:
+            for (int p = 0; p < 2; ++p)
+                for (int j = 0; j < 2; ++j) {
+                    h->m.tune_pending[p][j] = value != 0;
+                    if (!value) h->m.cut_tune[p][j] = imga::Mesh::CutTune();
+                }
+            imga::graphs_free(h->m);
+            return IMGA_OK;
         default:
             return fail(IMGA_ERR_INVALID_ARG, "unknown option");
     }
+}
+
+imga_status imga_tuning(imga_mesh h, int32_t* shape, float* ms) {
+    if (!h || !shape) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    for (int p = 0; p < 2; ++p)
+        for (int j = 0; j < 2; ++j) {
+            shape[4 * p + 2 * j] = h->m.cut_tune[p][j].wpb;
+            shape[4 * p + 2 * j + 1] = h->m.cut_tune[p][j].lpt;
+            if (ms)
+                for (int c = 0; c < 6; ++c) ms[12 * p + 6 * j + c] = h->m.cut_tune_ms[p][j][c];
+        }
+    return IMGA_OK;
 }
 
 imga_status imga_profile(imga_mesh h, int enable) {

@@ -471,7 +471,7 @@ int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags,
 void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
-                    d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.sq_elem, d.sq_x,
+                    d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.cut_order, d.sq_elem, d.sq_x,
                     d.sq_n, d.sq_w, d.sq_taub, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot};
     for (void* p : ptrs)
         if (p) cudaFree(p);

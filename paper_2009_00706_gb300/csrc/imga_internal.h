@@ -82,6 +82,7 @@ struct DeviceMesh {
     double* sq_n = nullptr;       // [n][3]
     double* sq_w = nullptr;
     double* sq_taub = nullptr;    // 1 / h_b
+    int32_t* cut_order = nullptr;   // Intercepted list positions by decreasing point count (autotuner)
     int32_t* sq_list = nullptr;   // elements hosting at least kNitscheDenseMin surface points
     int64_t* sq_off = nullptr;    // [n_sq_elem + 1] their point ranges in the sorted arrays
     // per-call node workspace (node_prep): value, tangent and force data of every independent and
@@ -147,6 +148,12 @@ struct Mesh {
     // CUDA-graph execution of residual / J v (imga_set_option): cached executable graphs keyed by the
     // call's pointers and parameters, and two side streams + fork/join events for parallel branches
     bool use_graphs = false;
+    // Intercepted-element bucket: warps per block and element order (0 Morton, 1 longest first),
+    // per [float64 0 / mixed 1][residual 0 / J v 1]; set by the autotuner
+    struct CutTune { int wpb = 4, lpt = 0; };
+    CutTune cut_tune[2][2];
+    float cut_tune_ms[2][2][6] = {};   // candidate times of the last tuning (ms per launch)
+    bool tune_pending[2][2] = {{false, false}, {false, false}};
     std::vector<std::pair<GraphKey, void*>> graphs;
     void* side[3] = {nullptr, nullptr, nullptr};   // two branch streams + the private capture stream
     void* fork_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // fork, 2 joins, caller->graph, graph->caller

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
 // ------------------------------------------------------------------------------------------
 // Intercepted elements: one warp per element
 // ------------------------------------------------------------------------------------------
-constexpr int WPB = 4;   // warps per block
+constexpr int WPB = 4;   // warps per block of the per-element surface kernel
 
 // Warp epilogue of the per-element kernels: lane l holds the monomial moments M of its points;
 // sum them over the lanes (transpose through shared memory s_m [32][32 + pad]), run the backward
@@ -172,17 +172,20 @@ __device__ __forceinline__ void warp_scatter_moments(const Args& A, const T M[32
     if ((lane & 3) == 0) scatter_t(A, id, r);
 }
 
-template <class T, bool JV>
-__global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 4 : 2) vms_cut(Args A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
-                                                    const void* __restrict__ pts, int64_t n) {
+// W warps per block (a tile shape the autotuner picks); `order` (or null) permutes the list
+template <class T, bool JV, int W>
+__global__ void __launch_bounds__(32 * W, (sizeof(T) == 4 ? 16 : 8) / W) vms_cut(Args A, const int32_t* __restrict__ list,
+                                                    const int64_t* __restrict__ off, const void* __restrict__ pts,
+                                                    const int32_t* __restrict__ order, int64_t n) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
     constexpr int PAD = 16 / (int)sizeof(T), MSTR = 32 + PAD;
-    __shared__ __align__(16) T s_nd[WPB][8 * CS];
-    __shared__ __align__(16) T s_m[WPB][32 * MSTR];
+    __shared__ __align__(16) T s_nd[W][8 * CS];
+    __shared__ __align__(16) T s_m[W][32 * MSTR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t idx = (int64_t)blockIdx.x * WPB + w;
+    const int64_t slot = (int64_t)blockIdx.x * W + w;
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
-    if (idx >= n) return;
+    if (slot >= n) return;
+    const int64_t idx = order ? (int64_t)order[slot] : slot;
     const int32_t e = list[idx];
     // every 8-lane group gathers the 8 corner rows and forms their monomial coefficients; lanes 0-7 store them
     const int c8 = lane & 7;
@@ -401,6 +404,72 @@ struct Timed {
     }
 };
 
+template <class T, bool JV>
+void launch_cut(const Mesh& m, const Args& A, cudaStream_t s, int wpb, int lpt) {
+    const int64_t nc = (int64_t)m.cut_list.size();
+    const void* pts = std::is_same<T, float>::value ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
+    const int32_t* order = lpt ? m.d.cut_order : nullptr;
+    switch (wpb) {
+        case 2: vms_cut<T, JV, 2><<<(unsigned)((nc + 1) / 2), 64, 0, s>>>(A, m.d.cut_list, m.d.cut_off, pts, order, nc); break;
+        case 8:
+            if constexpr (sizeof(T) == 4) {
+                vms_cut<T, JV, 8><<<(unsigned)((nc + 7) / 8), 256, 0, s>>>(A, m.d.cut_list, m.d.cut_off, pts, order, nc);
+                break;
+            }
+            [[fallthrough]];
+        default: vms_cut<T, JV, 4><<<(unsigned)((nc + 3) / 4), 128, 0, s>>>(A, m.d.cut_list, m.d.cut_off, pts, order, nc);
+    }
+}
+
+// Autotuner of the Intercepted-element bucket: with the node data of this call prepared, time every
+// (warps per block, element order) candidate on the call's own inputs (3 launches each after one
+// untimed) and keep the fastest.  Writes into the output vector, which the call then recomputes.
+template <class T, bool JV>
+int autotune_cut(Mesh& m, Args A, cudaStream_t s) {
+    const int64_t nc = (int64_t)m.cut_list.size();
+    Mesh::CutTune& ct = m.cut_tune[sizeof(T) == 4][JV];
+    m.tune_pending[sizeof(T) == 4][JV] = false;
+    if (nc == 0) return 0;
+    if (!m.d.cut_order) {   // longest first: positions of the list by decreasing point count
+        std::vector<int32_t> ord(nc);
+        for (int64_t i = 0; i < nc; ++i) ord[i] = (int32_t)i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+            return m.cut_off[a + 1] - m.cut_off[a] > m.cut_off[b + 1] - m.cut_off[b];
+        });
+        if (cudaMalloc((void**)&m.d.cut_order, nc * sizeof(int32_t)) != cudaSuccess ||
+            cudaMemcpy(m.d.cut_order, ord.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            return 1;
+    }
+    const int64_t next = m.n_nodes() + m.n_hang();
+    T* ndv = node_workspace<T>(m, nullptr);
+    A.ndv = ndv;
+    A.ndt = ndv + 8 * next;
+    A.ndf = A.F ? ndv + 16 * next : nullptr;
+    launch_node_prep<T, JV>(A, ndv, (T*)A.ndt, (T*)A.ndf, s);
+    const int wpbs[3] = {2, 4, 8};
+    const int nw = sizeof(T) == 4 ? 3 : 2;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int wi = 0; wi < nw; ++wi)
+        for (int lpt = 0; lpt < 2; ++lpt) {
+            launch_cut<T, JV>(m, A, s, wpbs[wi], lpt);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) launch_cut<T, JV>(m, A, s, wpbs[wi], lpt);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            m.cut_tune_ms[sizeof(T) == 4][JV][2 * wi + lpt] = ms;
+            if (ms < best) { best = ms; ct.wpb = wpbs[wi]; ct.lpt = lpt; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
 // Resident CTAs of the persistent interior kernel per SM (queried once; also sets its dynamic smem opt-in).
 template <class T, bool JV>
 int interior_blocks_per_sm() {
@@ -448,8 +517,8 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     }
     if (nc > 0) {
         Timed t(m, 1, sc);
-        const void* pts = std::is_same<T, float>::value ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
-        vms_cut<T, JV><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, 0, sc>>>(A, m.d.cut_list, m.d.cut_off, pts, nc);
+        const Mesh::CutTune& ct = m.cut_tune[sizeof(T) == 4][JV];
+        launch_cut<T, JV>(m, A, sc, ct.wpb, ct.lpt);
     }
     const int64_t nsp = m.n_sq_sparse, nse = m.n_sq_elem;
     if (nsp > 0) {
@@ -493,6 +562,17 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
     cudaStream_t s = (cudaStream_t)stream;
     Args A = make_args(m, u, up, up2, f, ph, v, out);
     const bool jv = v != nullptr;
+    if (m.tune_pending[precision != 0][jv] && !ws) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (cs == cudaStreamCaptureStatusNone) {
+            Mesh& mm = const_cast<Mesh&>(m);
+            const int rc = precision == 0 ? (jv ? autotune_cut<double, true>(mm, A, s) : autotune_cut<double, false>(mm, A, s))
+                                          : (jv ? autotune_cut<float, true>(mm, A, s) : autotune_cut<float, false>(mm, A, s));
+            if (rc) return 1;
+            graphs_free(mm);   // captured launches carry the old tile shapes
+        }
+    }
     if (m.use_graphs && !ws && !m.profiling) {
         // Replay (or capture once) the whole call as a CUDA graph with parallel branches.  Capture runs on
         // a private stream (the legacy default stream cannot be captured); the graph is launched on a

@@ -72,3 +72,24 @@ def test_graph_replay_equals_direct(dev, prec):
         assert rel(got, ref) <= (1e-12 if prec == 0 else 1e-6), k
     R = g.residual(w.physics, ud, upd, precision=prec).cpu().numpy()
     assert rel(R, m.residual(w.physics, ud, upd, precision=prec).cpu().numpy()) <= (1e-12 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [api.PRECISION_FP64, api.PRECISION_MIXED])
+def test_autotuned_cut_bucket_equals_default(dev, prec):
+    """The autotuner times every tile shape of the Intercepted-element kernel and keeps one; the
+    result does not depend on the shape (sums reorder only)."""
+    probs = [wl for wl, t, Re in I.batched_spheres(12) if t < 40000][:3]
+    B = api.Mesh.batch(probs, device=0)
+    u, up, v = I.state(B.n_nodes, 21)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ph = probs[0].physics
+    ref = B.jvp(ph, T(u), T(up), T(v), precision=prec).cpu().numpy()
+    B.autotune(True)
+    got = B.jvp(ph, T(u), T(up), T(v), precision=prec).cpu().numpy()
+    wpb, lpt, ms = B.tuning()[(prec, "jvp")]
+    assert wpb in ((2, 4, 8) if prec == api.PRECISION_MIXED else (2, 4)) and lpt in (0, 1)
+    assert all(t > 0 for t in ms[: (6 if prec == api.PRECISION_MIXED else 4)])
+    assert rel(got, ref) <= (1e-12 if prec == api.PRECISION_FP64 else 1e-6)
+    again = B.jvp(ph, T(u), T(up), T(v), precision=prec).cpu().numpy()
+    assert rel(again, ref) <= (1e-12 if prec == api.PRECISION_FP64 else 1e-6)
+    B.close()
