@@ -172,78 +172,155 @@ __global__ void markers_kernel(GeomView g, int8_t* marker, uint8_t* cflags, unsi
     marker[e] = (int8_t)(flags == 0xff ? 1 : flags == 0 ? 0 : 2);
 }
 
+// ------------------------------------------------------------------------------------------
+// Warp-cooperative ray parity: the whole warp casts one point's ray (P uniform across the warp);
+// lanes stride over the candidate triangles, the hit count is a warp sum and a graze anywhere is
+// a graze of the ray.  Same result as ray_parity / ray_classify (the parity of an integer sum).
+// ------------------------------------------------------------------------------------------
+__device__ int warp_ray_parity(const GeomView& g, const double P[3], int dir, bool* graze) {
+    const int lane = threadIdx.x & 31;
+    int count = 0;
+    bool gz = false;
+    if (dir == 0) {
+        const int a = (int)floor((P[1] - g.rg_y0) / g.rg_dy);
+        const int b = (int)floor((P[2] - g.rg_z0) / g.rg_dz);
+        if (g.rg_ny != 0 && a >= 0 && b >= 0 && a < g.rg_ny && b < g.rg_nz) {
+            const int c = a * g.rg_nz + b;
+            for (int32_t i = g.rg_off[c] + lane; i < g.rg_off[c + 1]; i += 32) count += mt_hit(g, g.rg_idx[i], P, 0, &gz);
+        }
+    } else {
+        for (int64_t t = lane; t < g.n_tri; t += 32) count += mt_hit(g, t, P, dir, &gz);
+    }
+    const unsigned total = __reduce_add_sync(0xffffffffu, (unsigned)count);
+    *graze = __any_sync(0xffffffffu, gz) != 0;
+    return (int)(total & 1u);
+}
+
+__device__ int warp_ray_classify(const GeomView& g, const double P[3], unsigned long long* nrays) {
+    if ((threadIdx.x & 31) == 0) atomicAdd(nrays, 1ull);
+    int par[3];
+    for (int dir = 0; dir < 3; ++dir) {
+        bool gz;
+        par[dir] = warp_ray_parity(g, P, dir, &gz);
+        if (!gz) return par[dir];
+    }
+    return (par[0] + par[1] + par[2]) >= 2 ? 1 : 0;
+}
+
+// Lanes whose normal test was undecided (r < 0 and `want`) get the ray verdict, one point at a time
+// for the whole warp.
+__device__ void warp_resolve(const GeomView& g, bool want, const double P[3], int& r, unsigned long long* nrays) {
+    unsigned need = __ballot_sync(0xffffffffu, want && r < 0);
+    while (need) {
+        const int src = __ffs(need) - 1;
+        double Q[3];
+        for (int k = 0; k < 3; ++k) Q[k] = __shfl_sync(0xffffffffu, P[k], src);
+        const int v = warp_ray_classify(g, Q, nrays);
+        if ((int)(threadIdx.x & 31) == src) r = v;
+        need &= need - 1;
+    }
+}
+
 struct Cell { uint8_t l; uint32_t i[3]; };
 
-// depth-first sub-cell walk of one Intercepted element; pts == nullptr counts only
-__device__ int64_t cut_walk(const GeomView& g, int64_t e, int lmax, double* pts, unsigned long long* nrays) {
+// Depth-first sub-cell walk of one Intercepted element (Fig. GP), a warp per element: lanes 0-7
+// classify the 8 Gauss points of the cell on top of the stack (undecided ones by warp-cooperative
+// rays); all In -> dropped, all Out -> kept, mixed -> split into 8 children (pushed by lanes 0-7 so
+// child 0 is visited first) until lmax, where the Out points are kept.  Kept points are compacted
+// in Gauss-point order.  pts == nullptr counts only.
+constexpr int kWalkWarps = 4;
+__device__ int64_t cut_walk_warp(const GeomView& g, int64_t e, int lmax, double* pts, float* ptsf,
+                                 unsigned long long* nrays, Cell* st) {
+    const int lane = threadIdx.x & 31, gp = lane & 7;
     const uint32_t* a = g.anc + 3 * e;
-    double h = (double)(1u << (kMaxDepth - g.lev[e])) * g.scale, hh = 0.5 * h;
+    const double h = (double)(1u << (kMaxDepth - g.lev[e])) * g.scale, hh = 0.5 * h;
     double x0[3];
     for (int k = 0; k < 3; ++k) x0[k] = g.lo[k] + (double)a[k] * g.scale;
-    Cell st[8 * 6];
-    int sp = 0;
-    st[sp++] = Cell{0, {0, 0, 0}};
+    if (lane == 0) st[0] = Cell{0, {0, 0, 0}};
+    __syncwarp();
+    int sp = 1;
     int64_t n = 0;
     while (sp > 0) {
-        Cell c = st[--sp];
-        double xi[8][3];
-        int in = 0;
-        for (int gp = 0; gp < 8; ++gp) {
-            double P[3];
-            for (int k = 0; k < 3; ++k) {
-                double num = (double)(2 * c.i[k] + 1) + (((gp >> k) & 1) ? kGauss : -kGauss);
-                xi[gp][k] = num / (double)(1u << c.l) - 1.0;
-                P[k] = x0[k] + (xi[gp][k] + 1.0) * hh;
-            }
-            if (is_in(g, e, P, nrays)) in |= 1 << gp;
+        const Cell c = st[--sp];
+        __syncwarp();
+        double xi[3], P[3];
+        for (int k = 0; k < 3; ++k) {
+            const double num = (double)(2 * c.i[k] + 1) + (((gp >> k) & 1) ? kGauss : -kGauss);
+            xi[k] = num / (double)(1u << c.l) - 1.0;
+            P[k] = x0[k] + (xi[k] + 1.0) * hh;
         }
-        double w = 1.0 / (double)(1u << (3 * c.l));
-        if (in == 0xff) continue;
-        if (in != 0 && c.l < lmax) {
-            for (int ch = 7; ch >= 0; --ch)
-                st[sp++] = Cell{(uint8_t)(c.l + 1), {2 * c.i[0] + (ch & 1), 2 * c.i[1] + ((ch >> 1) & 1), 2 * c.i[2] + ((ch >> 2) & 1)}};
+        int r = lane < 8 ? normal_test(g, e, P, 1e-12 * h) : 0;
+        warp_resolve(g, lane < 8, P, r, nrays);
+        const unsigned in = __ballot_sync(0xffffffffu, lane < 8 && r == 1) & 0xffu;
+        if (in == 0xffu) continue;
+        if (in != 0u && c.l < lmax) {
+            if (lane < 8)
+                st[sp + 7 - lane] = Cell{(uint8_t)(c.l + 1), {2 * c.i[0] + (lane & 1), 2 * c.i[1] + ((lane >> 1) & 1),
+                                                            2 * c.i[2] + ((lane >> 2) & 1)}};
+            __syncwarp();
+            sp += 8;
             continue;
         }
-        for (int gp = 0; gp < 8; ++gp) {
-            if ((in >> gp) & 1) continue;
-            if (pts) {
-                double* o = pts + 4 * n;
-                o[0] = xi[gp][0]; o[1] = xi[gp][1]; o[2] = xi[gp][2]; o[3] = w;
-            }
-            ++n;
+        const unsigned out = ~in & 0xffu;
+        if (pts && lane < 8 && ((out >> lane) & 1u)) {
+            const int64_t q = n + __popc(out & ((1u << lane) - 1u));
+            const double w = 1.0 / (double)(1u << (3 * c.l));
+            double* o = pts + 4 * q;
+            o[0] = xi[0]; o[1] = xi[1]; o[2] = xi[2]; o[3] = w;
+            float* of = ptsf + 4 * q;
+            of[0] = (float)xi[0]; of[1] = (float)xi[1]; of[2] = (float)xi[2]; of[3] = (float)w;
         }
+        n += __popc(out);
     }
     return n;
 }
 
-__global__ void cut_count_kernel(GeomView g, const int32_t* cut_list, int64_t n_cut, int lmax, int64_t* count,
-                                 unsigned long long* nrays) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kWalkWarps) cut_count_warp(GeomView g, const int32_t* cut_list, int64_t n_cut,
+                                                                  int lmax, int64_t* count, unsigned long long* nrays) {
+    __shared__ Cell st[kWalkWarps][8 * 6];
+    const int w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kWalkWarps + w;
     if (i >= n_cut) return;
-    count[i] = cut_walk(g, cut_list[i], lmax, nullptr, nrays);
+    const int64_t c = cut_walk_warp(g, cut_list[i], lmax, nullptr, nullptr, nrays, st[w]);
+    if ((threadIdx.x & 31) == 0) count[i] = c;
 }
 
-__global__ void cut_write_kernel(GeomView g, const int32_t* cut_list, int64_t n_cut, int lmax, const int64_t* off,
-                                 double* pts, float* ptsf, unsigned long long* nrays) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kWalkWarps) cut_write_warp(GeomView g, const int32_t* cut_list, int64_t n_cut,
+                                                                  int lmax, const int64_t* off, double* pts, float* ptsf,
+                                                                  unsigned long long* nrays) {
+    __shared__ Cell st[kWalkWarps][8 * 6];
+    const int w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kWalkWarps + w;
     if (i >= n_cut) return;
-    double* o = pts + 4 * off[i];
-    int64_t n = cut_walk(g, cut_list[i], lmax, o, nrays);
-    for (int64_t k = 0; k < 4 * n; ++k) ptsf[4 * off[i] + k] = (float)o[k];
+    cut_walk_warp(g, cut_list[i], lmax, pts + 4 * off[i], ptsf + 4 * off[i], nrays, st[w]);
 }
 
-__global__ void classify_kernel(GeomView g, const double* pts, int64_t n, uint8_t* flags, unsigned long long* nrays) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double P[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
-    int64_t I[3];
-    for (int k = 0; k < 3; ++k) {
-        double f = floor((P[k] - g.lo[k]) / g.scale);
-        if (!(f >= 0.0 && f < (double)g.hiI[k])) { flags[i] = 0; return; }
-        I[k] = (int64_t)f;
+// imga_classify with a lane per point and warp-cooperative rays for the undecided ones
+__global__ void classify_warp(GeomView g, const double* pts, int64_t n, uint8_t* flags, unsigned long long* nrays) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    double P[3] = {0.0, 0.0, 0.0};
+    int r = 0;
+    bool want = false;
+    int64_t e = -1;
+    if (valid) {
+        for (int k = 0; k < 3; ++k) P[k] = pts[3 * i + k];
+        bool inside = true;
+        int64_t I[3];
+        for (int k = 0; k < 3; ++k) {
+            const double f = floor((P[k] - g.lo[k]) / g.scale);
+            if (!(f >= 0.0 && f < (double)g.hiI[k])) inside = false;
+            else I[k] = (int64_t)f;
+        }
+        if (inside) e = d_find_leaf(g, I[0], I[1], I[2]);
+        if (e >= 0) {
+            const double h = (double)(1u << (kMaxDepth - g.lev[e])) * g.scale;
+            r = normal_test(g, e, P, 1e-12 * h);
+            want = true;
+        }
     }
-    int64_t e = d_find_leaf(g, I[0], I[1], I[2]);
-    flags[i] = e < 0 ? 0 : (uint8_t)is_in(g, e, P, nrays);
+    warp_resolve(g, want, P, r, nrays);
+    if (valid) flags[i] = (uint8_t)(e < 0 ? 0 : r);
 }
 
 GeomView view(const Mesh& m) {
@@ -354,7 +431,7 @@ bool device_cut_quadrature(Mesh& m, std::string& err) {
     int64_t* cnt = nullptr;
     if (!check(cudaMalloc((void**)&cnt, (nc + 1) * sizeof(int64_t)), err, "cudaMalloc")) return false;
     cudaMemset(g_nrays_dev, 0, sizeof(unsigned long long));
-    if (nc > 0) cut_count_kernel<<<(unsigned)((nc + 63) / 64), 64>>>(g, m.d.cut_list, nc, m.lmax, cnt, g_nrays_dev);
+    if (nc > 0) cut_count_warp<<<(unsigned)((nc + kWalkWarps - 1) / kWalkWarps), 32 * kWalkWarps>>>(g, m.d.cut_list, nc, m.lmax, cnt, g_nrays_dev);
     if (!check(cudaDeviceSynchronize(), err, "cut count kernel")) { cudaFree(cnt); return false; }
     std::vector<int64_t> c(nc);
     if (nc) cudaMemcpy(c.data(), cnt, nc * sizeof(int64_t), cudaMemcpyDeviceToHost);
@@ -366,8 +443,8 @@ bool device_cut_quadrature(Mesh& m, std::string& err) {
     if (!check(cudaMalloc((void**)&m.d.cut_pts, std::max<int64_t>(1, np) * 4 * sizeof(double)), err, "cudaMalloc")) return false;
     if (!check(cudaMalloc((void**)&m.d.cut_pts_f, std::max<int64_t>(1, np) * 4 * sizeof(float)), err, "cudaMalloc")) return false;
     if (nc > 0)
-        cut_write_kernel<<<(unsigned)((nc + 63) / 64), 64>>>(g, m.d.cut_list, nc, m.lmax, m.d.cut_off, m.d.cut_pts,
-                                                              m.d.cut_pts_f, g_nrays_dev);
+        cut_write_warp<<<(unsigned)((nc + kWalkWarps - 1) / kWalkWarps), 32 * kWalkWarps>>>(
+            g, m.d.cut_list, nc, m.lmax, m.d.cut_off, m.d.cut_pts, m.d.cut_pts_f, g_nrays_dev);
     if (!check(cudaDeviceSynchronize(), err, "cut write kernel")) return false;
     m.n_rays += read_rays() / 2;   // the write pass repeats the count pass's casts
     m.cut_pts.resize(4 * np);
@@ -464,7 +541,7 @@ bool device_upload_batch(Mesh& m, std::string& err) {
 int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream) {
     if (n <= 0) return 0;
     GeomView g = view(m);
-    classify_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(g, pts, n, flags, g_nrays_dev);
+    classify_warp<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(g, pts, n, flags, g_nrays_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

@@ -124,8 +124,7 @@ struct Args {
     const double* V;
     double* out;
     double rho, mu, theta, c0, c1, c2;   // c_k = time coefficients / dt
-    float thetaf, c0f, c2f;               // the same in float32
-    int theta1, has_c2;                   // theta == 1, c2 != 0 (tests off the float64 unit)
+    int theta1;                           // theta == 1
     const int* skip;                      // non-null and nonzero: return at once (solver steps captured in graphs)
     double K0dt;                         // 4 / dt^2
     double CInu2;                        // C_I nu^2
@@ -271,9 +270,6 @@ __device__ __forceinline__ float d2f(double x) {
     f += (rest > half || (rest == half && (f & 1u))) ? 1u : 0u;
     return __uint_as_float(f);
 }
-template <class T> __device__ __forceinline__ T tcoef(double d, float f);
-template <> __device__ __forceinline__ float tcoef<float>(double, float f) { return f; }
-template <> __device__ __forceinline__ double tcoef<double>(double d, float) { return d; }
 template <class T> __device__ __forceinline__ T to_t(double x);
 template <> __device__ __forceinline__ float to_t<float>(double x) { return d2f(x); }
 template <> __device__ __forceinline__ double to_t<double>(double x) { return x; }
@@ -295,13 +291,13 @@ __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T*
     double u[4], up[4], up2[4] = {0, 0, 0, 0};
     load4(A.U, n, u);
     load4(A.Up, n, up);
-    if (A.has_c2) load4(A.Up2, n, up2);
-    const T c0 = tcoef<T>(A.c0, A.c0f), c2 = tcoef<T>(A.c2, A.c2f), th = tcoef<T>(A.theta, A.thetaf);
+    if (A.c2 != 0.0) load4(A.Up2, n, up2);
+    const T c0 = (T)A.c0, c2 = (T)A.c2, th = (T)A.theta;
     T v8[8];
     for (int k = 0; k < 3; ++k) {
-        v8[k] = A.theta1 ? to_t<T>(u[k]) : to_t<T>(A.theta * u[k] + (1.0 - A.theta) * up[k]);
+        v8[k] = A.theta == 1.0 ? to_t<T>(u[k]) : to_t<T>(A.theta * u[k] + (1.0 - A.theta) * up[k]);
         T d1 = to_t<T>(u[k] - up[k]);
-        T d2 = A.has_c2 ? to_t<T>(up2[k] - up[k]) : T(0);
+        T d2 = A.c2 != 0.0 ? to_t<T>(up2[k] - up[k]) : T(0);
         v8[4 + k] = c0 * d1 + c2 * d2;
     }
     v8[3] = to_t<T>(u[3]);
@@ -852,11 +848,7 @@ inline Args make_args(const Mesh& m, const double* u, const double* up, const do
     A.c0 = c[0] / ph.dt;
     A.c1 = c[1] / ph.dt;
     A.c2 = c[2] / ph.dt;
-    A.thetaf = (float)A.theta;
-    A.c0f = (float)A.c0;
-    A.c2f = (float)A.c2;
     A.theta1 = A.theta == 1.0;
-    A.has_c2 = A.c2 != 0.0;
     A.K0dt = 4.0 / (ph.dt * ph.dt);
     const double nu = ph.mu / ph.rho;
     A.CInu2 = ph.C_I * nu * nu;
