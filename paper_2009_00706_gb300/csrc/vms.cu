@@ -44,7 +44,7 @@ namespace {
 // ------------------------------------------------------------------------------------------
 // Out elements: 8 threads per element
 // ------------------------------------------------------------------------------------------
-template <class T> struct Epb { static constexpr int value = sizeof(T) == 8 ? 16 : 32; };   // elements per block
+template <class T> struct Epb { static constexpr int value = 16; };   // elements per block
 
 template <class T> struct IntShape {
     static constexpr int EPB = Epb<T>::value;                                   // elements per block
@@ -63,7 +63,7 @@ template <class T> struct IntShape {
 // evaluates Gauss point c, writes the point's 32 monomial moments,
 // then sums moment column S = c over the 8 points and runs the backward butterfly: node c's rows.
 template <class T, bool JV>
-__global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, const int32_t* __restrict__ oconn,
+__global__ void __launch_bounds__(IntShape<T>::THREADS, sizeof(T) == 4 ? 4 : 2) vms_interior(Args A, const int32_t* __restrict__ oconn,
                                                     const uint8_t* __restrict__ olev,
                                                     const uint16_t* __restrict__ oprob, int64_t n) {
     typedef typename std::conditional<JV, Dual<T, sizeof(T) == 4>, T>::type S;
@@ -137,7 +137,27 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, 2) vms_interior(Args A, 
             r[0] += v[0]; r[1] += v[1]; r[2] += v[2]; r[3] += v[3];
         }
         for (int k = 0; k < 4; ++k) r[k] = hadamard_bwd<1>(r[k], c);
-        if (valid) scatter_t(A, id_cur, r);
+        // corners of this warp's 4 elements that are the same node add their rows in shared memory
+        // first; one lane per node scatters (fewer float64 atomics)
+        if constexpr (sizeof(T) == 4) {   // (float64: the plain scatter is faster)
+            const int lane = threadIdx.x & 31;
+            const unsigned grp = __match_any_sync(0xffffffffu, valid ? id_cur : -1 - lane);
+            __syncwarp();   // every lane has read its moment columns
+            st4s<T>(mrow, r[0], r[1], r[2], r[3]);
+            __syncwarp();
+            if (valid && lane == __ffs(grp) - 1) {
+                const T* rows = s_m + (threadIdx.x & ~31u) * MSTR;
+                T t[4] = {T(0), T(0), T(0), T(0)};
+                for (unsigned g = grp; g; g &= g - 1) {
+                    T v[4];
+                    ld4s<T>(rows + (__ffs(g) - 1) * MSTR, v);
+                    for (int k = 0; k < 4; ++k) t[k] += v[k];
+                }
+                scatter_t(A, id_cur, t);
+            }
+        } else {
+            if (valid) scatter_t(A, id_cur, r);
+        }
         __syncwarp();   // this buffer and the moments are rewritten by later iterations
         id_cur = id_next;
         id_next = id_after;
