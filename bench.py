@@ -41,6 +41,36 @@ FLOPS_JV_OUT_ELEMENT = 8 * (896 + 390 + 16) + 2048
 FLOPS_R_OUT_ELEMENT = 8 * (448 + 130 + 16) + 2048
 
 
+# algorithmic work per unit of the other kernels of the mixed J v step (BDF2)
+FLOPS_JV_SUBCELL_POINT = 896 + 390 + 16 + 256     # a Gauss point's work incl. its share of the contraction
+FLOPS_JV_SURFACE_POINT_EST = 920                  # estimate: interpolation 512, pointwise 150, rows 256
+BYTES_NODE_PREP_NODE = 4 * 32 + 2 * 32            # reads u, u_prev, u_prev2, v; writes value + tangent rows
+BYTES_NODE_PREP_HANGING = 3 * 2 * 32 + 2 * 32     # ~3 parents' two rows read, two rows written
+BYTES_STRONG_ROW_NODE = 1 + 32 + 32               # flag, source row, written row (upper bound)
+
+
+def kernel_rooflines(prof, steps, info, n_nodes, pk):
+    """Per kernel class of the timed step: average ms per step, bound, achieved, fraction of peak."""
+    out = {}
+    hbm = pk["hbm_gbs"]
+    fp32 = pk["fp32_tflops"]
+    work = {
+        "out_elements": ("alu", FLOPS_JV_OUT_ELEMENT * info["n_out"], fp32, "TFLOP/s"),
+        "cut_elements": ("alu", FLOPS_JV_SUBCELL_POINT * info["n_cut_points"], fp32, "TFLOP/s"),
+        "nitsche": ("alu (estimated flop)", FLOPS_JV_SURFACE_POINT_EST * info["n_surface_points"], fp32, "TFLOP/s"),
+        "node_prep": ("hbm", BYTES_NODE_PREP_NODE * n_nodes + BYTES_NODE_PREP_HANGING * info["n_hanging"], hbm, "GB/s"),
+        "strong_rows": ("hbm", BYTES_STRONG_ROW_NODE * n_nodes, hbm, "GB/s"),
+    }
+    for k, (bound, units, peak, unit) in work.items():
+        ms = prof[k][0] / max(1, steps)
+        if ms <= 0:
+            continue
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = units / (ms / 1e3) / scale
+        out[k] = {"ms_per_step": ms, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
+    return out
+
+
 def interior_traffic():
     """DRAM bytes per launch of vms_interior from the committed ncu record, or None when the kernel
     source changed since the counters were taken."""
@@ -283,6 +313,7 @@ def run_ours(args):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (of derived)",
             "flops_per_element": FLOPS_JV_OUT_ELEMENT, "avg_launch_ms": k_avg}
     kern_share = {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()}
+    kern_roof = kernel_rooflines(prof, args.steps, info, nn, pk)
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region: every
     # step copies its four input vectors in and its result out; the copies of step i+1's inputs and
     # of step i's result overlap step i's J v (double-buffered device vectors, copy streams).
@@ -416,7 +447,7 @@ def run_ours(args):
                            "cut_elements": info["n_cut"], "cut_points": info["n_cut_points"],
                            "surface_points": info["n_surface_points"], "nodes": nn, "precision": args.precision,
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "kernel_time_share": kern_share,
+                "roofline": roof, "kernel_roofline": kern_roof, "kernel_time_share": kern_share,
                 "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])), "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
                 "extra_elements_per_s": extra,
