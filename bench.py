@@ -424,6 +424,7 @@ def run_ours(args):
                             "converged": bool(st["converged"]), "rel_residual": st["res_norm"][-1] / st["res_norm"][0],
                             "workload": "small_sphere (7,288 elements, Re 10, BE dt 0.01), block-Jacobi, GMRES(50)"}
         smesh.close()
+    learned = run_learned(args, dev, stream, mesh, w) if not args.no_learned and rank == 0 else None
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -452,7 +453,7 @@ def run_ours(args):
                 "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])), "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
                 "extra_elements_per_s": extra,
-                "newton_step": newton, "batched": batched, "bluff_pair": bluff, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
+                "newton_step": newton, "learned_preconditioner": learned, "batched": batched, "bluff_pair": bluff, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -572,6 +573,64 @@ def run_bluff(args, dev, stream):
     return res
 
 
+def run_learned(args, dev, stream, les, w_les):
+    """Learned block preconditioner: the network is trained by the library's kernels on element Jacobian
+    blocks of the small sphere (seeds 0-15, all active elements) and of the sphere LES (50,000
+    sampled active elements, every Intercepted one kept), then evaluated in Newton-GMRES(50) on
+    held-out small-sphere states (seeds 16-19) against block-Jacobi and no preconditioner; the
+    float64 residual decides convergence."""
+    import torch
+
+    from paper_2009_00706_gb300 import api
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ws = I.small_sphere(0)
+    sm = api.Mesh.from_workload(ws, device=dev.index)
+    mk, _ = sm.markers()
+    elems = T(np.where(mk != 1)[0].astype(np.int32))
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    for seed in range(16):
+        u, up, _ = I.state(sm.n_nodes, seed)
+        X, Tt, _ = sm.precond_dataset(ws.physics, T(u), T(up), elems)
+        Xs.append(X)
+        Ts.append(Tt)
+    lmk, _ = les.markers()
+    cut, out_ = np.where(lmk == 2)[0], np.where(lmk == 0)[0]
+    pick = np.unique(np.concatenate([cut, out_[I.splitmix64(31, 50000 - cut.size) % out_.size]])).astype(np.int32)
+    u, up, _ = I.state(les.n_nodes, 0)
+    X, Tt, _ = les.precond_dataset(w_les.physics, T(u), T(up), T(pick), u_prev2=T(up))
+    Xs.append(X)
+    Ts.append(Tt)
+    X, Tt = torch.cat(Xs), torch.cat(Ts)
+    del Xs, Ts
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = api.Mlp(seed=11, device=dev.index)
+    t0 = time.perf_counter()
+    hist = net.train(X, Tt, epochs=20, batch=1024, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n_train = int(X.shape[0])
+    del X, Tt
+    sm.use_graphs(True)
+    res = {}
+    for seed in (16, 17, 18, 19):
+        u, up, _ = I.state(sm.n_nodes, seed)
+        for name, kw in (("block_jacobi", dict(precond=1)), ("learned", dict(precond=2, learned=net, learned_omega=0.5)),
+                         ("none", dict(precond=0, max_newton=10))):
+            ud = T(u)
+            st = sm.newton_step(ws.physics, ud, T(up), precision=api.PRECISION_MIXED, rtol=1e-8, gmres_m=50,
+                                max_krylov=1000, raise_on_failure=False, **kw)
+            res.setdefault(name, []).append({"ms": st["time_ms"], "newton_its": st["newton_its"],
+                                             "krylov_its": st["krylov_its"], "fallbacks": st.get("fallbacks"),
+                                             "converged": bool(st["converged"])})
+    net.close()
+    sm.close()
+    return {"train_samples": n_train, "dataset_s": t_data, "train_s": t_train, "epochs": 20,
+            "loss_first_last": [float(hist[0]), float(hist[-1])], "eval_seeds": [16, 17, 18, 19],
+            "precision": "mixed J v, float64 residual, graph-replayed GMRES(50)", "results": res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,6 +644,7 @@ def main():
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-GMRES step timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-bluff", action="store_true", help="skip the 19.8 M-element bluff-body pair measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner training and evaluation")
     ap.add_argument("--krylov-rtol", type=float, default=1e-3)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -547,16 +547,22 @@ public:
             if (jv(u, x, w)) return 1;
             cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
             axpby(-1.0, w, 1.0, r);
+            const double beta0 = beta;
             beta = norm(r);
             if (h.res <= target || its >= max_its) {
                 res = beta;
                 if (beta <= target * 1.0000001 || its >= max_its) break;
             }
+            if (stalled(beta, beta0)) { res = beta; break; }
         }
         *its_out = its;
         *res_out = res;
         return 0;
     }
+
+    // with a learned correction in use, a restart cycle that does not halve the residual ends the
+    // solve early: the caller then redoes it with block-Jacobi
+    bool stalled(double r, double r_cycle_start) const { return pmode >= 2 && r > 0.5 * r_cycle_start; }
 
     int solve(const double* u, const double* b, double* x, double rtol, int max_its, int* its_out, double* res_out) {
         if (M.use_graphs && !M.profiling) return gmres_dev(u, b, x, rtol, max_its, its_out, res_out);
@@ -634,6 +640,8 @@ public:
             if (jv(u, x, w)) return 1;
             cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
             axpby(-1.0, w, 1.0, r);
+            const double rn = norm(r);
+            if (stalled(rn, beta)) { res = rn; break; }
         }
         *its_out = its;
         *res_out = res;
