@@ -171,6 +171,11 @@ def reduce_max(x, world, dev=None):
     return float(t.item())
 
 
+def job_throughput(units_per_rank, steps, max_ms, world):
+    """Whole-job units/s: every rank processes units_per_rank per step; the slowest rank's time counts."""
+    return world * units_per_rank * steps / (max_ms / 1e3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -300,7 +305,7 @@ def run_ours(args):
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms = reduce_max(ms, world, dev)
     barrier(world)
-    value = world * n_active * args.steps / (ms / 1e3)
+    value = job_throughput(n_active, args.steps, ms, world)
     # dominant kernel roofline (Out elements, live CUDA events on the launching stream)
     k_ms, k_n = prof["out_elements"]
     k_avg = k_ms / max(k_n, 1)
@@ -631,7 +636,7 @@ def run_learned(args, dev, stream, les, w_les):
             "precision": "mixed J v, float64 residual, graph-replayed GMRES(50)", "results": res}
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -646,7 +651,11 @@ def main():
     ap.add_argument("--no-bluff", action="store_true", help="skip the 19.8 M-element bluff-body pair measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner training and evaluation")
     ap.add_argument("--krylov-rtol", type=float, default=1e-3)
-    args = ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def main():
+    args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
