@@ -39,6 +39,7 @@ L2_BYTES = 129 * 2 ** 20
 # + contraction of 8 nodes x 4 rows over 8 points (2048).
 FLOPS_JV_OUT_ELEMENT = 8 * (896 + 390 + 16) + 2048
 FLOPS_R_OUT_ELEMENT = 8 * (448 + 130 + 16) + 2048
+FP64_TFLOPS_NOMINAL = 1.25
 
 
 # algorithmic work per unit of the other kernels of the mixed J v step (BDF2)
@@ -386,6 +387,17 @@ def run_ours(args):
             torch.cuda.synchronize()
             tot += a.elapsed_time(b)
         extra[name] = n_active * reps / (tot / 1e3)
+    # the float64 Out-element kernel against the float64 pipe (GB300 nominal 1.25 TFLOP/s dense FP64)
+    mesh.profile(True)
+    for _ in range(3):
+        mesh.jvp(ph, ud, upd, vd, up2d, precision=0, out=out, stream=stream)
+    p64 = mesh.profile_read()
+    mesh.profile(False)
+    k64 = p64["out_elements"][0] / max(1, p64["out_elements"][1])
+    a64 = FLOPS_JV_OUT_ELEMENT * info["n_out"] / (k64 / 1e3) / 1e12
+    extra_roof = {"kernel": "vms_interior<double, J v>", "bound": "fp64 pipe", "avg_launch_ms": k64, "achieved": a64,
+                  "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": a64 / FP64_TFLOPS_NOMINAL,
+                  "peak_source": "nominal GB300 dense FP64 (no measured FP64 peak)"}
     # J v replayed as a CUDA graph (parallel branches for the Out / Intercepted / surface kernels)
     mesh.use_graphs(True)
     step()
@@ -454,7 +466,8 @@ def run_ours(args):
                            "cut_elements": info["n_cut"], "cut_points": info["n_cut_points"],
                            "surface_points": info["n_surface_points"], "nodes": nn, "precision": args.precision,
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-                "roofline": roof, "kernel_roofline": kern_roof, "kernel_time_share": kern_share,
+                "roofline": roof, "kernel_roofline": kern_roof, "fp64_roofline": extra_roof,
+                "kernel_time_share": kern_share,
                 "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])), "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
                 "extra_elements_per_s": extra,
