@@ -4,7 +4,8 @@ outputs the oracle computes one by one:
 * markers of a seeded sample of 20,000 elements and the sub-cell points of 40 Intercepted elements:
   bit-exact;
 * R and J v rows of a seeded sample of 3,000 nodes (the oracle evaluates every element touching
-  them, through the hanging-node operator): <= 1e-10 relative (float64 path), <= 2e-5 (mixed);
+  them, through the hanging-node operator), with the autotuned tile shapes the bench uses:
+  <= 1e-10 relative (float64 path), <= 2e-5 (mixed);
 * graph replay of the mixed J v equals the direct call.
 """
 import numpy as np
@@ -57,6 +58,7 @@ def test_sampled_residual_and_jvp(les):
     Ro, Jo = o.residual_jvp(w.physics, u, up, up, v=v, nodes=sel)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     ud, upd, vd = T(u), T(up), T(v)
+    g.autotune(True)   # the bench's launch configuration: tuned Intercepted-element tile shapes
     for prec, tol in ((api.PRECISION_FP64, 1e-10), (api.PRECISION_MIXED, 2e-5)):
         R = g.residual(w.physics, ud, upd, upd, precision=prec).cpu().numpy()
         J = g.jvp(w.physics, ud, upd, vd, upd, precision=prec).cpu().numpy()
