@@ -214,6 +214,17 @@ __device__ __forceinline__ void ld4(const void* base, int64_t i, T o[4]) {
     }
 }
 
+// 8 T to a 16-byte aligned global row with 16-byte stores
+template <class T>
+__device__ __forceinline__ void st8g(T* dst, const T v[8]) {
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+        for (int k = 0; k < 4; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+
 template <class T, bool JV>
 __device__ __forceinline__ void corner_data(const Args& A, int32_t id, T* dst) {
     ld8<T>(A.ndv, id, dst);
@@ -302,7 +313,7 @@ __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T*
     }
     v8[3] = to_t<T>(u[3]);
     v8[7] = T(0);
-    for (int k = 0; k < 8; ++k) ndv[8 * n + k] = v8[k];
+    st8g<T>(ndv + 8 * n, v8);
     if (ndf) {
         double f[4];
         load4(A.F, n, f);
@@ -317,7 +328,7 @@ __global__ void __launch_bounds__(256) node_prep(Args A, T* __restrict__ ndv, T*
         for (int k = 0; k < 3; ++k) { t8[k] = th * vt[k]; t8[4 + k] = c0 * vt[k]; }
         t8[3] = vt[3];
         t8[7] = T(0);
-        for (int k = 0; k < 8; ++k) ndt[8 * n + k] = t8[k];
+        st8g<T>(ndt + 8 * n, t8);
     }
 }
 
@@ -348,9 +359,9 @@ __global__ void __launch_bounds__(256) node_prep_hanging(Args A, T* __restrict__
             for (int k = 0; k < 4; ++k) c[k] += r[k];
         }
     }
-    for (int k = 0; k < 8; ++k) ndv[8 * n + k] = w * a[k];
-    if (JV)
-        for (int k = 0; k < 8; ++k) ndt[8 * n + k] = w * b[k];
+    for (int k = 0; k < 8; ++k) { a[k] *= w; b[k] *= w; }
+    st8g<T>(ndv + 8 * n, a);
+    if (JV) st8g<T>(ndt + 8 * n, b);
     if (ndf)
         for (int k = 0; k < 4; ++k) ndf[4 * n + k] = w * c[k];
 }
