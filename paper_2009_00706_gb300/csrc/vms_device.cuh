@@ -250,11 +250,9 @@ __device__ __forceinline__ void corner_async(const Args& A, int32_t id, T* dst) 
         const char* t = reinterpret_cast<const char*>(A.ndt) + (size_t)id * 8 * sizeof(T);
         for (int k = 0; k < C8; ++k) cp16(reinterpret_cast<char*>(dst + CT) + 16 * k, t + 16 * k);
     }
-    if (A.ndf) {
+    if (A.ndf) {   // (without a body force the force columns are never read)
         const char* f = reinterpret_cast<const char*>(A.ndf) + (size_t)id * 4 * sizeof(T);
         for (int k = 0; k < C8 / 2; ++k) cp16(reinterpret_cast<char*>(dst + CF) + 16 * k, f + 16 * k);
-    } else {
-        dst[CF] = dst[CF + 1] = dst[CF + 2] = dst[CF + 3] = T(0);
     }
 }
 
