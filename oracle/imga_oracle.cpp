@@ -20,8 +20,8 @@
 //   * Nitsche weak Dirichlet terms and tau_B, h_b ...... Eq. (weakbc) and the remark after it
 //   * skip In elements, Dirichlet on In-only nodes .... Algorithm 1, Fig. IBM caption
 //   * element matrix K_e = M_e^T k_e M_e, o2n ......... Algorithms 2 and 4
-// Where the paper is silent the readings listed in the design doc are taken (tau definitions,
-// in/out sign convention, ray directions, h_b, surface rule, CN treatment).
+// Where the paper is silent this oracle takes the reading stated at the function concerned (tau
+// definitions, in/out sign convention, ray directions, h_b, surface rule, CN treatment).
 //
 // Pins (tests/test_oracle_*.py): textbook Q1 element matrices at three special states,
 // a closed-form residual, the linear patch test across hanging nodes, zero residual for

@@ -527,13 +527,6 @@ __device__ __forceinline__ void pointwise(const Args& A, const Phys<T>& P, const
     out[12] = divu;
 }
 
-template <class S, class T>
-__device__ __forceinline__ void vms_point(const Args& A, const Phys<T>& P, const T fm[3], const T fp[3], const T* nd,
-                                          int stride, T g, S out[16]) {
-    Fields<S, T> F;
-    interp<S, T>(A, fm, fp, nd, stride, g, F);
-    pointwise<S, T>(A, P, F, g, out);
-}
 
 // ------------------------------------------------------------------------------------------
 // Monomial (Hadamard) form of the trilinear interpolant on the reference cube [-1,1]^3.
