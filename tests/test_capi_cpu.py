@@ -89,3 +89,17 @@ def test_invalid_arguments_are_rejected(lib):
     st = lib.imga_residual(m.h, C.c_void_p(16), C.c_void_p(16), None, None, C.byref(ph), 0, C.c_void_p(16), None)
     assert st == 1                                                        # host-only mesh: no compute
     assert b"host-only" in lib.imga_last_error()
+
+
+def test_options_and_queries_reject_bad_arguments(lib):
+    m = api.Mesh((0, 0, 0), (1, 1, 1), 1, [], None, 3, device=-1)
+    for opt in (1, 2):                                                    # graphs, autotune
+        assert lib.imga_set_option(m.h, opt, 1) == 1                      # host-only mesh
+    assert lib.imga_set_option(None, 1, 1) == 1
+    assert lib.imga_tuning(None, None, None) == 1
+    shape = np.zeros(8, np.int32)
+    assert lib.imga_tuning(m.h, shape.ctypes.data_as(C.c_void_p), None) == 0
+    assert (shape.reshape(2, 2, 2)[..., 0] == 4).all() and (shape.reshape(2, 2, 2)[..., 1] == 0).all()   # defaults
+    bad = C.c_int64()
+    assert lib.imga_selftest_conversions(0, -1, 1, C.byref(bad)) == 1    # n < 0
+    assert lib.imga_selftest_conversions(0, 10, 1, None) == 1             # null output
