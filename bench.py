@@ -465,6 +465,7 @@ def run_ours(args):
                 "workload": "sphere_les, block-Jacobi, GMRES(50), capped at 3 Newton x 300 GMRES iterations"}
         mesh.use_graphs(False)
     learned = run_learned(args, dev, stream, mesh, w) if not args.no_learned and rank == 0 else None
+    inout = run_inout(mesh, w, dev, stream)
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -494,7 +495,7 @@ def run_ours(args):
                 "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])), "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
                 "extra_elements_per_s": extra,
-                "newton_step": newton, "learned_preconditioner": learned, "batched": batched, "bluff_pair": bluff, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
+                "newton_step": newton, "learned_preconditioner": learned, "inout": inout, "batched": batched, "bluff_pair": bluff, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -612,6 +613,38 @@ def run_bluff(args, dev, stream):
     res["jv_mixed_graph"] = {"ms": ms, "elements_per_s": n_act / (ms / 1e3)}
     m.close()
     return res
+
+
+def run_inout(mesh, w, dev, stream):
+    """In/out classification (imga_classify) on the sphere LES: 5^3 points per Intercepted element
+    (a regular grid inside the element: the normal test decides most, the rest cast warp-cooperative
+    rays against 81,920 triangles), and points uniform over the box."""
+    import torch
+
+    ex = mesh.export()
+    mk, _ = mesh.markers()
+    cut = np.where(mk == 2)[0]
+    h = (2.0 ** (-ex["levels"][cut].astype(np.float64))) * max(np.subtract(w.hi, w.lo))
+    x0 = np.asarray(w.lo)[None, :] + ex["anchors"][cut].astype(np.float64) * (max(np.subtract(w.hi, w.lo)) / 2.0 ** 20)
+    t = (np.arange(5) + 0.5) / 5.0
+    g = np.stack(np.meshgrid(t, t, t, indexing="ij"), -1).reshape(-1, 3)
+    near = (x0[:, None, :] + h[:, None, None] * g[None, :, :]).reshape(-1, 3)
+    uni = np.asarray(w.lo) + I.uniform(41, 3 * near.shape[0]).reshape(-1, 3) * np.subtract(w.hi, w.lo)
+    out = {}
+    for name, pts in (("near_surface_5x5x5_per_cut_element", near), ("uniform_in_box", uni)):
+        P = torch.from_numpy(np.ascontiguousarray(pts)).to(dev)
+        flags = mesh.classify(P, stream=stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            mesh.classify(P, flags=flags, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 3
+        out[name] = {"points": int(P.shape[0]), "ms": ms, "points_per_s": P.shape[0] / (ms / 1e3),
+                     "fraction_in": float(flags.float().mean().item())}
+    return out
 
 
 def run_learned(args, dev, stream, les, w_les):
