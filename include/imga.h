@@ -280,7 +280,8 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * warps per block (8 in mixed precision only), elements in Morton order or longest first -- on the
  * call's own inputs and keeps the fastest for that mesh.  This follows the cost model of
  * Eq. (Wpart): the bucket of elements with uneven quadrature counts (8 to 4096 points).  Tuning
- * synchronises the stream and is skipped inside a stream capture.  Value 0 restores the default
+ * synchronises the stream, allocates (once per mesh) a 4-byte-per-element index of the Intercepted
+ * list, and is skipped inside a stream capture and by imga_jvp_noalloc.  Value 0 restores the default
  * shape (4 warps, Morton order).  Both values drop the cached graphs. */
 enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2 };
 imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
