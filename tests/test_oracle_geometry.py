@@ -218,3 +218,28 @@ def test_surface_quadrature_identities(small_sphere_oracle):
     # every point lies in the closed box of its owning element
     lo = m.anchors[el] * m.scale
     assert np.all((x >= lo - 1e-15) & (x <= lo + h[:, None] + 1e-15))
+
+
+def test_total_quadrature_volume_is_box_minus_body(small_sphere_oracle):
+    """Sum of all volume weights = box volume - polyhedron volume, within the sub-cell resolution:
+    Out elements give h^3, Intercepted elements the weights of their kept sub-cell points
+    (reference weight x h^3 / 8), In elements nothing.  The polyhedron volume is exact (divergence
+    theorem over the triangles); the error is bounded by the surface area times the finest
+    sub-cell edge h / 2^L_max (a quarter of it is asserted)."""
+    w, m = small_sphere_oracle
+    mk, _, _ = m.markers()
+    root = max(np.subtract(w.hi, w.lo))
+    h = root * 2.0 ** -m.levels.astype(np.float64)
+    vol = float(np.sum(h[mk == 0] ** 3))
+    for e in np.where(mk == 2)[0]:
+        vol += float(m.cut_points(e)[:, 3].sum()) * h[e] ** 3 / 8.0
+    tri = w.triangles()
+    v_body = float(np.einsum("ij,ij->i", tri[:, 0], np.cross(tri[:, 1], tri[:, 2])).sum()) / 6.0
+    area = float(0.5 * np.linalg.norm(np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]), axis=1).sum())
+    exact = float(np.prod(np.subtract(w.hi, w.lo))) - v_body
+    h_fine = h[mk == 2].min() / 2 ** w.lmax
+    assert abs(vol - exact) <= 0.25 * area * h_fine, (vol, exact, area * h_fine)   # measured 7e-6 vs 6e-5
+    # the sub-cell quadrature matters: counting Intercepted elements whole is off by far more
+    crude = vol - sum(float(m.cut_points(e)[:, 3].sum()) * h[e] ** 3 / 8.0 for e in np.where(mk == 2)[0]) \
+        + float(np.sum(h[mk == 2] ** 3))
+    assert abs(crude - exact) > 5 * abs(vol - exact)
