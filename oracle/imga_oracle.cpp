@@ -25,7 +25,8 @@
 //
 // Pins (tests/test_oracle_*.py): textbook Q1 element matrices at three special states,
 // a closed-form residual, the linear patch test across hanging nodes, zero residual for
-// uniform flow, central differences of R for J v, second-order MMS convergence, the printed
+// uniform flow, central differences of R for J v, the complex step Im R(u + i eps v) / eps against
+// the dual-number J v, second-order MMS convergence, the total volume of the quadrature, the printed
 // Gauss abscissae of Fig. GP, exact dyadic cuts, brute-force ray parity, the analytic
 // sphere, and divergence-theorem identities of the surface rule.
 // Parity unpinned (readings of silent passages, checked only for consistency): the constants
@@ -38,6 +39,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cmath>
+#include <complex>
 #include <vector>
 #include <array>
 #include <algorithm>
@@ -76,6 +78,22 @@ inline double val(Dual a) { return a.v; }
 template <class T> T mk0();
 template <> double mk0<double>() { return 0.0; }
 template <> Dual mk0<Dual>() { return mk(0.0); }
+
+// Complex step (an independent route to the same derivative, for the pins): the state is
+// u + i eps v and Im R / eps = J v to rounding, with no difference quotient.  Branches read the
+// real part, like val() of a dual.
+typedef std::complex<double> Cx;
+const double CSTEP = 1e-30;
+inline double val(Cx a) { return a.real(); }
+inline Cx dsqrt(Cx a) { return std::sqrt(a); }
+template <> Cx mk0<Cx>() { return Cx(0.0, 0.0); }
+// the scalar seeded with value v and direction d, and the derivative read back
+inline Dual seed(Dual*, double v, double d) { return {v, d}; }
+inline Cx seed(Cx*, double v, double d) { return Cx(v, CSTEP * d); }
+inline double value_of(Dual a) { return a.v; }
+inline double value_of(Cx a) { return a.real(); }
+inline double deriv_of(Dual a) { return a.d; }
+inline double deriv_of(Cx a) { return a.imag() / CSTEP; }
 
 // ------------------------------------------------------------------------------------
 // Morton keys (x in the lowest bit of every triple)
@@ -819,25 +837,26 @@ void scatter(const Mesh& m, int e, const double r[8][4], double* R) {
 }
 
 // local residual (value and tangent) of element e: volume + its surface points
+template <class T>
 void element_local(State& S, int e, const double ue[8][4], const double ve[8][4], const double upe[8][4],
                    const double up2e[8][4], const double fe[8][4], const Phys& ph, const std::vector<int>& sq_of_e,
-                   Dual r[8][4]) {
+                   T r[8][4]) {
     Mesh& m = S.mesh;
     Geom& g = S.geom;
     double c[3], theta;
     time_coeffs(ph.scheme, c, &theta);
-    Dual Us[8][3], P[8], At[8][3];
+    T Us[8][3], P[8], At[8][3];
     double F[8][3];
     for (int a = 0; a < 8; ++a) {
         for (int i = 0; i < 3; ++i) {
-            Dual u = {ue[a][i], ve[a][i]};
+            T u = seed((T*)nullptr, ue[a][i], ve[a][i]);
             Us[a][i] = theta * u + (1.0 - theta) * upe[a][i];
             At[a][i] = (c[0] * u + c[1] * upe[a][i] + c[2] * up2e[a][i]) / ph.dt;
             F[a][i] = fe[a][i];
         }
-        P[a] = {ue[a][3], ve[a][3]};
+        P[a] = seed((T*)nullptr, ue[a][3], ve[a][3]);
     }
-    for (int a = 0; a < 8; ++a) for (int k = 0; k < 4; ++k) r[a][k] = mk(0.0);
+    for (int a = 0; a < 8; ++a) for (int k = 0; k < 4; ++k) r[a][k] = mk0<T>();
     double h = elem_h(m, e);
     double detJ = (0.5 * h) * (0.5 * h) * (0.5 * h);
     compute_marker(g, e);
@@ -848,7 +867,7 @@ void element_local(State& S, int e, const double ue[8][4], const double ve[8][4]
             for (int k = 0; k < 3; ++k) xi[k] = ((gp >> k) & 1) ? GAUSS : -GAUSS;
             Basis B;
             eval_basis(xi, h, B);
-            vms_point<Dual>(B, 1.0 * detJ, ph, Us, P, At, F, r);
+            vms_point<T>(B, 1.0 * detJ, ph, Us, P, At, F, r);
         }
     } else {
         compute_cut(g, e);
@@ -856,7 +875,7 @@ void element_local(State& S, int e, const double ue[8][4], const double ve[8][4]
             double xi[3] = {q[0], q[1], q[2]};
             Basis B;
             eval_basis(xi, h, B);
-            vms_point<Dual>(B, q[3] * detJ, ph, Us, P, At, F, r);
+            vms_point<T>(B, q[3] * detJ, ph, Us, P, At, F, r);
         }
     }
     double x0[3];
@@ -867,11 +886,15 @@ void element_local(State& S, int e, const double ue[8][4], const double ve[8][4]
         for (int k = 0; k < 3; ++k) xi[k] = (q.x[k] - x0[k]) / (0.5 * h) - 1.0;
         Basis B;
         eval_basis(xi, h, B);
-        nitsche_point<Dual>(B, q, ph, Us, P, r);
+        nitsche_point<T>(B, q, ph, Us, P, r);
     }
 }
 
 }  // namespace
+
+template <class T>
+int residual_jvp_impl(void* s, const double* physv, const double* U, const double* Up, const double* Up2,
+                      const double* Fn, const double* V, const int64_t* sel, int64_t nsel, double* R, double* JV);
 
 // =====================================================================================
 // C interface for the Python test harness (ctypes)
@@ -1069,6 +1092,21 @@ void or_set_dirichlet(void* s, const uint8_t* mask, const double* vals) {
 // Outputs (may be NULL) are [N_n][4]; only the selected rows are meaningful.
 int or_residual_jvp(void* s, const double* physv, const double* U, const double* Up, const double* Up2,
                     const double* Fn, const double* V, const int64_t* sel, int64_t nsel, double* R, double* JV) {
+    return residual_jvp_impl<Dual>(s, physv, U, Up, Up2, Fn, V, sel, nsel, R, JV);
+}
+
+// The same with J v from the complex step instead of dual numbers (R from the real part).
+int or_residual_jvp_complex_step(void* s, const double* physv, const double* U, const double* Up, const double* Up2,
+                                 const double* Fn, const double* V, const int64_t* sel, int64_t nsel, double* R,
+                                 double* JV) {
+    return residual_jvp_impl<Cx>(s, physv, U, Up, Up2, Fn, V, sel, nsel, R, JV);
+}
+
+}  // extern "C"
+
+template <class T>
+int residual_jvp_impl(void* s, const double* physv, const double* U, const double* Up, const double* Up2,
+                      const double* Fn, const double* V, const int64_t* sel, int64_t nsel, double* R, double* JV) {
     State* S = (State*)s;
     Mesh& m = S->mesh;
     Geom& g = S->geom;
@@ -1119,11 +1157,12 @@ int or_residual_jvp(void* s, const double* physv, const double* U, const double*
         gather(m, e, Up, 4, upe);
         gather(m, e, UP2, 4, up2e);
         gather(m, e, F, 4, fe);
-        Dual r[8][4];
+        T r[8][4];
         auto it = sq_of.find(e);
-        element_local(*S, e, ue, ve, upe, up2e, fe, ph, it == sq_of.end() ? none : it->second, r);
+        element_local<T>(*S, e, ue, ve, upe, up2e, fe, ph, it == sq_of.end() ? none : it->second, r);
         double rv[8][4], rd[8][4];
-        for (int a = 0; a < 8; ++a) for (int k = 0; k < 4; ++k) { rv[a][k] = r[a][k].v; rd[a][k] = r[a][k].d; }
+        for (int a = 0; a < 8; ++a)
+            for (int k = 0; k < 4; ++k) { rv[a][k] = value_of(r[a][k]); rd[a][k] = deriv_of(r[a][k]); }
         scatter(m, e, rv, Rv.data());
         scatter(m, e, rd, Jv.data());
     }
@@ -1159,6 +1198,8 @@ int or_residual_jvp(void* s, const double* physv, const double* U, const double*
     return 0;
 }
 
+extern "C" {
+
 // Element matrix k_e = d r_e / d u_e (32 x 32, row a*4+i, column b*4+j) of the local residual,
 // volume + Nitsche, with respect to the element's own corner values (before M_e) -- the matrix
 // of Algorithm 4, built column by column from the exact tangent.
@@ -1188,7 +1229,7 @@ int or_element_matrix(void* s, const double* physv, const double* U, const doubl
         double ve[8][4];
         for (int a = 0; a < 8; ++a) for (int k = 0; k < 4; ++k) ve[a][k] = (a * 4 + k == col) ? 1.0 : 0.0;
         Dual r[8][4];
-        element_local(*S, (int)e, ue, ve, upe, up2e, fe, ph, mine, r);
+        element_local<Dual>(*S, (int)e, ue, ve, upe, up2e, fe, ph, mine, r);
         for (int a = 0; a < 8; ++a) for (int k = 0; k < 4; ++k) K[(a * 4 + k) * 32 + col] = r[a][k].d;
     }
     compute_marker(g, (int)e);

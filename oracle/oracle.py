@@ -53,6 +53,7 @@ def lib():
         L.or_counters.argtypes = [vp, C.c_void_p]
         L.or_set_dirichlet.argtypes = [vp, C.c_void_p, C.c_void_p]
         L.or_residual_jvp.argtypes = [vp, C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p, i64, C.c_void_p, C.c_void_p]
+        L.or_residual_jvp_complex_step.argtypes = L.or_residual_jvp.argtypes
         L.or_element_matrix.argtypes = [vp, C.c_void_p] + [C.c_void_p] * 4 + [i64, C.c_void_p]
         L.or_element_matrix.restype = i32
         L.or_element_residual.argtypes = [vp, C.c_void_p] + [C.c_void_p] * 4 + [i64, C.c_void_p]
@@ -192,6 +193,18 @@ class OracleMesh:
         lib().or_residual_jvp(self.h, _p(ph), _p(u), _p(up), _p(up2), _p(f), _p(v), _p(sel),
                               0 if sel is None else sel.size, _p(R), _p(J))
         return R, J
+
+    def jvp_complex_step(self, phys, u, u_prev, v, u_prev2=None, f=None):
+        """J v as Im R(u + i eps v) / eps (eps = 1e-30): the complex step, independent of the dual numbers."""
+        ph = np.array(phys.packed(), dtype=np.float64)
+        u, up, up2, f, v = _f64(u), _f64(u_prev), _f64(u_prev2), _f64(f), _f64(v)
+        if f is not None:
+            f4 = np.zeros((self.n_nodes, 4))
+            f4[:, :3] = f.reshape(self.n_nodes, -1)[:, :3]
+            f = f4
+        J = np.zeros((self.n_nodes, 4))
+        lib().or_residual_jvp_complex_step(self.h, _p(ph), _p(u), _p(up), _p(up2), _p(f), _p(v), None, 0, None, _p(J))
+        return J
 
     def residual(self, phys, u, u_prev, u_prev2=None, f=None, nodes=None):
         return self.residual_jvp(phys, u, u_prev, u_prev2, f, None, nodes)[0]

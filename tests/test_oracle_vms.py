@@ -338,3 +338,23 @@ def test_manufactured_solution_second_order():
     e2, e3, e4 = mms_error(2), mms_error(3), mms_error(4)
     assert e3 / e4 > 3.2, (e2, e3, e4)
     assert e2 / e3 > 2.5, (e2, e3, e4)
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_jvp_matches_complex_step(scheme):
+    """The dual-number J v against the complex step Im R(u + i eps v) / eps, a derivative with no
+    difference quotient: agreement to 1e-12 on a mesh with hanging nodes, Intercepted elements
+    and surface points, for BE, CN and BDF2."""
+    from oracle.oracle import OracleMesh
+    from paper_2009_00706_gb300 import inputs as I
+    c = (0.5, 0.5, 0.5)
+    regs = [I.Region(I.REGION_SPHERE_BAND, 4, (*c, 0.2, 0.05))]
+    tri = I.icosphere(2, 0.2, c, 1e-4, 1)
+    o = OracleMesh((0, 0, 0), (1, 1, 1), 2, regs, tri, 2)
+    u, up, v = I.state(o.n_nodes, 9, sigma=0.2)
+    up2 = up.copy()
+    up2[:, :3] += I.normal(10, 3 * o.n_nodes, 0.05).reshape(-1, 3)
+    ph = I.Physics(rho=1.0, mu=0.03, dt=0.02, scheme=scheme, g=(0.1, 0.0, 0.0))
+    _, Jd = o.residual_jvp(ph, u, up, up2, v=v)
+    Jc = o.jvp_complex_step(ph, u, up, v, up2)
+    assert np.linalg.norm(Jc - Jd) <= 1e-12 * np.linalg.norm(Jd), np.linalg.norm(Jc - Jd) / np.linalg.norm(Jd)
