@@ -104,6 +104,9 @@ typedef struct {
  * no GPU is touched, and the compute calls reject such a mesh with IMGA_ERR_INVALID_ARG. */
 imga_status imga_build_mesh(const double* tri_xyz_host, int64_t n_tri, const imga_mesh_params* params, int device,
                             imga_mesh* out);
+/* Free the mesh and every device array it owns (cached graphs, solver workspace, profiling events).
+ * NULL is a no-op.  The caller's work on the mesh must be finished or queued before the call: the
+ * device frees synchronise the device.  The handle is invalid afterwards. */
 void imga_destroy_mesh(imga_mesh mesh);
 
 /* Several independent problems in one mesh, so that one launch of each residual / J v / Jacobian
@@ -122,6 +125,8 @@ typedef struct {
 imga_status imga_build_mesh_batch(const imga_problem* problems, int n_problems, int device, imga_mesh* out);
 /* number of problems (1 for an ordinary mesh) and elem_off / node_off [n_problems + 1] (host) */
 imga_status imga_mesh_problems(imga_mesh mesh, int* n_problems, int64_t* elem_off, int64_t* node_off);
+/* Sizes and set-up timings of the mesh (host struct filled by the call).  Errors: IMGA_ERR_INVALID_ARG
+ * for a null mesh or info. */
 imga_status imga_mesh_get_info(imga_mesh mesh, imga_mesh_info* info);
 
 /* Host copies of the mesh tables (every pointer may be NULL to skip it).  anchors [n_elem][3]
@@ -243,6 +248,7 @@ imga_status imga_newton_step(imga_mesh mesh, double* u_inout, const double* u_pr
  * preconditioners tailored to the method for matrix-free solvers.  Device pointers unless named host. */
 typedef struct imga_mlp_s* imga_mlp;
 imga_status imga_mlp_create(int n_in, int width, int n_out, uint64_t seed, int device, imga_mlp* out);
+/* frees the network's weights and optimiser state; NULL is a no-op */
 void imga_mlp_destroy(imga_mlp mlp);
 /* number of parameters and the padded input width the layout uses (W1 is width x n_in_pad) */
 imga_status imga_mlp_shape(imga_mlp mlp, int64_t* n_params, int* n_in_pad);
@@ -310,6 +316,8 @@ imga_status imga_profile_read(imga_mesh mesh, double* ms, int64_t* launches);
  * being NaN).  Synchronous.  Errors: IMGA_ERR_INVALID_ARG (n < 0, null output), IMGA_ERR_CUDA. */
 imga_status imga_selftest_conversions(int device, int64_t n, uint64_t seed, int64_t* mismatches);
 
+/* Message of the last failing call on the calling thread ("" if none has failed).  The string
+ * is owned by the library and stays valid until the next failing call on the same thread. */
 const char* imga_last_error(void);
 
 #ifdef __cplusplus
