@@ -5,7 +5,9 @@ References that do not come from the oracle:
 * exact volumes and exact integrals of trilinear functions for cuts along dyadic sub-cell planes;
 * the analytic sphere (inscribed / circumscribed radii of the faceted surface);
 * an independent brute-force ray-parity count written here with numpy along a random direction;
-* the divergence theorem for the triangulated surface (sum w n = 0, sum w x.n = 3 V).
+* the divergence theorem for the triangulated surface (sum w n = 0, sum w x.n = 3 V, and the
+  quadratic fluxes x_i x_j n_k against the first moment of the polyhedron);
+* the barycentric moment formula int_T l_a l_b dA = A (1 + delta_ab) / 12 on each triangle.
 """
 import os
 
@@ -218,6 +220,47 @@ def test_surface_quadrature_identities(small_sphere_oracle):
     # every point lies in the closed box of its owning element
     lo = m.anchors[el] * m.scale
     assert np.all((x >= lo - 1e-15) & (x <= lo + h[:, None] + 1e-15))
+
+
+def test_surface_quadrature_is_exact_for_quadratics(small_sphere_oracle):
+    """The Nitsche integrands of Eq. (weakbc) are products of trilinear fields restricted to flat
+    triangles; the surface rule must integrate every quadratic exactly on each triangle.  Two
+    closed forms that do not involve the rule's points:
+    * per triangle, int_T x_i x_j dA = A/12 (sum_a v_ai v_aj + s_i s_j), s = v_0 + v_1 + v_2,
+      from the barycentric moments int_T l_a l_b dA = A (1 + delta_ab) / 12;
+    * over the closed surface, by the divergence theorem applied to x_i x_j e_k with the
+      fluid-outward (body-inward) normal, sum_q w x_i x_j n_k = -(delta_ik M_j + delta_jk M_i),
+      M = int_V x dV summed over the signed tetrahedra (0, a, b, c) as vol (a + b + c) / 4."""
+    w, m = small_sphere_oracle
+    tri = w.triangles()
+    sq = m.surface_points()
+    x, n, wq, t = sq[:, :3], sq[:, 3:6], sq[:, 6], sq[:, 9].astype(np.int64)
+    A = 0.5 * np.linalg.norm(np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]), axis=1)
+    s = tri.sum(axis=1)
+    exact = (A[:, None, None] / 12.0) * (np.einsum("tai,taj->tij", tri, tri) + s[:, :, None] * s[:, None, :])
+    got = np.zeros_like(exact)
+    np.add.at(got, t, wq[:, None, None] * x[:, :, None] * x[:, None, :])
+    assert np.abs(got - exact).max() <= 1e-14 * np.abs(exact).max()
+    # linear moments per triangle: int_T x dA = A s / 3
+    lin = np.zeros((tri.shape[0], 3))
+    np.add.at(lin, t, wq[:, None] * x)
+    assert np.abs(lin - A[:, None] * s / 3.0).max() <= 1e-14 * np.abs(s).max() * A.max()
+    vol_t = np.einsum("ti,ti->t", tri[:, 0], np.cross(tri[:, 1], tri[:, 2])) / 6.0
+    M = (vol_t[:, None] * s / 4.0).sum(axis=0)
+    D = np.eye(3)
+    want = -(D[:, None, :] * M[None, :, None] + D[None, :, :] * M[:, None, None])   # [i, j, k]
+    flux = np.einsum("q,qi,qj,qk->ijk", wq, x, x, n)
+    assert np.abs(flux - want).max() <= 1e-13 * np.abs(want).max()
+    # the rule is the degree-2 one: the third central moment of x over a triangle is not exact
+    c = s / 3.0
+    d = tri[:, :, 0] - c[:, 0:1]                                   # vertices relative to the centroid
+    cub = np.zeros(tri.shape[0])
+    np.add.at(cub, t, wq * (x[:, 0] - c[t, 0]) ** 3)
+    e3 = 6 * (d ** 3).sum(1) + 6 * sum(d[:, a] ** 2 * d[:, b] for a in range(3) for b in range(3) if a != b) \
+        + 6 * d[:, 0] * d[:, 1] * d[:, 2]
+    cub_exact = (2.0 * A / 120.0) * e3                             # int l^a l^b l^c = 2A a!b!c!/(a+b+c+2)!
+    big = np.abs(cub_exact) > 1e-3 * np.abs(cub_exact).max()
+    assert np.median(np.abs(cub - cub_exact)[big] / np.abs(cub_exact)[big]) > 0.1
 
 
 def test_total_quadrature_volume_is_box_minus_body(small_sphere_oracle):
