@@ -100,7 +100,7 @@ def test_learned_preconditioner_in_gmres(dev):
             st = mesh.newton_step(w.physics, ud, torch.from_numpy(up).to(dev), precision=api.PRECISION_FP64,
                                   rtol=1e-8, gmres_m=50, raise_on_failure=False, **kw)
             out.setdefault(name, []).append((st["krylov_its"], st["fallbacks"], st["converged"]))
-            # the float64 residual is the judge: the oracle's residual at the result
+            # the float64 residual decides: the oracle's residual at the result
             assert st["converged"], (name, st)
             assert np.linalg.norm(o.residual(w.physics, ud.cpu().numpy(), up)) <= 1.5e-8 * R0
     print("GMRES iterations (its, fallbacks, converged):", out, "training loss", hist[0], hist[-1])
