@@ -27,6 +27,16 @@ inline uint64_t part1by2(uint64_t v) {
 inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
     return part1by2(x) | (part1by2(y) << 1) | (part1by2(z) << 2);
 }
+// inverse of part1by2: bits 3b -> bit b (21 bits)
+inline uint32_t compact1by2(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return (uint32_t)v;
+}
 
 // Triangle tables (structure of arrays, float64), shared by the host and the device copies.
 struct TriHost {

@@ -23,6 +23,7 @@
 
 #ifdef _OPENMP
 #include <omp.h>
+#include <parallel/algorithm>
 #endif
 
 namespace imga {
@@ -130,16 +131,27 @@ bool build_octree(Mesh& m, std::string& err) {
         }
     }
     set_leaves(m, leaves);
-    // 2:1 balance: a leaf of level l forces every leaf it touches to level >= l - 1
+    // 2:1 balance: a leaf of level l forces every leaf it touches to level >= l - 1.  The fine
+    // leaf finds the coarse one by probing just outside each face, edge and vertex.  The first
+    // pass probes from every leaf.  After a pass, a violation needs a fine side that the pass
+    // created, or one that found a violation in it and was not split: a pair of untouched leaves
+    // was balanced before, and a new child G of a split leaf B is too coarse only for a leaf
+    // that was already more than one level finer than B.  So later passes probe from those
+    // leaves only.  Every split is forced, so the result is the coarsest balanced refinement
+    // whatever the order.
     static const int nb[26][3] = {{-1,-1,-1},{0,-1,-1},{1,-1,-1},{-1,0,-1},{0,0,-1},{1,0,-1},{-1,1,-1},{0,1,-1},{1,1,-1},
                                   {-1,-1,0},{0,-1,0},{1,-1,0},{-1,0,0},{1,0,0},{-1,1,0},{0,1,0},{1,1,0},
                                   {-1,-1,1},{0,-1,1},{1,-1,1},{-1,0,1},{0,0,1},{1,0,1},{-1,1,1},{0,1,1},{1,1,1}};
+    std::vector<int64_t> probe;
+    bool probe_all = true;
     for (int pass = 0; pass < 64; ++pass) {
-        int64_t n = m.n_elem();
-        std::vector<uint8_t> split(n, 0);
+        const int64_t n = m.n_elem();
+        const int64_t n_probe = probe_all ? n : (int64_t)probe.size();
+        std::vector<uint8_t> split(n, 0), found(n, 0);
         int any = 0;
 #pragma omp parallel for schedule(dynamic, 4096) reduction(| : any)
-        for (int64_t e = 0; e < n; ++e) {
+        for (int64_t i = 0; i < n_probe; ++i) {
+            const int64_t e = probe_all ? i : probe[i];
             int l = m.lev[e];
             if (l < 2) continue;
             int64_t s = octsize(l);
@@ -149,23 +161,37 @@ bool build_octree(Mesh& m, std::string& err) {
                 for (int k = 0; k < 3; ++k)
                     q[k] = nb[d][k] < 0 ? (int64_t)a[k] - 1 : nb[d][k] > 0 ? (int64_t)a[k] + s : (int64_t)a[k];
                 int64_t o = find_leaf(m, q[0], q[1], q[2]);
-                if (o >= 0 && m.lev[o] < l - 1) { split[o] = 1; any = 1; }
+                if (o >= 0 && m.lev[o] < l - 1) {
+                    __atomic_store_n(&split[o], (uint8_t)1, __ATOMIC_RELAXED);
+                    found[e] = 1;
+                    any = 1;
+                }
             }
         }
         if (!any) break;
         std::vector<Oct> next;
+        std::vector<int64_t> next_probe;
         next.reserve(n + 8 * std::count(split.begin(), split.end(), 1));
         for (int64_t e = 0; e < n; ++e) {
             const uint32_t* a = &m.anc[3 * e];
             int l = m.lev[e];
-            if (!split[e]) { next.push_back({{a[0], a[1], a[2]}, l}); continue; }
+            if (!split[e]) {
+                if (found[e]) next_probe.push_back((int64_t)next.size());
+                next.push_back({{a[0], a[1], a[2]}, l});
+                continue;
+            }
             uint32_t h = octsize(l) >> 1;
             for (int c = 0; c < 8; ++c) {
                 Oct ch{{a[0] + ((c & 1) ? h : 0), a[1] + ((c & 2) ? h : 0), a[2] + ((c & 4) ? h : 0)}, l + 1};
-                if (inside_box(m, ch.a[0], ch.a[1], ch.a[2])) next.push_back(ch);
+                if (inside_box(m, ch.a[0], ch.a[1], ch.a[2])) {
+                    next_probe.push_back((int64_t)next.size());
+                    next.push_back(ch);
+                }
             }
         }
         set_leaves(m, next);
+        probe.swap(next_probe);
+        probe_all = false;
         if (pass == 63) { err = "2:1 balance did not converge"; return false; }
     }
     for (int64_t e = 0; e < m.n_elem(); ++e)
@@ -185,22 +211,18 @@ bool build_nodes(Mesh& m, std::string& err) {
             ck[8 * e + c] = morton3(a[0] + ((c & 1) ? s : 0), a[1] + ((c & 2) ? s : 0), a[2] + ((c & 4) ? s : 0));
     }
     std::vector<uint64_t> uk(ck);
+#ifdef _OPENMP
+    __gnu_parallel::sort(uk.begin(), uk.end());
+#else
     std::sort(uk.begin(), uk.end());
+#endif
     uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
     const int64_t nu = (int64_t)uk.size();
-    // coordinates of each unique corner (taken from one element that has it)
+    // coordinates of each unique corner, read back from its Morton code
     std::vector<uint32_t> ux(3 * nu);
-    std::vector<int64_t> owner(nu, -1);
-    for (int64_t i = 0; i < 8 * ne; ++i) {
-        int64_t u = std::lower_bound(uk.begin(), uk.end(), ck[i]) - uk.begin();
-        if (owner[u] < 0) owner[u] = i;
-    }
 #pragma omp parallel for schedule(static)
-    for (int64_t u = 0; u < nu; ++u) {
-        int64_t e = owner[u] / 8, c = owner[u] % 8;
-        uint32_t s = octsize(m.lev[e]);
-        for (int k = 0; k < 3; ++k) ux[3 * u + k] = m.anc[3 * e + k] + (((c >> k) & 1) ? s : 0);
-    }
+    for (int64_t u = 0; u < nu; ++u)
+        for (int k = 0; k < 3; ++k) ux[3 * u + k] = compact1by2(uk[u] >> k);
     // hanging test: P is hanging when a leaf touching P does not have P as a corner
     std::vector<int8_t> np(nu, 0);
     std::vector<uint32_t> par(12 * nu);

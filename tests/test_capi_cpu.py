@@ -70,6 +70,15 @@ def test_host_mesh_matches_oracle_carved_box_and_cone(lib):
     _compare((0, 0, 0), (2, 1, 1), 2, regs, tri)
 
 
+@pytest.mark.parametrize("c", [(0.501, 0.502, 0.497), (0.26, 0.51, 0.74), (0.126, 0.377, 0.624)])
+def test_host_mesh_matches_oracle_deep_refinement(lib, c):
+    # a level-9 band in a level-1 mesh: 2:1 balance ripples outwards over 5 to 7 passes, the
+    # later ones probing only from the leaves that the previous pass created or that found a
+    # violation; the oracle rescans every leaf on every pass
+    m = _compare((0, 0, 0), (1, 1, 1), 1, [I.Region(I.REGION_SPHERE_BAND, 9, (*c, 0.01, 0.002))], None)
+    assert m.n_hang > 0 and int(m.export()["levels"].max()) == 9
+
+
 def test_host_mesh_without_body(lib):
     _compare((0, 0, 0), (1, 1, 1), 2, [I.Region(I.REGION_SPHERE_BAND, 4, (0.3, 0.6, 0.5, 0.2, 0.05))], None)
 
