@@ -465,7 +465,10 @@ def run_ours(args):
                 "workload": "sphere_les, block-Jacobi, GMRES(50), capped at 3 Newton x 300 GMRES iterations"}
         mesh.use_graphs(False)
     learned = run_learned(args, dev, stream, mesh, w) if not args.no_learned and rank == 0 else None
-    inout = run_inout(mesh, w, dev, stream)
+    try:
+        inout = run_inout(mesh, w, dev, stream)
+    except Exception as ex:          # reported in the JSON line instead of ending the run
+        inout = {"error": repr(ex)}
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -619,7 +622,10 @@ def run_bluff(args, dev, stream):
 def run_inout(mesh, w, dev, stream):
     """In/out classification (imga_classify) on the sphere LES: 5^3 points per Intercepted element
     (a regular grid inside the element: the normal test decides most, the rest cast warp-cooperative
-    rays against 81,920 triangles), and points uniform over the box."""
+    rays against 81,920 triangles), and points uniform over the box (most lie in elements without
+    background triangles and take the stored marker).  As in the paper's Table in-out: P_s, the
+    fraction of the normal-tested points that the normal test decides, and the time of the same
+    points when every one of them is classified by ray parity."""
     import torch
 
     ex = mesh.export()
@@ -631,20 +637,40 @@ def run_inout(mesh, w, dev, stream):
     g = np.stack(np.meshgrid(t, t, t, indexing="ij"), -1).reshape(-1, 3)
     near = (x0[:, None, :] + h[:, None, None] * g[None, :, :]).reshape(-1, 3)
     uni = np.asarray(w.lo) + I.uniform(41, 3 * near.shape[0]).reshape(-1, 3) * np.subtract(w.hi, w.lo)
+
+    def timed(P, flags, reps=3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            mesh.classify(P, flags=flags, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
     out = {}
     for name, pts in (("near_surface_5x5x5_per_cut_element", near), ("uniform_in_box", uni)):
         P = torch.from_numpy(np.ascontiguousarray(pts)).to(dev)
         flags = mesh.classify(P, stream=stream)
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(3):
-            mesh.classify(P, flags=flags, stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / 3
+        ms = timed(P, flags)
+        mesh.classify_counts(reset=True)
+        mesh.classify(P, flags=flags, stream=stream)
+        cnt = mesh.classify_counts(reset=True)
+        mesh.classify_rays_only(True)
+        try:
+            flags_r = mesh.classify(P, stream=stream)
+            torch.cuda.synchronize()
+            ms_r = timed(P, flags_r)
+            same = bool(torch.equal(flags_r, flags))
+        finally:
+            mesh.classify_rays_only(False)
+            mesh.classify_counts(reset=True)
+        p_s = cnt["normal_decided"] / cnt["normal_tests"] if cnt["normal_tests"] else None
         out[name] = {"points": int(P.shape[0]), "ms": ms, "points_per_s": P.shape[0] / (ms / 1e3),
-                     "fraction_in": float(flags.float().mean().item())}
+                     "fraction_in": float(flags.float().mean().item()), "counts": cnt,
+                     "P_s": p_s, "P_f": None if p_s is None else 1.0 - p_s,
+                     "ray_only": {"ms": ms_r, "points_per_s": P.shape[0] / (ms_r / 1e3), "same_flags": same},
+                     "speedup_vs_ray_only": ms_r / ms}
     return out
 
 

@@ -149,8 +149,22 @@ imga_status imga_export_background(imga_mesh mesh, int32_t* offsets, int32_t* tr
 imga_status imga_export_surface_points(imga_mesh mesh, double* out);
 
 /* In/out flags of n points (Algorithm 6): pts_dev float64 [n][3] device, flags_dev uint8 [n]
- * device, 1 = In, 0 = Out (points outside the box are Out). */
+ * device, 1 = In, 0 = Out (points outside the box are Out).  A point in an element whose box meets
+ * no triangle takes that element's stored marker (Algorithm 5): no triangle crosses the element,
+ * and the paper stores the markers so that such tests are not repeated.  A point in an element
+ * with background triangles gets the normal test over them, and ray parity when the test is
+ * undecided (Algorithm 6).  With IMGA_OPT_CLASSIFY_RAYS every point in the box goes to ray parity
+ * instead: the conventional test of the paper's in/out comparison (Table in-out).  Both modes give
+ * the same flags. */
 imga_status imga_classify(imga_mesh mesh, const double* pts_dev, int64_t n, uint8_t* flags_dev, void* stream);
+/* How imga_classify settled its points, summed over the calls on this mesh since it was built or
+ * last reset (host int64 counts[4]): [0] points in elements without background triangles, given
+ * the stored marker; [1] points given the normal test; [2] the points among them that the test
+ * decided; [3] points sent to ray parity.  Points outside the box are not counted.  The paper's
+ * success fraction of the normal test is P_s = counts[2] / counts[1], and P_f = 1 - P_s.
+ * Synchronises the mesh's device; reset = 1 zeroes the counts after reading them.  Errors:
+ * IMGA_ERR_INVALID_ARG (null argument, host-only or batched mesh), IMGA_ERR_CUDA. */
+imga_status imga_classify_counts(imga_mesh mesh, int64_t* counts, int reset);
 
 /* Residual R(u) [n_nodes][4] (device).  u_prev2 is read by BDF2 only (may be NULL otherwise);
  * f is a nodal body force [n_nodes][4] (components 0..2 used) or NULL.  precision 0: FP64
@@ -289,7 +303,9 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * synchronises the stream, allocates (once per mesh) a 4-byte-per-element index of the Intercepted
  * list, and is skipped inside a stream capture and by imga_jvp_noalloc.  Value 0 restores the default
  * shape (4 warps, Morton order).  Both values drop the cached graphs. */
-enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2 };
+/* IMGA_OPT_CLASSIFY_RAYS (value 1 on, 0 off, default off): imga_classify sends every point to ray
+ * parity, skipping the stored markers and the normal test; for the comparison of Table in-out. */
+enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2, IMGA_OPT_CLASSIFY_RAYS = 3 };
 imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
 
 /* The tile shapes in use.  shape[8] = {warps per block, longest-first order} for

@@ -273,6 +273,17 @@ class Mesh:
         of each precision and kind."""
         check(_lib.load().imga_set_option(self.h, 2, 1 if on else 0))
 
+    def classify_rays_only(self, on=True):
+        """imga_set_option(IMGA_OPT_CLASSIFY_RAYS): classify every point by ray parity."""
+        check(_lib.load().imga_set_option(self.h, 3, 1 if on else 0))
+
+    def classify_counts(self, reset=False):
+        """How imga_classify settled its points since the last reset (synchronises):
+        {'marker', 'normal_tests', 'normal_decided', 'rays'}."""
+        c = np.zeros(4, np.int64)
+        check(_lib.load().imga_classify_counts(self.h, c.ctypes.data_as(C.c_void_p), 1 if reset else 0))
+        return {"marker": int(c[0]), "normal_tests": int(c[1]), "normal_decided": int(c[2]), "rays": int(c[3])}
+
     def tuning(self):
         """{(precision, 'residual' | 'jvp'): (warps per block, longest first, candidate ms[6])}."""
         shape = np.zeros(8, np.int32)

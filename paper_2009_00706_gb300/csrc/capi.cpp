@@ -252,6 +252,24 @@ imga_status imga_classify(imga_mesh h, const double* pts, int64_t n, uint8_t* fl
     return IMGA_OK;
 }
 
+imga_status imga_classify_counts(imga_mesh h, int64_t* counts, int reset) {
+    if (!h || !counts) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (h->m.host_only || h->m.batched || !h->m.d.counters)
+        return fail(IMGA_ERR_INVALID_ARG, "mesh has no classification counts (host-only or batched)");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    unsigned long long c[imga::kClassifyCounts] = {};
+    cudaError_t e = cudaSetDevice(h->m.device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c, h->m.d.counters, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(h->m.d.counters, 0, sizeof(c));
+    if (e == cudaSuccess && reset) e = cudaDeviceSynchronize();
+    cudaSetDevice(cur);
+    if (e != cudaSuccess) return fail(IMGA_ERR_CUDA, std::string("classify counts: ") + cudaGetErrorString(e));
+    for (int k = 0; k < imga::kClassifyCounts; ++k) counts[k] = (int64_t)c[k];
+    return IMGA_OK;
+}
+
 static imga_status apply(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
                          const imga_physics* ph, int precision, const double* v, double* out, void* stream) {
     if (!h || !u || !up || !out) return fail(IMGA_ERR_INVALID_ARG, "null vector");
@@ -404,6 +422,10 @@ imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
                     if (!value) h->m.cut_tune[p][j] = imga::Mesh::CutTune();
                 }
             imga::graphs_free(h->m);
+            return IMGA_OK;
+        case IMGA_OPT_CLASSIFY_RAYS:
+            if (h->m.batched) return fail(IMGA_ERR_INVALID_ARG, "batched meshes do not classify points");
+            h->m.classify_ray_only = value != 0;
             return IMGA_OK;
         default:
             return fail(IMGA_ERR_INVALID_ARG, "unknown option");

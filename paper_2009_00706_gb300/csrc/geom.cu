@@ -49,6 +49,7 @@ struct GeomView {
     const int32_t* rg_idx;
     int rg_ny, rg_nz;
     double rg_y0, rg_z0, rg_dy, rg_dz;
+    const int8_t* marker;   // element markers (read by the classification of arbitrary points)
 };
 
 __device__ __forceinline__ uint64_t dpart1by2(uint64_t v) {
@@ -197,7 +198,7 @@ __device__ int warp_ray_parity(const GeomView& g, const double P[3], int dir, bo
 }
 
 __device__ int warp_ray_classify(const GeomView& g, const double P[3], unsigned long long* nrays) {
-    if ((threadIdx.x & 31) == 0) atomicAdd(nrays, 1ull);
+    if (nrays && (threadIdx.x & 31) == 0) atomicAdd(nrays, 1ull);
     int par[3];
     for (int dir = 0; dir < 3; ++dir) {
         bool gz;
@@ -295,13 +296,20 @@ __global__ void __launch_bounds__(32 * kWalkWarps) cut_write_warp(GeomView g, co
     cut_walk_warp(g, cut_list[i], lmax, pts + 4 * off[i], ptsf + 4 * off[i], nrays, st[w]);
 }
 
-// imga_classify with a lane per point and warp-cooperative rays for the undecided ones
-__global__ void classify_warp(GeomView g, const double* pts, int64_t n, uint8_t* flags, unsigned long long* nrays) {
+// imga_classify with a lane per point and warp-cooperative rays for the undecided ones.  A point
+// in an element whose box meets no triangle takes the element's stored marker: no triangle crosses
+// the element, so all its points share the verdict that Algorithm 5 reached for it.  Points in
+// elements with background triangles get the normal test of Algorithm 6, then a ray if it is
+// undecided.  ray_only sends every point in the box to ray parity (the conventional test the
+// paper compares against).  cnt[4] (may be null) accumulates, one atomic per warp and counter,
+// the points settled by the marker, given the normal test, decided by it, and sent to a ray.
+__global__ void classify_warp(GeomView g, const double* pts, int64_t n, uint8_t* flags, int ray_only,
+                              unsigned long long* cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     double P[3] = {0.0, 0.0, 0.0};
     int r = 0;
-    bool want = false;
+    bool want = false, by_marker = false, tested = false;
     int64_t e = -1;
     if (valid) {
         for (int k = 0; k < 3; ++k) P[k] = pts[3 * i + k];
@@ -314,12 +322,32 @@ __global__ void classify_warp(GeomView g, const double* pts, int64_t n, uint8_t*
         }
         if (inside) e = d_find_leaf(g, I[0], I[1], I[2]);
         if (e >= 0) {
-            const double h = (double)(1u << (kMaxDepth - g.lev[e])) * g.scale;
-            r = normal_test(g, e, P, 1e-12 * h);
-            want = true;
+            if (ray_only) {
+                r = -1;
+                want = true;
+            } else if (g.bt_off[e] == g.bt_off[e + 1]) {
+                r = g.marker[e] == 1 ? 1 : 0;
+                by_marker = true;
+            } else {
+                const double h = (double)(1u << (kMaxDepth - g.lev[e])) * g.scale;
+                r = normal_test(g, e, P, 1e-12 * h);
+                tested = true;
+                want = true;
+            }
         }
     }
-    warp_resolve(g, want, P, r, nrays);
+    if (cnt) {
+        const unsigned full = 0xffffffffu;
+        const unsigned bm = __ballot_sync(full, by_marker), bt = __ballot_sync(full, tested),
+                       bd = __ballot_sync(full, tested && r >= 0), br = __ballot_sync(full, want && r < 0);
+        if ((threadIdx.x & 31) == 0) {
+            if (bm) atomicAdd(cnt + 0, (unsigned long long)__popc(bm));
+            if (bt) atomicAdd(cnt + 1, (unsigned long long)__popc(bt));
+            if (bd) atomicAdd(cnt + 2, (unsigned long long)__popc(bd));
+            if (br) atomicAdd(cnt + 3, (unsigned long long)__popc(br));
+        }
+    }
+    warp_resolve(g, want, P, r, nullptr);
     if (valid) flags[i] = (uint8_t)(e < 0 ? 0 : r);
 }
 
@@ -345,10 +373,9 @@ GeomView view(const Mesh& m) {
     g.rg_z0 = m.grid.z0;
     g.rg_dy = m.grid.dy;
     g.rg_dz = m.grid.dz;
+    g.marker = m.d.marker;
     return g;
 }
-
-unsigned long long* g_nrays_dev = nullptr;
 
 template <class T>
 bool upload(T** dst, const std::vector<T>& src, std::string& err, size_t min_elems = 1) {
@@ -383,27 +410,29 @@ bool device_upload_geometry(Mesh& m, std::string& err) {
         return false;
     if (!check(cudaMalloc((void**)&d.marker, std::max<int64_t>(1, d.n_elem)), err, "cudaMalloc")) return false;
     if (!check(cudaMalloc((void**)&d.cflags, std::max<int64_t>(1, d.n_elem)), err, "cudaMalloc")) return false;
-    if (!g_nrays_dev && !check(cudaMalloc((void**)&g_nrays_dev, sizeof(unsigned long long)), err, "cudaMalloc")) return false;
-    return true;
+    if (!check(cudaMalloc((void**)&d.counters, kCounters * sizeof(unsigned long long)), err, "cudaMalloc")) return false;
+    return check(cudaMemset(d.counters, 0, kCounters * sizeof(unsigned long long)), err, "cudaMemset");
 }
 
-static int64_t read_rays() {
+// rays cast while building (markers, sub-cell quadrature): counters[kBuildRays]
+static int64_t read_rays(const Mesh& m) {
     unsigned long long n = 0;
-    cudaMemcpy(&n, g_nrays_dev, sizeof(n), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&n, m.d.counters + kBuildRays, sizeof(n), cudaMemcpyDeviceToHost);
     return (int64_t)n;
 }
 
 bool device_markers(Mesh& m, std::string& err) {
     const int64_t ne = m.n_elem();
-    cudaMemset(g_nrays_dev, 0, sizeof(unsigned long long));
+    unsigned long long* nrays = m.d.counters + kBuildRays;
+    cudaMemset(nrays, 0, sizeof(unsigned long long));
     GeomView g = view(m);
-    if (ne > 0) markers_kernel<<<(unsigned)((ne + 127) / 128), 128>>>(g, m.d.marker, m.d.cflags, g_nrays_dev);
+    if (ne > 0) markers_kernel<<<(unsigned)((ne + 127) / 128), 128>>>(g, m.d.marker, m.d.cflags, nrays);
     if (!check(cudaDeviceSynchronize(), err, "markers kernel")) return false;
     m.marker.resize(ne);
     m.cflags.resize(ne);
     if (!check(cudaMemcpy(m.marker.data(), m.d.marker, ne, cudaMemcpyDeviceToHost), err, "copy markers")) return false;
     if (!check(cudaMemcpy(m.cflags.data(), m.d.cflags, ne, cudaMemcpyDeviceToHost), err, "copy flags")) return false;
-    m.n_rays = read_rays();
+    m.n_rays = read_rays(m);
     m.out_list.clear();
     m.cut_list.clear();
     m.n_in = 0;
@@ -430,8 +459,9 @@ bool device_cut_quadrature(Mesh& m, std::string& err) {
     }
     int64_t* cnt = nullptr;
     if (!check(cudaMalloc((void**)&cnt, (nc + 1) * sizeof(int64_t)), err, "cudaMalloc")) return false;
-    cudaMemset(g_nrays_dev, 0, sizeof(unsigned long long));
-    if (nc > 0) cut_count_warp<<<(unsigned)((nc + kWalkWarps - 1) / kWalkWarps), 32 * kWalkWarps>>>(g, m.d.cut_list, nc, m.lmax, cnt, g_nrays_dev);
+    unsigned long long* nrays = m.d.counters + kBuildRays;
+    cudaMemset(nrays, 0, sizeof(unsigned long long));
+    if (nc > 0) cut_count_warp<<<(unsigned)((nc + kWalkWarps - 1) / kWalkWarps), 32 * kWalkWarps>>>(g, m.d.cut_list, nc, m.lmax, cnt, nrays);
     if (!check(cudaDeviceSynchronize(), err, "cut count kernel")) { cudaFree(cnt); return false; }
     std::vector<int64_t> c(nc);
     if (nc) cudaMemcpy(c.data(), cnt, nc * sizeof(int64_t), cudaMemcpyDeviceToHost);
@@ -444,9 +474,9 @@ bool device_cut_quadrature(Mesh& m, std::string& err) {
     if (!check(cudaMalloc((void**)&m.d.cut_pts_f, std::max<int64_t>(1, np) * 4 * sizeof(float)), err, "cudaMalloc")) return false;
     if (nc > 0)
         cut_write_warp<<<(unsigned)((nc + kWalkWarps - 1) / kWalkWarps), 32 * kWalkWarps>>>(
-            g, m.d.cut_list, nc, m.lmax, m.d.cut_off, m.d.cut_pts, m.d.cut_pts_f, g_nrays_dev);
+            g, m.d.cut_list, nc, m.lmax, m.d.cut_off, m.d.cut_pts, m.d.cut_pts_f, nrays);
     if (!check(cudaDeviceSynchronize(), err, "cut write kernel")) return false;
-    m.n_rays += read_rays() / 2;   // the write pass repeats the count pass's casts
+    m.n_rays += read_rays(m) / 2;   // the write pass repeats the count pass's casts
     m.cut_pts.resize(4 * np);
     if (np) cudaMemcpy(m.cut_pts.data(), m.d.cut_pts, 4 * np * sizeof(double), cudaMemcpyDeviceToHost);
     m.cut_off_elem.assign(m.n_elem() + 1, 0);
@@ -541,7 +571,8 @@ bool device_upload_batch(Mesh& m, std::string& err) {
 int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream) {
     if (n <= 0) return 0;
     GeomView g = view(m);
-    classify_warp<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(g, pts, n, flags, g_nrays_dev);
+    classify_warp<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(g, pts, n, flags, m.classify_ray_only ? 1 : 0,
+                                                                                 m.d.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -549,7 +580,8 @@ void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
                     d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.cut_order, d.sq_elem, d.sq_x,
-                    d.sq_n, d.sq_w, d.sq_taub, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot};
+                    d.sq_n, d.sq_w, d.sq_taub, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
+                    d.counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh();

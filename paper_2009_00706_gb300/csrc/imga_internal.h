@@ -13,6 +13,9 @@ namespace imga {
 
 constexpr int kMaxDepth = 20;     // integer coordinates on [0, 2^20] per root edge
 constexpr int kMaxLevel = 15;     // deepest leaf level the mesh accepts (+1 internal)
+// DeviceMesh::counters: points imga_classify settled by the stored marker, gave the normal test,
+// decided by it, sent to ray parity; then the rays cast while building the mesh
+constexpr int kClassifyCounts = 4, kBuildRays = 4, kCounters = 5;
 
 // Morton code: bit b of x, y, z -> bits 3b, 3b+1, 3b+2
 inline uint64_t part1by2(uint64_t v) {
@@ -100,6 +103,8 @@ struct DeviceMesh {
     float* nd_f = nullptr;        // [3][n_nodes + n_hang][8]
     double* nd_d = nullptr;
     int32_t* slot = nullptr;      // [n_elem] position of an element in a requested list, or -1
+    // [kCounters]: the kClassifyCounts point counts of imga_classify, then the rays cast while building
+    unsigned long long* counters = nullptr;
     // boundary rows
     uint8_t* bcflag = nullptr;    // [n_nodes] bits 0-3 box Dirichlet, bit 4 In-only node
     uint8_t* bcmask_user = nullptr;
@@ -155,6 +160,7 @@ struct Mesh {
     bool user_bc = false;
     bool host_only = false;
     bool batched = false;
+    bool classify_ray_only = false;      // imga_classify: ray parity for every point (IMGA_OPT_CLASSIFY_RAYS)
     // CUDA-graph execution of residual / J v (imga_set_option): cached executable graphs keyed by the
     // call's pointers and parameters, and two side streams + fork/join events for parallel branches
     bool use_graphs = false;

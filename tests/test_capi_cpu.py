@@ -102,9 +102,13 @@ def test_invalid_arguments_are_rejected(lib):
 
 def test_options_and_queries_reject_bad_arguments(lib):
     m = api.Mesh((0, 0, 0), (1, 1, 1), 1, [], None, 3, device=-1)
-    for opt in (1, 2):                                                    # graphs, autotune
+    for opt in (1, 2, 3):                                                 # graphs, autotune, ray-only classify
         assert lib.imga_set_option(m.h, opt, 1) == 1                      # host-only mesh
     assert lib.imga_set_option(None, 1, 1) == 1
+    counts = np.zeros(4, np.int64)
+    assert lib.imga_classify_counts(m.h, counts.ctypes.data_as(C.c_void_p), 0) == 1   # host-only: no counts
+    assert lib.imga_classify_counts(None, counts.ctypes.data_as(C.c_void_p), 0) == 1
+    assert lib.imga_classify_counts(m.h, None, 0) == 1
     assert lib.imga_tuning(None, None, None) == 1
     shape = np.zeros(8, np.int32)
     assert lib.imga_tuning(m.h, shape.ctypes.data_as(C.c_void_p), None) == 0

@@ -78,8 +78,7 @@ def test_surface_points_bit_exact(sphere):
     assert np.array_equal(g.surface_points(), o.surface_points())
 
 
-def test_classify_bit_exact(sphere, dev):
-    w, g, o = sphere
+def _classify_points():
     pts = I.uniform(99, 3 * 20000).reshape(-1, 3)
     # concentrate half of the points around the sphere surface, where the test is hardest
     r = 0.1 + 0.01 * (I.uniform(98, 10000) - 0.5)
@@ -87,9 +86,48 @@ def test_classify_bit_exact(sphere, dev):
     d /= np.linalg.norm(d, axis=1)[:, None]
     pts[:10000] = 0.5 + r[:, None] * d
     pts[0] = (-0.1, 0.5, 0.5)        # outside the box
+    return pts
+
+
+def test_classify_bit_exact(sphere, dev):
+    w, g, o = sphere
+    pts = _classify_points()
     f = g.classify(T(pts, dev)).cpu().numpy()
     assert np.array_equal(f, o.classify(pts))
     assert g.classify(T(np.zeros((0, 3)), dev)).numel() == 0
+
+
+def test_classify_counts_and_ray_only_mode(sphere, dev):
+    """Points in elements without background triangles take the stored marker; the normal test of
+    Algorithm 6 is given to, and decides, exactly the points the oracle's is given and decides;
+    rays go to the undecided ones only.  The ray-only mode (the conventional test of Table in-out)
+    sends every point in the box to a ray and gives the same flags."""
+    w, g, o = sphere
+    pts = _classify_points()
+    n_box = int(np.all((pts >= 0.0) & (pts < 1.0), axis=1).sum())
+    P = T(pts, dev)
+    g.classify_counts(reset=True)
+    f = g.classify(P).cpu().numpy()
+    cnt = g.classify_counts(reset=True)
+    c0 = o.counters()
+    of = o.classify(pts)
+    c1 = o.counters()
+    assert np.array_equal(f, of)
+    assert cnt["marker"] + cnt["normal_tests"] == n_box
+    assert cnt["normal_tests"] == c1["normal_tests"] - c0["normal_tests"]
+    assert cnt["normal_decided"] == c1["normal_decided"] - c0["normal_decided"]
+    assert cnt["rays"] == cnt["normal_tests"] - cnt["normal_decided"]
+    # the oracle casts a ray for every point of an element without triangles as well
+    assert c1["rays"] - c0["rays"] == cnt["rays"] + cnt["marker"]
+    assert cnt["marker"] > 1000 and cnt["normal_decided"] > 0.5 * cnt["normal_tests"] and cnt["rays"] > 0
+    g.classify_rays_only(True)
+    try:
+        fr = g.classify(P).cpu().numpy()
+        cr = g.classify_counts(reset=True)
+    finally:
+        g.classify_rays_only(False)
+    assert np.array_equal(fr, of)
+    assert cr == {"marker": 0, "normal_tests": 0, "normal_decided": 0, "rays": n_box}
 
 
 @pytest.mark.parametrize("seed", [0, 1])
