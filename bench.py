@@ -469,6 +469,11 @@ def run_ours(args):
         inout = run_inout(mesh, w, dev, stream)
     except Exception as ex:          # reported in the JSON line instead of ending the run
         inout = {"error": repr(ex)}
+    if not args.no_inout_table and rank == 0:
+        try:
+            inout["table_in_out"] = run_inout_table(dev, stream)
+        except Exception as ex:
+            inout["table_in_out"] = {"error": repr(ex)}
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -674,6 +679,58 @@ def run_inout(mesh, w, dev, stream):
     return out
 
 
+def run_inout_table(dev, stream, levels=(6, 7, 8)):
+    """The analogue of Table in-out: a truck (two filleted boxes) in uniform 64^3, 128^3 and 256^3
+    grids, 5^3 Gauss-Legendre points per Intercepted element, classified by the normal test with
+    ray fallback and, for comparison, every point by ray parity.  Per grid: P_s (points the normal
+    test decides, of all the points), both times, the time per point and the speed-up."""
+    import gc
+
+    import torch
+
+    from paper_2009_00706_gb300 import api
+    xi = np.polynomial.legendre.leggauss(5)[0]
+    g = np.stack(np.meshgrid(xi, xi, xi, indexing="ij"), -1).reshape(-1, 3)
+    rows = []
+    for lev in levels:
+        w = I.inout_truck(lev)
+        m = api.Mesh.from_workload(w, device=dev.index)
+        ex = m.export()
+        mk, _ = m.markers()
+        cut = np.where(mk == 2)[0]
+        h = (w.hi[0] - w.lo[0]) / 2.0 ** lev
+        x0 = np.asarray(w.lo)[None, :] + ex["anchors"][cut].astype(np.float64) * ((w.hi[0] - w.lo[0]) / 2.0 ** 20)
+        pts = (x0[:, None, :] + 0.5 * h * (g[None, :, :] + 1.0)).reshape(-1, 3)
+        P = torch.from_numpy(np.ascontiguousarray(pts)).to(dev)
+        res = {}
+        for mode in ("normal_then_ray", "ray_only"):
+            m.classify_rays_only(mode == "ray_only")
+            flags = m.classify(P, stream=stream)
+            torch.cuda.synchronize()
+            m.classify_counts(reset=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.classify(P, flags=flags, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            res[mode] = (a.elapsed_time(b), m.classify_counts(reset=True), flags)
+        m.classify_rays_only(False)
+        (ms, cnt, f), (ms_r, cnt_r, f_r) = res["normal_then_ray"], res["ray_only"]
+        n = int(P.shape[0])
+        rows.append({"grid": "%d^3" % (1 << lev), "elements": m.n_elem, "cut_elements": int(cut.size),
+                     "points": n, "triangles": int(m.info["n_tri"]),
+                     "P_s": cnt["normal_decided"] / max(1, cnt["normal_tests"]),
+                     "P_f": cnt["rays"] / max(1, cnt["normal_tests"]), "counts": cnt,
+                     "ms": ms, "ns_per_point": 1e6 * ms / n, "ray_only_ms": ms_r, "ray_only_ns_per_point": 1e6 * ms_r / n,
+                     "speedup_vs_ray_only": ms_r / ms, "same_flags": bool(torch.equal(f, f_r)),
+                     "fraction_in": float(f.float().mean().item())})
+        del m, P, res, f, f_r
+        gc.collect()
+        torch.cuda.empty_cache()
+    return {"workload": "truck (cab + trailer, 24,576 triangles) in a 6.4 cube, uniform grids, 5^3 "
+                        "Gauss-Legendre points per Intercepted element", "grids": rows}
+
+
 def run_learned(args, dev, stream, les, w_les):
     """Learned block preconditioner: the network is trained by the library's kernels on element Jacobian
     blocks of the small sphere (seeds 0-15, all active elements) and of the sphere LES (50,000
@@ -742,6 +799,7 @@ def parse_args(argv=None):
     ap.add_argument("--sample-nodes", type=int, default=60000)
     ap.add_argument("--ref-sample-nodes", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-inout-table", action="store_true", help="skip the 64^3-256^3 in/out comparison")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-GMRES step timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-bluff", action="store_true", help="skip the 19.8 M-element bluff-body pair measurement")

@@ -269,6 +269,19 @@ def bluff_pair(seed: int = 0, levels: int = 0, n_per_edge: int = 91) -> Workload
                                         truck(x2, yc, zb, n_per_edge, 1e-5, seed + 2)]), seed=seed)
 
 
+def inout_truck(level: int, seed: int = 0, n_per_edge: int = 32) -> Workload:
+    """The in/out comparison of Table in-out on a uniform grid: one truck (cab and trailer, fillet
+    0.05, 0.05 gap between them; 12 n^2 triangles per box, n = 32: 24,576 triangles, jitter 1e-5)
+    centred in a cube of edge 6.4, meshed uniformly at `level` (6, 7, 8: the paper's 64^3, 128^3,
+    256^3 grids), no refinement regions."""
+    edge = 6.4
+    c = 0.5 * edge
+    return Workload(
+        name="inout_truck_%d" % (1 << level), lo=(0.0, 0.0, 0.0), hi=(edge, edge, edge), base_level=level,
+        regions=[], lmax=3, physics=Physics(),
+        surface=lambda: truck(c - 0.5 * TRUCK_L, c, c - 0.5, n_per_edge, 1e-5, seed), seed=seed)
+
+
 def state(n_nodes: int, seed: int = 0, sigma: float = 0.01):
     """u_prev = uniform inflow (1, 0, 0), p = 0; u = u_prev + N(0, sigma^2) on the velocity;
     v ~ N(0, 1) on every dof.  Node-major [n_nodes, 4] float64 (u, v, w, p)."""
