@@ -21,17 +21,19 @@
 //   * skip In elements, Dirichlet on In-only nodes .... Algorithm 1, Fig. IBM caption
 //   * element matrix K_e = M_e^T k_e M_e, o2n ......... Algorithms 2 and 4
 // Where the paper is silent this oracle takes the reading stated at the function concerned (tau
-// definitions, in/out sign convention, ray directions, h_b, surface rule, CN treatment).
+// definitions, in/out sign convention, ray directions, the widened box of B_T, h_b, surface rule,
+// CN treatment).
 //
 // Pins (tests/test_oracle_*.py): textbook Q1 element matrices at three special states,
 // a closed-form residual, the linear patch test across hanging nodes, zero residual for
 // uniform flow, central differences of R for J v, the complex step Im R(u + i eps v) / eps against
 // the dual-number J v, second-order MMS convergence, the total volume of the quadrature, the printed
-// Gauss abscissae of Fig. GP, exact dyadic cuts, brute-force ray parity, the analytic
-// sphere, and divergence-theorem identities of the surface rule.
+// Gauss abscissae of Fig. GP, exact dyadic cuts, brute-force ray parity (also with faces on grid
+// planes), the analytic sphere, rigid-motion equivariance of R and J v, and divergence-theorem
+// and barycentric-moment identities of the surface rule.
 // Parity unpinned (readings of silent passages, checked only for consistency): the constants
 // of tau_M / tau_C / tau-bar (C_I = 36, the metric form), the Crank-Nicolson placement of the
-// pressure, the h_b definition, the 3-point surface rule, and the in/out tolerance.
+// pressure, the h_b definition, the choice of degree-2 surface rule, and the in/out tolerance.
 //
 // Compile with -ffp-contract=off: the in/out decisions must be reproducible bit for bit.
 
@@ -408,18 +410,27 @@ struct Geom {
 
 double elem_h(const Mesh& m, int e) { return (double)osize(m.lev[e]) * m.scale; }
 
+// B_T(e), Algorithm 1: the triangles whose bounding box meets the closed box of e, widened on
+// every side by g_bt_pad times the edge of e.  A face lying on a grid plane then belongs to the
+// elements on both sides of it whatever its rounding.  The normal test of Algorithm 6 needs the
+// face that a point is in front of to be in B_T; without it, the planes of neighbouring
+// triangles can all put the point behind them.  A larger B_T only turns decisions into ray
+// casts, never into other decisions.
+double g_bt_pad = 1e-2;
+
 const std::vector<int>& get_bt(Geom& g, int e) {
     if (!g.bt_done[e]) {
         const Mesh& m = *g.m;
         double b0[3], b1[3];
         uint32_t a[3] = {m.anc[e][0], m.anc[e][1], m.anc[e][2]};
         octbox(m, a, m.lev[e], b0, b1);
+        const double pad = g_bt_pad * elem_h(m, e);
         std::vector<int>& L = g.bt[e];
         for (size_t t = 0; t < g.tris.size(); ++t) {
             const Tri& T = g.tris[t];
             bool hit = true;
             for (int k = 0; k < 3; ++k)
-                if (!(T.bmin[k] <= b1[k] && T.bmax[k] >= b0[k])) { hit = false; break; }
+                if (!(T.bmin[k] <= b1[k] + pad && T.bmax[k] >= b0[k] - pad)) { hit = false; break; }
             if (hit) L.push_back((int)t);
         }
         g.bt_done[e] = 1;
@@ -1070,6 +1081,10 @@ int64_t or_surface_points(void* s, double* out, int64_t cap) {
     }
     return (int64_t)Q.size();
 }
+
+// test knob: the widening of B_T as a fraction of the element edge; it applies to the elements whose
+// B_T is computed after the call, so set it before building the mesh it is meant for
+void or_set_bt_pad(double pad) { g_bt_pad = pad; }
 
 void or_counters(void* s, int64_t* out) {
     Geom& g = ((State*)s)->geom;

@@ -51,6 +51,7 @@ def lib():
         L.or_surface_points.argtypes = [vp, C.c_void_p, i64]
         L.or_surface_points.restype = i64
         L.or_counters.argtypes = [vp, C.c_void_p]
+        L.or_set_bt_pad.argtypes = [C.c_double]
         L.or_set_dirichlet.argtypes = [vp, C.c_void_p, C.c_void_p]
         L.or_residual_jvp.argtypes = [vp, C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p, i64, C.c_void_p, C.c_void_p]
         L.or_residual_jvp_complex_step.argtypes = L.or_residual_jvp.argtypes
@@ -68,6 +69,12 @@ def _p(a):
 
 def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_bt_pad(pad: float) -> None:
+    """Widening of the background-triangle boxes as a fraction of the element edge (default 1e-2);
+    applies to meshes built afterwards.  A test knob: 0 restores the plain closed-box overlap."""
+    lib().or_set_bt_pad(float(pad))
 
 
 class OracleMesh:

@@ -322,7 +322,19 @@ bool build_triangles(Mesh& m, const double* t, int64_t n, std::string& err) {
 
 // Background triangles: for every triangle, descend the octree from the root through the
 // octants its bounding box meets, down to the leaves; B_T(e) = triangles whose box meets the
-// closed box of e.  Stored as CSR sorted by element, then triangle.
+// closed box of e widened on every side by kBtPad times its edge.  Stored as CSR sorted by
+// element, then triangle.
+//
+// The widening keeps the normal test of Algorithm 6 sound where a face of the body lies on a
+// plane of the grid, as axis-aligned faces at round coordinates do.  Whether such a face's
+// triangles meet the exact closed box of the element beside it is then a matter of rounding or
+// of the surface's noise.  A point of that element in front of the face, but behind the planes
+// of neighbouring triangles that reach into the element, would be called In when the face is
+// left out.  A larger B_T is never less safe: an added triangle either agrees with the others
+// or makes the test undecided, and the point goes to the exact ray.  Octants are widened by the
+// same fraction of their own edge, which covers the widened boxes of the leaves inside them.
+constexpr double kBtPad = 1e-2;
+
 void build_background(Mesh& m) {
     const int64_t nt = m.tri.n, ne = m.n_elem();
     std::vector<std::vector<std::pair<int32_t, int32_t>>> local;
@@ -354,18 +366,21 @@ void build_background(Mesh& m) {
                 double b0[3], b1[3];
                 uint32_t s = octsize(o.l);
                 phys_box(m, o.a, s, b0, b1);
+                const double pad_o = kBtPad * ((double)s * m.scale);
                 bool meet = true;
                 for (int k = 0; k < 3; ++k)
-                    if (!(lo[k] <= b1[k] && hi[k] >= b0[k])) meet = false;
+                    if (!(lo[k] <= b1[k] + pad_o && hi[k] >= b0[k] - pad_o)) meet = false;
                 if (!meet) continue;
                 int64_t e = find_leaf(m, o.a[0], o.a[1], o.a[2]);
                 if (e >= 0 && m.lev[e] <= o.l) {
-                    // the octant lies inside leaf e: test the leaf's own box
+                    // the octant lies inside leaf e: test the leaf's own widened box
                     double c0[3], c1[3];
-                    phys_box(m, &m.anc[3 * e], octsize(m.lev[e]), c0, c1);
+                    const uint32_t se = octsize(m.lev[e]);
+                    phys_box(m, &m.anc[3 * e], se, c0, c1);
+                    const double pad = kBtPad * ((double)se * m.scale);
                     bool hit = true;
                     for (int k = 0; k < 3; ++k)
-                        if (!(lo[k] <= c1[k] && hi[k] >= c0[k])) hit = false;
+                        if (!(lo[k] <= c1[k] + pad && hi[k] >= c0[k] - pad)) hit = false;
                     if (hit) mine.push_back({(int32_t)e, (int32_t)t});
                     continue;
                 }

@@ -14,6 +14,7 @@ import os
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from oracle.oracle import OracleMesh
 from paper_2009_00706_gb300 import inputs as I
 
@@ -164,6 +165,96 @@ def test_inout_icosphere_vs_brute_force_and_analytic():
     assert np.all(got[r < r_in - 1e-9]) and not np.any(got[r > r_out + 1e-9])
     cnt = m.counters()
     assert cnt["normal_decided"] > 0.5 * cnt["normal_tests"]
+
+
+def binned_parity(pts, tri, d):
+    """Ray parity along d like brute_parity, for many points: the points are sorted by their
+    coordinate along one axis perpendicular to d, so that each triangle only tests the points in
+    its slab.  Returns (inside, ok), ok False within 1e-9 of a triangle edge."""
+    d = d / np.linalg.norm(d)
+    a = np.cross(d, [1.0, 0.0, 0.0] if abs(d[0]) < 0.9 else [0.0, 1.0, 0.0])
+    a /= np.linalg.norm(a)
+    b = np.cross(d, a)
+    pa, pb = pts @ a, pts @ b
+    order = np.argsort(pa)
+    sa = pa[order]
+    hits = np.zeros(pts.shape[0], np.int64)
+    near = np.zeros(pts.shape[0], bool)
+    for t in tri:
+        ta, tb = t @ a, t @ b
+        i0, i1 = np.searchsorted(sa, ta.min() - 1e-9), np.searchsorted(sa, ta.max() + 1e-9, side="right")
+        idx = order[i0:i1]
+        idx = idx[(pb[idx] >= tb.min() - 1e-9) & (pb[idx] <= tb.max() + 1e-9)]
+        if idx.size == 0:
+            continue
+        e1, e2 = t[1] - t[0], t[2] - t[0]
+        pv = np.cross(d, e2)
+        det = e1 @ pv
+        if det == 0.0:
+            continue
+        tv = pts[idx] - t[0]
+        u = (tv @ pv) / det
+        qv = np.cross(tv, e1)
+        v = (qv @ d) / det
+        tt = (qv @ e2) / det
+        hit = (u >= 0) & (v >= 0) & (u + v <= 1) & (tt > 0)
+        close = (np.minimum(np.minimum(np.abs(u), np.abs(v)), np.abs(1 - u - v)) < 1e-9) & (tt > 0) & \
+                (u > -1e-9) & (v > -1e-9) & (u + v < 1 + 1e-9)
+        hits[idx] += hit
+        near[idx] |= close
+    return hits % 2 == 1, ~near
+
+
+def _grid_plane_boxes(seed):
+    """Two filleted boxes (fillet 1/32) whose flat faces lie on planes of the level-5 grid of the
+    unit cube, up to a vertex jitter of 1e-5."""
+    return np.concatenate([I.rounded_box((0.25, 0.25, 0.3125), (0.75, 0.625, 0.6875), 1.0 / 32, 16, 1e-5, seed),
+                           I.rounded_box((0.78125, 0.25, 0.3125), (0.90625, 0.5, 0.5), 1.0 / 32, 8, 1e-5, seed + 7)])
+
+
+def _inout_errors(pad, seed=1):
+    """Oracle in/out against binned ray parity along a random direction, for the 5^3 Gauss points
+    of every Intercepted element and the corners of every element with background triangles.
+    Returns (point errors, corner errors, points checked)."""
+    tri = _grid_plane_boxes(seed)
+    O.set_bt_pad(pad)
+    try:
+        m = OracleMesh((0, 0, 0), (1, 1, 1), 5, [], tri, 3)
+        mk, cf, nbt = m.markers()
+        h = 1.0 / 32
+        xi = np.polynomial.legendre.leggauss(5)[0]
+        G = np.stack(np.meshgrid(xi, xi, xi, indexing="ij"), -1).reshape(-1, 3)
+        x0 = m.anchors.astype(np.float64) * m.scale
+        cut = np.where(mk == 2)[0]
+        pts = (x0[cut][:, None, :] + 0.5 * h * (G[None] + 1.0)).reshape(-1, 3)
+        got = m.classify(pts).astype(bool)
+        has = np.where(nbt > 0)[0]
+        off = np.array([[(c >> k) & 1 for k in range(3)] for c in range(8)], dtype=np.float64)
+        corners = (x0[has][:, None, :] + h * off[None]).reshape(-1, 3)
+        cflag = (((cf[has][:, None] >> np.arange(8)[None]) & 1) == 1).reshape(-1)
+    finally:
+        O.set_bt_pad(1e-2)
+    d = I.normal(5, 3)
+    truth, ok = binned_parity(pts, tri, d)
+    ctruth, cok = binned_parity(corners, tri, d)
+    assert ok.mean() > 0.999 and cok.mean() > 0.99
+    return int((got != truth)[ok].sum()), int((cflag != ctruth)[cok].sum()), int(ok.sum())
+
+
+def test_inout_exact_with_faces_on_grid_planes():
+    """Faces on grid planes: with B_T taken over the element box widened by 1e-2 of its edge, the
+    normal test with ray fallback (Algorithm 6) and the markers (Algorithm 5) agree with ray
+    parity at every Gauss point and every corner."""
+    pe, ce, n = _inout_errors(1e-2)
+    assert (pe, ce) == (0, 0) and n > 200000
+
+
+def test_inout_plain_box_overlap_misclassifies_with_faces_on_grid_planes():
+    """The same body with B_T over the exact closed box: points just in front of a face whose
+    triangles miss the element box, behind the planes of the triangles that reach in, are called
+    In.  This is what the widening removes."""
+    pe, ce, n = _inout_errors(0.0)
+    assert pe > 0 and ce > 0
 
 
 def test_inout_two_disjoint_bodies_and_polyhedra():
