@@ -130,6 +130,10 @@ struct Mesh {
     std::vector<imga_region> regions;
     // octree
     std::vector<uint64_t> key;
+    // key_lut[p] = first leaf whose key has the top kLutBits bits >= p (p = 0 .. 2^kLutBits);
+    // valid while key_lut_n == key.size()
+    std::vector<int32_t> key_lut;
+    size_t key_lut_n = 0;
     std::vector<uint32_t> anc;    // [n][3]
     std::vector<uint8_t> lev;
     // nodes

@@ -88,10 +88,22 @@ struct Oct { uint32_t a[3]; int l; };
 
 }  // namespace
 
+// Leaf lookup: keys are 60-bit Morton codes of 20-bit anchors.  The table of the top kLutBits
+// bits (an octant of level kLutBits / 3) narrows the binary search to the leaves under that
+// octant.  A coarser leaf spans several such octants and leaves their ranges empty: the answer
+// is then the leaf just before the range, as the plain search over all keys would find.
+constexpr int kLutBits = 21, kLutShift = 3 * kMaxDepth - kLutBits;
+
 int64_t find_leaf(const Mesh& m, int64_t x, int64_t y, int64_t z) {
     if (!inside_box(m, x, y, z)) return -1;
     uint64_t k = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
-    auto it = std::upper_bound(m.key.begin(), m.key.end(), k);
+    auto first = m.key.begin(), last = m.key.end();
+    if (m.key_lut_n == m.key.size() && !m.key_lut.empty()) {
+        const uint64_t p = k >> kLutShift;
+        first = m.key.begin() + m.key_lut[p];
+        last = m.key.begin() + m.key_lut[p + 1];
+    }
+    auto it = std::upper_bound(first, last, k);
     if (it == m.key.begin()) return -1;
     int64_t e = (int64_t)(it - m.key.begin()) - 1;
     uint32_t s = octsize(m.lev[e]);
@@ -105,11 +117,21 @@ static void set_leaves(Mesh& m, const std::vector<Oct>& L) {
     m.anc.resize(3 * n);
     m.lev.resize(n);
     m.key.resize(n);
-    for (size_t i = 0; i < n; ++i) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)n; ++i) {
         for (int k = 0; k < 3; ++k) m.anc[3 * i + k] = L[i].a[k];
         m.lev[i] = (uint8_t)L[i].l;
         m.key[i] = morton3(L[i].a[0], L[i].a[1], L[i].a[2]);
     }
+    // prefix table: key_lut[p] = lower bound of p << kLutShift
+    const size_t np = (size_t)1 << kLutBits;
+    m.key_lut.assign(np + 1, (int32_t)n);
+    size_t i = 0;
+    for (size_t p = 0; p <= np; ++p) {
+        while (i < n && (m.key[i] >> kLutShift) < p) ++i;
+        m.key_lut[p] = (int32_t)i;
+    }
+    m.key_lut_n = n;
 }
 
 bool build_octree(Mesh& m, std::string& err) {
