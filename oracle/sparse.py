@@ -1,0 +1,163 @@
+"""Matrix-based linear-solver path of the method, for the oracle: the global Jacobian assembled in
+4 x 4 blocks and BiCGStab.
+
+TEST INFRASTRUCTURE ONLY: the tests and the CPU legs of the benchmark use this module; the
+product never imports it.
+
+* Assembly (Algorithms 2 and 4): K = sum_e M_e^T k_e M_e, where k_e is the 32 x 32 element
+  Jacobian (8 corners x 4 unknowns, row a*4+i, column b*4+k) and M_e the corner-to-node operator
+  with the hanging-node interpolation of Algorithm 3 (weights 1/2 on edges, 1/4 on faces).
+  Rows that the residual replaces by U - g (strong Dirichlet rows on the box, Algorithm 1's nodes
+  touched by In elements only) become identity rows.  Stored as a block-sparse matrix with 4 x 4
+  blocks, block columns sorted within each block row.
+* BiCGStab (appendix "Details of solver selection": the linear systems of the Newton steps are
+  solved by BiCGStab), in the form of van der Vorst (1992) with right preconditioning, float64.
+"""
+import numpy as np
+import scipy.sparse as sp
+
+
+def strong_mask(m):
+    """Bit k of mask[i] set: row (i, k) of the residual is U - g (box faces but the outlet carry
+    the velocity, the outlet x = hi the pressure; every unknown of a node touched by no active
+    element).  A mask set with set_dirichlet replaces the box rows."""
+    if getattr(m, "_bc", None) is not None:
+        mask = np.array(m._bc[0], dtype=np.uint8)
+    else:
+        ijk = m.node_ijk.astype(np.int64)
+        outlet = ijk[:, 0] == m.hiI[0]
+        other = (ijk == 0).any(1) | (ijk[:, 1] == m.hiI[1]) | (ijk[:, 2] == m.hiI[2])
+        mask = np.where(other, 7, 0).astype(np.uint8) | np.where(outlet, 8, 0).astype(np.uint8)
+    mk, _, _ = m.markers()
+    active = np.zeros(m.n_nodes, bool)
+    for el in np.where(mk != 1)[0]:
+        for c in range(8):
+            idx = m.conn[el, c]
+            if idx < m.n_nodes:
+                active[idx] = True
+            else:
+                h = idx - m.n_nodes
+                active[m.hang_parents[h, :m.hang_np[h]]] = True
+    mask[~active] = 15
+    return mask
+
+
+def corner_operator(m, e):
+    """(nodes, weights) of the 8 corners of element e: corner c is sum_p weights[c][p] * node
+    nodes[c][p] (one node with weight 1, or the 2 / 4 parents of a hanging node)."""
+    out = []
+    for c in range(8):
+        idx = int(m.conn[e, c])
+        if idx < m.n_nodes:
+            out.append(([idx], [1.0]))
+        else:
+            h = idx - m.n_nodes
+            k = int(m.hang_np[h])
+            out.append(([int(p) for p in m.hang_parents[h, :k]], [1.0 / k] * k))
+    return out
+
+
+def assemble_bsr(m, phys, u, u_prev, u_prev2=None, f=None, mask=None):
+    """The assembled Jacobian dR/dU as a scipy bsr_matrix with 4 x 4 blocks (n_nodes x n_nodes
+    blocks).  The block pattern is structural: every pair of nodes reached from the corners of a
+    common Out or Intercepted element (through M_e), and the diagonal block of every node with a
+    strong row.  In elements contribute nothing (Algorithm 1).  The rows of `mask` (default
+    strong_mask(m)) are identity rows; their other entries stay in the pattern as zeros."""
+    n = m.n_nodes
+    if mask is None:
+        mask = strong_mask(m)
+    mk, _, _ = m.markers()
+    blocks = {}
+    for e in np.where(mk != 1)[0]:
+        K, _ = m.element_matrix(phys, u, u_prev, int(e), u_prev2=u_prev2, f=f)
+        ops = corner_operator(m, int(e))
+        for a in range(8):
+            for b in range(8):
+                kab = K[4 * a:4 * a + 4, 4 * b:4 * b + 4]
+                for ni, wi in zip(*ops[a]):
+                    for nj, wj in zip(*ops[b]):
+                        key = (ni, nj)
+                        if key not in blocks:
+                            blocks[key] = np.zeros((4, 4))
+                        blocks[key] += (wi * wj) * kab
+    # strong rows: zero the row, then a 1 on the diagonal
+    fixed = ((mask[:, None] >> np.arange(4)[None, :]) & 1).astype(bool)
+    for (i, j), B in blocks.items():
+        B[fixed[i], :] = 0.0
+    for i in np.where(fixed.any(1))[0]:
+        B = blocks.setdefault((int(i), int(i)), np.zeros((4, 4)))
+        for k in np.where(fixed[i])[0]:
+            B[k, k] = 1.0
+    keys = sorted(blocks)
+    rows = np.array([k[0] for k in keys], dtype=np.int64)
+    cols = np.array([k[1] for k in keys], dtype=np.int64)
+    data = np.stack([blocks[k] for k in keys]) if keys else np.zeros((0, 4, 4))
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(indptr, rows + 1, 1)
+    indptr = np.cumsum(indptr)
+    return sp.bsr_matrix((data, cols, indptr), shape=(4 * n, 4 * n))
+
+
+def bicgstab(matvec, b, x0=None, rtol=1e-8, atol=0.0, maxiter=1000, precond=None):
+    """BiCGStab (van der Vorst 1992) for A x = b, A given by matvec, with right preconditioning:
+    the directions p and s are mapped by M^-1 = precond before each product with A, so the
+    recurrence runs on the true residual b - A x.  Stops when ||b - A x|| <= max(rtol ||b||,
+    atol).  Returns (x, iterations, converged, residual norms)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    Minv = (lambda z: z) if precond is None else precond
+    r = b - matvec(x)
+    tol = max(rtol * np.linalg.norm(b), atol)
+    hist = [np.linalg.norm(r)]
+    if hist[-1] <= tol:
+        return x, 0, True, hist
+    r_hat = r.copy()
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    for it in range(1, maxiter + 1):
+        rho = float(r_hat @ r)
+        if rho == 0.0:
+            return x, it - 1, False, hist          # breakdown: r orthogonal to the shadow residual
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        p_hat = Minv(p)
+        v = matvec(p_hat)
+        alpha = rho / float(r_hat @ v)
+        s = r - alpha * v
+        if np.linalg.norm(s) <= tol:
+            x = x + alpha * p_hat
+            hist.append(np.linalg.norm(s))
+            return x, it, True, hist
+        s_hat = Minv(s)
+        t = matvec(s_hat)
+        tt = float(t @ t)
+        omega = float(t @ s) / tt if tt > 0.0 else 0.0
+        x = x + alpha * p_hat + omega * s_hat
+        r = s - omega * t
+        hist.append(np.linalg.norm(r))
+        if hist[-1] <= tol:
+            return x, it, True, hist
+        if omega == 0.0:
+            return x, it, False, hist              # stagnation
+        rho_old = rho
+    return x, maxiter, False, hist
+
+
+def block_jacobi(A):
+    """Inverse of the 4 x 4 diagonal blocks of a block-sparse matrix, as a preconditioner.  A block
+    whose smallest singular value is at most 1e-14 of its largest entry (all zero, for a node that
+    only Intercepted elements without quadrature points touch) is replaced by the identity."""
+    A = A.tobsr(blocksize=(4, 4))
+    n = A.shape[0] // 4
+    D = np.zeros((n, 4, 4))
+    for i in range(n):
+        for q in range(A.indptr[i], A.indptr[i + 1]):
+            if A.indices[q] == i:
+                D[i] = A.data[q]
+    scale = np.abs(D).max(axis=(1, 2))
+    smin = np.linalg.svd(D, compute_uv=False)[:, -1]
+    singular = ~(smin > 1e-14 * scale)
+    D[singular] = np.eye(4)
+    Dinv = np.linalg.inv(D)
+    return lambda z: np.einsum("nij,nj->ni", Dinv, z.reshape(n, 4)).reshape(-1)
