@@ -206,6 +206,16 @@ imga_status imga_jvp_noalloc(imga_mesh mesh, const double* u, const double* u_pr
  * val_dev float64 [n_nodes][4].  Both device pointers; copied.  Pass NULL, NULL to restore. */
 imga_status imga_set_dirichlet(imga_mesh mesh, const uint8_t* mask_dev, const double* val_dev, void* stream);
 
+/* Block pattern of the Jacobian assembled in 4 x 4 blocks, K = sum_e M_e^T k_e M_e (Algorithms 2
+ * and 4): block (i, j) is present when nodes i and j both enter one element through M_e, as corners
+ * or as parents of a hanging corner (Algorithm 3).  Every element counts, In elements too, so the
+ * pattern depends on the octree alone; every diagonal block is present.  Host arrays: indptr
+ * [n_nodes + 1] (int64) and indices [*n_blocks] (int32, increasing within each block row); pass
+ * NULL for both to read *n_blocks first.  Built on the host at the first call and kept by the mesh;
+ * works on host-only and batched meshes (block-diagonal over the problems).  Errors:
+ * IMGA_ERR_INVALID_ARG (null mesh or n_blocks), IMGA_ERR_OOM. */
+imga_status imga_bsr_pattern(imga_mesh mesh, int64_t* n_blocks, int64_t* indptr, int32_t* indices);
+
 /* Element Jacobians k_e = d r_e / d u_e for a list of elements (Algorithm 4's element matrix, before
  * the hanging correction M_e^T k_e M_e of Algorithm 2): elems_dev int32 [n] device, distinct
  * element indices; K_dev float64 [n][32][32] device, row a*4+i (corner a, component i), column

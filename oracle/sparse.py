@@ -59,18 +59,18 @@ def corner_operator(m, e):
 
 def assemble_bsr(m, phys, u, u_prev, u_prev2=None, f=None, mask=None):
     """The assembled Jacobian dR/dU as a scipy bsr_matrix with 4 x 4 blocks (n_nodes x n_nodes
-    blocks).  The block pattern is structural: every pair of nodes reached from the corners of a
-    common Out or Intercepted element (through M_e), and the diagonal block of every node with a
-    strong row.  In elements contribute nothing (Algorithm 1).  The rows of `mask` (default
-    strong_mask(m)) are identity rows; their other entries stay in the pattern as zeros."""
+    blocks).  The block pattern is structural and depends on the octree alone: every pair of nodes
+    reached from the corners of a common element through M_e, In elements included.  In elements
+    contribute zeros (Algorithm 1).  The rows of `mask` (default strong_mask(m)) are identity
+    rows; their other entries stay in the pattern as zeros."""
     n = m.n_nodes
     if mask is None:
         mask = strong_mask(m)
     mk, _, _ = m.markers()
     blocks = {}
-    for e in np.where(mk != 1)[0]:
-        K, _ = m.element_matrix(phys, u, u_prev, int(e), u_prev2=u_prev2, f=f)
-        ops = corner_operator(m, int(e))
+    for e in range(m.n_elem):
+        K = np.zeros((32, 32)) if mk[e] == 1 else m.element_matrix(phys, u, u_prev, e, u_prev2=u_prev2, f=f)[0]
+        ops = corner_operator(m, e)
         for a in range(8):
             for b in range(8):
                 kab = K[4 * a:4 * a + 4, 4 * b:4 * b + 4]

@@ -273,6 +273,18 @@ class Mesh:
         of each precision and kind."""
         check(_lib.load().imga_set_option(self.h, 2, 1 if on else 0))
 
+    def bsr_pattern(self):
+        """(indptr int64 [n_nodes + 1], indices int32 [n_blocks]) of the Jacobian's 4 x 4 block
+        pattern (host arrays)."""
+        L = _lib.load()
+        nb = C.c_int64()
+        check(L.imga_bsr_pattern(self.h, C.byref(nb), None, None))
+        indptr = np.zeros(self.n_nodes + 1, np.int64)
+        indices = np.zeros(max(1, nb.value), np.int32)
+        check(L.imga_bsr_pattern(self.h, C.byref(nb), indptr.ctypes.data_as(C.c_void_p),
+                                 indices.ctypes.data_as(C.c_void_p)))
+        return indptr, indices[:nb.value]
+
     def classify_rays_only(self, on=True):
         """imga_set_option(IMGA_OPT_CLASSIFY_RAYS): classify every point by ray parity."""
         check(_lib.load().imga_set_option(self.h, 3, 1 if on else 0))

@@ -252,6 +252,24 @@ imga_status imga_classify(imga_mesh h, const double* pts, int64_t n, uint8_t* fl
     return IMGA_OK;
 }
 
+imga_status imga_bsr_pattern(imga_mesh h, int64_t* n_blocks, int64_t* indptr, int32_t* indices) {
+    if (!h || !n_blocks) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    imga::Mesh& m = h->m;
+    if (m.bsr_ptr.size() != (size_t)m.n_nodes() + 1) {
+        try {
+            imga::build_bsr_pattern(m);
+        } catch (const std::bad_alloc&) {
+            m.bsr_ptr.clear();
+            m.bsr_idx.clear();
+            return fail(IMGA_ERR_OOM, "block pattern: host allocation failed");
+        }
+    }
+    *n_blocks = (int64_t)m.bsr_idx.size();
+    if (indptr) std::copy(m.bsr_ptr.begin(), m.bsr_ptr.end(), indptr);
+    if (indices) std::copy(m.bsr_idx.begin(), m.bsr_idx.end(), indices);
+    return IMGA_OK;
+}
+
 imga_status imga_classify_counts(imga_mesh h, int64_t* counts, int reset) {
     if (!h || !counts) return fail(IMGA_ERR_INVALID_ARG, "null argument");
     if (h->m.host_only || h->m.batched || !h->m.d.counters)

@@ -155,6 +155,9 @@ struct Mesh {
     int64_t n_sq_sparse = 0;             // surface points of elements hosting < kNitscheDenseMin (stored first)
     int64_t n_sq_elem = 0;               // elements hosting >= kNitscheDenseMin surface points
     std::vector<uint8_t> bcflag;
+    // block pattern of the assembled Jacobian (imga_bsr_pattern), built on first use
+    std::vector<int64_t> bsr_ptr;        // [n_nodes + 1]
+    std::vector<int32_t> bsr_idx;        // [n_blocks] block columns, increasing within a row
     int64_t n_in = 0, n_rays = 0;
     // batched meshes: element -> problem, per-problem viscosity and element/node offsets
     std::vector<uint16_t> eprob;
@@ -203,6 +206,7 @@ void build_ray_grid(Mesh& m);
 void build_surface_points(Mesh& m);
 void build_bc_flags(Mesh& m);
 int64_t find_leaf(const Mesh& m, int64_t x, int64_t y, int64_t z);
+void build_bsr_pattern(Mesh& m);
 
 // device stages (geom.cu)
 bool device_upload_geometry(Mesh& m, std::string& err);

@@ -543,4 +543,74 @@ void build_bc_flags(Mesh& m) {
     }
 }
 
+// Block pattern of the Jacobian assembled in 4 x 4 blocks, K = sum_e M_e^T k_e M_e (Algorithms 2
+// and 4): block (i, j) is present when nodes i and j both enter one element through M_e -- as
+// corners, or as parents of a hanging corner (Algorithm 3).  Every element counts, In elements
+// too (their blocks stay zero), so the pattern depends on the octree alone and holds whatever the
+// body does; every node is in some element, so every diagonal block is present.
+void build_bsr_pattern(Mesh& m) {
+    const int64_t ne = m.n_elem(), nn = m.n_nodes();
+    // the distinct nodes that element e reaches through M_e (at most 8 x 4)
+    auto nodes_of = [&](int64_t e, int32_t* out) {
+        int k = 0;
+        for (int c = 0; c < 8; ++c) {
+            const int32_t id = m.conn[8 * e + c];
+            if (id < nn) { out[k++] = id; continue; }
+            const int64_t h = id - nn;
+            for (int p = 0; p < m.hnp[h]; ++p) out[k++] = m.hpar[4 * h + p];
+        }
+        std::sort(out, out + k);
+        return (int)(std::unique(out, out + k) - out);
+    };
+    // node -> elements
+    std::vector<int64_t> off(nn + 1, 0);
+    for (int64_t e = 0; e < ne; ++e) {
+        int32_t buf[32];
+        const int k = nodes_of(e, buf);
+        for (int i = 0; i < k; ++i) ++off[buf[i] + 1];
+    }
+    for (int64_t i = 0; i < nn; ++i) off[i + 1] += off[i];
+    std::vector<int32_t> elems(off[nn]);
+    {
+        std::vector<int64_t> pos(off.begin(), off.end() - 1);
+        for (int64_t e = 0; e < ne; ++e) {
+            int32_t buf[32];
+            const int k = nodes_of(e, buf);
+            for (int i = 0; i < k; ++i) elems[pos[buf[i]]++] = (int32_t)e;
+        }
+    }
+    // row i = sorted union of the node sets of its elements; counted, then written
+    auto row = [&](int64_t i, std::vector<int32_t>& tmp) {
+        tmp.clear();
+        for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+            int32_t buf[32];
+            const int k = nodes_of(elems[q], buf);
+            tmp.insert(tmp.end(), buf, buf + k);
+        }
+        std::sort(tmp.begin(), tmp.end());
+        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    };
+    m.bsr_ptr.assign(nn + 1, 0);
+#pragma omp parallel
+    {
+        std::vector<int32_t> tmp;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t i = 0; i < nn; ++i) {
+            row(i, tmp);
+            m.bsr_ptr[i + 1] = (int64_t)tmp.size();
+        }
+    }
+    for (int64_t i = 0; i < nn; ++i) m.bsr_ptr[i + 1] += m.bsr_ptr[i];
+    m.bsr_idx.resize(m.bsr_ptr[nn]);
+#pragma omp parallel
+    {
+        std::vector<int32_t> tmp;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t i = 0; i < nn; ++i) {
+            row(i, tmp);
+            std::copy(tmp.begin(), tmp.end(), m.bsr_idx.begin() + m.bsr_ptr[i]);
+        }
+    }
+}
+
 }  // namespace imga

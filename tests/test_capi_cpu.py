@@ -83,6 +83,27 @@ def test_host_mesh_without_body(lib):
     _compare((0, 0, 0), (1, 1, 1), 2, [I.Region(I.REGION_SPHERE_BAND, 4, (0.3, 0.6, 0.5, 0.2, 0.05))], None)
 
 
+def test_bsr_pattern_matches_oracle_assembly(lib):
+    """The block pattern of the assembled Jacobian (imga_bsr_pattern, built on the host) equals the
+    pattern of the oracle's block assembly, index for index."""
+    from oracle import sparse as S
+    c = (0.5, 0.5, 0.5)
+    regs = [I.Region(I.REGION_SPHERE_BAND, 4, (*c, 0.2, 0.05))]
+    tri = I.icosphere(2, 0.2, c, 1e-4, 3)
+    m = api.Mesh((0, 0, 0), (1, 1, 1), 2, regs, tri, 3, device=-1)
+    o = OracleMesh((0, 0, 0), (1, 1, 1), 2, regs, tri, 3)
+    ptr, idx = m.bsr_pattern()
+    u, up, _ = I.state(o.n_nodes, 2)
+    A = S.assemble_bsr(o, I.Physics(), u, up)
+    assert m.n_hang > 0 and ptr[-1] == idx.size == A.indices.size
+    assert np.array_equal(ptr, A.indptr) and np.array_equal(idx, A.indices)
+    # a mesh without a body, and a repeated call (the pattern is kept)
+    m2 = api.Mesh((0, 0, 0), (2, 1, 1), 1, [I.Region(I.REGION_BOX, 3, (0.2, 0.1, 0.1, 0.5, 0.4, 0.3))], None, 3, device=-1)
+    p1, i1 = m2.bsr_pattern()
+    p2, i2 = m2.bsr_pattern()
+    assert np.array_equal(p1, p2) and np.array_equal(i1, i2) and np.all(np.diff(p1) >= 8)
+
+
 def test_invalid_arguments_are_rejected(lib):
     with pytest.raises(_lib.ImgaError) as e:
         api.Mesh((0, 0, 0), (1, 0.3, 1), 1, [], None, 3, device=-1)      # edge not a whole number of cells
@@ -109,6 +130,8 @@ def test_options_and_queries_reject_bad_arguments(lib):
     assert lib.imga_classify_counts(m.h, counts.ctypes.data_as(C.c_void_p), 0) == 1   # host-only: no counts
     assert lib.imga_classify_counts(None, counts.ctypes.data_as(C.c_void_p), 0) == 1
     assert lib.imga_classify_counts(m.h, None, 0) == 1
+    assert lib.imga_bsr_pattern(None, C.byref(C.c_int64()), None, None) == 1
+    assert lib.imga_bsr_pattern(m.h, None, None, None) == 1
     assert lib.imga_tuning(None, None, None) == 1
     shape = np.zeros(8, np.int32)
     assert lib.imga_tuning(m.h, shape.ctypes.data_as(C.c_void_p), None) == 0

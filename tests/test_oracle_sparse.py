@@ -109,16 +109,14 @@ def test_kron_helper_agrees_for_one_step_schemes():
 
 def test_block_pattern_is_element_adjacency(body_mesh):
     m, ph, u, up, up2, v, A = body_mesh
-    mk, _, _ = m.markers()
     want = set()
-    for el in np.where(mk != 1)[0]:
+    for el in range(m.n_elem):
         nodes = set()
         for c in range(8):
             idx = int(m.conn[el, c])
             nodes |= {idx} if idx < m.n_nodes else set(int(p) for p in m.hang_parents[idx - m.n_nodes, :m.hang_np[idx - m.n_nodes]])
         want |= {(i, j) for i in nodes for j in nodes}
-    mask = S.strong_mask(m)
-    want |= {(int(i), int(i)) for i in np.where(mask != 0)[0]}
+    assert all((i, i) in want for i in range(m.n_nodes))      # every node is in some element
     got = set()
     for i in range(m.n_nodes):
         cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
