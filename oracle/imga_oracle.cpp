@@ -20,6 +20,7 @@
 //   * Nitsche weak Dirichlet terms and tau_B, h_b ...... Eq. (weakbc) and the remark after it
 //   * skip In elements, Dirichlet on In-only nodes .... Algorithm 1, Fig. IBM caption
 //   * element matrix K_e = M_e^T k_e M_e, o2n ......... Algorithms 2 and 4
+//   * force on the body from the weak-boundary terms . Eq. (weakbc) tested with w = e_i
 // Where the paper is silent this oracle takes the reading stated at the function concerned (tau
 // definitions, in/out sign convention, ray directions, the widened box of B_T, h_b, surface rule,
 // CN treatment).
@@ -1080,6 +1081,47 @@ int64_t or_surface_points(void* s, double* out, int64_t cap) {
         o[6] = Q[i].w; o[7] = Q[i].hb; o[8] = Q[i].elem; o[9] = Q[i].tri;
     }
     return (int64_t)Q.size();
+}
+
+// Force of the fluid on the body: the surface terms of Eq. (weakbc) tested with w = e_i, i.e.
+// summed over every node's momentum rows (partition of unity: sum_c phi_c = 1, sum_c grad phi_c
+// = 0).  Per surface point that leaves w_q [ -(sigma(u_s, p) n)_i - [u.n < 0] rho (u.n)(u - g)_i
+// + tau_B (u - g)_i ] with n the fluid-outward normal; the conservative force of weak Dirichlet
+// conditions.  u_s is the state of the spatial terms (theta u + (1 - theta) u_prev).  F[3].
+void or_surface_force(void* s, const double* physv, const double* U, const double* Up, double* F) {
+    State* S = (State*)s;
+    Mesh& m = S->mesh;
+    Geom& g = S->geom;
+    if (!g.m) g.m = &m;
+    Phys ph;
+    ph.rho = physv[0]; ph.mu = physv[1]; ph.dt = physv[2]; ph.scheme = (int)physv[3];
+    ph.Cb = physv[4]; ph.CI = physv[5];
+    for (int k = 0; k < 3; ++k) { ph.g[k] = physv[6 + k]; ph.uinf[k] = physv[9 + k]; }
+    ph.drop_visc = (int)physv[12];
+    double c[3], theta;
+    time_coeffs(ph.scheme, c, &theta);
+    compute_surface(g);
+    for (int k = 0; k < 3; ++k) F[k] = 0.0;
+    for (const SurfQP& q : g.sqp) {
+        const int e = q.elem;
+        double ue[8][4], upe[8][4];
+        gather(m, e, U, 4, ue);
+        gather(m, e, Up, 4, upe);
+        double Us[8][3], P[8], r[8][4];
+        for (int a = 0; a < 8; ++a) {
+            for (int i = 0; i < 3; ++i) Us[a][i] = theta * ue[a][i] + (1.0 - theta) * upe[a][i];
+            P[a] = ue[a][3];
+            for (int k = 0; k < 4; ++k) r[a][k] = 0.0;
+        }
+        const double h = elem_h(m, e);
+        double xi[3];
+        for (int k = 0; k < 3; ++k) xi[k] = (q.x[k] - (m.lo[k] + (double)m.anc[e][k] * m.scale)) / (0.5 * h) - 1.0;
+        Basis B;
+        eval_basis(xi, h, B);
+        nitsche_point<double>(B, q, ph, Us, P, r);
+        for (int a = 0; a < 8; ++a)
+            for (int k = 0; k < 3; ++k) F[k] += r[a][k];
+    }
 }
 
 // test knob: the widening of B_T as a fraction of the element edge; it applies to the elements whose

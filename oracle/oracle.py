@@ -52,6 +52,7 @@ def lib():
         L.or_surface_points.restype = i64
         L.or_counters.argtypes = [vp, C.c_void_p]
         L.or_set_bt_pad.argtypes = [C.c_double]
+        L.or_surface_force.argtypes = [vp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_set_dirichlet.argtypes = [vp, C.c_void_p, C.c_void_p]
         L.or_residual_jvp.argtypes = [vp, C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p, i64, C.c_void_p, C.c_void_p]
         L.or_residual_jvp_complex_step.argtypes = L.or_residual_jvp.argtypes
@@ -200,6 +201,13 @@ class OracleMesh:
         lib().or_residual_jvp(self.h, _p(ph), _p(u), _p(up), _p(up2), _p(f), _p(v), _p(sel),
                               0 if sel is None else sel.size, _p(R), _p(J))
         return R, J
+
+    def surface_force(self, phys, u, u_prev):
+        """Force of the fluid on the body from the weak-boundary terms (float64 [3])."""
+        ph = np.array(phys.packed(), dtype=np.float64)
+        F = np.zeros(3)
+        lib().or_surface_force(self.h, _p(ph), _p(_f64(u)), _p(_f64(u_prev)), _p(F))
+        return F
 
     def jvp_complex_step(self, phys, u, u_prev, v, u_prev2=None, f=None):
         """J v as Im R(u + i eps v) / eps (eps = 1e-30): the complex step, independent of the dual numbers."""
