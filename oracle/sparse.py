@@ -161,3 +161,69 @@ def block_jacobi(A):
     D[singular] = np.eye(4)
     Dinv = np.linalg.inv(D)
     return lambda z: np.einsum("nij,nj->ni", Dinv, z.reshape(n, 4)).reshape(-1)
+
+
+# ------------------------------------------------------------------------------------------
+# Two-level preconditioner: piecewise constants on octants as the coarse space
+# ------------------------------------------------------------------------------------------
+def octant_aggregates(m, level):
+    """Aggregate of every node: the level-`level` octant that contains it (a node on an octant's
+    upper face or on the box's upper boundary goes to the octant below it in that direction).
+    Returns (agg [n_nodes] in 0 .. n_agg - 1, numbered in Morton order of the octants, n_agg)."""
+    shift = 20 - level
+    ijk = m.node_ijk.astype(np.int64)
+    top = (np.asarray(m.hiI, dtype=np.int64) - 1) >> shift
+    o = np.minimum(ijk >> shift, top[None, :])
+
+    def spread(v):
+        out = np.zeros_like(v)
+        for b in range(21):
+            out |= ((v >> b) & 1) << (3 * b)
+        return out
+
+    key = spread(o[:, 0]) | (spread(o[:, 1]) << 1) | (spread(o[:, 2]) << 2)
+    uniq, agg = np.unique(key, return_inverse=True)
+    return agg.astype(np.int64), int(uniq.size)
+
+
+def coarse_space(A, agg, n_agg):
+    """Prolongation P [4 n x 4 n_agg], one constant per aggregate and unknown, zero on the rows
+    that A holds fixed (identity rows) or that are empty (decoupled nodes), and the Galerkin
+    coarse matrix A_c = P^T A P (scipy sparse)."""
+    import scipy.sparse as sp
+    B = A.tocsr()
+    n4 = B.shape[0]
+    diag = B.diagonal()
+    nnz_row = np.diff(B.indptr)
+    absrow = np.asarray(np.abs(B).sum(axis=1)).ravel()
+    fixed = (nnz_row > 0) & (diag == 1.0) & (absrow == 1.0)
+    empty = absrow == 0.0
+    free = ~(fixed | empty)
+    rows = np.arange(n4)[free]
+    cols = 4 * agg[rows // 4] + rows % 4
+    P = sp.csr_matrix((np.ones(rows.size), (rows, cols)), shape=(n4, 4 * n_agg))
+    keep = np.asarray(P.sum(axis=0)).ravel() > 0                 # drop coarse unknowns with no free row
+    P = P[:, np.where(keep)[0]]
+    Ac = (P.T @ B @ P).tocsc()
+    return P.tocsr(), Ac
+
+
+def two_level(A, P, Ac, mode="multiplicative"):
+    """Preconditioner from block-Jacobi and the coarse correction Q r = P A_c^-1 P^T r:
+    additive, z = D^-1 r + Q r; multiplicative (coarse first), x = Q r, z = x + D^-1 (r - A x)."""
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(Ac)
+    Dinv = block_jacobi(A)
+    B = A.tocsr()
+
+    def Q(r):
+        return P @ lu.solve(P.T @ r)
+
+    if mode == "additive":
+        return lambda r: Dinv(r) + Q(r)
+
+    def mult(r):
+        x = Q(r)
+        return x + Dinv(r - B @ x)
+
+    return mult

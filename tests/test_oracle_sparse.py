@@ -168,3 +168,50 @@ def test_bicgstab_block_jacobi_solves_assembled_system(body_mesh):
     # the preconditioner helps: fewer iterations than without it
     _, its0, ok0, _ = S.bicgstab(lambda z: B @ z, b, rtol=1e-10, maxiter=4000)
     assert (not ok0) or its0 > its
+
+
+# ---------------------------------------------------------------------------------------
+# two-level preconditioner (piecewise constants on octants)
+# ---------------------------------------------------------------------------------------
+def test_octant_aggregates_contain_their_nodes(body_mesh):
+    m = body_mesh[0]
+    for lev in (1, 2, 3):
+        agg, na = S.octant_aggregates(m, lev)
+        assert agg.min() == 0 and agg.max() == na - 1 and np.unique(agg).size == na
+        s = 1 << (20 - lev)
+        ijk = m.node_ijk.astype(np.int64)
+        for a in range(na):
+            pts = ijk[agg == a]
+            lo = (pts.min(0) // s) * s
+            # every node of the aggregate lies in one closed octant of edge s
+            assert np.all(pts - lo[None, :] <= s)
+
+
+def test_coarse_correction_is_galerkin_orthogonal(body_mesh):
+    import scipy.sparse.linalg as spla
+    m, ph, u, up, up2, v, A = body_mesh
+    B = A.tocsr()
+    agg, na = S.octant_aggregates(m, 3)
+    P, Ac = S.coarse_space(A, agg, na)
+    r = I.normal(3, B.shape[0])
+    r[np.abs(B).sum(1).A.ravel() == 0] = 0.0
+    x = P @ spla.splu(Ac).solve(P.T @ r)
+    # the residual after the coarse correction has no component in the coarse space
+    assert np.abs(P.T @ (r - B @ x)).max() <= 1e-12 * np.abs(r).max()
+
+
+def test_two_level_beats_block_jacobi_and_is_exact_at_the_finest_level(body_mesh):
+    m, ph, u, up, up2, v, A = body_mesh
+    B = A.tocsr()
+    b = -m.residual(ph, u, up, up2).reshape(-1)
+    _, its_bj, ok, _ = S.bicgstab(lambda z: B @ z, b, rtol=1e-8, maxiter=3000, precond=S.block_jacobi(A))
+    assert ok
+    its = {}
+    for lev in (2, 3, 20):                          # level 20: every node its own aggregate
+        agg, na = S.octant_aggregates(m, lev)
+        P, Ac = S.coarse_space(A, agg, na)
+        x, its[lev], ok, _ = S.bicgstab(lambda z: B @ z, b, rtol=1e-8, maxiter=3000,
+                                        precond=S.two_level(A, P, Ac, "multiplicative"))
+        assert ok and np.linalg.norm(b - B @ x) <= 1e-8 * np.linalg.norm(b) * 1.0001
+    assert its[20] == 1                             # the coarse solve is exact on the free unknowns
+    assert its[3] <= its[2] < its_bj, (its, its_bj)
