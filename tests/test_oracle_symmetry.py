@@ -138,6 +138,9 @@ def test_residual_and_jvp_commute_with_rigid_motions(original, T):
             want = _move_nodal(T, XA)[keep]
             got = XB[img[keep]]
             assert np.abs(got - want).max() <= 1e-12 * np.abs(XA).max(), scheme
+        # the force on the body moves with it (a polar vector: reflected with the body)
+        FA, FB = A.surface_force(phA, u, up), B.surface_force(phB, moved(u), moved(up))
+        assert np.abs(FB - T.vec(FA)).max() <= 1e-12 * np.abs(FA).max(), scheme
 
 
 def test_symmetry_pin_detects_a_one_axis_slip(original):
