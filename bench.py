@@ -35,7 +35,7 @@ METRIC = "VMS Jv elements/s; Newton-GMRES step time to 1e-8, mixed/learned vs FP
 UNIT = "elements/s"
 L2_BYTES = 129 * 2 ** 20
 
-# Algorithmic FP32 work of one Out element in the forward-mode J v (counted in the design notes):
+# Algorithmic FP32 work of one Out element in the forward-mode J v, counted in the nodal form:
 # 8 Gauss points x (interpolation of values + tangents 896, pointwise VMS + tangent 390, weights 16)
 # + contraction of 8 nodes x 4 rows over 8 points (2048).
 FLOPS_JV_OUT_ELEMENT = 8 * (896 + 390 + 16) + 2048

@@ -5,9 +5,9 @@ Bars:
   surface points): bit-exact;
 * FP64 residual and J v: relative L2 error <= 1e-10 (and max-abs reported);
 * mixed precision (FP32 element arithmetic, FP64 gathers / accumulation / Nitsche penalty):
-  relative L2 error <= 2e-5 for R and J v, the bound derived in the design notes from FP32
-  rounding (~6e-8 per operation, a few hundred dependent operations per element, cancellation in
-  the momentum rows bounded by the ratio of term magnitudes to the row norm).
+  relative L2 error <= 2e-5 for R and J v, a bound from FP32 rounding (~6e-8 per operation, a few
+  hundred dependent operations per element, cancellation in the momentum rows bounded by the
+  ratio of term magnitudes to the row norm).
 """
 import numpy as np
 import pytest
