@@ -425,7 +425,8 @@ def run_ours(args):
 
     # Newton-GMRES step to 1e-8 (float64 residual), block-Jacobi, J v in FP64 vs mixed precision, on the
     # small-sphere problem (7,288 elements: the size the learned preconditioner is evaluated at).  On the
-    # 2M-element sphere LES nodal block-Jacobi does not bring GMRES(50) to 1e-8 (see the design notes).
+    # 2M-element sphere LES nodal block-Jacobi does not bring GMRES(50) to 1e-8: after the first Newton
+    # step every linear solve reaches its cap, held back by global pressure coupling.
     newton = {}
     if not args.no_newton:
         ws = I.small_sphere(0)
@@ -448,7 +449,7 @@ def run_ours(args):
                             "converged": bool(st["converged"]), "rel_residual": st["res_norm"][-1] / st["res_norm"][0],
                             "workload": "small_sphere (7,288 elements, Re 10, BE dt 0.01), block-Jacobi, GMRES(50)"}
         smesh.close()
-        # the sphere LES itself: block-Jacobi GMRES(50) does not converge it (see the design notes), so a
+        # the sphere LES itself: block-Jacobi GMRES(50) does not converge it, so a
         # capped run (3 Newton steps, 300 GMRES iterations each) compares mixed and float64 J v on the
         # same solver: residual history and time per Newton step
         mesh.use_graphs(True)
