@@ -39,7 +39,6 @@ L2_BYTES = 129 * 2 ** 20
 # 8 Gauss points x (interpolation of values + tangents 896, pointwise VMS + tangent 390, weights 16)
 # + contraction of 8 nodes x 4 rows over 8 points (2048).
 FLOPS_JV_OUT_ELEMENT = 8 * (896 + 390 + 16) + 2048
-FLOPS_R_OUT_ELEMENT = 8 * (448 + 130 + 16) + 2048
 FP64_TFLOPS_NOMINAL = 1.25
 
 
@@ -72,6 +71,22 @@ def kernel_rooflines(prof, steps, info, n_nodes, pk):
     # microseconds, bound by launch latency rather than by a pipe
     out["strong_rows"] = {"ms_per_step": prof["strong_rows"][0] / max(1, steps), "bound": "launch latency"}
     return out
+
+
+def wpart_costs(prof, steps, info):
+    """Eq. Wpart's costs on this GPU, from the per-kernel times of the timed J v steps: T_v per
+    volume Gauss point (the Out elements' 8 and the Intercepted elements' kept sub-cell points),
+    T_s per surface Gauss point (the Nitsche kernels), in picoseconds.  With n_Tgp = 8 for Q1,
+    W(e) = n_Vgp(e) / 8 + (T_s / T_v) n_Sgp(e) / 8."""
+    s = max(1, steps)
+    t_out, t_cut, t_sur = (prof[k][0] / s for k in ("out_elements", "cut_elements", "nitsche"))
+    n_out, n_cut, n_sur = 8 * info["n_out"], info["n_cut_points"], info["n_surface_points"]
+    if n_out + n_cut == 0 or n_sur == 0:
+        return None
+    tv = (t_out + t_cut) / (n_out + n_cut) * 1e9
+    ts = t_sur / n_sur * 1e9
+    return {"T_v_ps": tv, "T_s_ps": ts, "T_s_over_T_v": ts / tv,
+            "T_out_point_ps": t_out / max(1, n_out) * 1e9, "T_cut_point_ps": t_cut / max(1, n_cut) * 1e9}
 
 
 def interior_traffic():
@@ -312,7 +327,7 @@ def run_ours(args):
     k_ms, k_n = prof["out_elements"]
     k_avg = k_ms / max(k_n, 1)
     pk = peaks()
-    flops = (FLOPS_JV_OUT_ELEMENT if True else FLOPS_R_OUT_ELEMENT) * info["n_out"]
+    flops = FLOPS_JV_OUT_ELEMENT * info["n_out"]
     achieved = flops / (k_avg / 1e3) / 1e12
     roof = {"kernel": "vms_interior (Out elements, J v)", "bound": "alu", "achieved": achieved,
             "peak": pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None, "unit": "TFLOP/s",
@@ -322,6 +337,10 @@ def run_ours(args):
             "flops_per_element": FLOPS_JV_OUT_ELEMENT, "avg_launch_ms": k_avg}
     kern_share = {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()}
     kern_roof = kernel_rooflines(prof, args.steps, info, nn, pk)
+    try:
+        wpart = wpart_costs(prof, args.steps, info)
+    except Exception as ex:          # reported, never fatal
+        wpart = {"error": repr(ex)}
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region: every
     # step copies its four input vectors in and its result out; the copies of step i+1's inputs and
     # of step i's result overlap step i's J v (double-buffered device vectors, copy streams).
@@ -501,7 +520,7 @@ def run_ours(args):
                            if prec == 1 else "fp64",
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roof, "kernel_roofline": kern_roof, "fp64_roofline": extra_roof,
-                "kernel_time_share": kern_share,
+                "kernel_time_share": kern_share, "wpart": wpart,
                 "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])), "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
                 "extra_elements_per_s": extra,
