@@ -186,6 +186,14 @@ def octant_aggregates(m, level):
     return agg.astype(np.int64), int(uniq.size)
 
 
+def morton_aggregates(n_nodes, n_agg):
+    """Aggregates of equal size: nodes are numbered in Morton order of their coordinates, so
+    contiguous ranges of that order are spatially compact.  Node i goes to aggregate
+    floor(i n_agg / n_nodes).  Returns (agg, n_agg)."""
+    n_agg = max(1, min(int(n_agg), n_nodes))
+    return (np.arange(n_nodes, dtype=np.int64) * n_agg // n_nodes), n_agg
+
+
 def coarse_space(A, agg, n_agg):
     """Prolongation P [4 n x 4 n_agg], one constant per aggregate and unknown, zero on the rows
     that A holds fixed (identity rows) or that are empty (decoupled nodes), and the Galerkin

@@ -215,3 +215,17 @@ def test_two_level_beats_block_jacobi_and_is_exact_at_the_finest_level(body_mesh
         assert ok and np.linalg.norm(b - B @ x) <= 1e-8 * np.linalg.norm(b) * 1.0001
     assert its[20] == 1                             # the coarse solve is exact on the free unknowns
     assert its[3] <= its[2] < its_bj, (its, its_bj)
+
+
+def test_morton_range_aggregates(body_mesh):
+    m, ph, u, up, up2, v, A = body_mesh
+    agg, na = S.morton_aggregates(m.n_nodes, 512)
+    cnt = np.bincount(agg)
+    assert na == 512 and cnt.size == 512 and cnt.max() - cnt.min() <= 1
+    assert np.all(np.diff(agg) >= 0)                             # contiguous ranges
+    B = A.tocsr()
+    b = -m.residual(ph, u, up, up2).reshape(-1)
+    _, its_bj, _, _ = S.bicgstab(lambda z: B @ z, b, rtol=1e-8, maxiter=3000, precond=S.block_jacobi(A))
+    P, Ac = S.coarse_space(A, agg, na)
+    x, its, ok, _ = S.bicgstab(lambda z: B @ z, b, rtol=1e-8, maxiter=3000, precond=S.two_level(A, P, Ac))
+    assert ok and its < its_bj
