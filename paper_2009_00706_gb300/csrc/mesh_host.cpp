@@ -134,11 +134,10 @@ static void set_leaves(Mesh& m, const std::vector<Oct>& L) {
     m.key_lut_n = n;
 }
 
-bool build_octree(Mesh& m, std::string& err) {
-    // top-down refinement, depth first in Morton child order: leaves come out sorted
-    std::vector<Oct> leaves;
+// depth-first refinement of the subtree rooted at o, children in Morton order: leaves come out sorted
+static void refine_subtree(const Mesh& m, Oct root, std::vector<Oct>& leaves) {
     std::vector<Oct> stack;
-    stack.push_back({{0, 0, 0}, 0});
+    stack.push_back(root);
     while (!stack.empty()) {
         Oct o = stack.back();
         stack.pop_back();
@@ -150,6 +149,50 @@ bool build_octree(Mesh& m, std::string& err) {
             }
         } else {
             leaves.push_back(o);
+        }
+    }
+}
+
+bool build_octree(Mesh& m, std::string& err) {
+    // top-down refinement.  The octants of the first kSplitLevel levels are visited depth first;
+    // each octant of level kSplitLevel that still needs refining is a subtree refined on its own
+    // thread.  Concatenating leaves and subtrees in visiting order gives the same Morton-ordered
+    // list as one depth-first pass.
+    constexpr int kSplitLevel = 4;
+    std::vector<Oct> items;          // leaves above kSplitLevel, and the subtree roots at it
+    std::vector<char> is_root;
+    {
+        std::vector<Oct> stack;
+        stack.push_back({{0, 0, 0}, 0});
+        while (!stack.empty()) {
+            Oct o = stack.back();
+            stack.pop_back();
+            if (o.l < wanted_level(m, o.a, o.l)) {
+                if (o.l == kSplitLevel) { items.push_back(o); is_root.push_back(1); continue; }
+                uint32_t h = octsize(o.l) >> 1;
+                for (int c = 7; c >= 0; --c) {
+                    Oct ch{{o.a[0] + ((c & 1) ? h : 0), o.a[1] + ((c & 2) ? h : 0), o.a[2] + ((c & 4) ? h : 0)}, o.l + 1};
+                    if (inside_box(m, ch.a[0], ch.a[1], ch.a[2])) stack.push_back(ch);
+                }
+            } else {
+                items.push_back(o);
+                is_root.push_back(0);
+            }
+        }
+    }
+    std::vector<std::vector<Oct>> sub(items.size());
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < (int64_t)items.size(); ++i)
+        if (is_root[i]) refine_subtree(m, items[i], sub[i]);
+    std::vector<Oct> leaves;
+    {
+        size_t total = 0;
+        for (size_t i = 0; i < items.size(); ++i) total += is_root[i] ? sub[i].size() : 1;
+        leaves.reserve(total);
+        for (size_t i = 0; i < items.size(); ++i) {
+            if (is_root[i]) leaves.insert(leaves.end(), sub[i].begin(), sub[i].end());
+            else leaves.push_back(items[i]);
+            std::vector<Oct>().swap(sub[i]);
         }
     }
     set_leaves(m, leaves);
