@@ -358,3 +358,21 @@ def test_jvp_matches_complex_step(scheme):
     _, Jd = o.residual_jvp(ph, u, up, up2, v=v)
     Jc = o.jvp_complex_step(ph, u, up, v, up2)
     assert np.linalg.norm(Jc - Jd) <= 1e-12 * np.linalg.norm(Jd), np.linalg.norm(Jc - Jd) / np.linalg.norm(Jd)
+
+
+def test_steady_velocity_makes_the_time_schemes_agree(small_sphere_oracle):
+    """With the velocity unchanged between time levels (u = u_prev = u_prev2) the time derivative
+    vanishes and the spatial terms see the same velocity under BE, CN (theta = 1/2) and BDF2.
+    The pressure differs from p_prev: with the pressure taken at n+1 (reading of the CN scheme)
+    the three residuals coincide; an averaged or lagged pressure would break this.  (J v differs:
+    the schemes weight the tangent by theta and by their time coefficient.)"""
+    w, m = small_sphere_oracle
+    u, up, v = I.state(m.n_nodes, 8)
+    u[:, :3] = up[:, :3]
+    u[:, 3] = I.normal(21, m.n_nodes, 0.3)                      # p != p_prev = 0
+    out = {}
+    for scheme in (I.SCHEME_BE, I.SCHEME_CN, I.SCHEME_BDF2):
+        ph = I.Physics(rho=1.0, mu=0.02, dt=0.01, scheme=scheme)
+        out[scheme] = m.residual(ph, u, up, up)
+    for scheme in (I.SCHEME_CN, I.SCHEME_BDF2):
+        assert np.abs(out[scheme] - out[I.SCHEME_BE]).max() <= 1e-13 * np.abs(out[I.SCHEME_BE]).max(), scheme
