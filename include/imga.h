@@ -129,6 +129,13 @@ imga_status imga_mesh_problems(imga_mesh mesh, int* n_problems, int64_t* elem_of
  * for a null mesh or info. */
 imga_status imga_mesh_get_info(imga_mesh mesh, imga_mesh_info* info);
 
+/* Coordinates of the independent nodes, float64 [n_nodes][3] = lo + node_ijk * scale, in the node
+ * order of every node vector (Sec. "Octree based Mesh Generation": nodes of the octree mesh).  For
+ * a mesh built on a device, xyz is a device pointer of that device, written by a copy on `stream`
+ * that the call waits for; for a mesh built host-only (device < 0), xyz is a host pointer and
+ * stream is ignored.  Errors: IMGA_ERR_INVALID_ARG (null mesh or xyz), IMGA_ERR_OOM, IMGA_ERR_CUDA. */
+imga_status imga_node_coords(imga_mesh mesh, double* xyz, void* stream);
+
 /* Host copies of the mesh tables (every pointer may be NULL to skip it).  anchors [n_elem][3]
  * integer anchors; levels [n_elem]; conn [n_elem][8] corner -> node index, or n_nodes + h for
  * hanging node h (corner c has bits (c&1, c>>1&1, c>>2&1) along x, y, z); node_ijk [n_nodes][3];

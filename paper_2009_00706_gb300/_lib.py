@@ -135,6 +135,7 @@ SIGNATURES = {
     "imga_classify": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "imga_classify_counts": (C.c_int, [_vp, _vp, _int]),
     "imga_bsr_pattern": (C.c_int, [_vp, C.POINTER(C.c_int64), _vp, _vp]),
+    "imga_node_coords": (C.c_int, [_vp, _vp, _vp]),
     "imga_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp]),
     "imga_jvp": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),
     "imga_jvp_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(Physics), _int, _vp, _vp, _vp]),

@@ -273,6 +273,19 @@ class Mesh:
         of each precision and kind."""
         check(_lib.load().imga_set_option(self.h, 2, 1 if on else 0))
 
+    def node_coords(self, out=None, stream=None):
+        """float64 [n_nodes, 3] node coordinates: a tensor on the mesh's device (or `out`), or a
+        numpy array for a host-only mesh."""
+        if self.device < 0:
+            xyz = np.zeros((self.n_nodes, 3))
+            check(_lib.load().imga_node_coords(self.h, xyz.ctypes.data_as(C.c_void_p), None))
+            return xyz
+        import torch
+        if out is None:
+            out = torch.empty((self.n_nodes, 3), dtype=torch.float64, device=torch.device("cuda", self.device))
+        check(_lib.load().imga_node_coords(self.h, _ptr(out), _stream(stream)))
+        return out
+
     def bsr_pattern(self):
         """(indptr int64 [n_nodes + 1], indices int32 [n_blocks]) of the Jacobian's 4 x 4 block
         pattern (host arrays)."""

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "imga_internal.h"
 
@@ -249,6 +250,30 @@ imga_status imga_classify(imga_mesh h, const double* pts, int64_t n, uint8_t* fl
     if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
     if (h->m.batched) return fail(IMGA_ERR_INVALID_ARG, "classify a point against one of the problems' own meshes");
     if (imga::device_classify(h->m, pts, n, flags, stream)) return cuda_status("classify");
+    return IMGA_OK;
+}
+
+imga_status imga_node_coords(imga_mesh h, double* xyz, void* stream) {
+    if (!h || !xyz) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    const imga::Mesh& m = h->m;
+    const int64_t nn = m.n_nodes();
+    std::vector<double> c;
+    try {
+        c.resize(3 * nn);
+    } catch (const std::bad_alloc&) {
+        return fail(IMGA_ERR_OOM, "node coordinates: host allocation failed");
+    }
+    for (int64_t i = 0; i < nn; ++i)
+        for (int k = 0; k < 3; ++k) c[3 * i + k] = m.lo[k] + (double)m.nijk[3 * i + k] * m.scale;
+    if (m.host_only) {
+        std::copy(c.begin(), c.end(), xyz);
+        return IMGA_OK;
+    }
+    if (nn == 0) return IMGA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(xyz, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);     // the host buffer must outlive the copy
+    if (e != cudaSuccess) return fail(IMGA_ERR_CUDA, std::string("node coordinates: ") + cudaGetErrorString(e));
     return IMGA_OK;
 }
 

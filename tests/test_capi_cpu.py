@@ -104,6 +104,16 @@ def test_bsr_pattern_matches_oracle_assembly(lib):
     assert np.array_equal(p1, p2) and np.array_equal(i1, i2) and np.all(np.diff(p1) >= 8)
 
 
+def test_node_coords_match_oracle(lib):
+    w = I.small_sphere()
+    m = api.Mesh(w.lo, w.hi, w.base_level, w.regions, w.triangles(), w.lmax, device=-1)
+    o = OracleMesh(w.lo, w.hi, w.base_level, w.regions, w.triangles(), w.lmax)
+    xyz = m.node_coords()
+    assert xyz.shape == (o.n_nodes, 3) and np.array_equal(xyz, o.node_xyz)
+    assert lib.imga_node_coords(None, xyz.ctypes.data_as(C.c_void_p), None) == 1
+    assert lib.imga_node_coords(m.h, None, None) == 1
+
+
 def test_invalid_arguments_are_rejected(lib):
     with pytest.raises(_lib.ImgaError) as e:
         api.Mesh((0, 0, 0), (1, 0.3, 1), 1, [], None, 3, device=-1)      # edge not a whole number of cells
