@@ -202,6 +202,23 @@ class OracleMesh:
                               0 if sel is None else sel.size, _p(R), _p(J))
         return R, J
 
+    def wpart_weights(self, ts_over_tv):
+        """Eq. (Wpart), the cost of element e relative to an Out element:
+        W(e) = n_Vgp(e) / n_Tgp + (T_s / T_v) n_Sgp(e) / n_Tgp, with n_Tgp = 8 for trilinear
+        hexahedra.  n_Vgp is the number of volume Gauss points evaluated (8 for Out elements, the
+        kept sub-cell points for Intercepted ones, none for In ones) and n_Sgp the number of its
+        surface points."""
+        mk, _, _ = self.markers()
+        W = np.zeros(self.n_elem)
+        W[mk == 0] = 1.0
+        for e in np.where(mk == 2)[0]:
+            W[e] = self.cut_points(int(e)).shape[0] / 8.0
+        sq = self.surface_points()
+        if sq.shape[0]:
+            ns = np.bincount(sq[:, 8].astype(np.int64), minlength=self.n_elem)
+            W += ts_over_tv * ns / 8.0
+        return W
+
     def surface_force(self, phys, u, u_prev):
         """Force of the fluid on the body from the weak-boundary terms (float64 [3])."""
         ph = np.array(phys.packed(), dtype=np.float64)
