@@ -1,8 +1,7 @@
 """Matrix-based linear-solver path of the method, for the oracle: the global Jacobian assembled in
 4 x 4 blocks and BiCGStab.
 
-TEST INFRASTRUCTURE ONLY: the tests and the CPU legs of the benchmark use this module; the
-product never imports it.
+TEST INFRASTRUCTURE ONLY: the tests use this module; the product never imports it.
 
 * Assembly (Algorithms 2 and 4): K = sum_e M_e^T k_e M_e, where k_e is the 32 x 32 element
   Jacobian (8 corners x 4 unknowns, row a*4+i, column b*4+k) and M_e the corner-to-node operator
