@@ -11,6 +11,10 @@ TEST INFRASTRUCTURE ONLY: the tests use this module; the product never imports i
   blocks, block columns sorted within each block row.
 * BiCGStab (appendix "Details of solver selection": the linear systems of the Newton steps are
   solved by BiCGStab), in the form of van der Vorst (1992) with right preconditioning, float64.
+* Preconditioners: nodal block-Jacobi, and a two-level one that adds a coarse space of piecewise
+  constants on aggregates of nodes (octants, or equal ranges of the Morton node order), with the
+  Galerkin coarse matrix P^T A P.  The paper preconditions with additive Schwarz; its conclusion
+  asks for preconditioners suited to the method.
 """
 import numpy as np
 import scipy.sparse as sp
