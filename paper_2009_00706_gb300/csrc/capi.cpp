@@ -50,11 +50,8 @@ bool physics_ok(const imga_physics* p) {
 
 }  // namespace
 
-extern "C" {
-
-const char* imga_last_error(void) { return imga::g_last_error.c_str(); }
-
-imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_params* P, int device, imga_mesh* out) {
+static imga_status build_mesh_impl(const double* tri, int64_t n_tri, const imga_mesh_params* P, int device,
+                                   imga_mesh* out, imga_mesh_s*& hold) {
     if (!out || !P) return fail(IMGA_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (n_tri < 0 || (n_tri > 0 && !tri)) return fail(IMGA_ERR_INVALID_ARG, "bad triangle array");
@@ -69,6 +66,7 @@ imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_pa
     if (!host_only && cudaSetDevice(device) != cudaSuccess) return cuda_status("cudaSetDevice");
     imga_mesh_s* h = new (std::nothrow) imga_mesh_s();
     if (!h) return fail(IMGA_ERR_OOM, "host allocation failed");
+    hold = h;
     imga::Mesh& m = h->m;
     m.device = device;
     if (!host_only) cudaDeviceGetAttribute(&m.n_sm, cudaDevAttrMultiProcessorCount, device);
@@ -76,7 +74,7 @@ imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_pa
     for (int k = 0; k < 3; ++k) {
         m.lo[k] = P->lo[k];
         m.hi[k] = P->hi[k];
-        if (!(P->hi[k] > P->lo[k])) { delete h; return fail(IMGA_ERR_INVALID_ARG, "empty box"); }
+        if (!(P->hi[k] > P->lo[k])) { delete h; hold = nullptr; return fail(IMGA_ERR_INVALID_ARG, "empty box"); }
         L = std::max(L, P->hi[k] - P->lo[k]);
     }
     m.scale = L / (double)(1u << imga::kMaxDepth);
@@ -88,16 +86,16 @@ imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_pa
         m.hiI[k] = (int64_t)std::llround(f);
         int64_t cell = 1ll << (imga::kMaxDepth - P->base_level);
         if (std::fabs(f - (double)m.hiI[k]) > 1e-6 || m.hiI[k] % cell != 0) {
-            delete h;
+            delete h; hold = nullptr;
             return fail(IMGA_ERR_INVALID_ARG, "box edge " + std::to_string(k) + " is not a whole number of base-level cells");
         }
     }
     std::string err;
     auto t0 = std::chrono::steady_clock::now();
-    if (!imga::build_octree(m, err) || !imga::build_nodes(m, err)) { delete h; return fail(IMGA_ERR_INVALID_ARG, err); }
+    if (!imga::build_octree(m, err) || !imga::build_nodes(m, err)) { delete h; hold = nullptr; return fail(IMGA_ERR_INVALID_ARG, err); }
     m.setup_ms[0] = ms_since(t0);
     t0 = std::chrono::steady_clock::now();
-    if (!imga::build_triangles(m, tri, n_tri, err)) { delete h; return fail(IMGA_ERR_SURFACE, err); }
+    if (!imga::build_triangles(m, tri, n_tri, err)) { delete h; hold = nullptr; return fail(IMGA_ERR_SURFACE, err); }
     imga::build_background(m);
     imga::build_ray_grid(m);
     m.setup_ms[1] = ms_since(t0);
@@ -109,27 +107,28 @@ imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_pa
     t0 = std::chrono::steady_clock::now();
     if (!imga::device_upload_geometry(m, err) || !imga::device_markers(m, err) || !imga::device_cut_quadrature(m, err)) {
         imga::device_free(m);
-        delete h;
+        delete h; hold = nullptr;
         return fail(IMGA_ERR_CUDA, err);
     }
     m.setup_ms[2] = ms_since(t0);
     t0 = std::chrono::steady_clock::now();
     imga::build_surface_points(m);
     imga::build_bc_flags(m);
-    if (!imga::device_upload_quadrature(m, err)) { imga::device_free(m); delete h; return fail(IMGA_ERR_CUDA, err); }
-    if (cudaDeviceSynchronize() != cudaSuccess) { imga::device_free(m); delete h; return cuda_status("build"); }
+    if (!imga::device_upload_quadrature(m, err)) { imga::device_free(m); delete h; hold = nullptr; return fail(IMGA_ERR_CUDA, err); }
+    if (cudaDeviceSynchronize() != cudaSuccess) { imga::device_free(m); delete h; hold = nullptr; return cuda_status("build"); }
     m.setup_ms[3] = ms_since(t0);
     *out = h;
     return IMGA_OK;
 }
 
-imga_status imga_build_mesh_batch(const imga_problem* probs, int n, int device, imga_mesh* out) {
+static imga_status build_batch_impl(const imga_problem* probs, int n, int device, imga_mesh* out,
+                                   std::vector<imga_mesh>& parts, imga_mesh_s*& hold) {
     if (!out || !probs || n < 1 || n > 65535) return fail(IMGA_ERR_INVALID_ARG, "bad problem list");
     *out = nullptr;
     if (device < 0) return fail(IMGA_ERR_INVALID_ARG, "batched meshes need a device");
-    std::vector<imga_mesh> parts(n, nullptr);
+    parts.assign(n, nullptr);
     std::vector<double> mu(n);
-    auto cleanup = [&]() { for (imga_mesh q : parts) imga_destroy_mesh(q); };
+    auto cleanup = [&]() { for (imga_mesh& q : parts) { imga_destroy_mesh(q); q = nullptr; } };
     for (int p = 0; p < n; ++p) {
         if (!(probs[p].mu >= 0.0)) { cleanup(); return fail(IMGA_ERR_INVALID_ARG, "bad problem viscosity"); }
         imga_status st = imga_build_mesh(probs[p].tri_xyz_host, probs[p].n_tri, &probs[p].params, device, &parts[p]);
@@ -138,6 +137,7 @@ imga_status imga_build_mesh_batch(const imga_problem* probs, int n, int device, 
     }
     imga_mesh_s* h = new (std::nothrow) imga_mesh_s();
     if (!h) { cleanup(); return fail(IMGA_ERR_OOM, "host allocation failed"); }
+    hold = h;
     imga::Mesh& m = h->m;
     m.device = device;
     m.batched = true;
@@ -149,9 +149,46 @@ imga_status imga_build_mesh_batch(const imga_problem* probs, int n, int device, 
     for (int k = 0; k < 4; ++k)
         for (imga_mesh q : parts) m.setup_ms[k] += q->m.setup_ms[k];
     cleanup();
-    if (!ok || cudaDeviceSynchronize() != cudaSuccess) { imga::device_free(m); delete h; return fail(IMGA_ERR_CUDA, err.empty() ? "batch upload" : err); }
+    if (!ok || cudaDeviceSynchronize() != cudaSuccess) { imga::device_free(m); delete h; hold = nullptr; return fail(IMGA_ERR_CUDA, err.empty() ? "batch upload" : err); }
     *out = h;
     return IMGA_OK;
+}
+
+// An exception (a host allocation failing inside the builders) must not cross the C ABI: free
+// what was built so far and report it.
+static imga_status abandon(imga_mesh_s*& hold, imga_mesh* out, const std::exception& e) {
+    if (hold) {
+        if (hold->m.device >= 0) imga::device_free(hold->m);
+        delete hold;
+        hold = nullptr;
+    }
+    if (out) *out = nullptr;
+    if (dynamic_cast<const std::bad_alloc*>(&e)) return fail(IMGA_ERR_OOM, "host allocation failed while building the mesh");
+    return fail(IMGA_ERR_INVALID_ARG, std::string("mesh build failed: ") + e.what());
+}
+
+extern "C" {
+
+const char* imga_last_error(void) { return imga::g_last_error.c_str(); }
+
+imga_status imga_build_mesh(const double* tri, int64_t n_tri, const imga_mesh_params* P, int device, imga_mesh* out) {
+    imga_mesh_s* hold = nullptr;
+    try {
+        return build_mesh_impl(tri, n_tri, P, device, out, hold);
+    } catch (const std::exception& e) {
+        return abandon(hold, out, e);
+    }
+}
+
+imga_status imga_build_mesh_batch(const imga_problem* probs, int n, int device, imga_mesh* out) {
+    std::vector<imga_mesh> parts;
+    imga_mesh_s* hold = nullptr;
+    try {
+        return build_batch_impl(probs, n, device, out, parts, hold);
+    } catch (const std::exception& e) {
+        for (imga_mesh& q : parts) { imga_destroy_mesh(q); q = nullptr; }
+        return abandon(hold, out, e);
+    }
 }
 
 imga_status imga_mesh_problems(imga_mesh h, int* n_problems, int64_t* elem_off, int64_t* node_off) {
