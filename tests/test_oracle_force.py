@@ -59,3 +59,18 @@ def test_force_equals_summed_momentum_rows_without_strong_rows():
     assert np.abs(R[:, :3].sum(axis=0) - F).max() <= 1e-12 * np.abs(F).max()
     if m.surface_points().shape[0] == 3 * tri.shape[0]:
         assert np.abs(F + cp * _volume(tri)).max() <= 1e-12 * np.abs(F).max()
+
+
+def test_crank_nicolson_force_sees_the_midpoint_velocity(small_sphere_oracle):
+    """Under CN the surface terms are evaluated at u_s = (u + u_prev) / 2 with the pressure at
+    n+1: the CN force at (u, u_prev) equals the BE force at that state."""
+    w, m = small_sphere_oracle
+    u, up, _ = I.state(m.n_nodes, 12)
+    u[:, 3] = I.normal(23, m.n_nodes, 0.2)
+    up[:, :3] += I.normal(24, m.n_nodes * 3, 0.05).reshape(-1, 3)
+    mid = u.copy()
+    mid[:, :3] = 0.5 * (u[:, :3] + up[:, :3])
+    g = (0.1, 0.0, -0.05)
+    F_cn = m.surface_force(I.Physics(scheme=I.SCHEME_CN, g=g), u, up)
+    F_be = m.surface_force(I.Physics(scheme=I.SCHEME_BE, g=g), mid, mid)
+    assert np.abs(F_cn - F_be).max() <= 1e-13 * np.abs(F_be).max()
