@@ -7,7 +7,9 @@ What is fixed independently of the oracle:
   (the surface rule integrates p n exactly on flat triangles);
 * a body moving with a uniform flow feels no force;
 * with no strong rows, every node's momentum rows summed equal F in the hydrostatic state: the
-  volume terms cancel by partition of unity (sum_a phi_a = 1, sum_a grad phi_a = 0).
+  volume terms cancel by partition of unity (sum_a phi_a = 1, sum_a grad phi_a = 0);
+* under Crank-Nicolson the force is the backward-Euler force at the midpoint velocity, with the
+  pressure at n+1.
 """
 import numpy as np
 import pytest
