@@ -275,7 +275,27 @@ bool build_nodes(Mesh& m, std::string& err) {
         for (int c = 0; c < 8; ++c)
             ck[8 * e + c] = morton3(a[0] + ((c & 1) ? s : 0), a[1] + ((c & 2) ? s : 0), a[2] + ((c & 4) ? s : 0));
     }
-    std::vector<uint64_t> uk(ck);
+    // unique corner codes: neighbouring leaves in Morton order share most corners, so each chunk
+    // of leaves is sorted and deduplicated on its own first (in cache, in parallel); the global
+    // sort then sees a few keys per node instead of up to eight
+    std::vector<uint64_t> uk;
+    {
+        constexpr int64_t kChunk = 1 << 14;                         // leaves per chunk
+        const int64_t nchunk = (ne + kChunk - 1) / kChunk;
+        std::vector<std::vector<uint64_t>> part(nchunk);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t c = 0; c < nchunk; ++c) {
+            const int64_t a = 8 * c * kChunk, b = std::min<int64_t>(8 * ne, 8 * (c + 1) * kChunk);
+            std::vector<uint64_t>& v = part[c];
+            v.assign(ck.begin() + a, ck.begin() + b);
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+        }
+        size_t total = 0;
+        for (const auto& v : part) total += v.size();
+        uk.reserve(total);
+        for (auto& v : part) { uk.insert(uk.end(), v.begin(), v.end()); std::vector<uint64_t>().swap(v); }
+    }
 #ifdef _OPENMP
     __gnu_parallel::sort(uk.begin(), uk.end());
 #else
