@@ -221,10 +221,18 @@ bool build_octree(Mesh& m, std::string& err) {
             if (l < 2) continue;
             int64_t s = octsize(l);
             const uint32_t* a = &m.anc[3 * e];
+            // the grandparent octant (edge 4s) has been refined, so every leaf inside it has level
+            // >= l - 1: only probes that leave it can find a leaf two levels coarser
+            int64_t g0[3];
+            for (int k = 0; k < 3; ++k) g0[k] = (int64_t)a[k] & ~(4 * s - 1);
             for (int d = 0; d < 26; ++d) {
                 int64_t q[3];
-                for (int k = 0; k < 3; ++k)
+                bool out = false;
+                for (int k = 0; k < 3; ++k) {
                     q[k] = nb[d][k] < 0 ? (int64_t)a[k] - 1 : nb[d][k] > 0 ? (int64_t)a[k] + s : (int64_t)a[k];
+                    out = out || q[k] < g0[k] || q[k] >= g0[k] + 4 * s;
+                }
+                if (!out) continue;
                 int64_t o = find_leaf(m, q[0], q[1], q[2]);
                 if (o >= 0 && m.lev[o] < l - 1) {
                     __atomic_store_n(&split[o], (uint8_t)1, __ATOMIC_RELAXED);
