@@ -238,3 +238,79 @@ def two_level(A, P, Ac, mode="multiplicative"):
         return x + Dinv(r - B @ x)
 
     return mult
+
+
+# ------------------------------------------------------------------------------------------
+# Multilevel preconditioner: the two-level construction applied recursively
+# ------------------------------------------------------------------------------------------
+def _block_diag_inverse(A, n):
+    """Inverses of the 4 x 4 diagonal blocks of A (n blocks); a singular block becomes the identity
+    (the reading of block_jacobi)."""
+    coo = A.tocoo()
+    sel = (coo.row // 4) == (coo.col // 4)
+    D = np.zeros((n, 4, 4))
+    np.add.at(D, (coo.row[sel] // 4, coo.row[sel] % 4, coo.col[sel] % 4), coo.data[sel])
+    scale = np.abs(D).max(axis=(1, 2))
+    smin = np.linalg.svd(D, compute_uv=False)[:, -1]
+    D[~(smin > 1e-14 * scale)] = np.eye(4)
+    return np.linalg.inv(D)
+
+
+def hierarchy(A, agg_size=6, coarse_max=200):
+    """Levels of the multilevel preconditioner.  Level 0 is A (4 x 4 blocks, one per node, nodes
+    in Morton order).  Each coarser level aggregates agg_size consecutive unknown-blocks of the
+    level above (Morton ranges, so aggregates stay compact), with a piecewise-constant
+    prolongation per unknown that leaves out the fixed and empty rows of level 0 and the dead
+    rows of coarser levels; A_{l+1} = P_l^T A_l P_l, and a coarse unknown that no free row
+    reaches gets an identity row.  The last level (at most coarse_max blocks) is factorised."""
+    import scipy.sparse.linalg as spla
+    A = A.tocsr()
+    n = A.shape[0] // 4
+    diag = A.diagonal()
+    absrow = np.asarray(np.abs(A).sum(axis=1)).ravel()
+    free = ~(((diag == 1.0) & (absrow == 1.0)) | (absrow == 0.0))
+    levels = []
+    while True:
+        Dinv = _block_diag_inverse(A, n)
+        if n <= coarse_max:
+            Ad = A.toarray()
+            dead = np.abs(Ad).sum(axis=1) == 0
+            Ad[dead, dead] = 1.0
+            levels.append({"A": A, "Dinv": Dinv, "n": n, "lu": spla.splu(sp.csc_matrix(Ad))})
+            return levels
+        na = (n + agg_size - 1) // agg_size
+        agg = np.minimum(np.arange(n) // agg_size, na - 1)
+        rows = np.where(free)[0]
+        P = sp.csr_matrix((np.ones(rows.size), (rows, 4 * agg[rows // 4] + rows % 4)), shape=(4 * n, 4 * na))
+        Ac = (P.T @ A @ P).tocsr()
+        dead = np.asarray(np.abs(Ac).sum(axis=1)).ravel() == 0
+        levels.append({"A": A, "Dinv": Dinv, "n": n, "P": P})
+        A, n, free = (Ac + sp.diags(dead.astype(float))).tocsr(), na, ~dead
+
+
+def vcycle(levels, r, nu=1, omega=0.5, level=0):
+    """One V-cycle applied to r: nu damped block-Jacobi sweeps (weight omega), the coarse
+    correction of the level below, nu more sweeps; the last level is solved exactly.  Damping
+    matters: the Jacobian is an indefinite saddle-point matrix, on which undamped block-Jacobi
+    is not a convergent smoother."""
+    L = levels[level]
+    if "lu" in L:
+        return L["lu"].solve(r)
+    A, Dinv, n = L["A"], L["Dinv"], L["n"]
+
+    def smooth(z):
+        return omega * np.einsum("nij,nj->ni", Dinv, z.reshape(n, 4)).reshape(-1)
+
+    x = np.zeros_like(r)
+    for _ in range(nu):
+        x = x + smooth(r - A @ x)
+    x = x + L["P"] @ vcycle(levels, L["P"].T @ (r - A @ x), nu, omega, level + 1)
+    for _ in range(nu):
+        x = x + smooth(r - A @ x)
+    return x
+
+
+def multilevel(A, agg_size=6, coarse_max=200, nu=1, omega=0.5):
+    """Preconditioner r -> vcycle(r) over hierarchy(A)."""
+    levels = hierarchy(A, agg_size, coarse_max)
+    return lambda r: vcycle(levels, r, nu, omega)

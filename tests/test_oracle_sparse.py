@@ -229,3 +229,50 @@ def test_morton_range_aggregates(body_mesh):
     P, Ac = S.coarse_space(A, agg, na)
     x, its, ok, _ = S.bicgstab(lambda z: B @ z, b, rtol=1e-8, maxiter=3000, precond=S.two_level(A, P, Ac))
     assert ok and its < its_bj
+
+
+# ---------------------------------------------------------------------------------------
+# multilevel preconditioner
+# ---------------------------------------------------------------------------------------
+def _consistent_rhs(B, seed):
+    b = I.normal(seed, B.shape[0])
+    b[np.abs(B).sum(1).A.ravel() == 0] = 0.0
+    return b
+
+
+def test_single_level_hierarchy_is_an_exact_solve(body_mesh):
+    from oracle.krylov import gmres
+    m, ph, u, up, up2, v, A = body_mesh
+    B = A.tocsr()
+    lv = S.hierarchy(A, coarse_max=10 ** 6)
+    assert len(lv) == 1
+    b = _consistent_rhs(B, 41)
+    x, k, _ = gmres(lambda z: B @ z, b, m=20, rtol=1e-10, maxiter=20, precond=lambda r: S.vcycle(lv, r))
+    assert k == 1 and np.linalg.norm(b - B @ x) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_vcycle_is_linear_and_its_coarse_correction_galerkin_orthogonal(body_mesh):
+    m, ph, u, up, up2, v, A = body_mesh
+    B = A.tocsr()
+    lv = S.hierarchy(A, agg_size=6, coarse_max=300)
+    assert len(lv) == 2                                          # 1,147 -> 192 blocks
+    r1, r2 = _consistent_rhs(B, 42), _consistent_rhs(B, 43)
+    V = lambda r: S.vcycle(lv, r, nu=1, omega=0.5)
+    lhs, rhs = V(2.0 * r1 - 0.5 * r2), 2.0 * V(r1) - 0.5 * V(r2)
+    assert np.linalg.norm(lhs - rhs) <= 1e-10 * np.linalg.norm(rhs)
+    # with no smoothing the V-cycle is the coarse correction P A_c^-1 P^T r
+    P = lv[0]["P"]
+    x = S.vcycle(lv, r1, nu=0)
+    assert np.abs(P.T @ (r1 - B @ x)).max() <= 1e-10 * np.abs(r1).max()
+
+
+def test_multilevel_needs_fewer_iterations_than_block_jacobi(body_mesh):
+    from oracle.krylov import gmres
+    m, ph, u, up, up2, v, A = body_mesh
+    B = A.tocsr()
+    b = -m.residual(ph, u, up, up2).reshape(-1)
+    _, k_bj, _ = gmres(lambda z: B @ z, b, m=50, rtol=1e-8, maxiter=3000, precond=S.block_jacobi(A))
+    x, k_ml, _ = gmres(lambda z: B @ z, b, m=50, rtol=1e-8, maxiter=3000,
+                       precond=S.multilevel(A, agg_size=6, coarse_max=50))
+    assert np.linalg.norm(b - B @ x) <= 1e-8 * np.linalg.norm(b) * 1.0001
+    assert k_ml < k_bj, (k_ml, k_bj)
