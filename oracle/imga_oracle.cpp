@@ -30,8 +30,11 @@
 // uniform flow, central differences of R for J v, the complex step Im R(u + i eps v) / eps against
 // the dual-number J v, second-order MMS convergence, the total volume of the quadrature, the printed
 // Gauss abscissae of Fig. GP, exact dyadic cuts, brute-force ray parity (also with faces on grid
-// planes), the analytic sphere, rigid-motion equivariance of R and J v, and divergence-theorem
-// and barycentric-moment identities of the surface rule.
+// planes), the analytic sphere, rigid-motion equivariance of R and J v, divergence-theorem
+// and barycentric-moment identities of the surface rule, and for the Nitsche terms: zero residual
+// of an exact linear flow past an immersed body (consistency term), symmetric / skew element
+// Jacobians at rest (adjoint term), and second-order convergence of manufactured solutions with
+// an immersed box and an immersed sphere (g = u_exact per surface point).
 // Parity unpinned (readings of silent passages, checked only for consistency): the constants
 // of tau_M / tau_C / tau-bar (C_I = 36, the metric form), the Crank-Nicolson placement of the
 // pressure, the h_b definition, the choice of degree-2 surface rule, and the in/out tolerance.
@@ -387,7 +390,8 @@ struct Tri {
     double area;
 };
 
-struct SurfQP { double x[3], n[3], w, hb; int elem, tri; };
+// gv: velocity prescribed at this point (has_g), else the uniform body velocity of Phys
+struct SurfQP { double x[3], n[3], w, hb; int elem, tri; double gv[3]; bool has_g; };
 
 struct Geom {
     Mesh* m;
@@ -624,6 +628,8 @@ void compute_surface(Geom& g) {
             sq.hb = hb;
             sq.elem = e;
             sq.tri = (int)t;
+            sq.gv[0] = sq.gv[1] = sq.gv[2] = 0.0;
+            sq.has_g = false;
             g.sqp.push_back(sq);
         }
     }
@@ -779,8 +785,9 @@ void nitsche_point(const Basis& B, const SurfQP& q, const Phys& ph, const T Us[8
         }
     }
     const double* n = q.n;
+    const double* gq = q.has_g ? q.gv : ph.g;   // g of Eq. (weakbc) at this point
     T d[3];
-    for (int i = 0; i < 3; ++i) d[i] = us[i] - ph.g[i];
+    for (int i = 0; i < 3; ++i) d[i] = us[i] - gq[i];
     T un = us[0] * n[0] + us[1] * n[1] + us[2] * n[2];
     T dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
     bool inflow = val(un) < 0.0;
@@ -1122,6 +1129,23 @@ void or_surface_force(void* s, const double* physv, const double* U, const doubl
         for (int a = 0; a < 8; ++a)
             for (int k = 0; k < 3; ++k) F[k] += r[a][k];
     }
+}
+
+// Velocity g of Eq. (weakbc) per surface point, [n][3] in the order of or_surface_points (a body
+// that deforms or rotates, or an exact solution prescribed on the surface); g = NULL or n = 0
+// returns to the uniform body velocity of the physics parameters.  Returns -1 when n is not the
+// number of surface points.
+int or_set_surface_velocity(void* s, const double* g, int64_t n) {
+    State* S = (State*)s;
+    Geom& gm = S->geom;
+    if (!gm.m) gm.m = &S->mesh;
+    compute_surface(gm);
+    if (g && n != (int64_t)gm.sqp.size()) return -1;
+    for (size_t i = 0; i < gm.sqp.size(); ++i) {
+        gm.sqp[i].has_g = g != nullptr && n > 0;
+        for (int k = 0; k < 3; ++k) gm.sqp[i].gv[k] = gm.sqp[i].has_g ? g[3 * i + k] : 0.0;
+    }
+    return 0;
 }
 
 // test knob: the widening of B_T as a fraction of the element edge; it applies to the elements whose

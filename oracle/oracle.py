@@ -54,6 +54,8 @@ def lib():
         L.or_set_bt_pad.argtypes = [C.c_double]
         L.or_surface_force.argtypes = [vp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_set_dirichlet.argtypes = [vp, C.c_void_p, C.c_void_p]
+        L.or_set_surface_velocity.argtypes = [vp, C.c_void_p, i64]
+        L.or_set_surface_velocity.restype = i32
         L.or_residual_jvp.argtypes = [vp, C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p, i64, C.c_void_p, C.c_void_p]
         L.or_residual_jvp_complex_step.argtypes = L.or_residual_jvp.argtypes
         L.or_element_matrix.argtypes = [vp, C.c_void_p] + [C.c_void_p] * 4 + [i64, C.c_void_p]
@@ -186,6 +188,18 @@ class OracleMesh:
         vals = _f64(vals).reshape(-1, 4)
         self._bc = (mask, vals)
         lib().or_set_dirichlet(self.h, _p(mask), _p(vals))
+
+    def set_surface_velocity(self, g=None):
+        """Velocity g of Eq. (weakbc) at every surface point, [n_surface_points, 3] in the order of
+        surface_points(); None returns to the uniform body velocity of the physics."""
+        if g is None:
+            lib().or_set_surface_velocity(self.h, None, 0)
+            self._g = None
+            return
+        g = _f64(g).reshape(-1, 3)
+        self._g = g
+        if lib().or_set_surface_velocity(self.h, _p(g), g.shape[0]) != 0:
+            raise ValueError("one velocity per surface point is needed")
 
     def residual_jvp(self, phys, u, u_prev, u_prev2=None, f=None, v=None, nodes=None):
         """Returns (R, Jv) as [n_nodes, 4]; with `nodes`, only those rows are meaningful."""

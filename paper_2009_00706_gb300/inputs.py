@@ -154,6 +154,44 @@ def rounded_box(lo, hi, fillet: float, n_per_edge: int, jitter: float = 0.0, see
 # ------------------------------------------------------------------------------------------
 # workloads
 # ------------------------------------------------------------------------------------------
+def grid_box(lo, hi, grid: float, apex=(0.6180339887498949, 0.2763932022500210)) -> np.ndarray:
+    """Surface of the axis-aligned box [lo, hi], counter-clockwise seen from outside.  Each face is
+    cut into rectangles by its own edges and by the planes at whole multiples of `grid` between
+    them; each rectangle into 4 triangles around an interior vertex at the fractions `apex` of its
+    sides.  With the faces on sub-cell planes of an octree and `grid` its finest element size,
+    every triangle lies in one element face patch and no volume point is cut, so the quadrature of
+    the body is exact.  The interior vertex lies on neither diagonal of its rectangle, so rays cast
+    from element centres, which project onto rectangle centres, meet no triangle edge there."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+
+    def breaks(a, b):
+        k0, k1 = int(np.floor(a / grid)) + 1, int(np.ceil(b / grid)) - 1
+        inner = [k * grid for k in range(k0, k1 + 1) if a < k * grid < b]
+        return [a] + inner + [b]
+
+    tris = []
+    for k in range(3):
+        a, b = (k + 1) % 3, (k + 2) % 3          # e_a x e_b = e_k
+        ba, bb = breaks(lo[a], hi[a]), breaks(lo[b], hi[b])
+        for side in (0, 1):
+            x = hi[k] if side else lo[k]
+            for i in range(len(ba) - 1):
+                for j in range(len(bb) - 1):
+                    def P(sa, sb):
+                        p = np.zeros(3)
+                        p[k] = x
+                        p[a] = sa
+                        p[b] = sb
+                        return p
+                    c = [P(ba[i], bb[j]), P(ba[i + 1], bb[j]), P(ba[i + 1], bb[j + 1]), P(ba[i], bb[j + 1])]
+                    v = P(ba[i] + apex[0] * (ba[i + 1] - ba[i]), bb[j] + apex[1] * (bb[j + 1] - bb[j]))
+                    for q in range(4):
+                        p0, p1 = c[q], c[(q + 1) % 4]
+                        tris.append((p0, p1, v) if side else (p1, p0, v))   # outward +e_k / -e_k
+    return np.array(tris, dtype=np.float64)
+
+
 REGION_SPHERE_BAND, REGION_BOX, REGION_CONE = 0, 1, 2
 SCHEME_BE, SCHEME_CN, SCHEME_BDF2 = 0, 1, 2
 
