@@ -103,7 +103,12 @@ def interior_traffic():
         return None
 
 
-def peaks():
+def peaks(api=None, device=0):
+    """Roofline denominators.  HBM: MEASURED_PEAKS.json (the driver's copy benchmark).  FP32 / FP64:
+    the library's own FMA microbenchmark on this GPU (imga_peak_flops: scalar FFMA, packed FFMA2,
+    DFMA), the FP32 peak being the faster of the two FP32 forms; without a GPU the unit-count
+    formula SMs x 128 lanes x 2 x max clock, with the SM count read from the device when there is
+    one."""
     p = {"source": "fallback", "sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -112,8 +117,25 @@ def peaks():
                   "hbm_gbs": float(d.get("hbm_gbs", 6800.0))})
     except Exception:
         pass
-    # plain FP32 ALU peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
-    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    sms = 152
+    try:
+        import torch
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+    except Exception:
+        pass
+    p["sm_count"] = sms
+    p["fp32_tflops"] = sms * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    p["fp64_tflops"] = FP64_TFLOPS_NOMINAL
+    p["fp_source"] = f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock; FP64 nominal"
+    if api is not None:
+        try:
+            f32, f32x2, f64 = (api.peak_flops(k, device) for k in (0, 1, 2))
+            p.update({"fp32_ffma_tflops": f32, "fp32_ffma2_tflops": f32x2, "fp64_dfma_tflops": f64,
+                      "fp32_tflops": max(f32, f32x2), "fp64_tflops": f64,
+                      "fp_source": "measured: imga_peak_flops FMA microbenchmark on this GPU "
+                                   "(FP32 = faster of FFMA and packed FFMA2; FP64 = DFMA)"})
+        except Exception as ex:
+            p["fp_source"] += f" (microbenchmark failed: {ex!r})"
     return p
 
 
@@ -326,14 +348,14 @@ def run_ours(args):
     # dominant kernel roofline (Out elements, live CUDA events on the launching stream)
     k_ms, k_n = prof["out_elements"]
     k_avg = k_ms / max(k_n, 1)
-    pk = peaks()
+    pk = peaks(api, local)
     flops = FLOPS_JV_OUT_ELEMENT * info["n_out"]
     achieved = flops / (k_avg / 1e3) / 1e12
     roof = {"kernel": "vms_interior (Out elements, J v)", "bound": "alu", "achieved": achieved,
             "peak": pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None, "unit": "TFLOP/s",
             "frac": achieved / pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None,
             "traffic": interior_traffic() if prec == api.PRECISION_MIXED else None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock (of derived)",
+            "peak_source": pk["fp_source"], "peaks": {k: v for k, v in pk.items() if k.endswith("tflops") or k == "sm_count"},
             "flops_per_element": FLOPS_JV_OUT_ELEMENT, "avg_launch_ms": k_avg}
     kern_share = {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()}
     kern_roof = kernel_rooflines(prof, args.steps, info, nn, pk)
@@ -422,8 +444,8 @@ def run_ours(args):
     k64 = p64["out_elements"][0] / max(1, p64["out_elements"][1])
     a64 = FLOPS_JV_OUT_ELEMENT * info["n_out"] / (k64 / 1e3) / 1e12
     extra_roof = {"kernel": "vms_interior<double, J v>", "bound": "fp64 pipe", "avg_launch_ms": k64, "achieved": a64,
-                  "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": a64 / FP64_TFLOPS_NOMINAL,
-                  "peak_source": "nominal GB300 dense FP64 (no measured FP64 peak)"}
+                  "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": a64 / pk["fp64_tflops"],
+                  "peak_source": pk["fp_source"]}
     # J v replayed as a CUDA graph (parallel branches for the Out / Intercepted / surface kernels)
     mesh.use_graphs(True)
     step()
@@ -452,37 +474,50 @@ def run_ours(args):
         smesh = api.Mesh.from_workload(ws, device=local)
         su, sup, _ = I.state(smesh.n_nodes, 16 + rank)
         sud, supd = torch.from_numpy(su).to(dev), torch.from_numpy(sup).to(dev)
-        for name, p, gr in (("mixed", api.PRECISION_MIXED, False), ("fp64", api.PRECISION_FP64, False),
-                            ("mixed_graphs", api.PRECISION_MIXED, True)):
+        for name, p, gr, pc in (("mixed", api.PRECISION_MIXED, False, 1), ("fp64", api.PRECISION_FP64, False, 1),
+                                ("mixed_graphs", api.PRECISION_MIXED, True, 1),
+                                ("mixed_graphs_multilevel", api.PRECISION_MIXED, True, 4),
+                                ("fp64_graphs_multilevel", api.PRECISION_FP64, True, 4)):
             smesh.use_graphs(gr)
             runs = []
             for rep in range(2):   # the first run also allocates the Krylov workspace
                 uw = sud.clone()
                 torch.cuda.synchronize()
-                st = smesh.newton_step(ws.physics, uw, supd, precision=p, precond=1, rtol=1e-8, gmres_m=50,
+                st = smesh.newton_step(ws.physics, uw, supd, precision=p, precond=pc, rtol=1e-8, gmres_m=50,
                                     krylov_rtol=args.krylov_rtol, max_newton=20, max_krylov=500, stream=stream,
                                     raise_on_failure=False)
                 runs.append(st)
             st = runs[-1]
             newton[name] = {"ms": st["time_ms"], "newton_its": st["newton_its"], "krylov_its": st["krylov_its"],
                             "converged": bool(st["converged"]), "rel_residual": st["res_norm"][-1] / st["res_norm"][0],
-                            "workload": "small_sphere (7,288 elements, Re 10, BE dt 0.01), block-Jacobi, GMRES(50)"}
+                            "workload": "small_sphere (7,288 elements, Re 10, BE dt 0.01), "
+                                        + ("multilevel V-cycle" if pc == 4 else "block-Jacobi") + ", GMRES(50)"}
         smesh.close()
-        # the sphere LES itself: block-Jacobi GMRES(50) does not converge it, so a
-        # capped run (3 Newton steps, 300 GMRES iterations each) compares mixed and float64 J v on the
-        # same solver: residual history and time per Newton step
+        # the sphere LES itself: block-Jacobi GMRES(50) stalls on it (every linear solve after the first
+        # reaches its cap); the multilevel V-cycle (precond 4) brings the Newton step to 1e-8.  Mixed:
+        # float32 elements, hierarchy and V-cycle, float64 Krylov vectors, reductions and update; fp64:
+        # everything float64.  The error of the mixed solution against the float64 one is reported.
         mesh.use_graphs(True)
+        sol = {}
         for name, p in (("mixed", api.PRECISION_MIXED), ("fp64", api.PRECISION_FP64)):
             uw = ud.clone()
-            st = mesh.newton_step(ph, uw, upd, up2d, precision=p, precond=1, rtol=1e-8, gmres_m=50,
-                                  krylov_rtol=args.krylov_rtol, max_newton=3, max_krylov=300, stream=stream,
+            torch.cuda.synchronize()
+            st = mesh.newton_step(ph, uw, upd, up2d, precision=p, precond=4, rtol=1e-8, gmres_m=50,
+                                  krylov_rtol=args.krylov_rtol, max_newton=20, max_krylov=600, stream=stream,
                                   raise_on_failure=False)
+            sol[name] = uw
             r = st["res_norm"]
-            newton["sphere_les_capped_" + name] = {
+            newton["sphere_les_" + name] = {
                 "ms": st["time_ms"], "ms_per_newton": st["time_ms"] / max(1, st["newton_its"]),
-                "newton_its": st["newton_its"], "krylov_per_newton": st["krylov_per_newton"],
+                "newton_its": st["newton_its"], "krylov_its": st["krylov_its"],
+                "krylov_per_newton": st["krylov_per_newton"],
                 "rel_residual_history": [x / r[0] for x in r], "converged": bool(st["converged"]),
-                "workload": "sphere_les, block-Jacobi, GMRES(50), capped at 3 Newton x 300 GMRES iterations"}
+                "workload": "sphere_les (2,001,176 elements, Re 1e4, BDF2 dt 0.01), multilevel V-cycle "
+                            "(6 Morton-consecutive blocks per aggregate, damped block-Jacobi 0.5), GMRES(50), to 1e-8"}
+        d = (sol["mixed"] - sol["fp64"]).norm().item() / max(sol["fp64"].norm().item(), 1e-300)
+        newton["sphere_les_mixed"]["rel_error_vs_fp64_solution"] = d
+        rows, _ = mesh.multilevel_info()
+        newton["sphere_les_multilevel_levels"] = [int(x) for x in rows]
         mesh.use_graphs(False)
     learned = run_learned(args, dev, stream, mesh, w) if not args.no_learned and rank == 0 else None
     try:

@@ -83,6 +83,12 @@ typedef struct {
     double g_body[3];       /* velocity prescribed on the immersed surface (weakly)             */
     double u_inf[3];        /* velocity prescribed on the box faces (strongly, not the outlet)  */
     int drop_visc_strong;   /* 1: drop mu grad(div u) from the strong momentum residual         */
+    /* g of Eq. (weakbc) per surface point, overriding g_body there: DEVICE float64
+     * [n_surface_points][3] in the order of imga_export_surface_points (a rotating or deforming
+     * body, or an exact solution prescribed on the surface), or NULL for g_body everywhere.  Read
+     * by the residual, J v and element-Jacobian calls; nodes touched by no active element keep
+     * U = (g_body, 0). */
+    const double* g_points;
 } imga_physics;
 
 typedef struct {
@@ -175,8 +181,9 @@ imga_status imga_classify_counts(imga_mesh mesh, int64_t* counts, int reset);
 
 /* Residual R(u) [n_nodes][4] (device).  u_prev2 is read by BDF2 only (may be NULL otherwise);
  * f is a nodal body force [n_nodes][4] (components 0..2 used) or NULL.  precision 0: FP64
- * throughout; 1: element arithmetic in FP32 with FP64 nodal gathers, FP64 accumulation and FP64
- * Nitsche penalty terms.  Rows of strong Dirichlet nodes hold U - g; rows of nodes touched by no
+ * throughout; 1: element arithmetic in FP32 with FP64 nodal gathers and FP64 accumulation; the
+ * velocity jump u - g at every surface point and the Nitsche penalty tau_B w.(u - g) with its
+ * accumulation stay in FP64 (tau_B = C_b mu / h_b reaches 100 C_b mu / h on sliver cut cells).  Rows of strong Dirichlet nodes hold U - g; rows of nodes touched by no
  * active element (In-only nodes, Algorithm 1) hold U - (g_body, 0). */
 imga_status imga_residual(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
                           const double* f, const imga_physics* phys, int precision, double* R, void* stream);
@@ -203,7 +210,7 @@ imga_status imga_jvp(imga_mesh mesh, const double* u, const double* u_prev, cons
  *   uses before reading it, so nothing has to be cleared between calls; calls that overlap on
  *   the GPU race on the array: issue them on one stream or order their streams.
  *   The mesh's device must be current.  Calls no cudaMalloc, cudaFree or other allocating
- *   routine. */
+ *   routine, and records no profiling events (imga_profile does not see these calls). */
 imga_status imga_jvp_noalloc(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
                              const double* f, const imga_physics* phys, int precision, const double* v, double* Jv,
                              void* stream);
@@ -222,6 +229,51 @@ imga_status imga_set_dirichlet(imga_mesh mesh, const uint8_t* mask_dev, const do
  * works on host-only and batched meshes (block-diagonal over the problems).  Errors:
  * IMGA_ERR_INVALID_ARG (null mesh or n_blocks), IMGA_ERR_OOM. */
 imga_status imga_bsr_pattern(imga_mesh mesh, int64_t* n_blocks, int64_t* indptr, int32_t* indices);
+
+/* The Jacobian assembled in 4 x 4 blocks on the block pattern of imga_bsr_pattern (Algorithms 2 and 4:
+ * K = sum_e M_e^T k_e M_e, the matrix that imga_jvp applies without forming it, in the element
+ * precision `precision`, accumulated in float64), rows of prescribed components replaced by identity
+ * rows as in imga_residual.  vals: DEVICE float64 [n_blocks][4][4] (row component, column component),
+ * written on `stream`.  The first call on a mesh copies the block pattern to the device (kept by the
+ * mesh).  The scatter adds with float64 atomics: entries may differ in the last bits between runs.
+ * Errors: IMGA_ERR_INVALID_ARG, IMGA_ERR_OOM, IMGA_ERR_CUDA. */
+imga_status imga_bsr_assemble(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
+                              const double* f, const imga_physics* phys, int precision, double* vals, void* stream);
+/* y = K x with an assembled matrix vals of this mesh's block pattern; x, y DEVICE float64 [n_nodes][4].
+ * Needs the pattern on the device (any earlier imga_bsr_assemble or imga_multilevel_setup). */
+imga_status imga_bsr_spmv(imga_mesh mesh, const double* vals, const double* x, double* y, void* stream);
+
+/* Multilevel preconditioner by block coarsening of the assembled Jacobian (no counterpart in the
+ * paper, whose solver uses additive Schwarz; its conclusion asks for preconditioners suited to the
+ * method).  Level 0 is imga_bsr_assemble's matrix; level l + 1 sums `agg` consecutive block rows and
+ * columns of level l (ranges of the Morton node order) over their free unknowns (not identity or empty
+ * rows of level 0, not dead rows of coarser levels), A_{l+1} = P^T A_l P with P one 1 per free row; a
+ * coarse unknown no free row reaches gets an identity row; the level with at most `coarse_max` block
+ * rows (<= 24) is inverted densely.  imga_multilevel_apply runs one V-cycle z = B r: `sweeps` block-
+ * Jacobi sweeps damped by `omega` on each level, restriction, the coarse correction, prolongation and
+ * `sweeps` sweeps more.  precision 0: assembly, hierarchy and V-cycle in float64; 1: element
+ * arithmetic and the whole hierarchy in float32 (the assembly accumulates in float64); r, z stay
+ * float64 DEVICE [n_nodes][4].  Setup assembles at the given state (asynchronous on `stream`; the
+ * patterns of the levels are built on the host on the first call for an (agg, coarse_max) pair and
+ * kept by the mesh).  Errors: IMGA_ERR_INVALID_ARG, IMGA_ERR_OOM, IMGA_ERR_CUDA. */
+imga_status imga_multilevel_setup(imga_mesh mesh, const double* u, const double* u_prev, const double* u_prev2,
+                                  const double* f, const imga_physics* phys, int precision, int agg, int coarse_max,
+                                  int sweeps, double omega, void* stream);
+imga_status imga_multilevel_apply(imga_mesh mesh, const double* r, double* z, void* stream);
+/* number of levels (0 before any setup), block rows per level (host int64 [24], may be NULL) and
+ * whether the dense inverse of the last level met a singular pivot (synchronises; may be NULL) */
+imga_status imga_multilevel_info(imga_mesh mesh, int* n_levels, int64_t* rows, int* singular);
+
+/* Force of the fluid on the immersed body, F DEVICE float64 [3], at the state u (spatial terms at
+ * theta u + (1 - theta) u_prev as in imga_residual).  The paper reports drag coefficients (Sec.
+ * "Validation: flow past a sphere") without printing the formula; this is the weak-boundary reading:
+ * the surface terms of Eq. (weakbc) tested with w = e_i, summed over all nodes (partition of unity),
+ *     F_i = sum_q w_q [ -(sigma(u_s, p) n)_i - [u.n < 0] rho (u.n) (u - g)_i + tau_B (u - g)_i ],
+ * n the fluid-outward normal, g per point as in imga_physics.g_points; the force that keeps the
+ * discrete momentum balance.  Float64 throughout; partial sums in a fixed order (same bits on every
+ * call).  C_d = 2 F_x / (rho U^2 A).  The first call allocates 6 KiB kept by the mesh. */
+imga_status imga_surface_force(imga_mesh mesh, const double* u, const double* u_prev, const imga_physics* phys,
+                               double* F, void* stream);
 
 /* Element Jacobians k_e = d r_e / d u_e for a list of elements (Algorithm 4's element matrix, before
  * the hanging correction M_e^T k_e M_e of Algorithm 2): elems_dev int32 [n] device, distinct
@@ -242,12 +294,23 @@ typedef struct {
     int precond;            /* 0 none, 1 block-Jacobi (nodal 4x4 diagonal blocks of J), 2 block-Jacobi
                                plus the learned element-block correction of `learned`, 3 block-
                                Jacobi plus the exact element-block correction the network is
-                               trained to reproduce.  With 2 or 3, a linear solve that does not
+                               trained to reproduce, 4 one V-cycle of the multilevel preconditioner
+                               (rebuilt from the assembled Jacobian at every Newton iterate, in the
+                               precision of `precision`).  With 2 or 3, a linear solve that does not
                                reach krylov_rtol is redone with block-Jacobi alone (counted in
                                imga_solver_stats.fallbacks)                                     */
     int line_search;        /* 1: backtracking (Armijo, c = 1e-4, halving, <= 12 trials)          */
     const void* learned;    /* imga_mlp for precond 2 (n_in 1027, n_out 1024), else NULL         */
     double learned_omega;   /* weight of the learned correction, e.g. 0.5                          */
+    /* linear solver of the Newton steps: 0 GMRES(m) on the matrix-free J v; 1 BiCGStab (the solver
+     * of the paper's appendix) on the Jacobian assembled in 4 x 4 blocks (imga_bsr_assemble), the
+     * assembled matrix also judging the linear tolerance */
+    int linear_solver;
+    /* precond 4, the multilevel preconditioner of imga_multilevel_setup: block rows per aggregate
+     * (0: 6), block rows of the dense last level at most (0: 16, at most 24), damped block-Jacobi
+     * sweeps before and after the coarse correction (0: 1) and their weight (0: 0.5) */
+    int ml_agg, ml_coarse_max, ml_sweeps;
+    double ml_omega;
 } imga_solver_opts;
 
 typedef struct {
@@ -322,7 +385,17 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * shape (4 warps, Morton order).  Both values drop the cached graphs. */
 /* IMGA_OPT_CLASSIFY_RAYS (value 1 on, 0 off, default off): imga_classify sends every point to ray
  * parity, skipping the stored markers and the normal test; for the comparison of Table in-out. */
-enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2, IMGA_OPT_CLASSIFY_RAYS = 3 };
+/* IMGA_OPT_DETERMINISTIC (value 1 on, the default; 0 off): how imga_residual / imga_jvp (and
+ * imga_jvp_noalloc) sum the element vectors into the nodes (o2n of Algorithm 2).  On, every element
+ * kernel writes its 8 x 4 contributions to a slot owned by the mesh (a volume slot per Out or
+ * Intercepted element in the element precision, a float64 surface slot per element of the dense
+ * surface bucket and per point of the sparse one), and one pass over the nodes sums each node's slot
+ * rows in the fixed order of a node -> (slot, corner, hanging weight) list built with the mesh, in
+ * float64 (mixed precision: a float-float sum of the float32 rows, then float64), and applies the
+ * strong rows: two calls with the same inputs give the same bits.  Off, the element kernels add into
+ * the output with float64 atomics, whose order, and so the last bits, vary from run to run.  Both
+ * values drop the cached graphs. */
+enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2, IMGA_OPT_CLASSIFY_RAYS = 3, IMGA_OPT_DETERMINISTIC = 4 };
 imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
 
 /* The tile shapes in use.  shape[8] = {warps per block, longest-first order} for
@@ -348,6 +421,13 @@ imga_status imga_profile_read(imga_mesh mesh, double* ms, int64_t* launches);
  * *mismatches the number whose result differs in any bit from the hardware conversion (NaN: from
  * being NaN).  Synchronous.  Errors: IMGA_ERR_INVALID_ARG (n < 0, null output), IMGA_ERR_CUDA. */
 imga_status imga_selftest_conversions(int device, int64_t n, uint64_t seed, int64_t* mismatches);
+
+/* Measured throughput of an arithmetic pipe of `device`, for roofline denominators (no counterpart in
+ * the paper): 8 independent chains of fused multiply-adds per thread, 8 blocks of 256 threads per SM,
+ * best of 3 timed launches (synchronous).  kind 0: FP32 FMA; 1: packed FP32x2 FMA (two per
+ * instruction); 2: FP64 FMA.  *tflops = 2 x FMAs / second / 1e12.  Errors: IMGA_ERR_INVALID_ARG,
+ * IMGA_ERR_CUDA. */
+imga_status imga_peak_flops(int device, int kind, double* tflops);
 
 /* Message of the last failing call on the calling thread ("" if none has failed).  The string
  * is owned by the library and stays valid until the next failing call on the same thread. */

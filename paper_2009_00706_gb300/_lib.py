@@ -27,6 +27,8 @@ SOURCES = [
     ("vms.cu", []),
     ("jac.cu", []),
     ("solver.cu", []),
+    ("bsr.cu", ["-Xcompiler", "-fopenmp"]),
+    ("peak.cu", []),
     ("mlp.cu", []),
 ]
 HEADERS = ["imga_internal.h", "vms_device.cuh", os.path.join("..", "..", "include", "imga.h")]
@@ -94,7 +96,7 @@ class MeshParams(C.Structure):
 class Physics(C.Structure):
     _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("dt", C.c_double), ("time_scheme", C.c_int),
                 ("C_b", C.c_double), ("C_I", C.c_double), ("g_body", C.c_double * 3), ("u_inf", C.c_double * 3),
-                ("drop_visc_strong", C.c_int)]
+                ("drop_visc_strong", C.c_int), ("g_points", C.c_void_p)]
 
 
 class Problem(C.Structure):
@@ -111,7 +113,9 @@ class MeshInfo(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("gmres_m", C.c_int), ("max_newton", C.c_int), ("max_krylov", C.c_int), ("rtol", C.c_double),
                 ("atol", C.c_double), ("krylov_rtol", C.c_double), ("precision", C.c_int), ("precond", C.c_int),
-                ("line_search", C.c_int), ("learned", C.c_void_p), ("learned_omega", C.c_double)]
+                ("line_search", C.c_int), ("learned", C.c_void_p), ("learned_omega", C.c_double),
+                ("linear_solver", C.c_int), ("ml_agg", C.c_int), ("ml_coarse_max", C.c_int), ("ml_sweeps", C.c_int),
+                ("ml_omega", C.c_double)]
 
 
 class SolverStats(C.Structure):
@@ -159,6 +163,14 @@ SIGNATURES = {
     "imga_profile": (C.c_int, [_vp, _int]),
     "imga_profile_read": (C.c_int, [_vp, _vp, _vp]),
     "imga_last_error": (C.c_char_p, []),
+    "imga_bsr_assemble": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.POINTER(Physics), _int, _dp, _vp]),
+    "imga_bsr_spmv": (C.c_int, [_vp, _dp, _dp, _dp, _vp]),
+    "imga_multilevel_setup": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.POINTER(Physics), _int, _int, _int, _int, C.c_double,
+                                        _vp]),
+    "imga_multilevel_apply": (C.c_int, [_vp, _dp, _dp, _vp]),
+    "imga_multilevel_info": (C.c_int, [_vp, C.POINTER(C.c_int), _vp, _vp]),
+    "imga_peak_flops": (C.c_int, [_int, _int, C.POINTER(C.c_double)]),
+    "imga_surface_force": (C.c_int, [_vp, _dp, _dp, C.POINTER(Physics), _dp, _vp]),
 }
 
 _lib = None

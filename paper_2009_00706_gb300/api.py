@@ -16,14 +16,20 @@ from ._lib import MeshInfo, MeshParams, Physics, Problem, Region, SolverOpts, So
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 
-def physics_struct(ph) -> Physics:
-    """imga_physics from an inputs.Physics (or anything with the same fields)."""
+def physics_struct(ph, g_points=None) -> Physics:
+    """imga_physics from an inputs.Physics (or anything with the same fields); g_points: the
+    velocity per surface point, a float64 CUDA tensor [n_surface_points, 3] in the order of
+    Mesh.surface_points(), or None (g_body everywhere)."""
     s = Physics()
     s.rho, s.mu, s.dt, s.time_scheme = ph.rho, ph.mu, ph.dt, int(ph.scheme)
     s.C_b, s.C_I = ph.Cb, ph.CI
     s.g_body = (C.c_double * 3)(*ph.g)
     s.u_inf = (C.c_double * 3)(*ph.uinf)
     s.drop_visc_strong = int(ph.drop_visc)
+    if g_points is not None:
+        if not (g_points.is_cuda and str(g_points.dtype).endswith("float64") and g_points.is_contiguous()):
+            raise ValueError("g_points: expected a contiguous float64 CUDA tensor [n_surface_points, 3]")
+    s.g_points = None if g_points is None else g_points.data_ptr()
     return s
 
 
@@ -155,6 +161,11 @@ class Mesh:
         check(L.imga_mesh_export(self.h, f(anc), f(lev), f(conn), f(ijk), f(hp), f(hn)))
         return {"anchors": anc, "levels": lev, "conn": conn, "node_ijk": ijk, "hang_parents": hp[:nh], "hang_np": hn[:nh]}
 
+    def _gp(self, g_points):
+        if g_points is not None and g_points.numel() != 3 * self.info["n_surface_points"]:
+            raise ValueError(f"g_points: expected {self.info['n_surface_points']} x 3 values")
+        return g_points
+
     def markers(self):
         mk = np.zeros(self.n_elem, np.int8)
         cf = np.zeros(self.n_elem, np.uint8)
@@ -189,37 +200,39 @@ class Mesh:
         check(_lib.load().imga_classify(self.h, _ptr(pts), n, _ptr(flags), _stream(stream)))
         return flags
 
-    def residual(self, phys, u, u_prev, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None):
+    def residual(self, phys, u, u_prev, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None,
+                 g_points=None):
         import torch
         nn = self.n_nodes
         if out is None:
             out = torch.empty((nn, 4), dtype=torch.float64, device=u.device)
-        ps = physics_struct(phys)
+        ps = physics_struct(phys, self._gp(g_points))
         check(_lib.load().imga_residual(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
                                         _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps),
                                         precision, _ptr(out), _stream(stream)))
         return out
 
-    def jvp(self, phys, u, u_prev, v, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None):
+    def jvp(self, phys, u, u_prev, v, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None,
+            g_points=None):
         import torch
         nn = self.n_nodes
         if out is None:
             out = torch.empty((nn, 4), dtype=torch.float64, device=u.device)
-        ps = physics_struct(phys)
+        ps = physics_struct(phys, self._gp(g_points))
         check(_lib.load().imga_jvp(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
                                    _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps), precision,
                                    _ptr(_vec(v, nn, "v")), _ptr(out), _stream(stream)))
         return out
 
     def element_jacobians(self, phys, u, u_prev, elems, u_prev2=None, f=None, precision=PRECISION_FP64, out=None,
-                          stream=None):
+                          stream=None, g_points=None):
         """k_e [n, 32, 32] (float64, device) of the elements in `elems` (int32 device tensor)."""
         import torch
         nn = self.n_nodes
         n = elems.numel()
         if out is None:
             out = torch.empty((n, 32, 32), dtype=torch.float64, device=u.device)
-        ps = physics_struct(phys)
+        ps = physics_struct(phys, self._gp(g_points))
         check(_lib.load().imga_element_jacobians(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
                                                  _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")),
                                                  C.byref(ps), precision, _ptr(elems), n, _ptr(out), _stream(stream)))
@@ -227,13 +240,16 @@ class Mesh:
 
     def newton_step(self, phys, u, u_prev, u_prev2=None, f=None, gmres_m=50, max_newton=20, max_krylov=1000,
                     rtol=1e-8, atol=0.0, krylov_rtol=1e-3, precision=PRECISION_FP64, precond=1, line_search=1,
-                    stream=None, raise_on_failure=True, learned=None, learned_omega=0.5):
-        """Newton-GMRES in place on u; returns a stats dict.  precond 2 needs learned = an Mlp."""
+                    stream=None, raise_on_failure=True, learned=None, learned_omega=0.5, g_points=None,
+                    linear_solver=0, ml_agg=0, ml_coarse_max=0, ml_sweeps=0, ml_omega=0.0):
+        """Newton-GMRES (linear_solver 0) or Newton-BiCGStab on the assembled Jacobian (1) in place on u;
+        returns a stats dict.  precond 2 needs learned = an Mlp; precond 4 is the multilevel V-cycle."""
         nn = self.n_nodes
         o = SolverOpts(gmres_m, max_newton, max_krylov, rtol, atol, krylov_rtol, precision, precond, line_search,
-                       learned.h if learned is not None else None, learned_omega)
+                       learned.h if learned is not None else None, learned_omega, linear_solver, ml_agg,
+                       ml_coarse_max, ml_sweeps, ml_omega)
         st = SolverStats()
-        ps = physics_struct(phys)
+        ps = physics_struct(phys, self._gp(g_points))
         status = _lib.load().imga_newton_step(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
                                               _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")),
                                               C.byref(ps), C.byref(o), C.byref(st), _stream(stream))
@@ -244,6 +260,63 @@ class Mesh:
         if raise_on_failure and status != 0:
             check(status)
         return out
+
+    def bsr_assemble(self, phys, u, u_prev, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None,
+                     g_points=None):
+        """The assembled Jacobian: float64 CUDA tensor [n_blocks, 4, 4] on the pattern of bsr_pattern()."""
+        import torch
+        nn = self.n_nodes
+        nb = self.bsr_pattern()[1].size
+        if out is None:
+            out = torch.empty((nb, 4, 4), dtype=torch.float64, device=u.device)
+        ps = physics_struct(phys, self._gp(g_points))
+        check(_lib.load().imga_bsr_assemble(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                            _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps),
+                                            precision, _ptr(out), _stream(stream)))
+        return out
+
+    def bsr_spmv(self, vals, x, out=None, stream=None):
+        import torch
+        nn = self.n_nodes
+        if out is None:
+            out = torch.empty((nn, 4), dtype=torch.float64, device=x.device)
+        check(_lib.load().imga_bsr_spmv(self.h, _ptr(vals), _ptr(_vec(x, nn, "x")), _ptr(out), _stream(stream)))
+        return out
+
+    def surface_force(self, phys, u, u_prev, out=None, stream=None, g_points=None):
+        """Force of the fluid on the body (float64 CUDA tensor [3])."""
+        import torch
+        nn = self.n_nodes
+        if out is None:
+            out = torch.empty(3, dtype=torch.float64, device=u.device)
+        ps = physics_struct(phys, self._gp(g_points))
+        check(_lib.load().imga_surface_force(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                             C.byref(ps), _ptr(out), _stream(stream)))
+        return out
+
+    def multilevel_setup(self, phys, u, u_prev, u_prev2=None, f=None, precision=PRECISION_FP64, agg=6, coarse_max=16,
+                         sweeps=1, omega=0.5, stream=None, g_points=None):
+        nn = self.n_nodes
+        ps = physics_struct(phys, self._gp(g_points))
+        check(_lib.load().imga_multilevel_setup(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                                _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")),
+                                                C.byref(ps), precision, agg, coarse_max, sweeps, omega, _stream(stream)))
+
+    def multilevel_apply(self, r, out=None, stream=None):
+        import torch
+        nn = self.n_nodes
+        if out is None:
+            out = torch.empty((nn, 4), dtype=torch.float64, device=r.device)
+        check(_lib.load().imga_multilevel_apply(self.h, _ptr(_vec(r, nn, "r")), _ptr(out), _stream(stream)))
+        return out
+
+    def multilevel_info(self):
+        """(block rows per level, whether the dense last level met a singular pivot)"""
+        n = C.c_int(0)
+        rows = np.zeros(24, np.int64)
+        sing = C.c_int(0)
+        check(_lib.load().imga_multilevel_info(self.h, C.byref(n), rows.ctypes.data_as(C.c_void_p), C.byref(sing)))
+        return rows[: n.value].copy(), bool(sing.value)
 
     def precond_dataset(self, phys, u, u_prev, elems, u_prev2=None, f=None, precision=PRECISION_MIXED, targets=True,
                         ldx=1040, stream=None):
@@ -263,6 +336,10 @@ class Mesh:
 
     def profile(self, enable=True):
         check(_lib.load().imga_profile(self.h, 1 if enable else 0))
+
+    def deterministic(self, on=True):
+        """IMGA_OPT_DETERMINISTIC: slot writes + ordered node sums (on, default) or float64 atomics."""
+        check(_lib.load().imga_set_option(self.h, 4, 1 if on else 0))
 
     def use_graphs(self, on=True):
         """imga_set_option(IMGA_OPT_GRAPHS): replay residual / J v calls as CUDA graphs."""
@@ -395,6 +472,13 @@ class Mlp:
         check(_lib.load().imga_mlp_train(self.h, _ptr(X), X.shape[1], _ptr(T), X.shape[0], epochs, batch, lr,
                                          hist.ctypes.data_as(C.c_void_p), _stream(stream)))
         return hist[:epochs]
+
+
+def peak_flops(kind, device=0):
+    """Measured TFLOP/s of an arithmetic pipe: kind 0 FP32 FMA, 1 packed FP32x2 FMA, 2 FP64 FMA."""
+    t = C.c_double(0.0)
+    check(_lib.load().imga_peak_flops(device, kind, C.byref(t)))
+    return t.value
 
 
 def selftest_conversions(n=1 << 24, seed=1, device=0):

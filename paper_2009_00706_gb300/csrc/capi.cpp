@@ -208,6 +208,8 @@ void imga_destroy_mesh(imga_mesh h) {
     if (h->m.host_only) { delete h; return; }
     imga::profile_reset(h->m);
     imga::solver_free(h->m);
+    imga::multilevel_free(h->m);
+    if (h->m.force_part) cudaFree(h->m.force_part);
     imga::graphs_free(h->m);
     int cur = 0;
     cudaGetDevice(&cur);
@@ -386,6 +388,91 @@ imga_status imga_element_jacobians(imga_mesh h, const double* u, const double* u
     return IMGA_OK;
 }
 
+static imga_status state_ok(imga_mesh h, const double* u, const double* up, const double* up2, const imga_physics* ph,
+                            int precision) {
+    if (!h || !u || !up) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
+    if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
+    if (precision != 0 && precision != 1) return fail(IMGA_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    return IMGA_OK;
+}
+
+imga_status imga_bsr_assemble(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                              const imga_physics* ph, int precision, double* vals, void* stream) {
+    imga_status st = state_ok(h, u, up, up2, ph, precision);
+    if (st != IMGA_OK) return st;
+    if (!vals) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    std::string err;
+    const int64_t* bp;
+    const int32_t* bi;
+    double* ks;
+    try {
+        if (imga::bsr_device_pattern(h->m, &bp, &bi, &ks, err)) return fail(IMGA_ERR_OOM, err);
+    } catch (const std::bad_alloc&) {
+        return fail(IMGA_ERR_OOM, "block pattern: host allocation failed");
+    }
+    if (imga::bsr_assemble(h->m, u, up, up2, f, *ph, precision, bp, bi, vals, ks, stream)) return cuda_status("bsr_assemble");
+    return IMGA_OK;
+}
+
+imga_status imga_bsr_spmv(imga_mesh h, const double* vals, const double* x, double* y, void* stream) {
+    if (!h || !vals || !x || !y) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (h->m.host_only) return fail(IMGA_ERR_INVALID_ARG, "mesh was built host-only (device < 0)");
+    std::string err;
+    if (imga::bsr_spmv(h->m, vals, x, y, stream, err)) return fail(err.empty() ? IMGA_ERR_CUDA : IMGA_ERR_INVALID_ARG, err.empty() ? "bsr_spmv launch failed" : err);
+    return IMGA_OK;
+}
+
+imga_status imga_multilevel_setup(imga_mesh h, const double* u, const double* up, const double* up2, const double* f,
+                                  const imga_physics* ph, int precision, int agg, int coarse_max, int sweeps, double omega,
+                                  void* stream) {
+    imga_status st = state_ok(h, u, up, up2, ph, precision);
+    if (st != IMGA_OK) return st;
+    if (agg < 2 || coarse_max < 1 || coarse_max > 24 || sweeps < 1 || !(omega > 0.0))
+        return fail(IMGA_ERR_INVALID_ARG, "multilevel: agg >= 2, 1 <= coarse_max <= 24, sweeps >= 1, omega > 0");
+    std::string err;
+    try {
+        if (imga::multilevel_prepare(h->m, agg, coarse_max, err)) return fail(IMGA_ERR_OOM, err);
+    } catch (const std::bad_alloc&) {
+        return fail(IMGA_ERR_OOM, "multilevel: host allocation failed");
+    }
+    if (imga::multilevel_setup(h->m, u, up, up2, f, *ph, precision, sweeps, omega, stream, err)) return fail(IMGA_ERR_CUDA, err);
+    return IMGA_OK;
+}
+
+imga_status imga_multilevel_apply(imga_mesh h, const double* r, double* z, void* stream) {
+    if (!h || !r || !z) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (!h->m.mlev) return fail(IMGA_ERR_INVALID_ARG, "multilevel: call imga_multilevel_setup first");
+    if (imga::multilevel_apply(h->m, r, z, stream)) return cuda_status("multilevel_apply");
+    return IMGA_OK;
+}
+
+imga_status imga_multilevel_info(imga_mesh h, int* n_levels, int64_t* rows, int* singular) {
+    if (!h || !n_levels) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    *n_levels = imga::multilevel_info(h->m, rows, singular);
+    return IMGA_OK;
+}
+
+imga_status imga_surface_force(imga_mesh h, const double* u, const double* up, const imga_physics* ph, double* F,
+                               void* stream) {
+    imga_status st = state_ok(h, u, up, up, ph, 0);
+    if (st != IMGA_OK) return st;
+    if (!F) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    imga::Mesh& m = h->m;
+    if (!m.force_part && cudaMalloc((void**)&m.force_part, imga::kForcePartials * sizeof(double)) != cudaSuccess)
+        return fail(IMGA_ERR_OOM, "cudaMalloc failed");
+    if (imga::surface_force(m, u, up, *ph, F, m.force_part, stream)) return cuda_status("surface_force");
+    return IMGA_OK;
+}
+
+imga_status imga_peak_flops(int device, int kind, double* tflops) {
+    if (!tflops || kind < 0 || kind > 2) return fail(IMGA_ERR_INVALID_ARG, "kind must be 0, 1 or 2 and tflops non-null");
+    std::string err;
+    if (imga::peak_flops(device, kind, tflops, err)) return fail(IMGA_ERR_CUDA, err);
+    return IMGA_OK;
+}
+
 imga_status imga_newton_step(imga_mesh h, double* u, const double* up, const double* up2, const double* f,
                              const imga_physics* ph, const imga_solver_opts* o, imga_solver_stats* stats, void* stream) {
     if (!h || !u || !up || !o || !stats) return fail(IMGA_ERR_INVALID_ARG, "null argument");
@@ -393,7 +480,9 @@ imga_status imga_newton_step(imga_mesh h, double* u, const double* up, const dou
     if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
     if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
     if (o->gmres_m < 1 || o->gmres_m > 63 || o->max_newton < 0 || o->max_krylov < 1 || !(o->rtol >= 0.0) ||
-        !(o->krylov_rtol > 0.0) || (o->precision != 0 && o->precision != 1) || o->precond < 0 || o->precond > 3 ||
+        !(o->krylov_rtol > 0.0) || (o->precision != 0 && o->precision != 1) || o->precond < 0 || o->precond > 4 ||
+        (o->linear_solver != 0 && o->linear_solver != 1) || o->ml_agg < 0 || o->ml_agg == 1 || o->ml_coarse_max < 0 ||
+        o->ml_coarse_max > 24 || o->ml_sweeps < 0 || o->ml_omega < 0.0 ||
         (o->precond == 2 && !o->learned))
         return fail(IMGA_ERR_INVALID_ARG, "bad solver options");
     imga_solver_opts oo = *o;
@@ -506,6 +595,10 @@ imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
         case IMGA_OPT_CLASSIFY_RAYS:
             if (h->m.batched) return fail(IMGA_ERR_INVALID_ARG, "batched meshes do not classify points");
             h->m.classify_ray_only = value != 0;
+            return IMGA_OK;
+        case IMGA_OPT_DETERMINISTIC:
+            h->m.deterministic = value != 0;
+            imga::graphs_free(h->m);   // captured launches carry the scatter
             return IMGA_OK;
         default:
             return fail(IMGA_ERR_INVALID_ARG, "unknown option");

@@ -485,6 +485,53 @@ bool device_cut_quadrature(Mesh& m, std::string& err) {
     return true;
 }
 
+// Deterministic scatter (o2n of Algorithm 2 in a fixed order).  The element kernels write their
+// 8 x 4 contributions to slots: volume slots, one per Out element (out_list order) then one per
+// Intercepted element (cut_list order), in the element precision; surface slots in float64, one per
+// element of the dense surface bucket (sq_list order) then one per point of the sparse bucket.  The
+// incidence list holds, for every independent node, the (slot, corner, weight) entries that reach it
+// through M_e: weight 1 for a corner that is the node, 1/2 or 1/4 for a hanging corner whose parent
+// it is; entries ordered by slot, so the node sums in the same order on every call.
+// Entry encoding: bits 0-2 corner, bits 3-4 weight (0: 1, 1: 1/2, 2: 1/4), bits 5.. global slot
+// (volume slots first).
+bool build_incidence(Mesh& m, const std::vector<int32_t>& sq_el, const std::vector<int32_t>& dense, std::string& err) {
+    const int64_t nn = m.n_nodes(), nv = (int64_t)(m.out_list.size() + m.cut_list.size());
+    const int64_t ns = m.n_sq_elem + m.n_sq_sparse;
+    m.n_vslots = nv;
+    m.n_sslots = ns;
+    auto elem_of = [&](int64_t s) -> int64_t {
+        if (s < (int64_t)m.out_list.size()) return m.out_list[s];
+        if (s < nv) return m.cut_list[s - (int64_t)m.out_list.size()];
+        if (s < nv + m.n_sq_elem) return dense[s - nv];
+        return sq_el[s - nv - m.n_sq_elem];
+    };
+    std::vector<int64_t> ptr(nn + 1, 0);
+    auto visit = [&](auto&& fn) {
+        for (int64_t s = 0; s < nv + ns; ++s) {
+            const int64_t e = elem_of(s);
+            for (int c = 0; c < 8; ++c) {
+                const int32_t id = m.conn[8 * e + c];
+                if (id < nn) { fn(id, (uint64_t)(s << 5) | (uint64_t)c); continue; }
+                const int64_t h = id - nn;
+                const int np = m.hnp[h];
+                const uint64_t wc = np == 4 ? 2u : 1u;
+                for (int q = 0; q < np; ++q) fn(m.hpar[4 * h + q], (uint64_t)(s << 5) | (wc << 3) | (uint64_t)c);
+            }
+        }
+    };
+    visit([&](int64_t node, uint64_t) { ptr[node + 1] += 1; });
+    for (int64_t i = 0; i < nn; ++i) ptr[i + 1] += ptr[i];
+    std::vector<uint64_t> inc(std::max<int64_t>(1, ptr[nn]));
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    visit([&](int64_t node, uint64_t code) { inc[fill[node]++] = code; });
+    const size_t slot_bytes = (size_t)std::max<int64_t>(1, nv) * 32 * sizeof(double);
+    if (!upload(&m.d.inc_ptr, ptr, err) || !upload(&m.d.inc, inc, err)) return false;
+    if (!check(cudaMalloc((void**)&m.d.sv, slot_bytes), err, "cudaMalloc") ||
+        !check(cudaMalloc((void**)&m.d.ss, (size_t)std::max<int64_t>(1, ns) * 32 * sizeof(double)), err, "cudaMalloc"))
+        return false;
+    return true;
+}
+
 // surface points (sorted by owning element, reference coordinates) and boundary flags
 bool device_upload_quadrature(Mesh& m, std::string& err) {
     const int64_t ns = (int64_t)m.sq.size() / 10;
@@ -506,10 +553,11 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
         sparse.insert(sparse.end(), dense.begin(), dense.end());
         order.swap(sparse);
     }
-    std::vector<int32_t> el(ns);
+    std::vector<int32_t> el(ns), src(ns);
     std::vector<double> xr(3 * ns), nr(3 * ns), w(ns), tb(ns);
     for (int64_t j = 0; j < ns; ++j) {
         const double* r = &m.sq[10 * order[j]];
+        src[j] = (int32_t)order[j];
         int64_t e = (int64_t)r[8];
         el[j] = (int32_t)e;
         double h = (double)(1u << (kMaxDepth - m.lev[e])) * m.scale;
@@ -528,10 +576,15 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
         if (j == m.n_sq_sparse || el[j] != el[j - 1]) { sl.push_back(el[j]); so.push_back(j); }
     so.push_back(ns);
     m.n_sq_elem = (int64_t)sl.size();
+    m.sq_hosts.assign(el.begin(), el.end());
+    std::sort(m.sq_hosts.begin(), m.sq_hosts.end());
+    m.sq_hosts.erase(std::unique(m.sq_hosts.begin(), m.sq_hosts.end()), m.sq_hosts.end());
     if (!upload(&m.d.sq_elem, el, err) || !upload(&m.d.sq_x, xr, err) || !upload(&m.d.sq_n, nr, err) ||
         !upload(&m.d.sq_w, w, err) || !upload(&m.d.sq_taub, tb, err) || !upload(&m.d.sq_list, sl, err) ||
-        !upload(&m.d.sq_off, so, err) || !upload(&m.d.bcflag, m.bcflag, err))
+        !upload(&m.d.sq_off, so, err) || !upload(&m.d.sq_src, src, err) || !upload(&m.d.sq_hosts, m.sq_hosts, err) ||
+        !upload(&m.d.bcflag, m.bcflag, err))
         return false;
+    if (!build_incidence(m, el, sl, err)) return false;
     const size_t next = (size_t)(m.n_nodes() + m.n_hang());
     if (!check(cudaMalloc((void**)&m.d.slot, std::max<int64_t>(1, m.n_elem()) * sizeof(int32_t)), err, "cudaMalloc")) return false;
     if (!check(cudaMalloc((void**)&m.d.nd_f, std::max<size_t>(1, 24 * next) * sizeof(float)), err, "cudaMalloc") ||
@@ -580,7 +633,7 @@ void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
                     d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.cut_order, d.sq_elem, d.sq_x,
-                    d.sq_n, d.sq_w, d.sq_taub, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
+                    d.sq_n, d.sq_w, d.sq_taub, d.sq_src, d.sq_hosts, d.inc_ptr, d.inc, d.sv, d.ss, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
                     d.counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -95,7 +95,14 @@ struct DeviceMesh {
     double* sq_n = nullptr;       // [n][3]
     double* sq_w = nullptr;
     double* sq_taub = nullptr;    // 1 / h_b
+    int32_t* sq_src = nullptr;    // position of every surface point in the export order (imga_physics.g_points)
     int32_t* cut_order = nullptr;   // Intercepted list positions by decreasing point count (autotuner)
+    int32_t* sq_hosts = nullptr;  // every element hosting a surface point (increasing)
+    // deterministic scatter: node -> (slot, corner, weight) incidence and the element-contribution slots
+    int64_t* inc_ptr = nullptr;   // [n_nodes + 1]
+    uint64_t* inc = nullptr;      // bits 0-2 corner, 3-4 weight code, 5.. global slot
+    void* sv = nullptr;           // volume slots [n_vslots][8][4] of the element precision (sized for float64)
+    double* ss = nullptr;         // surface slots [n_sslots][8][4] float64
     int32_t* sq_list = nullptr;   // elements hosting at least kNitscheDenseMin surface points
     int64_t* sq_off = nullptr;    // [n_sq_elem + 1] their point ranges in the sorted arrays
     // per-call node workspace (node_prep): value, tangent and force data of every independent and
@@ -154,6 +161,9 @@ struct Mesh {
     std::vector<double> sq;              // [n][10] surface points (export layout)
     int64_t n_sq_sparse = 0;             // surface points of elements hosting < kNitscheDenseMin (stored first)
     int64_t n_sq_elem = 0;               // elements hosting >= kNitscheDenseMin surface points
+    std::vector<int32_t> sq_hosts;       // every element hosting a surface point (increasing)
+    int64_t n_vslots = 0, n_sslots = 0;  // deterministic scatter: volume slots (active elements), surface slots
+    bool deterministic = true;           // IMGA_OPT_DETERMINISTIC: slots + ordered node sums (1) or atomics (0)
     std::vector<uint8_t> bcflag;
     // block pattern of the assembled Jacobian (imga_bsr_pattern), built on first use
     std::vector<int64_t> bsr_ptr;        // [n_nodes + 1]
@@ -184,6 +194,8 @@ struct Mesh {
     DeviceMesh d;
     void* scratch = nullptr;             // device workspace for the kernels
     void* solver_work = nullptr;         // Krylov workspace (solver.cu)
+    void* mlev = nullptr;                // assembled matrix and multilevel hierarchy (bsr.cu)
+    double* force_part = nullptr;        // workspace of imga_surface_force
     // per-kernel profiling (CUDA events, one pair per launch, resolved at read time)
     bool profiling = false;
     struct ProfEv { void *a, *b; int launches; };   // event pair around `launches` kernels
@@ -209,6 +221,7 @@ int64_t find_leaf(const Mesh& m, int64_t x, int64_t y, int64_t z);
 void build_bsr_pattern(Mesh& m);
 
 // device stages (geom.cu)
+bool build_incidence(Mesh& m, const std::vector<int32_t>& sq_el, const std::vector<int32_t>& dense, std::string& err);
 bool device_upload_geometry(Mesh& m, std::string& err);
 bool device_markers(Mesh& m, std::string& err);
 bool device_cut_quadrature(Mesh& m, std::string& err);
@@ -231,6 +244,10 @@ int vms_jvp_noalloc(const Mesh& m, const double* u, const double* up, const doub
                     const imga_physics& ph, int precision, const double* v, double* out, void* stream,
                     std::string& err);
 
+int surface_force(const Mesh& m, const double* u, const double* up, const imga_physics& ph, double* F, double* part,
+                  void* stream);
+constexpr int kForcePartials = 256 * 3;   // doubles of workspace for surface_force
+
 void profile_reset(Mesh& m);
 int profile_collect(Mesh& m);
 void graphs_free(Mesh& m);
@@ -241,6 +258,9 @@ int element_jacobians(const Mesh& m, const double* u, const double* up, const do
 int block_jacobi_setup(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
                        const imga_physics& ph, int precision, double* D, double* Dinv, void* stream);
 int block_jacobi_apply(const Mesh& m, const double* Dinv, const double* x, double* y, void* stream);
+int bsr_assemble(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                 const imga_physics& ph, int precision, const int64_t* bptr, const int32_t* bidx, double* val,
+                 double* Ks, void* stream);
 
 // learned block preconditioner (mlp.cu)
 struct Mlp;
@@ -261,12 +281,26 @@ int precond_correction(const Mesh& m, const imga_physics& ph, const int32_t* ele
                        const float* scale, float omega, const double* v, double* zc, double* z, cudaStream_t s);
 int gemm_bf16_test(int M, int N, int K, const float* A, const float* B, float* C, cudaStream_t s);
 
+// assembled matrix and multilevel preconditioner (bsr.cu)
+int multilevel_prepare(Mesh& m, int agg, int coarse_max, std::string& err);
+int multilevel_setup(Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                     const imga_physics& ph, int precision, int nu, double omega, void* stream, std::string& err);
+int multilevel_apply(Mesh& m, const double* r, double* z, void* stream);
+int multilevel_info(Mesh& m, int64_t* rows, int* singular);
+void multilevel_free(Mesh& m);
+int bsr_spmv(Mesh& m, const double* val, const double* x, double* y, void* stream, std::string& err);
+int bsr_device_pattern(Mesh& m, const int64_t** ptr, const int32_t** idx, double** ks, std::string& err);
+double* multilevel_matrix(Mesh& m);
+
 // Newton-GMRES (solver.cu)
 int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const double* f, const imga_physics& ph,
                  const imga_solver_opts& o, imga_solver_stats* stats, void* stream, std::string& err);
 void solver_free(Mesh& m);
 
 bool merge_meshes(Mesh& m, const std::vector<const Mesh*>& parts, const std::vector<double>& mu, std::string& err);
+
+// arithmetic-pipe microbenchmark (peak.cu)
+int peak_flops(int device, int kind, double* tflops, std::string& err);
 
 void set_error(const std::string& s);
 

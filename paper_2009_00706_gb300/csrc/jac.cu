@@ -24,7 +24,47 @@ namespace imga {
 
 namespace {
 
-enum { FULL = 0, DIAG = 1 };
+enum { FULL = 0, DIAG = 1, BSR = 2 };
+
+// Position of block (row, col) in the block pattern (columns increasing within a row), or -1.
+__device__ __forceinline__ int64_t bsr_find(const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                            int32_t row, int32_t col) {
+    int64_t lo = ptr[row], hi = ptr[row + 1] - 1;
+    while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t c = idx[mid];
+        if (c == col) return mid;
+        if (c < col) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// node ids and weights a corner enters through M_e: itself, or the 2 / 4 parents of a hanging node
+__device__ __forceinline__ int corner_nodes(const Args& A, int32_t id, int32_t nd[4], double& w) {
+    if (id < A.n_nodes) { nd[0] = id; w = 1.0; return 1; }
+    const int32_t* hp = A.hpar + 4 * (int64_t)(id - A.n_nodes);
+    const int np = hp[2] >= 0 ? 4 : 2;
+    for (int p = 0; p < np; ++p) nd[p] = hp[p];
+    w = np == 4 ? 0.25 : 0.5;
+    return np;
+}
+
+// entry (row i of corner ida, column k of corner idb) of k_e added to the assembled matrix through
+// M_e^T k_e M_e (Algorithm 2): every parent pair (p, q) receives w_p w_q v in block (p, q)
+__device__ __forceinline__ void bsr_add(const Args& A, int32_t ida, int32_t idb, int i, int k, double v,
+                                        double* __restrict__ val) {
+    if (v == 0.0) return;
+    int32_t na[4], nb[4];
+    double wa, wb;
+    const int ca = corner_nodes(A, ida, na, wa), cb = corner_nodes(A, idb, nb, wb);
+    const double vw = wa * wb * v;
+    for (int p = 0; p < ca; ++p)
+        for (int q = 0; q < cb; ++q) {
+            const int64_t pos = bsr_find(A.bptr, A.bidx, na[p], nb[q]);
+            if (pos >= 0) atomicAdd(val + 16 * pos + 4 * i + k, vw);
+        }
+}
 
 // tangent fields of the seed (corner b, component k) at a point whose corner-b basis values are
 // phb, reference gradient dphb and reference mixed second derivatives d2b (01, 02, 12)
@@ -143,6 +183,10 @@ __global__ void __launch_bounds__(8 * JacShape<T>::EPB) jac_out(Args A, const in
             if (MODE == FULL) {
                 if (work)
                     for (int i = 0; i < 4; ++i) K[(int64_t)sl * 1024 + (c * 4 + i) * 32 + b * 4 + k] = (double)r[i];
+            } else if (MODE == BSR) {
+                const int32_t idb = __shfl_sync(0xffffffffu, id, (threadIdx.x & 31 & ~7) | b);
+                if (work)
+                    for (int i = 0; i < 4; ++i) bsr_add(A, id, idb, i, k, (double)r[i], K);
             } else if (b == c) {
                 for (int i = 0; i < 4; ++i) diag[i * 4 + k] = (double)r[i];
             }
@@ -218,6 +262,12 @@ __global__ void __launch_bounds__(32 * JWPB) jac_cut(Args A, const int32_t* __re
     }
     if (MODE == FULL) {
         for (int s = 0; s < 32; ++s) K[(int64_t)sl * 1024 + lane * 32 + s] = (double)acc[s];
+    } else if (MODE == BSR) {
+        const int32_t ida = __shfl_sync(0xffffffffu, my_id, a);
+        for (int s = 0; s < 32; ++s) {
+            const int32_t idb = __shfl_sync(0xffffffffu, my_id, s >> 2);
+            bsr_add(A, ida, idb, comp, s & 3, (double)acc[s], K);
+        }
     } else {
         // lane (a, comp) holds row comp of corner a's own block in acc[4a .. 4a+3]
         double blk[16];
@@ -240,7 +290,7 @@ __global__ void __launch_bounds__(128) jac_nitsche(Args A, const int32_t* __rest
     const int32_t sl = MODE == FULL ? slot[e] : 0;
     if (sl < 0) return;
     NitschePoint<T, T> V;
-    nitsche_fields<T, T, false>(A, e, xr + 3 * i, nr + 3 * i, V);
+    nitsche_fields<T, T, false>(A, e, i, xr + 3 * i, nr + 3 * i, V);
     const T w = (T)wr[i];
     const T tauB = (T)(A.Cb * (double)V.mu * taub[i]);
     for (int b = 0; b < 8; ++b) {
@@ -367,7 +417,80 @@ void launch_jac(const Mesh& m, Args A, const int32_t* slot, double* K, double* D
                                                                         m.d.sq_taub, ns, slot, K, D);
 }
 
+// k_e of the surface terms (one per host element, slot order) added to the assembled matrix
+__global__ void scatter_kmat(Args A, const int32_t* __restrict__ list, int64_t n, const double* __restrict__ Ks,
+                             double* __restrict__ val) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (element, row, column block)
+    if (t >= n * 256) return;
+    const int64_t s = t >> 8;
+    const int row = (int)((t >> 3) & 31), b = (int)(t & 7);
+    const int32_t e = list[s];
+    const int32_t ida = A.conn[8 * (int64_t)e + (row >> 2)], idb = A.conn[8 * (int64_t)e + b];
+    for (int k = 0; k < 4; ++k) bsr_add(A, ida, idb, row & 3, k, Ks[s * 1024 + row * 32 + 4 * b + k], val);
+}
+
+// rows of prescribed components become identity rows of the assembled matrix
+__global__ void bsr_strong_rows(int64_t nn, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                const uint8_t* __restrict__ flag, const uint8_t* __restrict__ umask, double* __restrict__ val) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    uint8_t mask = umask ? umask[n] : (uint8_t)(flag[n] & 15);
+    if (flag[n] & 16) mask = 15;
+    if (!mask) return;
+    for (int64_t q = ptr[n]; q < ptr[n + 1]; ++q)
+        for (int k = 0; k < 4; ++k)
+            if ((mask >> k) & 1)
+                for (int j = 0; j < 4; ++j) val[16 * q + 4 * k + j] = (idx[q] == n && j == k) ? 1.0 : 0.0;
+}
+
+template <class T>
+void launch_bsr_assembly(const Mesh& m, Args A, double* val, double* Ks, cudaStream_t s) {
+    const int64_t next = m.n_nodes() + m.n_hang();
+    T* ndv = node_workspace<T>(m, nullptr);
+    A.ndv = ndv;
+    A.ndt = ndv + 8 * next;
+    A.ndf = A.F ? ndv + 16 * next : nullptr;
+    if (next > 0) launch_node_prep<T, false>(A, ndv, ndv + 8 * next, (T*)A.ndf, s);
+    const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size(), ns = (int64_t)m.sq.size() / 10;
+    const int64_t nh = (int64_t)m.sq_hosts.size();
+    constexpr int EPB = JacShape<T>::EPB;
+    if (no > 0) jac_out<T, BSR><<<(unsigned)((no + EPB - 1) / EPB), 8 * EPB, 0, s>>>(A, m.d.out_list, no, nullptr, val, nullptr);
+    if (nc > 0) {
+        const void* pts = sizeof(T) == 4 ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
+        jac_cut<T, BSR><<<(unsigned)((nc + JWPB - 1) / JWPB), 32 * JWPB, 0, s>>>(A, m.d.cut_list, m.d.cut_off, pts, nc,
+                                                                              nullptr, val, nullptr);
+    }
+    if (ns > 0 && nh > 0) {
+        cudaMemsetAsync(m.d.slot, 0xff, (size_t)m.n_elem() * sizeof(int32_t), s);
+        fill_slots<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(nh, m.d.sq_hosts, m.d.slot);
+        cudaMemsetAsync(Ks, 0, (size_t)nh * 1024 * sizeof(double), s);
+        jac_nitsche<T, FULL><<<(unsigned)((ns + 127) / 128), 128, 0, s>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
+                                                                        m.d.sq_taub, ns, m.d.slot, Ks, nullptr);
+        scatter_kmat<<<(unsigned)((nh * 256 + 255) / 256), 256, 0, s>>>(A, m.d.sq_hosts, nh, Ks, val);
+    }
+}
+
 }  // namespace
+
+// The Jacobian assembled in 4 x 4 blocks on the mesh's block pattern: val [n_blocks][4][4] float64
+// (row component, column component), K = sum_e M_e^T k_e M_e with identity rows for the prescribed
+// components; Ks: workspace of 1024 doubles per surface-hosting element.
+int bsr_assemble(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
+                 const imga_physics& ph, int precision, const int64_t* bptr, const int32_t* bidx, double* val,
+                 double* Ks, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nb = (int64_t)m.bsr_idx.size(), nn = m.n_nodes();
+    Args A = make_args(m, u, up, up2, f, ph, nullptr, nullptr);
+    A.bptr = bptr;
+    A.bidx = bidx;
+    cudaMemsetAsync(val, 0, (size_t)nb * 16 * sizeof(double), s);
+    if (precision == 0) launch_bsr_assembly<double>(m, A, val, Ks, s);
+    else launch_bsr_assembly<float>(m, A, val, Ks, s);
+    if (nn > 0)
+        bsr_strong_rows<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, bptr, bidx, m.d.bcflag,
+                                                                    m.user_bc ? m.d.bcmask_user : nullptr, val);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
 
 int element_jacobians(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
                       const imga_physics& ph, int precision, const int32_t* elems, int64_t n, double* K, void* stream) {

@@ -91,6 +91,13 @@ __global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, 
         y[i] = a * x[i] + b * y[i];
 }
 
+// out = a x + b y + c z (out may be y)
+__global__ void lincomb3_kernel(int64_t n, double a, const double* __restrict__ x, double b, const double* y, double c,
+                                const double* __restrict__ z, double* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + b * y[i] + c * z[i];
+}
+
 __global__ void scale_copy_kernel(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a * x[i];
@@ -301,11 +308,13 @@ __global__ void __launch_bounds__(256) dg_combine(const GState* __restrict__ G, 
     }
 }
 
+constexpr int kVecs = 14;          // work vectors of n doubles
+
 struct Work {
     int m = 0;
     int64_t n = 0;
     double* V = nullptr;       // [(m+1)][n]
-    double* vec = nullptr;     // 8 vectors of n
+    double* vec = nullptr;     // kVecs vectors of n
     double* D = nullptr;       // [n_nodes][16]
     double* Dinv = nullptr;
     double* partial = nullptr; // [kRedBlocks][64]
@@ -334,7 +343,7 @@ public:
         w.m = mm;
         w.n = n;
         size_t bytes = (size_t)(mm + 1) * n * sizeof(double);
-        if (cudaMalloc((void**)&w.V, bytes) != cudaSuccess || cudaMalloc((void**)&w.vec, 8 * n * sizeof(double)) != cudaSuccess ||
+        if (cudaMalloc((void**)&w.V, bytes) != cudaSuccess || cudaMalloc((void**)&w.vec, kVecs * n * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.D, 4 * n * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.Dinv, 4 * n * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.partial, kRedBlocks * 64 * sizeof(double)) != cudaSuccess ||
@@ -400,11 +409,65 @@ public:
         return vms_apply(M, u, Up, Up2, F, P, O.precision, v, out, st);
     }
     int pmode = 0;   // preconditioner in use for the current linear solve (block-Jacobi fallback)
+    static bool learned_mode(int p) { return p == 2 || p == 3; }
     void precond(const double* x, double* y) {
+        if (pmode == 4) { multilevel_apply(M, x, y, st); return; }
         if (pmode >= 1) block_jacobi_apply(M, W.Dinv, x, y, st);
         else cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
-        if (pmode >= 2)
+        if (learned_mode(pmode))
             precond_correction(M, P, L.elems, L.n, L.C, L.scale, (float)O.learned_omega, x, L.zc, y, st);
+    }
+    void lincomb3(double a, const double* x, double b, const double* y, double c, const double* z, double* out) {
+        lincomb3_kernel<<<(unsigned)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256), 256, 0, st>>>(n, a, x, b, y, c, z, out);
+    }
+    double dot(const double* x, const double* y) {
+        double v;
+        mdot(x, 1, y, &v);
+        return v;
+    }
+
+    // BiCGStab (van der Vorst) with right preconditioning on the assembled Jacobian A: x = A^-1 b to
+    // ||b - A x|| <= rtol ||b|| (appendix "Details of solver selection"); x starts at 0
+    int bicgstab(const double* A, const double* b, double* x, double rtol, int max_its, int* its_out, double* res_out) {
+        double *r = vec(4), *rh = vec(5), *pv = vec(6), *v = vec(8), *sv = vec(9), *ph = vec(10), *sh = vec(11),
+               *t = vec(12);
+        std::string err;
+        auto Amul = [&](const double* in, double* out) { return bsr_spmv(M, A, in, out, st, err); };
+        cudaMemsetAsync(x, 0, n * sizeof(double), st);
+        cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(rh, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cudaMemsetAsync(v, 0, n * sizeof(double), st);
+        cudaMemsetAsync(pv, 0, n * sizeof(double), st);
+        const double bn = norm(b), tol = rtol * bn;
+        double res = bn, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        int it = 0;
+        if (res > tol) {
+            for (it = 1; it <= max_its; ++it) {
+                const double rho = dot(rh, r);
+                if (rho == 0.0) break;
+                const double beta = (rho / rho_old) * (alpha / omega);
+                lincomb3(1.0, r, beta, pv, -beta * omega, v, pv);
+                precond(pv, ph);
+                if (Amul(ph, v)) return 1;
+                alpha = rho / dot(rh, v);
+                axpby(1.0, r, 0.0, sv);
+                axpby(-alpha, v, 1.0, sv);
+                const double sn = norm(sv);
+                if (sn <= tol) { axpby(alpha, ph, 1.0, x); res = sn; break; }
+                precond(sv, sh);
+                if (Amul(sh, t)) return 1;
+                const double tt = dot(t, t);
+                omega = tt > 0.0 ? dot(t, sv) / tt : 0.0;
+                lincomb3(alpha, ph, 1.0, x, omega, sh, x);
+                lincomb3(1.0, sv, 0.0, sv, -omega, t, r);
+                res = norm(r);
+                if (res <= tol || omega == 0.0) break;
+                rho_old = rho;
+            }
+        }
+        *its_out = std::min(it, max_its);
+        *res_out = res;
+        return 0;
     }
 
     // learned correction: network inputs of every active element, one inference per Newton iteration
@@ -452,7 +515,7 @@ public:
 
     // ---- device-resident GMRES: one Arnoldi step per replay of a captured graph ----
     static constexpr int kChunk = 8;   // steps launched between two reads of the stop flag
-    cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t step_graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;
 
     double* dev_field(size_t off) { return reinterpret_cast<double*>(reinterpret_cast<char*>(W.G) + off); }
@@ -562,7 +625,7 @@ public:
 
     // with a learned correction in use, a restart cycle that does not halve the residual ends the
     // solve early: the caller then redoes it with block-Jacobi
-    bool stalled(double r, double r_cycle_start) const { return pmode >= 2 && r > 0.5 * r_cycle_start; }
+    bool stalled(double r, double r_cycle_start) const { return learned_mode(pmode) && r > 0.5 * r_cycle_start; }
 
     int solve(const double* u, const double* b, double* x, double rtol, int max_its, int* its_out, double* res_out) {
         if (M.use_graphs && !M.profiling) return gmres_dev(u, b, x, rtol, max_its, its_out, res_out);
@@ -663,18 +726,35 @@ public:
         int it = 0;
         for (; it < O.max_newton && it < 32; ++it) {
             if (rn <= target) break;
-            if (O.precond >= 1 &&
+            if (O.precond >= 1 && O.precond <= 3 &&
                 block_jacobi_setup(M, u, Up, Up2, F, P, O.precision, W.D, W.Dinv, st)) {
                 err = "block-Jacobi setup failed";
                 return 1;
             }
-            if (O.precond >= 2 && learned_setup(u)) { err = "learned preconditioner setup failed"; return 1; }
+            if (learned_mode(O.precond) && learned_setup(u)) { err = "learned preconditioner setup failed"; return 1; }
+            const double* Aasm = nullptr;
+            if (O.precond == 4) {
+                if (multilevel_setup(M, u, Up, Up2, F, P, O.precision, O.ml_sweeps > 0 ? O.ml_sweeps : 1,
+                                     O.ml_omega > 0.0 ? O.ml_omega : 0.5, st, err))
+                    return 1;
+                Aasm = multilevel_matrix(M);
+            } else if (O.linear_solver == 1) {
+                const int64_t* bp;
+                const int32_t* bi;
+                double* ks;
+                if (bsr_device_pattern(M, &bp, &bi, &ks, err)) return 3;
+                double* A0 = multilevel_matrix(M);
+                if (bsr_assemble(M, u, Up, Up2, F, P, O.precision, bp, bi, A0, ks, st)) { err = "assembly failed"; return 1; }
+                Aasm = A0;
+            }
             scale_copy(-1.0, R, b);
             int kits = 0;
             double kres = 0.0;
             pmode = O.precond;
-            if (solve(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
-            if (pmode >= 2 && !(kres <= O.krylov_rtol * rn * 1.0000001)) {
+            if (O.linear_solver == 1) {
+                if (bicgstab(Aasm, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "BiCGStab failed"; return 1; }
+            } else if (solve(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
+            if (learned_mode(pmode) && !(kres <= O.krylov_rtol * rn * 1.0000001)) {
                 // the correction did not bring GMRES to its tolerance: redo the solve with block-Jacobi
                 S->fallbacks += 1;
                 S->krylov_its += kits;
@@ -721,9 +801,12 @@ int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const 
     std::memset(stats, 0, sizeof(*stats));
     Solver S(m, ph, o, (cudaStream_t)stream, up, up2, f);
     if (S.alloc(err)) return 3;
-    if (o.precond >= 2 && S.learned_alloc(err)) return 3;
+    if ((o.precond == 2 || o.precond == 3) && S.learned_alloc(err)) return 3;
+    if ((o.precond == 4 || o.linear_solver == 1) &&
+        multilevel_prepare(m, o.ml_agg > 0 ? o.ml_agg : 6, o.ml_coarse_max > 0 ? o.ml_coarse_max : 16, err))
+        return 3;
     int rc = S.newton(u, stats, err);
-    if (o.precond >= 2) { cudaStreamSynchronize((cudaStream_t)stream); S.learned_free(); }
+    if (o.precond == 2 || o.precond == 3) { cudaStreamSynchronize((cudaStream_t)stream); S.learned_free(); }
     return rc;
 }
 

@@ -137,9 +137,12 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, sizeof(T) == 4 ? 4 : 2) 
             r[0] += v[0]; r[1] += v[1]; r[2] += v[2]; r[3] += v[3];
         }
         for (int k = 0; k < 4; ++k) r[k] = hadamard_bwd<1>(r[k], c);
-        // corners of this warp's 4 elements that are the same node add their rows in shared memory
-        // first; one lane per node scatters (fewer float64 atomics)
-        if constexpr (sizeof(T) == 4) {   // (float64: the plain scatter is faster)
+        if (A.sv) {
+            // deterministic scatter: node c's 4 rows into the element's slot (one 16- or 32-byte store)
+            if (valid) st4s<T>((T*)A.sv + 32 * idx + 4 * c, r[0], r[1], r[2], r[3]);
+        } else if constexpr (sizeof(T) == 4) {
+            // corners of this warp's 4 elements that are the same node add their rows in shared memory
+            // first; one lane per node scatters (fewer float64 atomics; float64: the plain scatter is faster)
             const int lane = threadIdx.x & 31;
             const unsigned grp = __match_any_sync(0xffffffffu, valid ? id_cur : -1 - lane);
             __syncwarp();   // every lane has read its moment columns
@@ -175,8 +178,12 @@ constexpr int WPB = 4;   // warps per block of the per-element surface kernel
 // sum them over the lanes (transpose through shared memory s_m [32][32 + pad]), run the backward
 // butterfly so lane 4 a + k holds row (node a, component k), and scatter node a from lane 4 a.
 // my_id: the node id of corner (lane & 7).
+// extra: a float64 addend of this lane's row (node a = lane / 4, component lane % 4).  With the
+// deterministic scatter the 32 rows go to a slot instead: vdst (element precision, volume terms)
+// or sdst (float64, surface terms), row a * 4 + k at lane 4 a + k.
 template <class T>
-__device__ __forceinline__ void warp_scatter_moments(const Args& A, const T M[32], T* s_m, int lane, int32_t my_id) {
+__device__ __forceinline__ void warp_scatter_moments(const Args& A, const T M[32], T* s_m, int lane, int32_t my_id,
+                                                     double extra = 0.0, T* vdst = nullptr, double* sdst = nullptr) {
     constexpr int MSTR = 32 + 16 / (int)sizeof(T);
     T* mrow = s_m + lane * MSTR;
     for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
@@ -185,11 +192,14 @@ __device__ __forceinline__ void warp_scatter_moments(const Args& A, const T M[32
 #pragma unroll 8
     for (int t = 0; t < 32; ++t) acc += s_m[t * MSTR + lane];
     acc = hadamard_bwd<4>(acc, lane >> 2);
+    if (vdst) { vdst[lane] = acc; return; }
+    const double row = (double)acc + extra;
+    if (sdst) { sdst[lane] = row; return; }
     const int a = lane >> 2;
-    T r[4];
-    for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(0xffffffffu, acc, (lane & ~3) + k);
+    double r[4];
+    for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(0xffffffffu, row, (lane & ~3) + k);
     const int32_t id = __shfl_sync(0xffffffffu, my_id, a);
-    if ((lane & 3) == 0) scatter_t(A, id, r);
+    if ((lane & 3) == 0) scatter(A, id, r);
 }
 
 // W warps per block (a tile shape the autotuner picks); `order` (or null) permutes the list
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(32 * W, (sizeof(T) == 4 ? 16 : 8) / W) vms_cut
         for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
         add_moments<T, false>(m, w16, M);
     }
-    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id);
+    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id, 0.0, A.sv ? (T*)A.sv + 32 * (A.n_out_slots + idx) : nullptr);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -256,16 +266,27 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
     if (i >= n) return;
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     NitschePoint<S, T> P;
-    nitsche_fields<S, T, JV>(A, el[i], xr + 3 * i, nr + 3 * i, P);
+    const int32_t e = el[i];
+    nitsche_fields<S, T, JV>(A, e, i, xr + 3 * i, nr + 3 * i, P);
     const T w = (T)wr[i];
-    const T tauB = (T)(A.Cb * (double)P.mu * taub[i]);
+    // the penalty w tau_B phi_c (u - g) in float64
+    const double wpen = wr[i] * A.Cb * Phys<double>(A, prob_of(A, e)).mu * taub[i];
+    const double* dpen = JV ? P.ddt : P.dd;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         S t[4];
-        nitsche_rows<S, T>(A, P, c, tauB, t);
-        T r[4];
-        for (int k = 0; k < 4; ++k) r[k] = w * Pick<T, JV>::get(t[k]);
-        scatter_t(A, P.ids[c], r);
+        nitsche_rows<S, T, false>(A, P, c, T(0), t);
+        const double pc = wpen * P.phid[c];
+        double r[4];
+        for (int k = 0; k < 4; ++k) r[k] = (double)(w * Pick<T, JV>::get(t[k]));
+        for (int k = 0; k < 3; ++k) r[k] = fma(pc, dpen[k], r[k]);
+        if (A.ss) {
+            double* d = A.ss + 32 * (A.n_dense_slots + i) + 4 * c;
+            reinterpret_cast<double2*>(d)[0] = make_double2(r[0], r[1]);
+            reinterpret_cast<double2*>(d)[1] = make_double2(r[2], r[3]);
+        } else {
+            scatter(A, P.ids[c], r);
+        }
     }
 }
 
@@ -290,23 +311,28 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     if (idx >= n) return;
     const int32_t e = list[idx];
-    // corner rows: u_s (0-2), p (3), jump d = u_s - g formed in float64 (4-6), tangents at CT
+    // corner rows: u_s (0-2), p (3), jump d = u_s - g_body formed in float64 (4-6), tangents at CT;
+    // s_pd: the float64 monomial coefficients of the jump (or, for J v, of its tangent theta v)
+    __shared__ __align__(16) double s_pd[WPB][8][3];
     const int c8 = lane & 7;
     const int32_t my_id = A.conn[8 * (int64_t)e + c8];
     {
         T a8[8], t8[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         ld8<T>(A.ndv, my_id, a8);
         if (JV) ld8<T>(A.ndt, my_id, t8);
-        double u4[4], up4[4];
+        double u4[4], up4[4], v4[4];
         gather(A, A.U, my_id, u4);
         if (!A.theta1) gather(A, A.Up, my_id, up4);
+        if (JV) gather(A, A.V, my_id, v4);
         T rw[CS];
+        double pd[3];
         for (int k = 0; k < 3; ++k) {
             const double usk = A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
             rw[k] = a8[k];
             rw[4 + k] = (T)(usk - A.g[k]);
             rw[CT + k] = t8[k];
             rw[CT + 4 + k] = t8[k];
+            pd[k] = hadamard_fwd(JV ? A.theta * v4[k] : usk - A.g[k], c8);
         }
         rw[3] = a8[3];
         rw[CT + 3] = t8[3];
@@ -317,6 +343,7 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
             for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + j] = rw[j];
             if (JV)
                 for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + CT + j] = rw[CT + j];
+            for (int k = 0; k < 3; ++k) s_pd[w][lane][k] = pd[k];
         }
     }
     __syncwarp();
@@ -327,13 +354,20 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         mu = Ph.mu;
         rho = Ph.rho;
     }
-    const double Cbmu = A.Cb * (double)mu;
+    const double Cbmu = A.Cb * Phys<double>(A, prob_of(A, e)).mu;
     T M[32];
     for (int k = 0; k < 32; ++k) M[k] = T(0);
     const int64_t q0 = off[idx], q1 = off[idx + 1];
     for (int64_t q = q0 + lane; q < q1; q += 32) {
         T xi[3], nn[3], m[8];
         for (int k = 0; k < 3; ++k) { xi[k] = (T)xr[3 * q + k]; nn[k] = (T)nr[3 * q + k]; }
+        // the jump relative to g_body at the corners, corrected to this point's g (its value enters
+        // the tangent of the inflow term)
+        T dg[3] = {T(0), T(0), T(0)};
+        if (A.gpts) {
+            const double* gq = point_g(A, q);
+            for (int k = 0; k < 3; ++k) dg[k] = (T)(A.g[k] - gq[k]);
+        }
         monomials<T>(xi, m);
         // u_s, grad u_s, p, d at the point
         S us[3], Gu[3][3], p, d[3];
@@ -353,18 +387,19 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
                 if (t & (1 << k))
                     for (int i = 0; i < 3; ++i) Gu[i][k] = madd(m[t ^ (1 << k)], a[i], Gu[i][k]);
         }
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i) {
+            d[i] = d[i] + dg[i];
             for (int j = 0; j < 3; ++j) Gu[i][j] = g * Gu[i][j];
+        }
         const S un = mmadd(us[2], S(make<S, T>(nn[2], T(0))), mmadd(us[1], S(make<S, T>(nn[1], T(0))), us[0] * nn[0]));
         const S dn = madd(nn[2], d[2], madd(nn[1], d[1], nn[0] * d[0]));
         const bool inflow = value(un) < T(0);
-        const T tauB = (T)(Cbmu * taub[q]);
         const T wq = (T)wr[q], wqg = wq * g;
         T c[16];
         for (int k = 0; k < 3; ++k) {
             S tr = (-nn[k]) * p;
             for (int j = 0; j < 3; ++j) tr = madd(mu * nn[j], Gu[k][j] + Gu[j][k], tr);
-            S fk = tauB * d[k] - tr;
+            S fk = T(-1) * tr;
             if (inflow) fk = fk - rho * (un * d[k]);
             c[k] = wq * Pick<T, JV>::get(fk);
             for (int j = 0; j < 3; ++j) c[3 + 3 * k + j] = (-wqg * mu) * Pick<T, JV>::get(madd(nn[j], d[k], nn[k] * d[j]));
@@ -373,7 +408,40 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         c[13] = c[14] = c[15] = T(0);
         add_moments<T, false>(m, c, M);
     }
-    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id);
+    // penalty w tau_B phi_c (u - g) in float64: moments P[S][k] = sum_q w tau_B m_S (u - g)_k
+    double Pm[24];
+    for (int k = 0; k < 24; ++k) Pm[k] = 0.0;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+        double md[8];
+        monomials<double>(xr + 3 * q, md);
+        double dq[3];
+        const double* gq = point_g(A, q);
+        for (int k = 0; k < 3; ++k) dq[k] = JV ? 0.0 : A.g[k] - gq[k];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            for (int k = 0; k < 3; ++k) dq[k] = fma(md[t], s_pd[w][t][k], dq[k]);
+        const double cq = wr[q] * Cbmu * taub[q];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const double ct = cq * md[t];
+            for (int k = 0; k < 3; ++k) Pm[3 * t + k] = fma(ct, dq[k], Pm[3 * t + k]);
+        }
+    }
+    // sum over the lanes; lane 4 a + k (k < 3) takes corner a's value sum_S sigma_{a,S} P[S][k]
+#pragma unroll
+    for (int k = 0; k < 24; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Pm[k] += __shfl_xor_sync(0xffffffffu, Pm[k], o);
+    double pen = 0.0;
+    {
+        const int a = lane >> 2, kk = lane & 3;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const double pk = kk == 0 ? Pm[3 * t] : kk == 1 ? Pm[3 * t + 1] : kk == 2 ? Pm[3 * t + 2] : 0.0;
+            pen += ((__popc(t & ~a) & 1) ? -1.0 : 1.0) * pk;
+        }
+    }
+    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id, pen, nullptr, A.ss ? A.ss + 32 * idx : nullptr);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -404,15 +472,87 @@ __global__ void strong_rows(Args A, const uint8_t* __restrict__ flag, const uint
         if ((mask >> k) & 1) A.out[4 * n + k] = jv ? src[4 * n + k] : src[4 * n + k] - gv[k];
 }
 
-// optional event pair around a launch (profiling)
+// float-float accumulation on the FP32 pipe (Knuth's TwoSum): hi + lo carries the sum of floats to
+// about 48 bits, in a fixed order
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// Deterministic o2n (Algorithm 2): every independent node sums the slot rows of its incidence list in
+// list order (a hanging corner's rows times 1/2 or 1/4 for each parent), then its strong rows take
+// U - g (R) or v (J v) as in strong_rows.  Writes every row of out: no zeroing before the call.
+template <class T>
+__global__ void __launch_bounds__(256) node_gather(Args A, const int64_t* __restrict__ ptr,
+                                                   const uint64_t* __restrict__ inc, int64_t nv,
+                                                   const uint8_t* __restrict__ flag, const uint8_t* __restrict__ umask,
+                                                   const double* __restrict__ uval, double ux, double uy, double uz,
+                                                   int jv) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= A.n_nodes) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t q = ptr[n], q1 = ptr[n + 1]; q < q1; ++q) {
+        const uint64_t e = inc[q];
+        const int c = (int)(e & 7), wc = (int)((e >> 3) & 3);
+        const int64_t s = (int64_t)(e >> 5);
+        if (s < nv) {
+            T v[4];
+            ld4<T>((const T*)A.sv + 32 * s, c, v);
+            const T w = wc == 0 ? T(1) : (wc == 1 ? T(0.5) : T(0.25));
+            if constexpr (sizeof(T) == 4) {
+                for (int k = 0; k < 4; ++k) ff_add(hi[k], lo[k], w * v[k]);
+            } else {
+                for (int k = 0; k < 4; ++k) acc[k] += w * v[k];
+            }
+        } else {
+            const double* d = A.ss + 32 * (s - nv) + 4 * c;
+            const double2 a = reinterpret_cast<const double2*>(d)[0], b = reinterpret_cast<const double2*>(d)[1];
+            const double w = wc == 0 ? 1.0 : (wc == 1 ? 0.5 : 0.25);
+            acc[0] += w * a.x; acc[1] += w * a.y; acc[2] += w * b.x; acc[3] += w * b.y;
+        }
+    }
+    if constexpr (sizeof(T) == 4)
+        for (int k = 0; k < 4; ++k) acc[k] += f2d(hi[k]) + f2d(lo[k]);
+    // strong rows (as strong_rows)
+    const uint8_t f = flag[n];
+    uint8_t mask;
+    double gv[4];
+    if (umask) {
+        mask = umask[n];
+        for (int k = 0; k < 4; ++k) gv[k] = uval[4 * n + k];
+    } else {
+        mask = f & 15;
+        gv[0] = ux; gv[1] = uy; gv[2] = uz; gv[3] = 0.0;
+    }
+    if (f & 16) {
+        for (int k = 0; k < 4; ++k)
+            if (!((mask >> k) & 1)) { mask |= (uint8_t)(1 << k); gv[k] = k < 3 ? A.g[k] : 0.0; }
+    }
+    if (mask) {
+        const double* src = jv ? A.V : A.U;
+        for (int k = 0; k < 4; ++k)
+            if ((mask >> k) & 1) acc[k] = jv ? src[4 * n + k] : src[4 * n + k] - gv[k];
+    }
+    double2* o = reinterpret_cast<double2*>(A.out + 4 * n);
+    o[0] = make_double2(acc[0], acc[1]);
+    o[1] = make_double2(acc[2], acc[3]);
+}
+
+// optional event pair around a launch (profiling); never for calls on a caller's workspace
+// (imga_jvp_noalloc), which create no events and leave the mesh untouched
 struct Timed {
     Mesh* m;
     int k, nk;
     cudaStream_t s;
     cudaEvent_t a = nullptr, b = nullptr;
-    Timed(const Mesh& mesh, int kind, cudaStream_t st, int launches = 1)
+    Timed(const Mesh& mesh, int kind, cudaStream_t st, int launches = 1, bool enable = true)
         : m(const_cast<Mesh*>(&mesh)), k(kind), nk(launches), s(st) {
-        if (!m->profiling) return;
+        if (!enable || !m->profiling) return;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
         cudaEventRecord(a, s);
@@ -515,7 +655,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     A.ndt = ndt;
     A.ndf = ndf;
     if (next > 0) {
-        Timed t(m, 4, s, (A.n_nodes > 0) + (A.n_hang > 0));
+        Timed t(m, 4, s, (A.n_nodes > 0) + (A.n_hang > 0), !ws);
         launch_node_prep<T, JV>(A, ndv, ndt, ndf, s);
     }
     // fork: the Intercepted-element and surface kernels run beside the Out-element kernel
@@ -528,7 +668,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     const int64_t no = (int64_t)m.out_list.size(), nc = (int64_t)m.cut_list.size();
     constexpr int EPB = Epb<T>::value;
     if (no > 0) {
-        Timed t(m, 0, s);
+        Timed t(m, 0, s, 1, !ws);
         const int bps = interior_blocks_per_sm<T, JV>();
         const size_t smem = IntShape<T>::smem;
         const int64_t groups = (no + EPB - 1) / EPB;
@@ -536,18 +676,18 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, smem, s>>>(A, m.d.out_conn, m.d.out_lev, m.d.out_prob, no);
     }
     if (nc > 0) {
-        Timed t(m, 1, sc);
+        Timed t(m, 1, sc, 1, !ws);
         const Mesh::CutTune& ct = m.cut_tune[sizeof(T) == 4][JV];
         launch_cut<T, JV>(m, A, sc, ct.wpb, ct.lpt);
     }
     const int64_t nsp = m.n_sq_sparse, nse = m.n_sq_elem;
     if (nsp > 0) {
-        Timed t(m, 2, ss);
+        Timed t(m, 2, ss, 1, !ws);
         nitsche<T, JV><<<(unsigned)((nsp + 127) / 128), 128, 0, ss>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
                                                                       m.d.sq_taub, nsp);
     }
     if (nse > 0) {
-        Timed t(m, 2, ss);
+        Timed t(m, 2, ss, 1, !ws);
         nitsche_el<T, JV><<<(unsigned)((nse + WPB - 1) / WPB), 32 * WPB, 0, ss>>>(A, m.d.sq_list, m.d.sq_off, m.d.sq_x,
                                                                                 m.d.sq_n, m.d.sq_w, m.d.sq_taub, nse);
     }
@@ -559,9 +699,23 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     }
 }
 
-void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bool jv, cudaStream_t s) {
+// strong rows; with the deterministic scatter, the node sums (which write every row) and the strong rows
+void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bool jv, cudaStream_t s,
+                        bool timed = true, int precision = 0) {
     const int64_t nn = m.n_nodes();
-    Timed t(m, 3, s);
+    Timed t(m, 3, s, 1, timed);
+    if (nn > 0 && A.sv) {
+        const uint8_t* um = m.user_bc ? m.d.bcmask_user : nullptr;
+        const double* uv = m.user_bc ? m.d.bcval_user : nullptr;
+        const unsigned g = (unsigned)((nn + 255) / 256);
+        if (precision == 0)
+            node_gather<double><<<g, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
+                                                  ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
+        else
+            node_gather<float><<<g, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
+                                                 ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
+        return;
+    }
     if (nn > 0)
         strong_rows<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(A, m.d.bcflag, m.user_bc ? m.d.bcmask_user : nullptr,
                                                                 m.user_bc ? m.d.bcval_user : nullptr, ph.u_inf[0],
@@ -620,13 +774,13 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
             else { interior_blocks_per_sm<float, true>(); interior_blocks_per_sm<float, false>(); }
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return 1;
-            cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), cs);
+            if (!A.sv) cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), cs);
             if (precision == 0) {
                 if (jv) launch_all<double, true>(m, A, cs, nullptr, s1, s2, ev); else launch_all<double, false>(m, A, cs, nullptr, s1, s2, ev);
             } else {
                 if (jv) launch_all<float, true>(m, A, cs, nullptr, s1, s2, ev); else launch_all<float, false>(m, A, cs, nullptr, s1, s2, ev);
             }
-            launch_strong_rows(m, A, ph, jv, cs);
+            launch_strong_rows(m, A, ph, jv, cs, true, precision);
             const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
             if (ec != cudaSuccess || !graph) return 1;
             const cudaError_t rc = cudaGraphInstantiate(&exec, graph, 0);
@@ -643,14 +797,61 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
         if (cudaEventRecord(ev[4], cs) != cudaSuccess || cudaStreamWaitEvent(s, ev[4], 0) != cudaSuccess) return 1;
         return 0;
     }
-    if (cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
+    if (!A.sv && cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
     if (precision == 0) {
         if (jv) launch_all<double, true>(m, A, s, ws); else launch_all<double, false>(m, A, s, ws);
     } else {
         if (jv) launch_all<float, true>(m, A, s, ws); else launch_all<float, false>(m, A, s, ws);
     }
-    launch_strong_rows(m, A, ph, jv, s);
+    launch_strong_rows(m, A, ph, jv, s, !ws, precision);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Force of the fluid on the body: the surface terms of Eq. (weakbc) tested with w = e_i, i.e. summed
+// over every node's momentum rows (partition of unity), in float64.  Per surface point
+//   w_q [ -(sigma(u_s, p) n)_i - [u.n < 0] rho (u.n) (u - g)_i + tau_B (u - g)_i ],
+// n the fluid-outward normal: the force that keeps the discrete momentum balance of weak Dirichlet
+// conditions.  Each block sums its points in a fixed order, then one block sums the partials in
+// block order (same bits on every call).
+// ------------------------------------------------------------------------------------------
+constexpr int kForceBlocks = 256;
+
+__global__ void __launch_bounds__(256) surface_force_partial(Args A, const int32_t* __restrict__ el,
+                                                             const double* __restrict__ xr, const double* __restrict__ nr,
+                                                             const double* __restrict__ wr, const double* __restrict__ taub,
+                                                             int64_t n, double* __restrict__ part) {
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        NitschePoint<double, double> P;
+        nitsche_fields<double, double, false>(A, el[i], i, xr + 3 * i, nr + 3 * i, P);
+        const double tauB = A.Cb * P.mu * taub[i];
+        for (int k = 0; k < 3; ++k) {
+            double t = -P.tr[k] + tauB * P.dd[k];
+            if (P.inflow) t -= P.rho * P.un * P.dd[k];
+            f[k] += wr[i] * t;
+        }
+    }
+    __shared__ double red[3][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 3; ++k) {
+        double v = f[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) v += red[threadIdx.x][j];
+        part[3 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+__global__ void surface_force_final(int nb, const double* __restrict__ part, double* __restrict__ F) {
+    if (threadIdx.x >= 3) return;
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) v += part[3 * b + threadIdx.x];
+    F[threadIdx.x] = v;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -716,13 +917,13 @@ int vms_apply_skip(const Mesh& m, const double* u, const double* up, const doubl
     Args A = make_args(m, u, up, up2, f, ph, v, out);
     A.skip = skip;
     const bool jv = v != nullptr;
-    if (cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
+    if (!A.sv && cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
     if (precision == 0) {
         if (jv) launch_all<double, true>(m, A, s); else launch_all<double, false>(m, A, s);
     } else {
         if (jv) launch_all<float, true>(m, A, s); else launch_all<float, false>(m, A, s);
     }
-    launch_strong_rows(m, A, ph, jv, s);
+    launch_strong_rows(m, A, ph, jv, s, true, precision);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -776,6 +977,25 @@ int vms_jvp_noalloc(const Mesh& m, const double* u, const double* up, const doub
     }
     if (vms_apply_ws(m, u, up, up2, f, ph, precision, v, out, stream, ws)) { err = "launch failed"; return 1; }
     return 0;
+}
+
+// F [3] (device) = force of the fluid on the body at the state (u, u_prev); part: kForceBlocks x 3
+// doubles of workspace
+int surface_force(const Mesh& m, const double* u, const double* up, const imga_physics& ph, double* F, double* part,
+                  void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    Args A = make_args(m, u, up, up, nullptr, ph, nullptr, nullptr);
+    const int64_t next = m.n_nodes() + m.n_hang();
+    double* ndv = node_workspace<double>(m, nullptr);
+    A.ndv = ndv;
+    A.ndt = ndv + 8 * next;
+    A.ndf = nullptr;
+    if (next > 0) launch_node_prep<double, false>(A, ndv, ndv + 8 * next, nullptr, s);
+    const int64_t ns = (int64_t)m.sq.size() / 10;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kForceBlocks, (ns + 255) / 256));
+    surface_force_partial<<<nb, 256, 0, s>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w, m.d.sq_taub, ns, part);
+    surface_force_final<<<1, 32, 0, s>>>(nb, part, F);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
 void profile_reset(Mesh& m) {

@@ -133,6 +133,8 @@ struct Args {
     double CI3;
     double Cb;
     double g[3];
+    const double* gpts;                   // g per surface point [n][3] in export order, or null: g
+    const int32_t* sq_src;                // export position of every surface point (device order)
     int drop_visc;
     // batched meshes: element -> problem and the viscosity of every problem (null: the scalars)
     const uint16_t* eprob;
@@ -140,6 +142,15 @@ struct Args {
     const float* pmuf;
     double CI;
     float CIf;
+    // assembled-matrix block pattern (element-Jacobian assembly only)
+    const int64_t* bptr;
+    const int32_t* bidx;
+    // deterministic scatter: element contributions go to slots (sv: volume, element precision;
+    // ss: surface, float64) instead of atomic additions into out; null: atomics
+    void* sv;
+    double* ss;
+    int64_t n_out_slots;                  // volume slots of the Out elements (Intercepted ones follow)
+    int64_t n_dense_slots;                // surface slots of the dense bucket (sparse points follow)
 };
 
 // node values through the hanging-node interpolation (u_e = M_e U)
@@ -745,7 +756,14 @@ struct NitschePoint {
     int32_t ids[8];
     S us[3], Gu[3][3], p, d[3], un, dn, tr[3];
     bool inflow;
+    // float64 copies for the penalty: basis values, the jump u_s - g and (J v) its tangent theta v
+    double phid[8], dd[3], ddt[3];
 };
+
+// g of Eq. (weakbc) at surface point q (device order)
+__device__ __forceinline__ const double* point_g(const Args& A, int64_t q) {
+    return A.gpts ? A.gpts + 3 * (int64_t)A.sq_src[q] : A.g;
+}
 
 template <class S, class T>
 __device__ __forceinline__ void finish_nitsche(const Args& A, NitschePoint<S, T>& P) {
@@ -760,11 +778,21 @@ __device__ __forceinline__ void finish_nitsche(const Args& A, NitschePoint<S, T>
                            (P.Gu[k][2] + P.Gu[2][k]) * nn[2]) - P.p * nn[k];
 }
 
-// u_s, p and grad u_s from the node data; the velocity jump d = u_s - g from corner values formed
-// in float64 (the penalty multiplies it by tau_B, up to 100 C_b mu / h on sliver cut cells).
+// Q1 basis values in float64 at reference point xi (corner c = bits along x, y, z)
+__device__ __forceinline__ void basis_values_d(const double* xi, double phi[8]) {
+    double fm[3], fp[3];
+    for (int k = 0; k < 3; ++k) { fm[k] = 0.5 * (1.0 - xi[k]); fp[k] = 0.5 * (1.0 + xi[k]); }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) phi[c] = ((c & 1) ? fp[0] : fm[0]) * ((c & 2) ? fp[1] : fm[1]) * ((c & 4) ? fp[2] : fm[2]);
+}
+
+// u_s, p and grad u_s from the node data at surface point q (device order).  The velocity jump
+// d = u_s - g is formed in float64 from the float64 nodal values at the point: the penalty multiplies
+// it by tau_B, up to 100 C_b mu / h on sliver cut cells.  For J v, ddt is its tangent theta v in
+// float64.
 template <class S, class T, bool JV>
-__device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, const double* xr, const double* nr,
-                                               NitschePoint<S, T>& P) {
+__device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, int64_t q, const double* xr,
+                                               const double* nr, NitschePoint<S, T>& P) {
     P.g = lvl_g<T>(A, A.lev[e]);
     {
         const Phys<T> Ph(A, prob_of(A, e));
@@ -774,8 +802,12 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, const d
     T xi[3] = {(T)xr[0], (T)xr[1], (T)xr[2]};
     for (int k = 0; k < 3; ++k) P.nn[k] = (T)nr[k];
     basis<T>(xi, P.B);
+    basis_values_d(xr, P.phid);
+    const double* gq = point_g(A, q);
     P.p = zero<S>();
-    for (int k = 0; k < 3; ++k) { P.us[k] = zero<S>(); P.d[k] = zero<S>(); for (int j = 0; j < 3; ++j) P.Gu[k][j] = zero<S>(); }
+    double us_d[3] = {0.0, 0.0, 0.0};
+    T dtan[3] = {T(0), T(0), T(0)};
+    for (int k = 0; k < 3; ++k) { P.us[k] = zero<S>(); P.ddt[k] = 0.0; for (int j = 0; j < 3; ++j) P.Gu[k][j] = zero<S>(); }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         P.ids[c] = A.conn[8 * (int64_t)e + c];
@@ -785,30 +817,41 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, const d
         double u4[4], up4[4];
         gather(A, A.U, P.ids[c], u4);
         if (!A.theta1) gather(A, A.Up, P.ids[c], up4);
+        if (JV) {
+            double v4[4];
+            gather(A, A.V, P.ids[c], v4);
+            for (int k = 0; k < 3; ++k) P.ddt[k] = fma(P.phid[c], A.theta * v4[k], P.ddt[k]);
+        }
         const T ph = P.B.phi[c];
         for (int k = 0; k < 3; ++k) {
             S vu = make<S, T>(a8[k], t8[k]);
-            double usk = A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
-            S jump = make<S, T>((T)(usk - A.g[k]), t8[k]);
+            const double usk = A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
+            us_d[k] = fma(P.phid[c], usk, us_d[k]);
+            dtan[k] = dtan[k] + ph * t8[k];
             P.us[k] = P.us[k] + ph * vu;
-            P.d[k] = P.d[k] + ph * jump;
             for (int j = 0; j < 3; ++j) P.Gu[k][j] = P.Gu[k][j] + P.B.dphi[c][j] * vu;
         }
         P.p = P.p + ph * make<S, T>(a8[3], t8[3]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        P.dd[k] = us_d[k] - gq[k];
+        P.d[k] = make<S, T>((T)P.dd[k], dtan[k]);
     }
     finish_nitsche(A, P);
 }
 
 // the 4 rows of corner c (test functions phi_c e_i and q = phi_c), not yet times the weight;
-// tau_TAN = tau_NOR: both penalty parts sum to tau_B (u - g)
-template <class S, class T>
+// tau_TAN = tau_NOR: both penalty parts sum to tau_B (u - g).  PEN = false leaves the penalty out
+// (the residual and J v kernels add it in float64).
+template <class S, class T, bool PEN = true>
 __device__ __forceinline__ void nitsche_rows(const Args& A, const NitschePoint<S, T>& P, int c, T tauB, S t[4]) {
     const T ph = P.B.phi[c];
     const T* nn = P.nn;
     const T gn = P.g * (P.B.dphi[c][0] * nn[0] + P.B.dphi[c][1] * nn[1] + P.B.dphi[c][2] * nn[2]);
     S gd = P.g * (P.B.dphi[c][0] * P.d[0] + P.B.dphi[c][1] * P.d[1] + P.B.dphi[c][2] * P.d[2]);
     for (int k = 0; k < 3; ++k) {
-        S v = (tauB * ph) * P.d[k] - ph * P.tr[k] - P.mu * (gn * P.d[k] + nn[k] * gd);
+        S v = T(-1) * (ph * P.tr[k] + P.mu * (gn * P.d[k] + nn[k] * gd));
+        if (PEN) v = v + (tauB * ph) * P.d[k];
         if (P.inflow) v = v - (ph * P.rho) * (P.un * P.d[k]);
         t[k] = v;
     }
@@ -863,12 +906,20 @@ inline Args make_args(const Mesh& m, const double* u, const double* up, const do
     A.CI3f = (float)A.CI3;
     A.Cb = ph.C_b;
     for (int k = 0; k < 3; ++k) A.g[k] = ph.g_body[k];
+    A.gpts = ph.g_points;
+    A.sq_src = m.d.sq_src;
     A.drop_visc = ph.drop_visc_strong;
     A.eprob = m.d.eprob;
     A.pmu = m.d.pmu;
     A.pmuf = m.d.pmuf;
     A.CI = ph.C_I;
     A.CIf = (float)ph.C_I;
+    A.bptr = nullptr;
+    A.bidx = nullptr;
+    A.sv = m.deterministic ? m.d.sv : nullptr;
+    A.ss = m.deterministic ? m.d.ss : nullptr;
+    A.n_out_slots = (int64_t)m.out_list.size();
+    A.n_dense_slots = m.n_sq_elem;
     return A;
 }
 

@@ -137,4 +137,6 @@ def test_graph_replayed_gmres_matches_host_driven(sphere, dev, prec):
     finally:
         g.use_graphs(False)
     assert out[True]["newton_its"] == out[False]["newton_its"]
-    assert abs(out[True]["krylov_its"] - out[False]["krylov_its"]) <= 0.05 * out[False]["krylov_its"] + 5, out
+    # J v is bitwise reproducible (deterministic scatter); the two drivers differ only in where the
+    # Givens rotations and reductions are computed (host against device arithmetic)
+    assert abs(out[True]["krylov_its"] - out[False]["krylov_its"]) <= 0.02 * out[False]["krylov_its"] + 2, out
