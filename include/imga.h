@@ -331,6 +331,48 @@ imga_status imga_newton_step(imga_mesh mesh, double* u_inout, const double* u_pr
                              const double* f, const imga_physics* phys, const imga_solver_opts* opts,
                              imga_solver_stats* stats, void* stream);
 
+/* n_steps time steps of the scheme of phys (Sec. "Validation: flow past a sphere": the sphere is run in
+ * time and its drag recorded): every step solves R(u^{n+1}; u^n, u^{n-1}) = 0 by imga_newton_step with
+ * `opts`, starting from u^n, then shifts the levels; BDF2 takes backward Euler for its first step.
+ * u (in: u^n, out: the last level) and u_prev (in: u^{n-1}, ignored by the first step; out: the level
+ * before the last) are DEVICE [n_nodes][4].  force_hist (host [n_steps][3], may be NULL) receives
+ * imga_surface_force after every step, newton_hist / krylov_hist (host [n_steps], may be NULL) the
+ * iterations.  Synchronous; allocates two node vectors for the call.  Returns IMGA_ERR_NOT_CONVERGED
+ * after the first step whose Newton solve misses its tolerance (histories filled up to it). */
+imga_status imga_time_steps(imga_mesh mesh, double* u, double* u_prev, const double* f, const imga_physics* phys,
+                            const imga_solver_opts* opts, int n_steps, double* force_hist, int* newton_hist,
+                            int* krylov_hist, void* stream);
+
+/* ---- weighted partition into k parts with halo exchange -------------------------------------------
+ * Sec. "Partitioning": the Morton order of the elements is cut into k contiguous ranges of equal total
+ * weight under Eq. (Wpart), W(e) = n_Vgp(e)/8 + (T_s/T_v) n_Sgp(e)/8 (volume points evaluated: 8 for
+ * Out, the kept sub-cell points for Intercepted, 0 for In; n_Sgp its surface points), ts_over_tv the
+ * measured cost ratio T_s/T_v.  Part p owns the nodes it is the lowest part to touch through M_e and
+ * keeps the other nodes its elements touch as ghosts (the ghost layer of Sec. "Octree based Mesh
+ * Generation").  imga_partition_residual / imga_partition_jvp compute imga_residual / imga_jvp as k
+ * parts on this GPU with the data flow of a multi-GPU step: owned rows in, halo gather of the ghost
+ * rows through explicit send / receive buffers, the element kernels of each part on its own sub-mesh,
+ * halo reduce-add of the ghost rows into their owners (in part order, prescribed components skipped),
+ * owned rows out.  Vectors are the global DEVICE [n_nodes][4] ones.  On a mesh built host-only the
+ * partition holds the split and the halo lists only (unit weights; the compute calls refuse it).
+ * Refused: batched meshes, meshes with imga_set_dirichlet rows, physics with g_points.  The partition
+ * reads the mesh, which must outlive it. */
+typedef struct imga_partition_s* imga_partition;
+imga_status imga_partition_build(imga_mesh mesh, int k, double ts_over_tv, imga_partition* out);
+void imga_partition_destroy(imga_partition part);
+/* *k parts; host arrays (each may be NULL): elem_off [k + 1] element ranges, weight [k] their Eq.
+ * (Wpart) weight, n_owned [k], n_ghost [k] */
+imga_status imga_partition_info(imga_partition part, int* k, int64_t* elem_off, double* weight, int64_t* n_owned,
+                                int64_t* n_ghost);
+/* part p's nodes (host int64 [n_owned + n_ghost], global indices, owned first) and the owning part of
+ * each ghost (host int32 [n_ghost]); either may be NULL */
+imga_status imga_partition_nodes(imga_partition part, int p, int64_t* nodes, int32_t* ghost_owner);
+imga_status imga_partition_residual(imga_partition part, const double* u, const double* u_prev, const double* u_prev2,
+                                    const double* f, const imga_physics* phys, int precision, double* R, void* stream);
+imga_status imga_partition_jvp(imga_partition part, const double* u, const double* u_prev, const double* u_prev2,
+                               const double* f, const imga_physics* phys, int precision, const double* v, double* Jv,
+                               void* stream);
+
 /* ---- learned block preconditioner -------------------------------------------------------------
  * A 3-layer MLP (ReLU, widths n_in -> width -> width -> n_out) with BF16 weights and activations on
  * the tensor cores, FP32 accumulation and FP32 master weights, trained by Adam on the mean squared

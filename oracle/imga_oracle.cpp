@@ -52,6 +52,9 @@
 #include <unordered_map>
 #include <unordered_set>
 #include <string>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -422,6 +425,7 @@ double elem_h(const Mesh& m, int e) { return (double)osize(m.lev[e]) * m.scale; 
 // triangles can all put the point behind them.  A larger B_T only turns decisions into ray
 // casts, never into other decisions.
 double g_bt_pad = 1e-2;
+int g_threads = 1;   // threads of the element loop of or_residual_jvp (or_set_threads)
 
 const std::vector<int>& get_bt(Geom& g, int e) {
     if (!g.bt_done[e]) {
@@ -1148,6 +1152,9 @@ int or_set_surface_velocity(void* s, const double* g, int64_t n) {
     return 0;
 }
 
+// threads of the element loop of or_residual_jvp (default 1); the CPU baseline times it on all cores
+void or_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
 // test knob: the widening of B_T as a fraction of the element edge; it applies to the elements whose
 // B_T is computed after the call, so set it before building the mesh it is meant for
 void or_set_bt_pad(double pad) { g_bt_pad = pad; }
@@ -1222,15 +1229,38 @@ int residual_jvp_impl(void* s, const double* physv, const double* U, const doubl
     const double* VV = V ? V : zero4.data();
     const double* UP2 = Up2 ? Up2 : Up;
     static const std::vector<int> none;
-    g.nevals = 0;
+    // geometry of the selected elements first (markers, sub-cell points): computed once and cached,
+    // so the element loop below only reads it; active nodes and the element count
+    std::vector<int> act;
     for (int e : elems) {
         compute_marker(g, e);
         if (g.marker[e] == 1) continue;
-        ++g.nevals;
+        if (g.marker[e] == 2) compute_cut(g, e);
+        act.push_back(e);
         for (int c = 0; c < 8; ++c) {
             int id = m.conn[e][c];
             if (id < Nni) active[id] = 1;
             else for (int p = 0; p < m.hnp[id - Nni]; ++p) active[m.hpar[id - Nni][p]] = 1;
+        }
+    }
+    g.nevals = (int64_t)act.size();
+    // the element loop: one element at a time, scattered into the thread's own vectors when several
+    // threads run (g_threads, default 1), which are then added in thread order
+    const int nth = std::max(1, g_threads);
+    std::vector<std::vector<double>> Rt(nth > 1 ? nth : 0), Jt(nth > 1 ? nth : 0);
+#pragma omp parallel for num_threads(nth) schedule(dynamic, 64)
+    for (size_t i = 0; i < act.size(); ++i) {
+        const int e = act[i];
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* Rd = Rv.data();
+        double* Jd = Jv.data();
+        if (nth > 1) {
+            if (Rt[tid].empty()) { Rt[tid].assign(Nn * 4, 0.0); Jt[tid].assign(Nn * 4, 0.0); }
+            Rd = Rt[tid].data();
+            Jd = Jt[tid].data();
         }
         double ue[8][4], ve[8][4], upe[8][4], up2e[8][4], fe[8][4];
         gather(m, e, U, 4, ue);
@@ -1244,8 +1274,12 @@ int residual_jvp_impl(void* s, const double* physv, const double* U, const doubl
         double rv[8][4], rd[8][4];
         for (int a = 0; a < 8; ++a)
             for (int k = 0; k < 4; ++k) { rv[a][k] = value_of(r[a][k]); rd[a][k] = deriv_of(r[a][k]); }
-        scatter(m, e, rv, Rv.data());
-        scatter(m, e, rd, Jv.data());
+        scatter(m, e, rv, Rd);
+        scatter(m, e, rd, Jd);
+    }
+    for (int t = 0; t < (int)Rt.size(); ++t) {
+        if (Rt[t].empty()) continue;
+        for (size_t q = 0; q < Nn * 4; ++q) { Rv[q] += Rt[t][q]; Jv[q] += Jt[t][q]; }
     }
     // strong rows: box Dirichlet (u = u_inf on all faces but the outlet x = hi, p = 0 on the
     // outlet) or the caller's override; then nodes touched by no active element (In-only

@@ -24,7 +24,8 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_OUT), exist_ok=True)
         tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp,
+                               _SRC])
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -52,6 +53,7 @@ def lib():
         L.or_surface_points.restype = i64
         L.or_counters.argtypes = [vp, C.c_void_p]
         L.or_set_bt_pad.argtypes = [C.c_double]
+        L.or_set_threads.argtypes = [i32]
         L.or_surface_force.argtypes = [vp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_set_dirichlet.argtypes = [vp, C.c_void_p, C.c_void_p]
         L.or_set_surface_velocity.argtypes = [vp, C.c_void_p, i64]
@@ -72,6 +74,12 @@ def _p(a):
 
 def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's element loop in residual / J v (default 1); each thread scatters into
+    its own vectors, added in thread order afterwards."""
+    lib().or_set_threads(int(n))
 
 
 def set_bt_pad(pad: float) -> None:

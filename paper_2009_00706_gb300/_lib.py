@@ -29,6 +29,7 @@ SOURCES = [
     ("solver.cu", []),
     ("bsr.cu", ["-Xcompiler", "-fopenmp"]),
     ("peak.cu", []),
+    ("partition.cu", []),
     ("mlp.cu", []),
 ]
 HEADERS = ["imga_internal.h", "vms_device.cuh", os.path.join("..", "..", "include", "imga.h")]
@@ -171,6 +172,14 @@ SIGNATURES = {
     "imga_multilevel_info": (C.c_int, [_vp, C.POINTER(C.c_int), _vp, _vp]),
     "imga_peak_flops": (C.c_int, [_int, _int, C.POINTER(C.c_double)]),
     "imga_surface_force": (C.c_int, [_vp, _dp, _dp, C.POINTER(Physics), _dp, _vp]),
+    "imga_time_steps": (C.c_int, [_vp, _dp, _dp, _dp, C.POINTER(Physics), C.POINTER(SolverOpts), _int, _vp, _vp, _vp,
+                                  _vp]),
+    "imga_partition_build": (C.c_int, [_vp, _int, C.c_double, C.POINTER(_vp)]),
+    "imga_partition_destroy": (None, [_vp]),
+    "imga_partition_info": (C.c_int, [_vp, C.POINTER(C.c_int), _vp, _vp, _vp, _vp]),
+    "imga_partition_nodes": (C.c_int, [_vp, _int, _vp, _vp]),
+    "imga_partition_residual": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.POINTER(Physics), _int, _dp, _vp]),
+    "imga_partition_jvp": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.POINTER(Physics), _int, _dp, _dp, _vp]),
 }
 
 _lib = None

@@ -283,6 +283,26 @@ class Mesh:
         check(_lib.load().imga_bsr_spmv(self.h, _ptr(vals), _ptr(_vec(x, nn, "x")), _ptr(out), _stream(stream)))
         return out
 
+    def time_steps(self, phys, u, u_prev, n_steps, f=None, gmres_m=50, max_newton=20, max_krylov=1000, rtol=1e-8,
+                   atol=0.0, krylov_rtol=1e-3, precision=PRECISION_FP64, precond=4, line_search=1, stream=None,
+                   g_points=None, linear_solver=0, raise_on_failure=True):
+        """imga_time_steps: n_steps Newton-solved time steps in place on (u, u_prev); returns the force
+        history [n_steps, 3] (host) and the Newton and Krylov iterations per step."""
+        nn = self.n_nodes
+        o = SolverOpts(gmres_m, max_newton, max_krylov, rtol, atol, krylov_rtol, precision, precond, line_search,
+                       None, 0.5, linear_solver, 0, 0, 0, 0.0)
+        ps = physics_struct(phys, self._gp(g_points))
+        F = np.zeros((max(1, n_steps), 3))
+        nh = np.zeros(max(1, n_steps), np.int32)
+        kh = np.zeros(max(1, n_steps), np.int32)
+        status = _lib.load().imga_time_steps(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                             _ptr(_vec(f, nn, "f")), C.byref(ps), C.byref(o), n_steps,
+                                             F.ctypes.data_as(C.c_void_p), nh.ctypes.data_as(C.c_void_p),
+                                             kh.ctypes.data_as(C.c_void_p), _stream(stream))
+        if raise_on_failure and status != 0:
+            check(status)
+        return {"status": status, "force": F[:n_steps], "newton_its": nh[:n_steps], "krylov_its": kh[:n_steps]}
+
     def surface_force(self, phys, u, u_prev, out=None, stream=None, g_points=None):
         """Force of the fluid on the body (float64 CUDA tensor [3])."""
         import torch
@@ -472,6 +492,65 @@ class Mlp:
         check(_lib.load().imga_mlp_train(self.h, _ptr(X), X.shape[1], _ptr(T), X.shape[0], epochs, batch, lr,
                                          hist.ctypes.data_as(C.c_void_p), _stream(stream)))
         return hist[:epochs]
+
+
+class Partition:
+    """imga_partition_*: the mesh split into k weighted Morton ranges with halo exchange."""
+
+    def __init__(self, mesh, k, ts_over_tv=0.0):
+        self.mesh = mesh
+        h = C.c_void_p()
+        check(_lib.load().imga_partition_build(mesh.h, k, ts_over_tv, C.byref(h)))
+        self.h = h
+        kk = C.c_int(0)
+        self.elem_off = np.zeros(k + 1, np.int64)
+        self.weight = np.zeros(k)
+        self.n_owned = np.zeros(k, np.int64)
+        self.n_ghost = np.zeros(k, np.int64)
+        f = lambda a: a.ctypes.data_as(C.c_void_p)
+        check(_lib.load().imga_partition_info(h, C.byref(kk), f(self.elem_off), f(self.weight), f(self.n_owned),
+                                              f(self.n_ghost)))
+        self.k = kk.value
+
+    def nodes(self, p):
+        """(global nodes of part p, owned first; owning part of every ghost)"""
+        n = np.zeros(max(1, int(self.n_owned[p] + self.n_ghost[p])), np.int64)
+        o = np.zeros(max(1, int(self.n_ghost[p])), np.int32)
+        check(_lib.load().imga_partition_nodes(self.h, p, n.ctypes.data_as(C.c_void_p), o.ctypes.data_as(C.c_void_p)))
+        return n[: self.n_owned[p] + self.n_ghost[p]], o[: self.n_ghost[p]]
+
+    def residual(self, phys, u, u_prev, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None):
+        import torch
+        nn = self.mesh.n_nodes
+        if out is None:
+            out = torch.empty((nn, 4), dtype=torch.float64, device=u.device)
+        ps = physics_struct(phys)
+        check(_lib.load().imga_partition_residual(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                                  _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")),
+                                                  C.byref(ps), precision, _ptr(out), _stream(stream)))
+        return out
+
+    def jvp(self, phys, u, u_prev, v, u_prev2=None, f=None, precision=PRECISION_FP64, out=None, stream=None):
+        import torch
+        nn = self.mesh.n_nodes
+        if out is None:
+            out = torch.empty((nn, 4), dtype=torch.float64, device=u.device)
+        ps = physics_struct(phys)
+        check(_lib.load().imga_partition_jvp(self.h, _ptr(_vec(u, nn, "u")), _ptr(_vec(u_prev, nn, "u_prev")),
+                                             _ptr(_vec(u_prev2, nn, "u_prev2")), _ptr(_vec(f, nn, "f")), C.byref(ps),
+                                             precision, _ptr(_vec(v, nn, "v")), _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().imga_partition_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def peak_flops(kind, device=0):

@@ -14,6 +14,10 @@
 struct imga_mesh_s {
     imga::Mesh m;
 };
+struct imga_partition_s {
+    imga::Partition* P = nullptr;
+    const imga::Mesh* mesh = nullptr;
+};
 struct imga_mlp_s {
     imga::Mlp* M = nullptr;
     int nin = 0, nout = 0, device = 0;
@@ -464,6 +468,116 @@ imga_status imga_surface_force(imga_mesh h, const double* u, const double* up, c
         return fail(IMGA_ERR_OOM, "cudaMalloc failed");
     if (imga::surface_force(m, u, up, *ph, F, m.force_part, stream)) return cuda_status("surface_force");
     return IMGA_OK;
+}
+
+imga_status imga_time_steps(imga_mesh h, double* u, double* u_prev, const double* f, const imga_physics* ph,
+                            const imga_solver_opts* o, int n_steps, double* force_hist, int* newton_hist,
+                            int* krylov_hist, void* stream) {
+    if (!h || !u || !u_prev || !ph || !o || n_steps < 0) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    imga_status st = state_ok(h, u, u_prev, u_prev, ph, o->precision);
+    if (st != IMGA_OK) return st;
+    imga::Mesh& m = h->m;
+    const size_t bytes = (size_t)m.n_nodes() * 4 * sizeof(double);
+    cudaStream_t s = (cudaStream_t)stream;
+    double *up2 = nullptr, *un = nullptr, *F = nullptr;
+    if (cudaMalloc((void**)&up2, std::max<size_t>(bytes, 8)) != cudaSuccess ||
+        cudaMalloc((void**)&un, std::max<size_t>(bytes, 8)) != cudaSuccess || cudaMalloc((void**)&F, 3 * sizeof(double)) != cudaSuccess) {
+        cudaFree(up2); cudaFree(un);
+        return fail(IMGA_ERR_OOM, "cudaMalloc failed");
+    }
+    if (!m.force_part && cudaMalloc((void**)&m.force_part, imga::kForcePartials * sizeof(double)) != cudaSuccess) {
+        cudaFree(up2); cudaFree(un); cudaFree(F);
+        return fail(IMGA_ERR_OOM, "cudaMalloc failed");
+    }
+    imga_status rc = IMGA_OK;
+    for (int k = 0; k < n_steps && rc == IMGA_OK; ++k) {
+        // BDF2 starts with one backward-Euler step (no second previous level yet)
+        imga_physics p = *ph;
+        if (p.time_scheme == 2 && k == 0) p.time_scheme = 0;
+        cudaMemcpyAsync(un, u, bytes, cudaMemcpyDeviceToDevice, s);   // the new level starts from u^n
+        imga_solver_stats stats;
+        rc = imga_newton_step(h, un, u, p.time_scheme == 2 ? up2 : nullptr, f, &p, o, &stats, stream);
+        if (rc != IMGA_OK && rc != IMGA_ERR_NOT_CONVERGED) break;
+        if (newton_hist) newton_hist[k] = stats.newton_its;
+        if (krylov_hist) krylov_hist[k] = stats.krylov_its;
+        const imga_status conv = rc;
+        rc = IMGA_OK;
+        cudaMemcpyAsync(up2, u, bytes, cudaMemcpyDeviceToDevice, s);   // shift the levels
+        cudaMemcpyAsync(u_prev, u, bytes, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(u, un, bytes, cudaMemcpyDeviceToDevice, s);
+        if (force_hist) {
+            if (imga::surface_force(m, u, u_prev, p, F, m.force_part, s)) { rc = cuda_status("surface_force"); break; }
+            cudaMemcpyAsync(force_hist + 3 * k, F, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        }
+        if (conv == IMGA_ERR_NOT_CONVERGED) rc = fail(IMGA_ERR_NOT_CONVERGED, "a time step's Newton solve did not converge");
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(up2); cudaFree(un); cudaFree(F);
+    return rc;
+}
+
+imga_status imga_partition_build(imga_mesh h, int k, double ts_over_tv, imga_partition* out) {
+    if (!h || !out) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (h->m.batched) return fail(IMGA_ERR_INVALID_ARG, "batched meshes are not partitioned");
+    if (h->m.user_bc) return fail(IMGA_ERR_INVALID_ARG, "partitions take the default strong rows (no imga_set_dirichlet)");
+    if (!(ts_over_tv >= 0.0)) return fail(IMGA_ERR_INVALID_ARG, "ts_over_tv must be >= 0");
+    std::string err;
+    imga::Partition* P = nullptr;
+    try {
+        if (imga::partition_build(h->m, k, ts_over_tv, &P, err)) return fail(err.rfind("partition: 1", 0) == 0 ? IMGA_ERR_INVALID_ARG : IMGA_ERR_OOM, err);
+    } catch (const std::bad_alloc&) {
+        return fail(IMGA_ERR_OOM, "partition: host allocation failed");
+    }
+    imga_partition_s* ps = new imga_partition_s();
+    ps->P = P;
+    ps->mesh = &h->m;
+    *out = ps;
+    return IMGA_OK;
+}
+
+void imga_partition_destroy(imga_partition p) {
+    if (!p) return;
+    imga::partition_free(p->P);
+    delete p;
+}
+
+imga_status imga_partition_info(imga_partition p, int* k, int64_t* elem_off, double* weight, int64_t* n_owned,
+                                int64_t* n_ghost) {
+    if (!p || !k) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    imga::partition_info(p->P, elem_off, weight, n_owned, n_ghost);
+    *k = imga::partition_count(p->P);
+    return IMGA_OK;
+}
+
+imga_status imga_partition_nodes(imga_partition p, int part, int64_t* nodes, int32_t* ghost_owner) {
+    if (!p || part < 0 || part >= imga::partition_count(p->P)) return fail(IMGA_ERR_INVALID_ARG, "bad argument");
+    imga::partition_nodes(p->P, part, nodes, ghost_owner);
+    return IMGA_OK;
+}
+
+static imga_status partition_apply(imga_partition p, const double* u, const double* up, const double* up2, const double* f,
+                                   const imga_physics* ph, int precision, const double* v, double* out, void* stream) {
+    if (!p || !out) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (!u || !up) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    if (p->mesh->host_only) return fail(IMGA_ERR_INVALID_ARG, "partition of a host-only mesh has no device parts");
+    if (!physics_ok(ph)) return fail(IMGA_ERR_INVALID_ARG, "bad physics parameters");
+    if (ph->time_scheme == 2 && !up2) return fail(IMGA_ERR_INVALID_ARG, "BDF2 needs u_prev2");
+    if (precision != 0 && precision != 1) return fail(IMGA_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    if (ph->g_points) return fail(IMGA_ERR_INVALID_ARG, "partitions take the uniform body velocity (g_points = NULL)");
+    if (imga::partition_apply(p->P, u, up, up2, f, *ph, precision, v, out, stream)) return cuda_status("partition");
+    return IMGA_OK;
+}
+
+imga_status imga_partition_residual(imga_partition p, const double* u, const double* up, const double* up2,
+                                    const double* f, const imga_physics* ph, int precision, double* R, void* stream) {
+    return partition_apply(p, u, up, up2, f, ph, precision, nullptr, R, stream);
+}
+
+imga_status imga_partition_jvp(imga_partition p, const double* u, const double* up, const double* up2, const double* f,
+                               const imga_physics* ph, int precision, const double* v, double* Jv, void* stream) {
+    if (!v) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    return partition_apply(p, u, up, up2, f, ph, precision, v, Jv, stream);
 }
 
 imga_status imga_peak_flops(int device, int kind, double* tflops) {

@@ -621,6 +621,28 @@ bool device_upload_batch(Mesh& m, std::string& err) {
     return device_upload_quadrature(m, err);
 }
 
+// the arrays a part of a partitioned mesh needs for residual / J v (its own elements and nodes)
+bool device_upload_part(Mesh& m, std::string& err) {
+    DeviceMesh& d = m.d;
+    d.n_elem = m.n_elem();
+    d.n_nodes = m.n_nodes();
+    d.n_hang = m.n_hang();
+    d.n_tri = 0;
+    std::vector<int32_t> oc(8 * m.out_list.size());
+    std::vector<uint8_t> ol(m.out_list.size());
+    for (size_t i = 0; i < m.out_list.size(); ++i) {
+        for (int c = 0; c < 8; ++c) oc[8 * i + c] = m.conn[8 * (size_t)m.out_list[i] + c];
+        ol[i] = m.lev[m.out_list[i]];
+    }
+    std::vector<float> ptsf(m.cut_pts.begin(), m.cut_pts.end());
+    if (!upload(&d.lev, m.lev, err) || !upload(&d.conn, m.conn, err) || !upload(&d.hpar, m.hpar, err) ||
+        !upload(&d.marker, m.marker, err) || !upload(&d.cflags, m.cflags, err) || !upload(&d.out_list, m.out_list, err) ||
+        !upload(&d.out_conn, oc, err) || !upload(&d.out_lev, ol, err) || !upload(&d.cut_list, m.cut_list, err) ||
+        !upload(&d.cut_off, m.cut_off, err) || !upload(&d.cut_pts, m.cut_pts, err) || !upload(&d.cut_pts_f, ptsf, err))
+        return false;
+    return device_upload_quadrature(m, err);
+}
+
 int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream) {
     if (n <= 0) return 0;
     GeomView g = view(m);

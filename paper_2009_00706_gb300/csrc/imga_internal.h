@@ -227,6 +227,7 @@ bool device_markers(Mesh& m, std::string& err);
 bool device_cut_quadrature(Mesh& m, std::string& err);
 bool device_upload_quadrature(Mesh& m, std::string& err);
 bool device_upload_batch(Mesh& m, std::string& err);
+bool device_upload_part(Mesh& m, std::string& err);
 int device_classify(const Mesh& m, const double* pts, int64_t n, uint8_t* flags, void* stream);
 void device_free(Mesh& m);
 
@@ -298,6 +299,16 @@ int newton_solve(Mesh& m, double* u, const double* up, const double* up2, const 
 void solver_free(Mesh& m);
 
 bool merge_meshes(Mesh& m, const std::vector<const Mesh*>& parts, const std::vector<double>& mu, std::string& err);
+
+// weighted SFC partition into k parts with halo exchange (partition.cu)
+struct Partition;
+int partition_build(const Mesh& m, int k, double ts_over_tv, Partition** out, std::string& err);
+int partition_apply(Partition* P, const double* u, const double* up, const double* up2, const double* f,
+                    const imga_physics& ph, int precision, const double* v, double* out, void* stream);
+int partition_info(const Partition* P, int64_t* elem_off, double* weight, int64_t* n_owned, int64_t* n_ghost);
+int partition_nodes(const Partition* P, int p, int64_t* nodes, int32_t* ghost_owner);
+int partition_count(const Partition* P);
+void partition_free(Partition* P);
 
 // arithmetic-pipe microbenchmark (peak.cu)
 int peak_flops(int device, int kind, double* tflops, std::string& err);
