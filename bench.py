@@ -503,28 +503,42 @@ def run_ours(args):
                                         + ("multilevel V-cycle" if pc == 4 else "block-Jacobi") + ", GMRES(50)"}
         smesh.close()
         # the sphere LES itself: block-Jacobi GMRES(50) stalls on it (every linear solve after the first
-        # reaches its cap); the multilevel V-cycle (precond 4) brings the Newton step to 1e-8.  Mixed:
-        # float32 elements, hierarchy and V-cycle, float64 Krylov vectors, reductions and update; fp64:
-        # everything float64.  The error of the mixed solution against the float64 one is reported.
+        # reaches its cap); the multilevel V-cycle (precond 4) solves its linear systems.  Mixed: float32
+        # elements, hierarchy and V-cycle, float64 Krylov vectors, reductions and update; fp64: everything
+        # float64.  (a) One Newton step whose GMRES(50) solve reaches 1e-8 relative, mixed against fp64,
+        # and the error of the mixed step against the fp64 one.  (b) The nonlinear solve toward 1e-8
+        # (mixed, two smoothing sweeps): at Re 1e4 Newton converges only linearly on this residual.
         mesh.use_graphs(True)
         sol = {}
         for name, p in (("mixed", api.PRECISION_MIXED), ("fp64", api.PRECISION_FP64)):
             uw = ud.clone()
             torch.cuda.synchronize()
             st = mesh.newton_step(ph, uw, upd, up2d, precision=p, precond=4, rtol=1e-8, gmres_m=50,
-                                  krylov_rtol=args.krylov_rtol, max_newton=20, max_krylov=600, stream=stream,
+                                  krylov_rtol=1e-8, max_newton=1, max_krylov=2000, stream=stream,
                                   raise_on_failure=False)
             sol[name] = uw
             r = st["res_norm"]
-            newton["sphere_les_" + name] = {
-                "ms": st["time_ms"], "ms_per_newton": st["time_ms"] / max(1, st["newton_its"]),
-                "newton_its": st["newton_its"], "krylov_its": st["krylov_its"],
-                "krylov_per_newton": st["krylov_per_newton"],
-                "rel_residual_history": [x / r[0] for x in r], "converged": bool(st["converged"]),
-                "workload": "sphere_les (2,001,176 elements, Re 1e4, BDF2 dt 0.01), multilevel V-cycle "
-                            "(6 Morton-consecutive blocks per aggregate, damped block-Jacobi 0.5), GMRES(50), to 1e-8"}
-        d = (sol["mixed"] - sol["fp64"]).norm().item() / max(sol["fp64"].norm().item(), 1e-300)
-        newton["sphere_les_mixed"]["rel_error_vs_fp64_solution"] = d
+            newton["sphere_les_step_" + name] = {
+                "ms": st["time_ms"], "krylov_its": st["krylov_its"], "linear_rel_residual": st["krylov_rel"][0],
+                "linear_converged": bool(st["krylov_rel"][0] <= 1e-8 * 1.0000001),
+                "nonlinear_rel_residual_after": r[-1] / r[0],
+                "workload": "sphere_les (2,001,176 elements, Re 1e4, BDF2 dt 0.01): one Newton step, GMRES(50) to "
+                            "1e-8 relative, multilevel V-cycle (6 Morton-consecutive blocks per aggregate, damped "
+                            "block-Jacobi 0.5), whole solve as one CUDA graph"}
+        d = (sol["mixed"] - sol["fp64"]).norm().item() / max((sol["fp64"] - ud).norm().item(), 1e-300)
+        newton["sphere_les_step_mixed"]["rel_error_of_update_vs_fp64"] = d
+        uw = ud.clone()
+        st = mesh.newton_step(ph, uw, upd, up2d, precision=api.PRECISION_MIXED, precond=4, rtol=1e-8, gmres_m=50,
+                              krylov_rtol=args.krylov_rtol, max_newton=20, max_krylov=600, ml_sweeps=2,
+                              stream=stream, raise_on_failure=False)
+        r = st["res_norm"]
+        newton["sphere_les_solve_mixed"] = {
+            "ms": st["time_ms"], "ms_per_newton": st["time_ms"] / max(1, st["newton_its"]),
+            "newton_its": st["newton_its"], "krylov_its": st["krylov_its"],
+            "krylov_per_newton": st["krylov_per_newton"], "rel_residual_history": [x / r[0] for x in r],
+            "converged": bool(st["converged"]),
+            "workload": "sphere_les, Newton toward 1e-8 with GMRES(50) to 1e-3 per step, multilevel V-cycle with "
+                        "two sweeps, at most 20 Newton iterations"}
         rows, _ = mesh.multilevel_info()
         newton["sphere_les_multilevel_levels"] = [int(x) for x in rows]
         mesh.use_graphs(False)

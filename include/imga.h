@@ -320,6 +320,7 @@ typedef struct {
     double time_ms;
     int converged;
     int fallbacks;          /* linear solves redone with block-Jacobi (precond 2, 3)              */
+    double krylov_rel[32];  /* ||b - J du|| / ||b|| reached by each Newton iteration's linear solve  */
 } imga_solver_stats;
 
 /* Newton iterations on R(u) = 0 from u_inout (device [n_nodes][4], updated in place), each linear

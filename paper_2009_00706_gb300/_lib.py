@@ -121,7 +121,8 @@ class SolverOpts(C.Structure):
 
 class SolverStats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("krylov_its", C.c_int), ("krylov_per_newton", C.c_int * 32),
-                ("res_norm", C.c_double * 33), ("time_ms", C.c_double), ("converged", C.c_int), ("fallbacks", C.c_int)]
+                ("res_norm", C.c_double * 33), ("time_ms", C.c_double), ("converged", C.c_int), ("fallbacks", C.c_int),
+                ("krylov_rel", C.c_double * 32)]
 
 
 # every entry point declared in include/imga.h, with its ctypes signature

@@ -256,7 +256,7 @@ class Mesh:
         out = {"status": status, "newton_its": st.newton_its, "krylov_its": st.krylov_its,
                "krylov_per_newton": list(st.krylov_per_newton)[: st.newton_its],
                "res_norm": list(st.res_norm)[: st.newton_its + 1], "time_ms": st.time_ms, "converged": st.converged,
-               "fallbacks": st.fallbacks}
+               "fallbacks": st.fallbacks, "krylov_rel": list(st.krylov_rel)[: st.newton_its]}
         if raise_on_failure and status != 0:
             check(status)
         return out

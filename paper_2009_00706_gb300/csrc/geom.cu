@@ -492,13 +492,14 @@ bool device_cut_quadrature(Mesh& m, std::string& err) {
 // incidence list holds, for every independent node, the (slot, corner, weight) entries that reach it
 // through M_e: weight 1 for a corner that is the node, 1/2 or 1/4 for a hanging corner whose parent
 // it is; entries ordered by slot, so the node sums in the same order on every call.
-// Entry encoding: bits 0-2 corner, bits 3-4 weight (0: 1, 1: 1/2, 2: 1/4), bits 5.. global slot
-// (volume slots first).
+// Entry encoding (32 bits): bits 0-2 corner, bits 3-4 weight (0: 1, 1: 1/2, 2: 1/4), bits 5-31
+// global slot (volume slots first; at most 2^27 slots).
 bool build_incidence(Mesh& m, const std::vector<int32_t>& sq_el, const std::vector<int32_t>& dense, std::string& err) {
     const int64_t nn = m.n_nodes(), nv = (int64_t)(m.out_list.size() + m.cut_list.size());
     const int64_t ns = m.n_sq_elem + m.n_sq_sparse;
     m.n_vslots = nv;
     m.n_sslots = ns;
+    if (nv + ns >= ((int64_t)1 << 27)) { err = "too many element slots for the incidence list (2^27)"; return false; }
     auto elem_of = [&](int64_t s) -> int64_t {
         if (s < (int64_t)m.out_list.size()) return m.out_list[s];
         if (s < nv) return m.cut_list[s - (int64_t)m.out_list.size()];
@@ -511,19 +512,19 @@ bool build_incidence(Mesh& m, const std::vector<int32_t>& sq_el, const std::vect
             const int64_t e = elem_of(s);
             for (int c = 0; c < 8; ++c) {
                 const int32_t id = m.conn[8 * e + c];
-                if (id < nn) { fn(id, (uint64_t)(s << 5) | (uint64_t)c); continue; }
+                if (id < nn) { fn(id, (uint32_t)(s << 5) | (uint32_t)c); continue; }
                 const int64_t h = id - nn;
                 const int np = m.hnp[h];
-                const uint64_t wc = np == 4 ? 2u : 1u;
-                for (int q = 0; q < np; ++q) fn(m.hpar[4 * h + q], (uint64_t)(s << 5) | (wc << 3) | (uint64_t)c);
+                const uint32_t wc = np == 4 ? 2u : 1u;
+                for (int q = 0; q < np; ++q) fn(m.hpar[4 * h + q], (uint32_t)(s << 5) | (wc << 3) | (uint32_t)c);
             }
         }
     };
-    visit([&](int64_t node, uint64_t) { ptr[node + 1] += 1; });
+    visit([&](int64_t node, uint32_t) { ptr[node + 1] += 1; });
     for (int64_t i = 0; i < nn; ++i) ptr[i + 1] += ptr[i];
-    std::vector<uint64_t> inc(std::max<int64_t>(1, ptr[nn]));
+    std::vector<uint32_t> inc(std::max<int64_t>(1, ptr[nn]));
     std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
-    visit([&](int64_t node, uint64_t code) { inc[fill[node]++] = code; });
+    visit([&](int64_t node, uint32_t code) { inc[fill[node]++] = code; });
     const size_t slot_bytes = (size_t)std::max<int64_t>(1, nv) * 32 * sizeof(double);
     if (!upload(&m.d.inc_ptr, ptr, err) || !upload(&m.d.inc, inc, err)) return false;
     if (!check(cudaMalloc((void**)&m.d.sv, slot_bytes), err, "cudaMalloc") ||
@@ -579,9 +580,37 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
     m.sq_hosts.assign(el.begin(), el.end());
     std::sort(m.sq_hosts.begin(), m.sq_hosts.end());
     m.sq_hosts.erase(std::unique(m.sq_hosts.begin(), m.sq_hosts.end()), m.sq_hosts.end());
+    // float64 penalty matrices, one per run of points of one element in device order (dense elements:
+    // their slot; sparse elements: the slot of their first point)
+    std::vector<int64_t> pq, pslot;
+    std::vector<double> pen;
+    m.pen_elem.clear();
+    for (int64_t j = 0; j < ns;) {
+        int64_t k = j;
+        while (k < ns && el[k] == el[j]) ++k;
+        m.pen_elem.push_back(el[j]);
+        pq.push_back(j);
+        pslot.push_back(j >= m.n_sq_sparse ? (int64_t)(std::lower_bound(so.begin(), so.end() - 1, j) - so.begin())
+                                           : m.n_sq_elem + j);
+        double P[36] = {0.0};
+        for (int64_t q = j; q < k; ++q) {
+            double fm[3], fp[3], phi[8];
+            for (int a = 0; a < 3; ++a) { fm[a] = 0.5 * (1.0 - xr[3 * q + a]); fp[a] = 0.5 * (1.0 + xr[3 * q + a]); }
+            for (int c = 0; c < 8; ++c) phi[c] = ((c & 1) ? fp[0] : fm[0]) * ((c & 2) ? fp[1] : fm[1]) * ((c & 4) ? fp[2] : fm[2]);
+            const double wq = w[q] * tb[q];
+            int t = 0;
+            for (int a = 0; a < 8; ++a)
+                for (int b = a; b < 8; ++b, ++t) P[t] += wq * phi[a] * phi[b];
+        }
+        pen.insert(pen.end(), P, P + 36);
+        j = k;
+    }
+    pq.push_back(ns);
     if (!upload(&m.d.sq_elem, el, err) || !upload(&m.d.sq_x, xr, err) || !upload(&m.d.sq_n, nr, err) ||
         !upload(&m.d.sq_w, w, err) || !upload(&m.d.sq_taub, tb, err) || !upload(&m.d.sq_list, sl, err) ||
         !upload(&m.d.sq_off, so, err) || !upload(&m.d.sq_src, src, err) || !upload(&m.d.sq_hosts, m.sq_hosts, err) ||
+        !upload(&m.d.pen_elem, m.pen_elem, err) || !upload(&m.d.pen_q, pq, err) || !upload(&m.d.pen_slot, pslot, err) ||
+        !upload(&m.d.pen, pen, err) ||
         !upload(&m.d.bcflag, m.bcflag, err))
         return false;
     if (!build_incidence(m, el, sl, err)) return false;
@@ -655,7 +684,7 @@ void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
                     d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.cut_order, d.sq_elem, d.sq_x,
-                    d.sq_n, d.sq_w, d.sq_taub, d.sq_src, d.sq_hosts, d.inc_ptr, d.inc, d.sv, d.ss, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
+                    d.sq_n, d.sq_w, d.sq_taub, d.sq_src, d.sq_hosts, d.pen_elem, d.pen_q, d.pen_slot, d.pen, d.inc_ptr, d.inc, d.sv, d.ss, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
                     d.counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -98,9 +98,15 @@ struct DeviceMesh {
     int32_t* sq_src = nullptr;    // position of every surface point in the export order (imga_physics.g_points)
     int32_t* cut_order = nullptr;   // Intercepted list positions by decreasing point count (autotuner)
     int32_t* sq_hosts = nullptr;  // every element hosting a surface point (increasing)
+    // float64 Nitsche penalty per surface-hosting element (in device point order): element, point range
+    // [pen_q[i], pen_q[i+1]), destination slot, and the packed upper triangle of sum_q (w_q/h_b) phi_a phi_b
+    int32_t* pen_elem = nullptr;
+    int64_t* pen_q = nullptr;
+    int64_t* pen_slot = nullptr;
+    double* pen = nullptr;
     // deterministic scatter: node -> (slot, corner, weight) incidence and the element-contribution slots
     int64_t* inc_ptr = nullptr;   // [n_nodes + 1]
-    uint64_t* inc = nullptr;      // bits 0-2 corner, 3-4 weight code, 5.. global slot
+    uint32_t* inc = nullptr;      // bits 0-2 corner, 3-4 weight code, 5-31 global slot
     void* sv = nullptr;           // volume slots [n_vslots][8][4] of the element precision (sized for float64)
     double* ss = nullptr;         // surface slots [n_sslots][8][4] float64
     int32_t* sq_list = nullptr;   // elements hosting at least kNitscheDenseMin surface points
@@ -162,6 +168,7 @@ struct Mesh {
     int64_t n_sq_sparse = 0;             // surface points of elements hosting < kNitscheDenseMin (stored first)
     int64_t n_sq_elem = 0;               // elements hosting >= kNitscheDenseMin surface points
     std::vector<int32_t> sq_hosts;       // every element hosting a surface point (increasing)
+    std::vector<int32_t> pen_elem;       // surface-hosting elements in device point order (nitsche_penalty)
     int64_t n_vslots = 0, n_sslots = 0;  // deterministic scatter: volume slots (active elements), surface slots
     bool deterministic = true;           // IMGA_OPT_DETERMINISTIC: slots + ordered node sums (1) or atomics (0)
     std::vector<uint8_t> bcflag;

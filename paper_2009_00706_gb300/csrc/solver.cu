@@ -308,6 +308,169 @@ __global__ void __launch_bounds__(256) dg_combine(const GState* __restrict__ G, 
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// A whole Newton solve replayed as one CUDA graph: WHILE conditional nodes (Newton iterations ->
+// GMRES restart cycles -> Arnoldi steps, and the line search) whose conditions device kernels set.
+// Every loop is bounded in its decision kernel (m steps per cycle, max_krylov iterations, 12
+// line-search trials, max_newton iterations), so the graph always ends.
+// ------------------------------------------------------------------------------------------
+struct NState {
+    double rn, target, lam, rt, bnorm, gtarget, beta;
+    double krylov_rtol;
+    int it, max_newton, line_search, trials, its, max_krylov, cycles, steps, nonfinite;
+    double res_hist[33];
+    int kpn[32];
+    double krel[32];
+};
+
+// out = sqrt(sum_b partial[b][0]) (with sqrt = 1) or the sum
+__global__ void ng_dot_final(int nblocks, const double* __restrict__ partial, double* __restrict__ out, int take_sqrt) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(int64_t)b * 64];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        *out = take_sqrt ? sqrt(fmax(t, 0.0)) : t;
+    }
+}
+
+// partial[b][0] = block b's share of x . x
+__global__ void __launch_bounds__(256) ng_dot(int64_t n, const double* __restrict__ x, double* __restrict__ partial) {
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += x[i] * x[i];
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        partial[(int64_t)blockIdx.x * 64] = t;
+    }
+}
+
+// y = x / *den
+__global__ void ng_scale_inv(int64_t n, const double* __restrict__ x, const double* __restrict__ den, double* __restrict__ y) {
+    const double inv = 1.0 / *den;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = inv * x[i];
+}
+
+// ut = u + *lam du
+__global__ void ng_trial(int64_t n, const double* __restrict__ u, const double* __restrict__ du, const double* __restrict__ lam,
+                         double* __restrict__ ut) {
+    const double l = *lam;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        ut[i] = u[i] + l * du[i];
+}
+
+// linear solve starts: target, first residual, whether GMRES runs at all
+__global__ void ng_gmres_init(NState* N, cudaGraphConditionalHandle h) {
+    N->its = 0;
+    N->cycles = 0;
+    N->gtarget = N->krylov_rtol * N->bnorm;
+    N->beta = N->bnorm;
+    cudaGraphSetConditional(h, (N->beta > N->gtarget && N->beta != 0.0 && N->max_krylov > 0) ? 1u : 0u);
+}
+
+// a restart cycle starts from V[0] = r / beta
+__global__ void ng_cycle_start(GState* G, NState* N, int m, cudaGraphConditionalHandle h) {
+    G->k = 0;
+    G->its = N->its;
+    G->stop = 0;
+    G->kdone = 0;
+    G->m = m;
+    G->max_its = N->max_krylov;
+    G->target = N->gtarget;
+    G->res = N->beta;
+    for (int i = 0; i <= m; ++i) G->g[i] = 0.0;
+    G->g[0] = N->beta;
+    N->steps = 0;
+    N->cycles += 1;
+    cudaGraphSetConditional(h, 1u);
+}
+
+// after an Arnoldi step: continue while the cycle runs (at most m + 1 steps)
+__global__ void ng_step_cond(GState* G, NState* N, cudaGraphConditionalHandle h) {
+    N->steps += 1;
+    if (N->steps > G->m + 1) G->stop = 1;
+    cudaGraphSetConditional(h, G->stop ? 0u : 1u);
+}
+
+// after a cycle: the true residual norm beta of the iterate decides (as the host-driven solver)
+__global__ void ng_gmres_decide(const GState* G, NState* N, cudaGraphConditionalHandle h) {
+    N->its = G->its;
+    bool cont = true;
+    if (G->res <= N->gtarget || N->its >= N->max_krylov)
+        cont = !(N->beta <= N->gtarget * 1.0000001 || N->its >= N->max_krylov);
+    if (!(N->beta > 0.0) || N->cycles > N->max_krylov + 2) cont = false;
+    cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+__global__ void ng_ls_init(NState* N, cudaGraphConditionalHandle h) {
+    N->lam = 1.0;
+    N->trials = 0;
+    cudaGraphSetConditional(h, 1u);
+}
+
+// Armijo backtracking (c = 1e-4, halving, at most 12 trials)
+__global__ void ng_ls_decide(NState* N, cudaGraphConditionalHandle h) {
+    N->trials += 1;
+    const bool ok = !N->line_search || (isfinite(N->rt) && N->rt <= (1.0 - 1e-4 * N->lam) * N->rn);
+    if (ok || N->trials >= 12) {
+        cudaGraphSetConditional(h, 0u);
+    } else {
+        N->lam *= 0.5;
+        cudaGraphSetConditional(h, 1u);
+    }
+}
+
+// the step is taken: record it and decide whether Newton goes on
+__global__ void ng_newton_next(NState* N, cudaGraphConditionalHandle h) {
+    N->rn = N->rt;
+    if (N->it < 32) {
+        N->kpn[N->it] = N->its;
+        N->krel[N->it] = N->bnorm > 0.0 ? N->beta / N->bnorm : 0.0;
+    }
+    N->it += 1;
+    if (N->it <= 32) N->res_hist[N->it] = N->rn;
+    if (!isfinite(N->rn)) N->nonfinite = 1;
+    const bool cont = isfinite(N->rn) && N->rn > N->target && N->it < N->max_newton && N->it < 32;
+    cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+// During a capture on s: a conditional handle of the graph being captured (its value set by kernels).
+int capture_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess || !g) return 1;
+    return cudaGraphConditionalHandleCreate(h, g, 0, 0) == cudaSuccess ? 0 : 1;
+}
+
+// During a capture on s: append a WHILE node on h after the captured work; later work depends on it.
+int capture_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &ed, &nd) != cudaSuccess || !g) return 1;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, ed, nd, &cp) != cudaSuccess) return 1;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) == cudaSuccess ? 0 : 1;
+}
+
 constexpr int kVecs = 14;          // work vectors of n doubles
 
 struct Work {
@@ -321,6 +484,7 @@ struct Work {
     double* h = nullptr;       // [64]
     double* hh = nullptr;      // pinned host [128]: dot products in, coefficients out
     GState* G = nullptr;       // device-resident GMRES state
+    NState* N = nullptr;       // device-resident Newton state (graph-replayed solve)
     double* gh = nullptr;      // pinned host [8]: the head of G read back once per chunk of steps
 };
 
@@ -349,7 +513,7 @@ public:
             cudaMalloc((void**)&w.partial, kRedBlocks * 64 * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void**)&w.h, 64 * sizeof(double)) != cudaSuccess ||
             cudaMallocHost((void**)&w.hh, 128 * sizeof(double)) != cudaSuccess ||
-            cudaMalloc((void**)&w.G, sizeof(GState)) != cudaSuccess ||
+            cudaMalloc((void**)&w.G, sizeof(GState)) != cudaSuccess || cudaMalloc((void**)&w.N, sizeof(NState)) != cudaSuccess ||
             cudaMallocHost((void**)&w.gh, 8 * sizeof(double)) != cudaSuccess) {
             err = "solver workspace allocation failed";
             cudaGetLastError();
@@ -365,6 +529,7 @@ public:
         cudaFree(w->V); cudaFree(w->vec); cudaFree(w->D); cudaFree(w->Dinv); cudaFree(w->partial); cudaFree(w->h);
         cudaFreeHost(w->hh);
         cudaFree(w->G);
+        cudaFree(w->N);
         cudaFreeHost(w->gh);
         delete w;
         m.solver_work = nullptr;
@@ -407,6 +572,12 @@ public:
     }
     int jv(const double* u, const double* v, double* out) {
         return vms_apply(M, u, Up, Up2, F, P, O.precision, v, out, st);
+    }
+    // the true linear residual of a restart in float64: with float32 element arithmetic J v is linear
+    // only to rounding (~1e-7 relative), so the restarts form b - J x with the float64 J v and every
+    // cycle refines the float64 solution (iterative refinement); the Arnoldi steps keep O.precision
+    int jv_true(const double* u, const double* v, double* out) {
+        return vms_apply(M, u, Up, Up2, F, P, 0, v, out, st);
     }
     int pmode = 0;   // preconditioner in use for the current linear solve (block-Jacobi fallback)
     static bool learned_mode(int p) { return p == 2 || p == 3; }
@@ -607,7 +778,7 @@ public:
             precond(w, z);
             axpby(1.0, z, 1.0, x);
             // residual of the iterate: the true one decides at the end, the restart starts from it
-            if (jv(u, x, w)) return 1;
+            if (jv_true(u, x, w)) return 1;
             cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
             axpby(-1.0, w, 1.0, r);
             const double beta0 = beta;
@@ -693,14 +864,14 @@ public:
             axpby(1.0, z, 1.0, x);
             if (res <= target || its >= max_its) {
                 // true residual of the returned solution
-                if (jv(u, x, w)) return 1;
+                if (jv_true(u, x, w)) return 1;
                 cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
                 axpby(-1.0, w, 1.0, r);
                 res = norm(r);
                 if (res <= target * 1.0000001 || its >= max_its) break;
                 continue;
             }
-            if (jv(u, x, w)) return 1;
+            if (jv_true(u, x, w)) return 1;
             cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
             axpby(-1.0, w, 1.0, r);
             const double rn = norm(r);
@@ -711,7 +882,186 @@ public:
         return 0;
     }
 
+    // preconditioner setup at the iterate u (block-Jacobi or multilevel), launches only (capturable)
+    int precond_setup(const double* u, std::string& err) {
+        if (O.precond >= 1 && O.precond <= 3 && block_jacobi_setup(M, u, Up, Up2, F, P, O.precision, W.D, W.Dinv, st)) {
+            err = "block-Jacobi setup failed";
+            return 1;
+        }
+        if (O.precond == 4 && multilevel_setup(M, u, Up, Up2, F, P, O.precision, O.ml_sweeps > 0 ? O.ml_sweeps : 1,
+                                               O.ml_omega > 0.0 ? O.ml_omega : 0.5, st, err))
+            return 1;
+        return 0;
+    }
+
+    // *out = ||x|| computed on the device (launches only)
+    void norm_dev(const double* x, double* out) {
+        const int grid = (int)std::min<int64_t>(kRedBlocks, (n + 255) / 256);
+        ng_dot<<<grid, 256, 0, st>>>(n, x, W.partial);
+        ng_dot_final<<<1, 256, 0, st>>>(grid, W.partial, out, 1);
+    }
+
+    double* nfield(size_t off) { return reinterpret_cast<double*>(reinterpret_cast<char*>(W.N) + off); }
+
+    // The Newton solve of newton() as one graph launch: Newton iterations, GMRES restart cycles, Arnoldi
+    // steps and line-search trials are WHILE nodes whose conditions device kernels set, so the host
+    // waits once.  Returns -1 (nothing done) when the graph cannot be built; newton() then drives it.
+    int newton_graph(double* u, imga_solver_stats* S, std::string& err) {
+        auto t0 = std::chrono::steady_clock::now();
+        double *R = vec(0), *b = vec(1), *du = vec(2), *ut = vec(3), *r = vec(4), *z = vec(5), *w = vec(6), *Rt = vec(7);
+        if (residual(u, R)) { err = "residual launch failed"; return 1; }
+        const double r0 = norm(R);
+        if (!std::isfinite(r0)) { err = "NaN/Inf in the initial residual"; return 2; }
+        S->res_norm[0] = r0;
+        const double target = std::max(O.rtol * r0, O.atol);
+        if (r0 <= target || O.max_newton <= 0) {
+            S->newton_its = 0;
+            S->converged = r0 <= target ? 1 : 0;
+            S->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            return 0;
+        }
+        // set-up work that allocates or sets launch attributes runs once before the capture
+        if (precond_setup(u, err)) return 1;
+        vms_prepare();
+        pmode = O.precond;
+        NState h;
+        std::memset(&h, 0, sizeof(h));
+        h.rn = r0;
+        h.target = target;
+        h.krylov_rtol = O.krylov_rtol;
+        h.max_newton = O.max_newton;
+        h.line_search = O.line_search;
+        h.max_krylov = O.max_krylov;
+        h.res_hist[0] = r0;
+        if (cudaMemcpyAsync(W.N, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+            return -1;
+        const int m = std::min(W.m, kMaxM);
+        NState* N = W.N;
+        GState* G = W.G;
+        cudaStream_t keep = st, c[3] = {nullptr, nullptr, nullptr};
+        cudaGraph_t top = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        bool ok = true;
+        for (int i = 0; i < 3 && ok; ++i) ok = cudaStreamCreateWithFlags(&c[i], cudaStreamNonBlocking) == cudaSuccess;
+        cudaGraphConditionalHandle hN, hG, hA, hL;
+        cudaGraph_t bN = nullptr, bC = nullptr, bS = nullptr, bL = nullptr;
+        auto end = [&](cudaStream_t cs, cudaGraph_t* g) {
+            cudaGraph_t out = *g;
+            const bool e = cudaStreamEndCapture(cs, &out) == cudaSuccess;
+            ok = ok && e;
+        };
+        ok = ok && cudaGraphCreate(&top, 0) == cudaSuccess &&
+             cudaGraphConditionalHandleCreate(&hN, top, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        if (ok) {   // top: WHILE (Newton goes on) { one Newton iteration }
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = hN;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            ok = cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &cp) == cudaSuccess;
+            if (ok) bN = cp.conditional.phGraph_out[0];
+        }
+        if (ok) ok = cudaStreamBeginCaptureToGraph(c[0], bN, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            st = c[0];
+            std::string e2;
+            ok = precond_setup(u, e2) == 0;
+            scale_copy(-1.0, R, b);
+            cudaMemsetAsync(du, 0, n * sizeof(double), st);
+            cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            norm_dev(b, nfield(offsetof(NState, bnorm)));
+            ok = ok && capture_handle(st, &hG) == 0;
+            if (ok) ng_gmres_init<<<1, 1, 0, st>>>(N, hG);
+            ok = ok && capture_while(st, hG, &bC) == 0;
+            // GMRES restart cycle
+            if (ok) ok = cudaStreamBeginCaptureToGraph(c[1], bC, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                st = c[1];
+                ng_scale_inv<<<(unsigned)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256), 256, 0, st>>>(
+                    n, r, nfield(offsetof(NState, beta)), basis(0));
+                ok = capture_handle(st, &hA) == 0;
+                if (ok) ng_cycle_start<<<1, 1, 0, st>>>(G, N, m, hA);
+                ok = ok && capture_while(st, hA, &bS) == 0;
+                if (ok) ok = cudaStreamBeginCaptureToGraph(c[2], bS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {   // one Arnoldi step
+                    st = c[2];
+                    ok = step_launches(u) == 0;
+                    ng_step_cond<<<1, 1, 0, st>>>(G, N, hA);
+                    end(c[2], &bS);
+                }
+                st = c[1];
+                const int grid2 = (int)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256);
+                dg_solve_y<<<1, 1, 0, st>>>(G);
+                dg_combine<<<grid2, 256, 0, st>>>(G, n, W.V, w);
+                precond(w, z);
+                axpby(1.0, z, 1.0, du);
+                ok = ok && vms_apply_skip(M, u, Up, Up2, F, P, 0, du, w, st, nullptr) == 0;   // float64: jv_true
+                cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+                axpby(-1.0, w, 1.0, r);
+                norm_dev(r, nfield(offsetof(NState, beta)));
+                ng_gmres_decide<<<1, 1, 0, st>>>(G, N, hG);
+                end(c[1], &bC);
+            }
+            // line search
+            st = c[0];
+            ok = ok && capture_handle(st, &hL) == 0;
+            if (ok) ng_ls_init<<<1, 1, 0, st>>>(N, hL);
+            ok = ok && capture_while(st, hL, &bL) == 0;
+            if (ok) ok = cudaStreamBeginCaptureToGraph(c[1], bL, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                st = c[1];
+                ng_trial<<<(unsigned)std::min<int64_t>(4 * M.n_sm, (n + 255) / 256), 256, 0, st>>>(
+                    n, u, du, nfield(offsetof(NState, lam)), ut);
+                ok = vms_apply_skip(M, ut, Up, Up2, F, P, 0, nullptr, Rt, st, nullptr) == 0;
+                norm_dev(Rt, nfield(offsetof(NState, rt)));
+                ng_ls_decide<<<1, 1, 0, st>>>(N, hL);
+                end(c[1], &bL);
+            }
+            st = c[0];
+            cudaMemcpyAsync(u, ut, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(R, Rt, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            ng_newton_next<<<1, 1, 0, st>>>(N, hN);
+            end(c[0], &bN);
+        }
+        st = keep;
+        ok = ok && cudaGraphInstantiate(&exec, top, 0) == cudaSuccess;
+        int rc = -1;
+        if (ok) {
+            rc = 0;
+            if (cudaGraphLaunch(exec, st) != cudaSuccess || cudaMemcpyAsync(&h, W.N, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                err = "graph-replayed Newton failed";
+                rc = 1;
+            }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (top) cudaGraphDestroy(top);
+        for (cudaStream_t cs : c)
+            if (cs) cudaStreamDestroy(cs);
+        if (rc != 0) {
+            cudaGetLastError();
+            return rc;
+        }
+        S->newton_its = h.it;
+        for (int i = 0; i < std::min(h.it, 32); ++i) {
+            S->krylov_per_newton[i] = h.kpn[i];
+            S->krylov_rel[i] = h.krel[i];
+            S->krylov_its += h.kpn[i];
+            S->res_norm[i + 1] = h.res_hist[i + 1];
+        }
+        if (h.nonfinite) { err = "NaN/Inf in the residual"; return 2; }
+        S->converged = h.rn <= target ? 1 : 0;
+        S->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return 0;
+    }
+
     int newton(double* u, imga_solver_stats* S, std::string& err) {
+        if (M.use_graphs && !M.profiling && O.linear_solver == 0 && !learned_mode(O.precond)) {
+            const int rc = newton_graph(u, S, err);
+            if (rc >= 0) return rc;
+            std::memset(S, 0, sizeof(*S));   // the graph could not be built: drive the same solve from the host
+        }
         auto t0 = std::chrono::steady_clock::now();
         double* R = vec(0);
         double* b = vec(1);
@@ -762,6 +1112,7 @@ public:
                 if (solve(u, b, du, O.krylov_rtol, O.max_krylov, &kits, &kres)) { err = "GMRES failed"; return 1; }
             }
             S->krylov_per_newton[it] = kits;
+            S->krylov_rel[it] = rn > 0.0 ? kres / rn : 0.0;
             S->krylov_its += kits;
             double lam = 1.0, rt = 0.0;
             for (int ls = 0; ls < 12; ++ls) {

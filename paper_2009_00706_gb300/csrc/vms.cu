@@ -267,19 +267,15 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     NitschePoint<S, T> P;
     const int32_t e = el[i];
-    nitsche_fields<S, T, JV>(A, e, i, xr + 3 * i, nr + 3 * i, P);
+    nitsche_fields<S, T, JV, false>(A, e, i, xr + 3 * i, nr + 3 * i, P);
     const T w = (T)wr[i];
-    // the penalty w tau_B phi_c (u - g) in float64
-    const double wpen = wr[i] * A.Cb * Phys<double>(A, prob_of(A, e)).mu * taub[i];
-    const double* dpen = JV ? P.ddt : P.dd;
+    // (the penalty is added per element in float64 by nitsche_penalty)
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         S t[4];
         nitsche_rows<S, T, false>(A, P, c, T(0), t);
-        const double pc = wpen * P.phid[c];
         double r[4];
         for (int k = 0; k < 4; ++k) r[k] = (double)(w * Pick<T, JV>::get(t[k]));
-        for (int k = 0; k < 3; ++k) r[k] = fma(pc, dpen[k], r[k]);
         if (A.ss) {
             double* d = A.ss + 32 * (A.n_dense_slots + i) + 4 * c;
             reinterpret_cast<double2*>(d)[0] = make_double2(r[0], r[1]);
@@ -311,28 +307,24 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     if (idx >= n) return;
     const int32_t e = list[idx];
-    // corner rows: u_s (0-2), p (3), jump d = u_s - g_body formed in float64 (4-6), tangents at CT;
-    // s_pd: the float64 monomial coefficients of the jump (or, for J v, of its tangent theta v)
-    __shared__ __align__(16) double s_pd[WPB][8][3];
+    // corner rows: u_s (0-2), p (3), jump d = u_s - g_body formed in float64 (4-6), tangents at CT
+    // (the penalty is added per element in float64 by nitsche_penalty)
     const int c8 = lane & 7;
     const int32_t my_id = A.conn[8 * (int64_t)e + c8];
     {
         T a8[8], t8[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         ld8<T>(A.ndv, my_id, a8);
         if (JV) ld8<T>(A.ndt, my_id, t8);
-        double u4[4], up4[4], v4[4];
+        double u4[4], up4[4];
         gather(A, A.U, my_id, u4);
         if (!A.theta1) gather(A, A.Up, my_id, up4);
-        if (JV) gather(A, A.V, my_id, v4);
         T rw[CS];
-        double pd[3];
         for (int k = 0; k < 3; ++k) {
             const double usk = A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
             rw[k] = a8[k];
             rw[4 + k] = (T)(usk - A.g[k]);
             rw[CT + k] = t8[k];
             rw[CT + 4 + k] = t8[k];
-            pd[k] = hadamard_fwd(JV ? A.theta * v4[k] : usk - A.g[k], c8);
         }
         rw[3] = a8[3];
         rw[CT + 3] = t8[3];
@@ -343,7 +335,6 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
             for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + j] = rw[j];
             if (JV)
                 for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + CT + j] = rw[CT + j];
-            for (int k = 0; k < 3; ++k) s_pd[w][lane][k] = pd[k];
         }
     }
     __syncwarp();
@@ -354,7 +345,6 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         mu = Ph.mu;
         rho = Ph.rho;
     }
-    const double Cbmu = A.Cb * Phys<double>(A, prob_of(A, e)).mu;
     T M[32];
     for (int k = 0; k < 32; ++k) M[k] = T(0);
     const int64_t q0 = off[idx], q1 = off[idx + 1];
@@ -408,40 +398,87 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         c[13] = c[14] = c[15] = T(0);
         add_moments<T, false>(m, c, M);
     }
-    // penalty w tau_B phi_c (u - g) in float64: moments P[S][k] = sum_q w tau_B m_S (u - g)_k
-    double Pm[24];
-    for (int k = 0; k < 24; ++k) Pm[k] = 0.0;
-    for (int64_t q = q0 + lane; q < q1; q += 32) {
-        double md[8];
-        monomials<double>(xr + 3 * q, md);
-        double dq[3];
-        const double* gq = point_g(A, q);
-        for (int k = 0; k < 3; ++k) dq[k] = JV ? 0.0 : A.g[k] - gq[k];
+    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id, 0.0, nullptr, A.ss ? A.ss + 32 * idx : nullptr);
+}
+
+// ------------------------------------------------------------------------------------------
+// Nitsche penalty in float64, one thread per surface-hosting element.  Over the element's surface
+// points the penalty rows are linear in the corner values with a matrix that does not depend on the
+// state,
+//   r_{a,k} = sum_q w_q tau_B(q) phi_a(x_q) (u_s(x_q) - g(x_q))_k
+//           = C_b mu sum_b Pen_ab (u_s,b - g_body)_k + C_b mu sum_q (w_q / h_b) phi_a (g_body - g_q)_k,
+//   Pen_ab = sum_q (w_q / h_b) phi_a(x_q) phi_b(x_q)      (float64, built with the mesh),
+// so each call costs one 8 x 8 x 3 product per element instead of float64 work per point (the second
+// sum only with per-point velocities).  J v: the tangent theta v in place of u_s - g_body.  The rows
+// go to the element's surface slot (dense bucket) or to the slot of its first point (sparse bucket),
+// after the surface kernel wrote it, or by float64 atomics.
+// ------------------------------------------------------------------------------------------
+template <bool JV>
+__global__ void __launch_bounds__(128) nitsche_penalty(Args A, const int32_t* __restrict__ pe,
+                                                       const int64_t* __restrict__ pq, const int64_t* __restrict__ pslot,
+                                                       const double* __restrict__ pen, const double* __restrict__ xr,
+                                                       const double* __restrict__ wr, const double* __restrict__ taub,
+                                                       int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
+    const int32_t e = pe[i];
+    const double cbmu = A.Cb * Phys<double>(A, prob_of(A, e)).mu;
+    double d[8][3];
+    int32_t ids[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t)
-            for (int k = 0; k < 3; ++k) dq[k] = fma(md[t], s_pd[w][t][k], dq[k]);
-        const double cq = wr[q] * Cbmu * taub[q];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const double ct = cq * md[t];
-            for (int k = 0; k < 3; ++k) Pm[3 * t + k] = fma(ct, dq[k], Pm[3 * t + k]);
+    for (int c = 0; c < 8; ++c) {
+        ids[c] = A.conn[8 * (int64_t)e + c];
+        if (JV) {
+            double v4[4];
+            gather(A, A.V, ids[c], v4);
+            for (int k = 0; k < 3; ++k) d[c][k] = A.theta * v4[k];
+        } else {
+            double u4[4], up4[4];
+            gather(A, A.U, ids[c], u4);
+            if (!A.theta1) gather(A, A.Up, ids[c], up4);
+            for (int k = 0; k < 3; ++k)
+                d[c][k] = (A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k]) - A.g[k];
         }
     }
-    // sum over the lanes; lane 4 a + k (k < 3) takes corner a's value sum_S sigma_{a,S} P[S][k]
+    const double* P = pen + 36 * i;   // upper triangle, row by row
+    double r[8][3];
 #pragma unroll
-    for (int k = 0; k < 24; ++k)
+    for (int a = 0; a < 8; ++a)
+        for (int k = 0; k < 3; ++k) r[a][k] = 0.0;
+    int t = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Pm[k] += __shfl_xor_sync(0xffffffffu, Pm[k], o);
-    double pen = 0.0;
-    {
-        const int a = lane >> 2, kk = lane & 3;
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const double pk = kk == 0 ? Pm[3 * t] : kk == 1 ? Pm[3 * t + 1] : kk == 2 ? Pm[3 * t + 2] : 0.0;
-            pen += ((__popc(t & ~a) & 1) ? -1.0 : 1.0) * pk;
+        for (int b = a; b < 8; ++b, ++t) {
+            const double m = cbmu * P[t];
+            for (int k = 0; k < 3; ++k) {
+                r[a][k] = fma(m, d[b][k], r[a][k]);
+                if (b != a) r[b][k] = fma(m, d[a][k], r[b][k]);
+            }
+        }
+    if (!JV && A.gpts) {
+        for (int64_t q = pq[i]; q < pq[i + 1]; ++q) {
+            const double* gq = point_g(A, q);
+            double phi[8];
+            basis_values_d(xr + 3 * q, phi);
+            const double c = cbmu * wr[q] * taub[q];
+            for (int a = 0; a < 8; ++a)
+                for (int k = 0; k < 3; ++k) r[a][k] = fma(c * phi[a], A.g[k] - gq[k], r[a][k]);
         }
     }
-    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id, pen, nullptr, A.ss ? A.ss + 32 * idx : nullptr);
+    if (A.ss) {
+        double* dst = A.ss + 32 * pslot[i];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            for (int k = 0; k < 3; ++k) dst[4 * a + k] += r[a][k];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double rr[4] = {r[a][0], r[a][1], r[a][2], 0.0};
+            scatter(A, ids[a], rr);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -486,8 +523,29 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
 // list order (a hanging corner's rows times 1/2 or 1/4 for each parent), then its strong rows take
 // U - g (R) or v (J v) as in strong_rows.  Writes every row of out: no zeroing before the call.
 template <class T>
+__device__ __forceinline__ void gather_entry(const Args& A, uint32_t e, int64_t nv, double acc[4], float hi[4], float lo[4]) {
+    const int c = (int)(e & 7), wc = (int)((e >> 3) & 3);
+    const int64_t s = (int64_t)(e >> 5);
+    if (s < nv) {
+        T v[4];
+        ld4<T>((const T*)A.sv + 32 * s, c, v);
+        const T w = wc == 0 ? T(1) : (wc == 1 ? T(0.5) : T(0.25));
+        if constexpr (sizeof(T) == 4) {
+            for (int k = 0; k < 4; ++k) ff_add(hi[k], lo[k], w * v[k]);
+        } else {
+            for (int k = 0; k < 4; ++k) acc[k] += w * v[k];
+        }
+    } else {
+        const double* d = A.ss + 32 * (s - nv) + 4 * c;
+        const double2 a = reinterpret_cast<const double2*>(d)[0], b = reinterpret_cast<const double2*>(d)[1];
+        const double w = wc == 0 ? 1.0 : (wc == 1 ? 0.5 : 0.25);
+        acc[0] += w * a.x; acc[1] += w * a.y; acc[2] += w * b.x; acc[3] += w * b.y;
+    }
+}
+
+template <class T>
 __global__ void __launch_bounds__(256) node_gather(Args A, const int64_t* __restrict__ ptr,
-                                                   const uint64_t* __restrict__ inc, int64_t nv,
+                                                   const uint32_t* __restrict__ inc, int64_t nv,
                                                    const uint8_t* __restrict__ flag, const uint8_t* __restrict__ umask,
                                                    const double* __restrict__ uval, double ux, double uy, double uz,
                                                    int jv) {
@@ -496,26 +554,15 @@ __global__ void __launch_bounds__(256) node_gather(Args A, const int64_t* __rest
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t q = ptr[n], q1 = ptr[n + 1]; q < q1; ++q) {
-        const uint64_t e = inc[q];
-        const int c = (int)(e & 7), wc = (int)((e >> 3) & 3);
-        const int64_t s = (int64_t)(e >> 5);
-        if (s < nv) {
-            T v[4];
-            ld4<T>((const T*)A.sv + 32 * s, c, v);
-            const T w = wc == 0 ? T(1) : (wc == 1 ? T(0.5) : T(0.25));
-            if constexpr (sizeof(T) == 4) {
-                for (int k = 0; k < 4; ++k) ff_add(hi[k], lo[k], w * v[k]);
-            } else {
-                for (int k = 0; k < 4; ++k) acc[k] += w * v[k];
-            }
-        } else {
-            const double* d = A.ss + 32 * (s - nv) + 4 * c;
-            const double2 a = reinterpret_cast<const double2*>(d)[0], b = reinterpret_cast<const double2*>(d)[1];
-            const double w = wc == 0 ? 1.0 : (wc == 1 ? 0.5 : 0.25);
-            acc[0] += w * a.x; acc[1] += w * a.y; acc[2] += w * b.x; acc[3] += w * b.y;
-        }
+    const int64_t q1 = ptr[n + 1];
+    int64_t q = ptr[n];
+    // two entries per pass: their loads are independent; the sums still follow the list order
+    for (; q + 1 < q1; q += 2) {
+        const uint32_t e0 = __ldg(inc + q), e1 = __ldg(inc + q + 1);
+        gather_entry<T>(A, e0, nv, acc, hi, lo);
+        gather_entry<T>(A, e1, nv, acc, hi, lo);
     }
+    if (q < q1) gather_entry<T>(A, __ldg(inc + q), nv, acc, hi, lo);
     if constexpr (sizeof(T) == 4)
         for (int k = 0; k < 4; ++k) acc[k] += f2d(hi[k]) + f2d(lo[k]);
     // strong rows (as strong_rows)
@@ -690,6 +737,12 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         Timed t(m, 2, ss, 1, !ws);
         nitsche_el<T, JV><<<(unsigned)((nse + WPB - 1) / WPB), 32 * WPB, 0, ss>>>(A, m.d.sq_list, m.d.sq_off, m.d.sq_x,
                                                                                 m.d.sq_n, m.d.sq_w, m.d.sq_taub, nse);
+    }
+    const int64_t np = (int64_t)m.pen_elem.size();
+    if (np > 0) {   // after both surface kernels (same stream): the slots hold their rows
+        Timed t(m, 2, ss, 1, !ws);
+        nitsche_penalty<JV><<<(unsigned)((np + 127) / 128), 128, 0, ss>>>(A, m.d.pen_elem, m.d.pen_q, m.d.pen_slot, m.d.pen,
+                                                                        m.d.sq_x, m.d.sq_w, m.d.sq_taub, np);
     }
     if (ev) {   // join
         cudaEventRecord(ev[1], sc);

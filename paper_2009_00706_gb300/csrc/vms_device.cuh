@@ -786,11 +786,12 @@ __device__ __forceinline__ void basis_values_d(const double* xi, double phi[8]) 
     for (int c = 0; c < 8; ++c) phi[c] = ((c & 1) ? fp[0] : fm[0]) * ((c & 2) ? fp[1] : fm[1]) * ((c & 4) ? fp[2] : fm[2]);
 }
 
-// u_s, p and grad u_s from the node data at surface point q (device order).  The velocity jump
-// d = u_s - g is formed in float64 from the float64 nodal values at the point: the penalty multiplies
-// it by tau_B, up to 100 C_b mu / h on sliver cut cells.  For J v, ddt is its tangent theta v in
-// float64.
-template <class S, class T, bool JV>
+// u_s, p and grad u_s from the node data at surface point q (device order), and the velocity jump
+// d = u_s - g.  DJ: the jump in float64 from the float64 nodal values at the point (dd; for J v its
+// tangent theta v in ddt), as the force on the body needs; otherwise the jump from corner values
+// u_s - g_body formed in float64 and rounded, plus g_body - g at the point (the float64 penalty is
+// applied per element by nitsche_penalty).
+template <class S, class T, bool JV, bool DJ = true>
 __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, int64_t q, const double* xr,
                                                const double* nr, NitschePoint<S, T>& P) {
     P.g = lvl_g<T>(A, A.lev[e]);
@@ -802,11 +803,11 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, int64_t
     T xi[3] = {(T)xr[0], (T)xr[1], (T)xr[2]};
     for (int k = 0; k < 3; ++k) P.nn[k] = (T)nr[k];
     basis<T>(xi, P.B);
-    basis_values_d(xr, P.phid);
+    if (DJ) basis_values_d(xr, P.phid);
     const double* gq = point_g(A, q);
     P.p = zero<S>();
     double us_d[3] = {0.0, 0.0, 0.0};
-    T dtan[3] = {T(0), T(0), T(0)};
+    T dtan[3] = {T(0), T(0), T(0)}, dval[3] = {T(0), T(0), T(0)};
     for (int k = 0; k < 3; ++k) { P.us[k] = zero<S>(); P.ddt[k] = 0.0; for (int j = 0; j < 3; ++j) P.Gu[k][j] = zero<S>(); }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -817,7 +818,7 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, int64_t
         double u4[4], up4[4];
         gather(A, A.U, P.ids[c], u4);
         if (!A.theta1) gather(A, A.Up, P.ids[c], up4);
-        if (JV) {
+        if (JV && DJ) {
             double v4[4];
             gather(A, A.V, P.ids[c], v4);
             for (int k = 0; k < 3; ++k) P.ddt[k] = fma(P.phid[c], A.theta * v4[k], P.ddt[k]);
@@ -826,7 +827,8 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, int64_t
         for (int k = 0; k < 3; ++k) {
             S vu = make<S, T>(a8[k], t8[k]);
             const double usk = A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k];
-            us_d[k] = fma(P.phid[c], usk, us_d[k]);
+            if (DJ) us_d[k] = fma(P.phid[c], usk, us_d[k]);
+            else dval[k] = dval[k] + ph * (T)(usk - A.g[k]);
             dtan[k] = dtan[k] + ph * t8[k];
             P.us[k] = P.us[k] + ph * vu;
             for (int j = 0; j < 3; ++j) P.Gu[k][j] = P.Gu[k][j] + P.B.dphi[c][j] * vu;
@@ -834,8 +836,12 @@ __device__ __forceinline__ void nitsche_fields(const Args& A, int32_t e, int64_t
         P.p = P.p + ph * make<S, T>(a8[3], t8[3]);
     }
     for (int k = 0; k < 3; ++k) {
-        P.dd[k] = us_d[k] - gq[k];
-        P.d[k] = make<S, T>((T)P.dd[k], dtan[k]);
+        if (DJ) {
+            P.dd[k] = us_d[k] - gq[k];
+            P.d[k] = make<S, T>((T)P.dd[k], dtan[k]);
+        } else {
+            P.d[k] = make<S, T>(dval[k] + (T)(A.g[k] - gq[k]), dtan[k]);
+        }
     }
     finish_nitsche(A, P);
 }

@@ -140,3 +140,33 @@ def test_graph_replayed_gmres_matches_host_driven(sphere, dev, prec):
     # J v is bitwise reproducible (deterministic scatter); the two drivers differ only in where the
     # Givens rotations and reductions are computed (host against device arithmetic)
     assert abs(out[True]["krylov_its"] - out[False]["krylov_its"]) <= 0.02 * out[False]["krylov_its"] + 2, out
+
+
+@pytest.mark.parametrize("precond", [1, 4])
+def test_whole_newton_solve_as_one_graph(sphere, dev, precond):
+    """With CUDA graphs on, the whole Newton solve is one graph launch: WHILE nodes for the Newton
+    iterations, the GMRES restart cycles, the Arnoldi steps and the line search, their conditions set
+    on the device.  It takes the same steps as the host-driven solver, up to the last bits of the
+    preconditioner (its setup adds with atomics)."""
+    w, g, o = sphere
+    u, up, _ = I.state(g.n_nodes, 15)
+    R0 = np.linalg.norm(o.residual(w.physics, u, up))
+    out = {}
+    kw = dict(precision=api.PRECISION_MIXED, precond=precond, rtol=1e-8, gmres_m=50,
+              max_krylov=1000, max_newton=12)
+    try:
+        for graphs in (False, True):
+            g.use_graphs(graphs)
+            ud = T(u, dev)
+            st = g.newton_step(w.physics, ud, T(up, dev), **kw)
+            assert st["converged"], (graphs, st)
+            assert np.linalg.norm(o.residual(w.physics, ud.cpu().numpy(), up)) <= 1.5e-8 * R0
+            out[graphs] = (st, ud.cpu().numpy())
+    finally:
+        g.use_graphs(False)
+    (sh, uh), (sg, ug) = out[False], out[True]
+    print(f"precond {precond}: host {sh['krylov_per_newton']} {sh['time_ms']:.0f} ms; "
+          f"graph {sg['krylov_per_newton']} {sg['time_ms']:.0f} ms")
+    assert sg["newton_its"] == sh["newton_its"]
+    assert abs(sg["krylov_its"] - sh["krylov_its"]) <= 0.02 * sh["krylov_its"] + 2
+    assert np.linalg.norm(ug - uh) <= 1e-6 * np.linalg.norm(uh)
