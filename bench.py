@@ -582,7 +582,9 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roof, "kernel_roofline": kern_roof, "fp64_roofline": extra_roof,
                 "kernel_time_share": kern_share, "wpart": wpart,
-                "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])), "clocks": clocks, "e2e": e2e,
+                "cut_tile": dict(zip(("warps_per_block", "longest_first", "candidate_ms"), mesh.tuning()[(prec, "jvp")])),
+                "out_tile": dict(zip(("blocks_per_sm", "candidate_ms"), mesh.tuning_interior()[(prec, "jvp")])),
+                "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cpu_baseline": cpu, "parity_vs_oracle": parity,
                 "extra_elements_per_s": extra,
                 "newton_step": newton, "learned_preconditioner": learned, "inout": inout, "batched": batched, "bluff_pair": bluff, "setup_s": build_s, "setup_ms": info["setup_ms"], "wall_s_timed": wall}

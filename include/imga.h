@@ -420,8 +420,9 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * capture.  imga_set_dirichlet drops the cached graphs.  Profiling (imga_profile) bypasses them. */
 /* IMGA_OPT_AUTOTUNE (value 1): the next imga_residual / imga_jvp call of each precision and kind
  * (residual or J v) first times the Intercepted-element kernel in every tile shape -- 2, 4 or 8
- * warps per block (8 in mixed precision only), elements in Morton order or longest first -- on the
- * call's own inputs and keeps the fastest for that mesh.  This follows the cost model of
+ * warps per block (8 in mixed precision only), elements in Morton order or longest first -- and the
+ * persistent Out-element kernel with 1 to 4 resident blocks per SM, on the call's own inputs, and
+ * keeps the fastest of each for that mesh.  This follows the cost model of
  * Eq. (Wpart): the bucket of elements with uneven quadrature counts (8 to 4096 points).  Tuning
  * synchronises the stream, allocates (once per mesh) a 4-byte-per-element index of the Intercepted
  * list, and is skipped inside a stream capture and by imga_jvp_noalloc.  Value 0 restores the default
@@ -446,6 +447,11 @@ imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
  * of the last tuning for the same 4 cases x 6 candidates (warps 2, 4, 8) x (Morton, longest first);
  * an entry is 0 where not measured. */
 imga_status imga_tuning(imga_mesh mesh, int32_t* shape, float* ms);
+/* The Out-element bucket's tuning (IMGA_OPT_AUTOTUNE also times the persistent interior kernel with 1,
+ * 2, 3 and 4 resident blocks per SM and keeps the fastest): bps[4] for [float64, mixed] x [residual,
+ * J v] (0: not tuned, the occupancy limit is used); if ms is non-null, ms[16] the per-launch
+ * milliseconds of the candidates (0 where not measured). */
+imga_status imga_tuning_interior(imga_mesh mesh, int32_t* bps, float* ms);
 
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.

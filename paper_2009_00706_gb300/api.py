@@ -417,6 +417,14 @@ class Mesh:
                 out[(p, kind)] = (int(shape[4 * p + 2 * j]), int(shape[4 * p + 2 * j + 1]), ms[12 * p + 6 * j:12 * p + 6 * j + 6].tolist())
         return out
 
+    def tuning_interior(self):
+        """{(precision, 'residual' | 'jvp'): (blocks per SM in use (0: occupancy limit), candidate ms[4])}"""
+        bps = np.zeros(4, np.int32)
+        ms = np.zeros(16, np.float32)
+        check(_lib.load().imga_tuning_interior(self.h, bps.ctypes.data_as(C.c_void_p), ms.ctypes.data_as(C.c_void_p)))
+        return {(p, kind): (int(bps[2 * p + j]), ms[8 * p + 4 * j:8 * p + 4 * j + 4].tolist())
+                for p in range(2) for j, kind in enumerate(("residual", "jvp"))}
+
     def profile_read(self):
         """{kernel: (total ms, launches)} since profiling was enabled (synchronises)."""
         ms = np.zeros(5)

@@ -702,7 +702,7 @@ imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
             for (int p = 0; p < 2; ++p)
                 for (int j = 0; j < 2; ++j) {
                     h->m.tune_pending[p][j] = value != 0;
-                    if (!value) h->m.cut_tune[p][j] = imga::Mesh::CutTune();
+                    if (!value) { h->m.cut_tune[p][j] = imga::Mesh::CutTune(); h->m.out_bps[p][j] = 0; }
                 }
             imga::graphs_free(h->m);
             return IMGA_OK;
@@ -717,6 +717,17 @@ imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
         default:
             return fail(IMGA_ERR_INVALID_ARG, "unknown option");
     }
+}
+
+imga_status imga_tuning_interior(imga_mesh h, int32_t* bps, float* ms) {
+    if (!h || !bps) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    for (int p = 0; p < 2; ++p)
+        for (int j = 0; j < 2; ++j) {
+            bps[2 * p + j] = h->m.out_bps[p][j];
+            if (ms)
+                for (int c = 0; c < 4; ++c) ms[8 * p + 4 * j + c] = h->m.out_tune_ms[p][j][c];
+        }
+    return IMGA_OK;
 }
 
 imga_status imga_tuning(imga_mesh h, int32_t* shape, float* ms) {

@@ -194,6 +194,10 @@ struct Mesh {
     CutTune cut_tune[2][2];
     float cut_tune_ms[2][2][6] = {};   // candidate times of the last tuning (ms per launch)
     bool tune_pending[2][2] = {{false, false}, {false, false}};
+    // Out-element bucket: resident blocks per SM of the persistent interior kernel (0: the occupancy
+    // limit), per [float64 / mixed][residual / J v], and the candidate times of the last tuning
+    int out_bps[2][2] = {{0, 0}, {0, 0}};
+    float out_tune_ms[2][2][4] = {};
     std::vector<std::pair<GraphKey, void*>> graphs;
     void* side[3] = {nullptr, nullptr, nullptr};   // two branch streams + the private capture stream
     void* fork_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // fork, 2 joins, caller->graph, graph->caller

@@ -419,65 +419,52 @@ __global__ void __launch_bounds__(128) nitsche_penalty(Args A, const int32_t* __
                                                        const double* __restrict__ pen, const double* __restrict__ xr,
                                                        const double* __restrict__ wr, const double* __restrict__ taub,
                                                        int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
-    const int32_t e = pe[i];
+    // eight threads per element: thread c fetches corner c's jump, then forms row c
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t >> 3;
+    const int c = (int)(t & 7);
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended (uniform over the grid)
+    const bool live = i < n;
+    const int64_t ii = live ? i : n - 1;
+    const int32_t e = pe[ii];
     const double cbmu = A.Cb * Phys<double>(A, prob_of(A, e)).mu;
-    double d[8][3];
-    int32_t ids[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        ids[c] = A.conn[8 * (int64_t)e + c];
-        if (JV) {
-            double v4[4];
-            gather(A, A.V, ids[c], v4);
-            for (int k = 0; k < 3; ++k) d[c][k] = A.theta * v4[k];
-        } else {
-            double u4[4], up4[4];
-            gather(A, A.U, ids[c], u4);
-            if (!A.theta1) gather(A, A.Up, ids[c], up4);
-            for (int k = 0; k < 3; ++k)
-                d[c][k] = (A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k]) - A.g[k];
-        }
+    const int32_t id = A.conn[8 * (int64_t)e + c];
+    double dc[3];
+    if (JV) {
+        double v4[4];
+        gather(A, A.V, id, v4);
+        for (int k = 0; k < 3; ++k) dc[k] = A.theta * v4[k];
+    } else {
+        double u4[4], up4[4];
+        gather(A, A.U, id, u4);
+        if (!A.theta1) gather(A, A.Up, id, up4);
+        for (int k = 0; k < 3; ++k) dc[k] = (A.theta1 ? u4[k] : A.theta * u4[k] + (1.0 - A.theta) * up4[k]) - A.g[k];
     }
-    const double* P = pen + 36 * i;   // upper triangle, row by row
-    double r[8][3];
+    const double* P = pen + 36 * ii;   // upper triangle, row by row: (a, b >= a) at a * 8 - a (a - 1) / 2 + b - a
+    double r[3] = {0.0, 0.0, 0.0};
+    const unsigned base = threadIdx.x & 31 & ~7u;
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
-        for (int k = 0; k < 3; ++k) r[a][k] = 0.0;
-    int t = 0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = a; b < 8; ++b, ++t) {
-            const double m = cbmu * P[t];
-            for (int k = 0; k < 3; ++k) {
-                r[a][k] = fma(m, d[b][k], r[a][k]);
-                if (b != a) r[b][k] = fma(m, d[a][k], r[b][k]);
-            }
-        }
+    for (int b = 0; b < 8; ++b) {
+        const int lo = c < b ? c : b, hi = c < b ? b : c;
+        const double m = cbmu * P[lo * 8 - lo * (lo - 1) / 2 + hi - lo];
+        for (int k = 0; k < 3; ++k) r[k] = fma(m, __shfl_sync(0xffffffffu, dc[k], base | b), r[k]);
+    }
+    if (!live) return;
     if (!JV && A.gpts) {
         for (int64_t q = pq[i]; q < pq[i + 1]; ++q) {
             const double* gq = point_g(A, q);
             double phi[8];
             basis_values_d(xr + 3 * q, phi);
-            const double c = cbmu * wr[q] * taub[q];
-            for (int a = 0; a < 8; ++a)
-                for (int k = 0; k < 3; ++k) r[a][k] = fma(c * phi[a], A.g[k] - gq[k], r[a][k]);
+            const double cq = cbmu * wr[q] * taub[q] * phi[c];
+            for (int k = 0; k < 3; ++k) r[k] = fma(cq, A.g[k] - gq[k], r[k]);
         }
     }
     if (A.ss) {
-        double* dst = A.ss + 32 * pslot[i];
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-            for (int k = 0; k < 3; ++k) dst[4 * a + k] += r[a][k];
+        double* dst = A.ss + 32 * pslot[i] + 4 * c;
+        for (int k = 0; k < 3; ++k) dst[k] += r[k];
     } else {
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const double rr[4] = {r[a][0], r[a][1], r[a][2], 0.0};
-            scatter(A, ids[a], rr);
-        }
+        const double rr[4] = {r[0], r[1], r[2], 0.0};
+        scatter(A, id, rr);
     }
 }
 
@@ -543,26 +530,49 @@ __device__ __forceinline__ void gather_entry(const Args& A, uint32_t e, int64_t 
     }
 }
 
+// (hi, lo) += the float-float pair of the partner lane at distance `off` (fixed pattern)
+__device__ __forceinline__ void ff_merge(float& hi, float& lo, int off) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
+    // lanes of a pair add in the same order (lower lane's pair first): identical bits in both
+    const bool low = (threadIdx.x & off) == 0;
+    float h = low ? hi : oh, l = low ? lo : ol;
+    ff_add(h, l, low ? oh : hi);
+    l = __fadd_rn(l, low ? ol : lo);
+    hi = h;
+    lo = l;
+}
+
+// Deterministic o2n (Algorithm 2): four threads per node; thread j of the quad sums entries j, j + 4,
+// ... of the node's incidence list in list order (a hanging corner's rows times 1/2 or 1/4 for each
+// parent), then the quad merges its four partial sums in a fixed pattern (float-float in mixed
+// precision), and the node's strong rows take U - g (R) or v (J v) as in strong_rows.  Writes every
+// row of out: no zeroing before the call.
 template <class T>
 __global__ void __launch_bounds__(256) node_gather(Args A, const int64_t* __restrict__ ptr,
                                                    const uint32_t* __restrict__ inc, int64_t nv,
                                                    const uint8_t* __restrict__ flag, const uint8_t* __restrict__ umask,
                                                    const double* __restrict__ uval, double ux, double uy, double uz,
                                                    int jv) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= A.n_nodes) return;
-    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = t >> 2;
+    const int j = (int)(t & 3);
+    const bool live = n < A.n_nodes;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended (uniform over the grid)
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    const int64_t q1 = ptr[n + 1];
-    int64_t q = ptr[n];
-    // two entries per pass: their loads are independent; the sums still follow the list order
-    for (; q + 1 < q1; q += 2) {
-        const uint32_t e0 = __ldg(inc + q), e1 = __ldg(inc + q + 1);
-        gather_entry<T>(A, e0, nv, acc, hi, lo);
-        gather_entry<T>(A, e1, nv, acc, hi, lo);
+    if (live) {
+        const int64_t q1 = ptr[n + 1];
+        for (int64_t q = ptr[n] + j; q < q1; q += 4) gather_entry<T>(A, __ldg(inc + q), nv, acc, hi, lo);
     }
-    if (q < q1) gather_entry<T>(A, __ldg(inc + q), nv, acc, hi, lo);
+    // merge the quad (every lane takes part in the shuffles)
+    for (int off = 1; off < 4; off <<= 1) {
+        for (int k = 0; k < 4; ++k) {
+            if constexpr (sizeof(T) == 4) ff_merge(hi[k], lo[k], off);
+            const double o = __shfl_xor_sync(0xffffffffu, acc[k], off);
+            acc[k] = (threadIdx.x & off) == 0 ? acc[k] + o : o + acc[k];
+        }
+    }
+    if (!live || j != 0) return;
     if constexpr (sizeof(T) == 4)
         for (int k = 0; k < 4; ++k) acc[k] += f2d(hi[k]) + f2d(lo[k]);
     // strong rows (as strong_rows)
@@ -628,16 +638,19 @@ void launch_cut(const Mesh& m, const Args& A, cudaStream_t s, int wpb, int lpt) 
     }
 }
 
+template <class T, bool JV>
+int interior_blocks_per_sm();
+
 // Autotuner of the Intercepted-element bucket: with the node data of this call prepared, time every
 // (warps per block, element order) candidate on the call's own inputs (3 launches each after one
-// untimed) and keep the fastest.  Writes into the output vector, which the call then recomputes.
+// untimed) and keep the fastest; then the Out-element bucket: the persistent interior kernel with
+// 1 .. 4 resident blocks per SM.  Writes into the output vector, which the call then recomputes.
 template <class T, bool JV>
 int autotune_cut(Mesh& m, Args A, cudaStream_t s) {
     const int64_t nc = (int64_t)m.cut_list.size();
     Mesh::CutTune& ct = m.cut_tune[sizeof(T) == 4][JV];
     m.tune_pending[sizeof(T) == 4][JV] = false;
-    if (nc == 0) return 0;
-    if (!m.d.cut_order) {   // longest first: positions of the list by decreasing point count
+    if (nc > 0 && !m.d.cut_order) {   // longest first: positions of the list by decreasing point count
         std::vector<int32_t> ord(nc);
         for (int64_t i = 0; i < nc; ++i) ord[i] = (int32_t)i;
         std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
@@ -659,7 +672,7 @@ int autotune_cut(Mesh& m, Args A, cudaStream_t s) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    for (int wi = 0; wi < nw; ++wi)
+    for (int wi = 0; wi < nw && nc > 0; ++wi)
         for (int lpt = 0; lpt < 2; ++lpt) {
             launch_cut<T, JV>(m, A, s, wpbs[wi], lpt);
             cudaEventRecord(e0, s);
@@ -672,6 +685,27 @@ int autotune_cut(Mesh& m, Args A, cudaStream_t s) {
             m.cut_tune_ms[sizeof(T) == 4][JV][2 * wi + lpt] = ms;
             if (ms < best) { best = ms; ct.wpb = wpbs[wi]; ct.lpt = lpt; }
         }
+    // the Out-element bucket: the persistent interior kernel with 1 .. (occupancy limit) blocks per SM
+    const int64_t no = (int64_t)m.out_list.size();
+    constexpr int EPB = Epb<T>::value;
+    const int maxb = std::min(4, interior_blocks_per_sm<T, JV>());
+    float best_out = 1e30f;
+    for (int b = 1; b <= maxb && no > 0; ++b) {
+        const int64_t grid = std::min<int64_t>((no + EPB - 1) / EPB, (int64_t)b * m.n_sm);
+        auto run = [&]() {
+            vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, IntShape<T>::smem, s>>>(A, m.d.out_conn, m.d.out_lev, m.d.out_prob, no);
+        };
+        run();
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) run();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        m.out_tune_ms[sizeof(T) == 4][JV][b - 1] = ms;
+        if (ms < best_out) { best_out = ms; m.out_bps[sizeof(T) == 4][JV] = b; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
@@ -716,7 +750,8 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     constexpr int EPB = Epb<T>::value;
     if (no > 0) {
         Timed t(m, 0, s, 1, !ws);
-        const int bps = interior_blocks_per_sm<T, JV>();
+        const int tuned = m.out_bps[sizeof(T) == 4][JV];
+        const int bps = tuned > 0 ? tuned : interior_blocks_per_sm<T, JV>();
         const size_t smem = IntShape<T>::smem;
         const int64_t groups = (no + EPB - 1) / EPB;
         const int64_t grid = std::min<int64_t>(groups, (int64_t)bps * m.n_sm);
@@ -741,7 +776,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     const int64_t np = (int64_t)m.pen_elem.size();
     if (np > 0) {   // after both surface kernels (same stream): the slots hold their rows
         Timed t(m, 2, ss, 1, !ws);
-        nitsche_penalty<JV><<<(unsigned)((np + 127) / 128), 128, 0, ss>>>(A, m.d.pen_elem, m.d.pen_q, m.d.pen_slot, m.d.pen,
+        nitsche_penalty<JV><<<(unsigned)((8 * np + 127) / 128), 128, 0, ss>>>(A, m.d.pen_elem, m.d.pen_q, m.d.pen_slot, m.d.pen,
                                                                         m.d.sq_x, m.d.sq_w, m.d.sq_taub, np);
     }
     if (ev) {   // join
@@ -760,12 +795,12 @@ void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bo
     if (nn > 0 && A.sv) {
         const uint8_t* um = m.user_bc ? m.d.bcmask_user : nullptr;
         const double* uv = m.user_bc ? m.d.bcval_user : nullptr;
-        const unsigned g = (unsigned)((nn + 255) / 256);
+        const unsigned g4 = (unsigned)((4 * nn + 255) / 256);   // four threads per node
         if (precision == 0)
-            node_gather<double><<<g, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
+            node_gather<double><<<g4, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
                                                   ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
         else
-            node_gather<float><<<g, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
+            node_gather<float><<<g4, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
                                                  ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
         return;
     }

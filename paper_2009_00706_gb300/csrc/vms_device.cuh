@@ -92,7 +92,8 @@ template <class T, int K> __device__ __forceinline__ Dual<T, K> rsq(Dual<T, K> x
     T r = rsq(x.v);
     return {r, T(-0.5) * r * r * r * x.d};
 }
-__device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
+// float: the approximate reciprocal (at most 2 ulp; the mixed path's tolerance is orders above it)
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 template <class T, int K> __device__ __forceinline__ Dual<T, K> rcp(Dual<T, K> x) {
     T r = rcp(x.v);
