@@ -470,6 +470,8 @@ def run_ours(args):
         gms += a.elapsed_time(b)
     extra["jv_mixed_graph"] = n_active * 20 / (gms / 1e3)
     mesh.use_graphs(False)
+    extra["fused"] = run_fused(mesh, step, flush, stream, n_active)
+    extra["scatter"] = run_scatter_modes(mesh, step, flush, stream, n_active)
     batched = run_batched(args, dev, stream) if not args.no_batched else None
     bluff = run_bluff(args, dev, stream) if not args.no_bluff else None
 
@@ -595,6 +597,144 @@ def run_ours(args):
     return 0
 
 
+def run_fused(mesh, step, flush, stream, n_active, reps=20):
+    """The same J v with the buckets in one persistent launch (IMGA_OPT_FUSED), direct and as a CUDA
+    graph, L2 flushed between steps; the fused kernel's own time from events around it."""
+    import torch
+
+    res = {}
+    mesh.fused(True)
+    try:
+        res["queue"] = mesh.fused_info()
+        # warps per block that start on the costly items: keep the fastest
+        split = {}
+        for hw in (4, 2, 1):
+            mesh.fused_split(hw)
+            step()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                a.record(stream)
+                step()
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            split[hw] = tot / reps
+        best = min(split, key=split.get)
+        mesh.fused_split(best)
+        res["split_ms_per_jv"] = {str(k): v for k, v in split.items()}
+        res["heavy_first_warps"] = best
+        for graphs in (False, True):
+            mesh.use_graphs(graphs)
+            step()
+            torch.cuda.synchronize()
+            tot = 0.0
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(reps):
+                flush.zero_()
+                a.record(stream)
+                step()
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            res["graph" if graphs else "direct"] = {"ms_per_jv": tot / reps, "elements_per_s": n_active * reps / (tot / 1e3)}
+        mesh.use_graphs(False)
+        mesh.profile(True)
+        for _ in range(reps):
+            flush.zero_()
+            step()
+        prof = mesh.profile_read()
+        mesh.profile(False)
+        res["kernel_ms"] = {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1]}
+    finally:
+        mesh.use_graphs(False)
+        mesh.fused_split(4)
+        mesh.fused(False)
+    return res
+
+
+def run_scatter_modes(mesh, step, flush, stream, n_active, reps=20):
+    """J v with the deterministic scatter (slots + ordered node sums, the default) against float64
+    atomic additions (IMGA_OPT_DETERMINISTIC off), L2 flushed between steps, with per-kernel times."""
+    import torch
+
+    res = {}
+    try:
+        for det in (True, False):
+            mesh.deterministic(det)
+            step()
+            torch.cuda.synchronize()
+            mesh.profile(True)
+            tot = 0.0
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(reps):
+                flush.zero_()
+                a.record(stream)
+                step()
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            prof = mesh.profile_read()
+            mesh.profile(False)
+            res["deterministic" if det else "atomic"] = {
+                "ms_per_jv": tot / reps, "elements_per_s": n_active * reps / (tot / 1e3),
+                "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1]}}
+    finally:
+        mesh.deterministic(True)
+    return res
+
+
+def run_batched_newton(B, sep, probs, states, dev, max_newton=4, max_krylov=600):
+    """One Newton solve of all 64 problems through the batched mesh (one GMRES on the block-diagonal
+    system, the whole solve replayed as one CUDA graph) against 64 solves one mesh after the other
+    (each also one graph).  Mixed precision, block-Jacobi, GMRES(50); capped at max_newton Newton and
+    max_krylov Krylov iterations per solve, since block-Jacobi does not bring every high-Reynolds
+    problem to 1e-8: the reductions reached are reported beside the times."""
+    import torch
+
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    kw = dict(precision=1, precond=1, rtol=1e-8, gmres_m=50, max_newton=max_newton, max_krylov=max_krylov,
+              raise_on_failure=False)
+    u0 = np.concatenate([s[0] for s in states])
+    up = T(np.concatenate([s[1] for s in states]))
+    out = {"max_newton": max_newton, "max_krylov": max_krylov}
+    B.use_graphs(True)
+    try:
+        B.newton_step(probs[0].physics, T(u0), up, **kw)   # capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = B.newton_step(probs[0].physics, T(u0), up, **kw)
+        torch.cuda.synchronize()
+        out["one_batched_graph"] = {"s": time.perf_counter() - t0, "newton_its": st["newton_its"],
+                                    "krylov_its": st["krylov_its"], "converged": bool(st["converged"]),
+                                    "rel_res": st["res_norm"][-1] / max(st["res_norm"][0], 1e-300)}
+    finally:
+        B.use_graphs(False)
+    rels, conv, kits = [], 0, 0
+    for m in sep:
+        m.use_graphs(True)
+    try:
+        ups = [T(s[1]) for s in states]
+        for m, w, s, u in zip(sep, probs, states, ups):   # capture
+            m.newton_step(w.physics, T(s[0]), u, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m, w, s, u in zip(sep, probs, states, ups):
+            st = m.newton_step(w.physics, T(s[0]), u, **kw)
+            rels.append(st["res_norm"][-1] / max(st["res_norm"][0], 1e-300))
+            conv += bool(st["converged"])
+            kits += st["krylov_its"]
+        torch.cuda.synchronize()
+        out["sequential_64_graphs"] = {"s": time.perf_counter() - t0, "converged": conv, "krylov_its": kits,
+                                       "rel_res_max": max(rels), "rel_res_median": float(np.median(rels))}
+    finally:
+        for m in sep:
+            m.use_graphs(False)
+    return out
+
+
 def run_batched(args, dev, stream):
     """64 independent sphere problems (5k-200k elements, Re 1-1e6): J v of all of them through one
     batched mesh (one launch of each kernel) vs 64 meshes called one after the other."""
@@ -649,6 +789,23 @@ def run_batched(args, dev, stream):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / 10
     res["one_batched_graph"] = {"ms_per_jv": ms, "elements_per_s": n_act / (ms / 1e3)}
+    B.use_graphs(False)
+    # the buckets of all 64 problems in one persistent launch
+    B.fused(True)
+    for graphs in (False, True):
+        B.use_graphs(graphs)
+        batched_step()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(10):
+            batched_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        res["one_fused_graph" if graphs else "one_fused_launch"] = {"ms_per_jv": ms, "elements_per_s": n_act / (ms / 1e3)}
+    B.use_graphs(False)
+    B.fused(False)
+    res["newton"] = run_batched_newton(B, sep, probs, states, dev)
     for m in sep:
         m.close()
     B.close()

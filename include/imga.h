@@ -421,7 +421,7 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
 /* IMGA_OPT_AUTOTUNE (value 1): the next imga_residual / imga_jvp call of each precision and kind
  * (residual or J v) first times the Intercepted-element kernel in every tile shape -- 2, 4 or 8
  * warps per block (8 in mixed precision only), elements in Morton order or longest first -- and the
- * persistent Out-element kernel with 1 to 4 resident blocks per SM, on the call's own inputs, and
+ * persistent Out-element kernel with 1 to 5 resident blocks per SM, on the call's own inputs, and
  * keeps the fastest of each for that mesh.  This follows the cost model of
  * Eq. (Wpart): the bucket of elements with uneven quadrature counts (8 to 4096 points).  Tuning
  * synchronises the stream, allocates (once per mesh) a 4-byte-per-element index of the Intercepted
@@ -439,7 +439,21 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * strong rows: two calls with the same inputs give the same bits.  Off, the element kernels add into
  * the output with float64 atomics, whose order, and so the last bits, vary from run to run.  Both
  * values drop the cached graphs. */
-enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2, IMGA_OPT_CLASSIFY_RAYS = 3, IMGA_OPT_DETERMINISTIC = 4 };
+/* IMGA_OPT_FUSED (value 1 on, 0 off, default off): imga_residual and imga_jvp (and the solvers built
+ * on them) evaluate the Out, Intercepted and surface buckets in ONE persistent launch.  Its warps
+ * drain a device work queue: first the Intercepted elements, the elements hosting many surface
+ * points and the groups of 32 points of the others, one per claim, in decreasing order of a cost
+ * estimate from Eq. (Wpart) (rounds of 32 points, surface points weighted by T_s/T_v = 4); then the
+ * Out elements, 4 per warp item and 8 items per claim.  The float64 Nitsche penalty follows as a
+ * second launch.  Results equal the bucketed launches' up to the order of the float64 atomic
+ * additions, and bit for bit with IMGA_OPT_DETERMINISTIC.  The first switch-on builds the queue (a
+ * synchronous upload).  Fails with IMGA_ERR_CUDA if that fails. */
+/* IMGA_OPT_FUSED_SPLIT (value 1 .. 4, default 4): how many of the fused kernel's 4 warps per block
+ * start on the costly items; the others start on the Out elements and take what is left of the
+ * costly items at the end, so latency-bound costly work can share the SMs with the arithmetic-bound
+ * Out elements. */
+enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2, IMGA_OPT_CLASSIFY_RAYS = 3, IMGA_OPT_DETERMINISTIC = 4, IMGA_OPT_FUSED = 5,
+       IMGA_OPT_FUSED_SPLIT = 6 };
 imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
 
 /* The tile shapes in use.  shape[8] = {warps per block, longest-first order} for
@@ -448,16 +462,21 @@ imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
  * an entry is 0 where not measured. */
 imga_status imga_tuning(imga_mesh mesh, int32_t* shape, float* ms);
 /* The Out-element bucket's tuning (IMGA_OPT_AUTOTUNE also times the persistent interior kernel with 1,
- * 2, 3 and 4 resident blocks per SM and keeps the fastest): bps[4] for [float64, mixed] x [residual,
- * J v] (0: not tuned, the occupancy limit is used); if ms is non-null, ms[16] the per-launch
- * milliseconds of the candidates (0 where not measured). */
+ * 2, 3 and 4 resident blocks per SM, and in mixed precision 5 with a register allocation made for 5,
+ * and keeps the fastest): bps[4] for [float64, mixed] x [residual, J v] (0: not tuned, the occupancy
+ * limit is used); if ms is non-null, ms[20] the per-launch milliseconds of the candidates 1 .. 5
+ * (0 where not measured). */
 imga_status imga_tuning_interior(imga_mesh mesh, int32_t* bps, float* ms);
+/* The fused launch's queue (IMGA_OPT_FUSED): counts[6] = {1 if on, Intercepted elements, dense
+ * surface elements, groups of 32 sparse surface points, Out elements, IMGA_OPT_FUSED_SPLIT}. */
+imga_status imga_fused_info(imga_mesh mesh, int64_t* counts);
 
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that
  * imga_residual / imga_jvp launch.  enable = 1 starts (and zeroes) the counters, 0 stops.
  * imga_profile_read synchronises the device and returns, per kernel class (0 Out elements,
- * 1 Intercepted elements, 2 Nitsche surface points, 3 strong rows, 4 node preparation), the
- * summed milliseconds ms[5] and the kernel launch counts launches[5] since profiling was enabled
+ * 1 Intercepted elements, 2 Nitsche surface points, 3 strong rows or node sums, 4 node preparation,
+ * 5 the fused launch of IMGA_OPT_FUSED), the summed milliseconds ms[6] and the kernel launch
+ * counts launches[6] since profiling was enabled
  * (node preparation is one timed span of up to two kernels; the surface class counts its
  * thread-per-point and warp-per-element kernels separately). */
 imga_status imga_profile(imga_mesh mesh, int enable);

@@ -182,6 +182,7 @@ SIGNATURES = {
     "imga_partition_residual": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.POINTER(Physics), _int, _dp, _vp]),
     "imga_partition_jvp": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.POINTER(Physics), _int, _dp, _dp, _vp]),
     "imga_tuning_interior": (C.c_int, [_vp, _vp, _vp]),
+    "imga_fused_info": (C.c_int, [_vp, _vp]),
 }
 
 _lib = None

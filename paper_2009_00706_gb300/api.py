@@ -417,20 +417,34 @@ class Mesh:
                 out[(p, kind)] = (int(shape[4 * p + 2 * j]), int(shape[4 * p + 2 * j + 1]), ms[12 * p + 6 * j:12 * p + 6 * j + 6].tolist())
         return out
 
+    def fused(self, on=True):
+        """IMGA_OPT_FUSED: the Out, Intercepted and surface buckets in one persistent launch."""
+        check(_lib.load().imga_set_option(self.h, 5, int(bool(on))))
+
+    def fused_split(self, heavy_warps):
+        """IMGA_OPT_FUSED_SPLIT: warps per block (1 .. 4) that start on the costly items."""
+        check(_lib.load().imga_set_option(self.h, 6, int(heavy_warps)))
+
+    def fused_info(self):
+        c = np.zeros(6, np.int64)
+        check(_lib.load().imga_fused_info(self.h, c.ctypes.data_as(C.c_void_p)))
+        return {"on": bool(c[0]), "cut_items": int(c[1]), "dense_surface_items": int(c[2]),
+                "sparse_surface_groups": int(c[3]), "out_elements": int(c[4]), "heavy_first_warps": int(c[5])}
+
     def tuning_interior(self):
-        """{(precision, 'residual' | 'jvp'): (blocks per SM in use (0: occupancy limit), candidate ms[4])}"""
+        """{(precision, 'residual' | 'jvp'): (blocks per SM in use (0: occupancy limit), candidate ms[5])}"""
         bps = np.zeros(4, np.int32)
-        ms = np.zeros(16, np.float32)
+        ms = np.zeros(20, np.float32)
         check(_lib.load().imga_tuning_interior(self.h, bps.ctypes.data_as(C.c_void_p), ms.ctypes.data_as(C.c_void_p)))
-        return {(p, kind): (int(bps[2 * p + j]), ms[8 * p + 4 * j:8 * p + 4 * j + 4].tolist())
+        return {(p, kind): (int(bps[2 * p + j]), ms[10 * p + 5 * j:10 * p + 5 * j + 5].tolist())
                 for p in range(2) for j, kind in enumerate(("residual", "jvp"))}
 
     def profile_read(self):
         """{kernel: (total ms, launches)} since profiling was enabled (synchronises)."""
-        ms = np.zeros(5)
-        n = np.zeros(5, np.int64)
+        ms = np.zeros(6)
+        n = np.zeros(6, np.int64)
         check(_lib.load().imga_profile_read(self.h, ms.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p)))
-        names = ("out_elements", "cut_elements", "nitsche", "strong_rows", "node_prep")
+        names = ("out_elements", "cut_elements", "nitsche", "strong_rows", "node_prep", "fused")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
 
     def set_dirichlet(self, mask=None, vals=None, stream=None):

@@ -714,9 +714,32 @@ imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
             h->m.deterministic = value != 0;
             imga::graphs_free(h->m);   // captured launches carry the scatter
             return IMGA_OK;
+        case IMGA_OPT_FUSED: {
+            if (value && !h->m.d.fq_cnt) {
+                std::string err;
+                if (imga::fused_prepare(h->m, err)) return fail(IMGA_ERR_CUDA, err);
+            }
+            h->m.fused = value != 0;
+            imga::graphs_free(h->m);   // captured launches carry the kernels
+            return IMGA_OK;
+        }
+        case IMGA_OPT_FUSED_SPLIT:
+            if (value < 1 || value > 4) return fail(IMGA_ERR_INVALID_ARG, "IMGA_OPT_FUSED_SPLIT takes 1 .. 4");
+            h->m.fused_heavy_warps = (int)value;
+            imga::graphs_free(h->m);
+            return IMGA_OK;
         default:
             return fail(IMGA_ERR_INVALID_ARG, "unknown option");
     }
+}
+
+imga_status imga_fused_info(imga_mesh h, int64_t* counts) {
+    if (!h || !counts) return fail(IMGA_ERR_INVALID_ARG, "null argument");
+    counts[0] = h->m.fused ? 1 : 0;
+    for (int k = 0; k < 3; ++k) counts[1 + k] = h->m.fq_counts[k];
+    counts[4] = (int64_t)h->m.out_list.size();
+    counts[5] = h->m.fused_heavy_warps;
+    return IMGA_OK;
 }
 
 imga_status imga_tuning_interior(imga_mesh h, int32_t* bps, float* ms) {
@@ -725,7 +748,7 @@ imga_status imga_tuning_interior(imga_mesh h, int32_t* bps, float* ms) {
         for (int j = 0; j < 2; ++j) {
             bps[2 * p + j] = h->m.out_bps[p][j];
             if (ms)
-                for (int c = 0; c < 4; ++c) ms[8 * p + 4 * j + c] = h->m.out_tune_ms[p][j][c];
+                for (int c = 0; c < 5; ++c) ms[10 * p + 5 * j + c] = h->m.out_tune_ms[p][j][c];
         }
     return IMGA_OK;
 }
@@ -752,7 +775,7 @@ imga_status imga_profile(imga_mesh h, int enable) {
 imga_status imga_profile_read(imga_mesh h, double* ms, int64_t* launches) {
     if (!h) return fail(IMGA_ERR_INVALID_ARG, "null mesh");
     if (imga::profile_collect(h->m)) return cuda_status("profile_read");
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < imga::kProfKinds; ++k) {
         if (ms) ms[k] = h->m.prof_ms[k];
         if (launches) launches[k] = h->m.prof_n[k];
     }

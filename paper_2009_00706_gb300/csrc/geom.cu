@@ -577,6 +577,7 @@ bool device_upload_quadrature(Mesh& m, std::string& err) {
         if (j == m.n_sq_sparse || el[j] != el[j - 1]) { sl.push_back(el[j]); so.push_back(j); }
     so.push_back(ns);
     m.n_sq_elem = (int64_t)sl.size();
+    m.sq_off_h = so;
     m.sq_hosts.assign(el.begin(), el.end());
     std::sort(m.sq_hosts.begin(), m.sq_hosts.end());
     m.sq_hosts.erase(std::unique(m.sq_hosts.begin(), m.sq_hosts.end()), m.sq_hosts.end());
@@ -685,7 +686,7 @@ void device_free(Mesh& m) {
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
                     d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.cut_order, d.sq_elem, d.sq_x,
                     d.sq_n, d.sq_w, d.sq_taub, d.sq_src, d.sq_hosts, d.pen_elem, d.pen_q, d.pen_slot, d.pen, d.inc_ptr, d.inc, d.sv, d.ss, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
-                    d.counters};
+                    d.counters, d.fq_items, d.fq_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh();

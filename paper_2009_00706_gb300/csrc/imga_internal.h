@@ -111,6 +111,9 @@ struct DeviceMesh {
     double* ss = nullptr;         // surface slots [n_sslots][8][4] float64
     int32_t* sq_list = nullptr;   // elements hosting at least kNitscheDenseMin surface points
     int64_t* sq_off = nullptr;    // [n_sq_elem + 1] their point ranges in the sorted arrays
+    // fused launch: work items (bits 30-31 kind, 0-29 index) and the claim counters [2]
+    uint32_t* fq_items = nullptr;
+    unsigned long long* fq_cnt = nullptr;
     // per-call node workspace (node_prep): value, tangent and force data of every independent and
     // hanging node, one float and one double copy
     float* nd_f = nullptr;        // [3][n_nodes + n_hang][8]
@@ -126,6 +129,8 @@ struct DeviceMesh {
 
 // elements hosting at least this many surface points take the warp-per-element surface kernel
 constexpr int kNitscheDenseMin = 8;
+// timed kernel classes: Out, Intercepted, surface, strong rows / node sums, node preparation, fused launch
+constexpr int kProfKinds = 6;
 
 struct GraphKey {
     const double *u, *up, *up2, *f, *v;
@@ -169,6 +174,7 @@ struct Mesh {
     int64_t n_sq_elem = 0;               // elements hosting >= kNitscheDenseMin surface points
     std::vector<int32_t> sq_hosts;       // every element hosting a surface point (increasing)
     std::vector<int32_t> pen_elem;       // surface-hosting elements in device point order (nitsche_penalty)
+    std::vector<int64_t> sq_off_h;       // host copy of DeviceMesh::sq_off
     int64_t n_vslots = 0, n_sslots = 0;  // deterministic scatter: volume slots (active elements), surface slots
     bool deterministic = true;           // IMGA_OPT_DETERMINISTIC: slots + ordered node sums (1) or atomics (0)
     std::vector<uint8_t> bcflag;
@@ -197,7 +203,13 @@ struct Mesh {
     // Out-element bucket: resident blocks per SM of the persistent interior kernel (0: the occupancy
     // limit), per [float64 / mixed][residual / J v], and the candidate times of the last tuning
     int out_bps[2][2] = {{0, 0}, {0, 0}};
-    float out_tune_ms[2][2][4] = {};
+    float out_tune_ms[2][2][5] = {};
+    // one persistent launch over the Out, Intercepted and surface buckets (IMGA_OPT_FUSED): the
+    // queue of per-warp items that are not Out elements, by decreasing estimated cost (Eq. Wpart)
+    bool fused = false;
+    int fused_heavy_warps = 4;           // warps per block that start on the costly items (1 .. 4)
+    int64_t fq_n = 0;                    // items in fq_items
+    int64_t fq_counts[3] = {0, 0, 0};    // Intercepted elements, dense surface elements, sparse point groups
     std::vector<std::pair<GraphKey, void*>> graphs;
     void* side[3] = {nullptr, nullptr, nullptr};   // two branch streams + the private capture stream
     void* fork_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // fork, 2 joins, caller->graph, graph->caller
@@ -210,9 +222,9 @@ struct Mesh {
     // per-kernel profiling (CUDA events, one pair per launch, resolved at read time)
     bool profiling = false;
     struct ProfEv { void *a, *b; int launches; };   // event pair around `launches` kernels
-    std::vector<ProfEv> prof_ev[5];
-    double prof_ms[5] = {0, 0, 0, 0, 0};
-    int64_t prof_n[5] = {0, 0, 0, 0, 0};
+    std::vector<ProfEv> prof_ev[kProfKinds];
+    double prof_ms[kProfKinds] = {};
+    int64_t prof_n[kProfKinds] = {};
     size_t scratch_bytes = 0;
 
     int64_t n_elem() const { return (int64_t)lev.size(); }
@@ -262,6 +274,7 @@ constexpr int kForcePartials = 256 * 3;   // doubles of workspace for surface_fo
 
 void profile_reset(Mesh& m);
 int profile_collect(Mesh& m);
+int fused_prepare(Mesh& m, std::string& err);
 void graphs_free(Mesh& m);
 
 // element Jacobians and block-Jacobi (jac.cu)

@@ -56,22 +56,99 @@ template <class T> struct IntShape {
     static constexpr size_t smem = (size_t)(2 * EPB * ESTR + EPB * 8 * MSTR) * sizeof(T);
 };
 
+// One Out element on 8 lanes of a warp (lane & 7 = corner c): the element's rows `nd` are in
+// shared memory (8 rows of CS, stride CS); the warp's moment rows s_mw [32][MSTR].  Thread c
+// transforms column c of the rows into monomial coefficients, evaluates Gauss point c (monomials m),
+// writes the point's 32 monomial moments, then sums moment column S = c over the 8 points and runs
+// the backward butterfly: node c's rows, scattered (or stored to the element's slot).  Every lane of
+// the warp takes part (valid: this lane's element exists).
+template <class T, bool JV>
+__device__ __forceinline__ void interior_element(const Args& A, T* nd, T* s_mw, const T m[8], int lane, int64_t idx,
+                                                 bool valid, int lv, int prob, int32_t id) {
+    typedef typename std::conditional<JV, Dual<T, sizeof(T) == 4>, T>::type S;
+    constexpr int MSTR = IntShape<T>::MSTR;
+    const int c = lane & 7;
+    T* mrow = s_mw + lane * MSTR;
+    const T* mcol = s_mw + (lane >> 3) * 8 * MSTR + 4 * c;
+    __syncwarp();
+    {   // corner values -> monomial coefficients: thread c transforms column c of the element's rows
+        if (c < 7) {
+            column_to_monomial<T>(nd + c);
+            if (JV) column_to_monomial<T>(nd + CT + c);
+        }
+        if (A.ndf && c < 3) column_to_monomial<T>(nd + CF + c);
+    }
+    __syncwarp();
+    const T g = lvl_g<T>(A, lv);
+    const Phys<T> P(A, prob);
+    S cf[16];
+    vms_point_modal<S, T>(A, P, m, nd, CS, g, cf);
+    const T wq = lvl_w<T>(A, lv), wqg = wq * g;
+    // F, G multiply phi; S, H multiply physical gradients = g x reference gradients
+    T w16[16];
+    for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
+    T M[32];
+    for (int k = 0; k < 32; ++k) M[k] = T(0);
+    add_moments<T, true>(m, w16, M);
+    for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
+    __syncwarp();
+    T r[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        T v[4];
+        ld4s<T>(mcol + q * MSTR, v);
+        r[0] += v[0]; r[1] += v[1]; r[2] += v[2]; r[3] += v[3];
+    }
+    for (int k = 0; k < 4; ++k) r[k] = hadamard_bwd<1>(r[k], c);
+    if (A.sv) {
+        // deterministic scatter: node c's 4 rows into the element's slot (one 16- or 32-byte store)
+        if (valid) st4s<T>((T*)A.sv + 32 * idx + 4 * c, r[0], r[1], r[2], r[3]);
+    } else if constexpr (sizeof(T) == 4) {
+        // corners of this warp's 4 elements that are the same node add their rows in shared memory
+        // first; one lane per node scatters (fewer float64 atomics; float64: the plain scatter is faster)
+        const unsigned grp = __match_any_sync(0xffffffffu, valid ? id : -1 - lane);
+        __syncwarp();   // every lane has read its moment columns
+        st4s<T>(mrow, r[0], r[1], r[2], r[3]);
+        __syncwarp();
+        if (valid && lane == __ffs(grp) - 1) {
+            T t[4] = {T(0), T(0), T(0), T(0)};
+            for (unsigned gm = grp; gm; gm &= gm - 1) {
+                T v[4];
+                ld4s<T>(s_mw + (__ffs(gm) - 1) * MSTR, v);
+                for (int k = 0; k < 4; ++k) t[k] += v[k];
+            }
+            scatter_t(A, id, t);
+        }
+    } else {
+        if (valid) scatter_t(A, id, r);
+    }
+    __syncwarp();   // the rows and the moments are rewritten by later elements
+}
+
+// Gauss point c of the 2x2x2 rule (xi_k = +-1/sqrt(3) by bit k of c) in monomial form
+template <class T>
+__device__ __forceinline__ void gauss_monomials(int c, T m[8]) {
+    const T gauss = (T)0.57735026918962576451;
+    T xi[3];
+    for (int k = 0; k < 3; ++k) xi[k] = ((c >> k) & 1) ? gauss : -gauss;
+    monomials<T>(xi, m);
+}
+
 // Persistent: a block walks element groups with a grid stride; while it computes group g its
 // threads already stream the node rows of group g + stride into the other shared buffer
-// (cp.async), so the gather latency hides behind the arithmetic.  Thread c of an element
-// gathers corner c, transforms column c of the element's rows into monomial coefficients,
-// evaluates Gauss point c, writes the point's 32 monomial moments,
-// then sums moment column S = c over the 8 points and runs the backward butterfly: node c's rows.
-template <class T, bool JV>
-__global__ void __launch_bounds__(IntShape<T>::THREADS, sizeof(T) == 4 ? 4 : 2) vms_interior(Args A, const int32_t* __restrict__ oconn,
+// (cp.async), so the gather latency hides behind the arithmetic.  Each warp computes 4 of the
+// group's 16 elements (interior_element).
+// MINB: resident blocks per SM the register allocation is made for (4: up to 128 registers per thread;
+// 5: up to 102, a few spills, one more block of warps to hide latency with)
+template <class T, bool JV, int MINB = (sizeof(T) == 4 ? 4 : 2)>
+__global__ void __launch_bounds__(IntShape<T>::THREADS, MINB) vms_interior(Args A, const int32_t* __restrict__ oconn,
                                                     const uint8_t* __restrict__ olev,
                                                     const uint16_t* __restrict__ oprob, int64_t n) {
-    typedef typename std::conditional<JV, Dual<T, sizeof(T) == 4>, T>::type S;
     constexpr int EPB = IntShape<T>::EPB, ESTR = IntShape<T>::ESTR, MSTR = IntShape<T>::MSTR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s_nd = reinterpret_cast<T*>(smem_raw);          // [2][EPB][ESTR]: 8 rows of CS per element
     T* s_m = s_nd + 2 * EPB * ESTR;                     // [EPB][8][MSTR]
-    const int c = threadIdx.x & 7, le = threadIdx.x >> 3;
+    const int c = threadIdx.x & 7, le = threadIdx.x >> 3, lane = threadIdx.x & 31;
     const int64_t ngroups = (n + EPB - 1) / EPB;
     int64_t gi = blockIdx.x;
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
@@ -81,89 +158,35 @@ __global__ void __launch_bounds__(IntShape<T>::THREADS, sizeof(T) == 4 ? 4 : 2) 
         if (idx >= n) idx = n - 1;
         return __ldg(oconn + 8 * idx + c);
     };
+    // level (and problem) of this lane's element of a group, loaded a group ahead of its use
+    auto level_prob = [&](int64_t grp) -> int {
+        int64_t idx = grp * EPB + le;
+        if (idx >= n) idx = n - 1;
+        return (int)__ldg(olev + idx) | (oprob ? (int)oprob[idx] << 8 : -256);
+    };
     auto row = [&](int buf) -> T* { return s_nd + (buf * EPB + le) * ESTR + c * CS; };
     int32_t id_cur = corner_id(gi);
     corner_async<T, JV>(A, id_cur, row(0));
     cp_commit();
     int32_t id_next = gi + gridDim.x < ngroups ? corner_id(gi + gridDim.x) : 0;
-    // Gauss point c: xi_k = +-1/sqrt(3) by bit k of c
+    int lp_cur = level_prob(gi);
     T m[8];
-    {
-        const T gauss = (T)0.57735026918962576451;
-        T xi[3];
-        for (int k = 0; k < 3; ++k) xi[k] = ((c >> k) & 1) ? gauss : -gauss;
-        monomials<T>(xi, m);
-    }
-    T* mrow = s_m + (le * 8 + c) * MSTR;
-    const T* mcol = s_m + le * 8 * MSTR + 4 * c;
+    gauss_monomials<T>(c, m);
+    T* s_mw = s_m + (threadIdx.x & ~31u) * MSTR;
     int buf = 0;
     for (; gi < ngroups; gi += gridDim.x) {
         const int64_t gnext = gi + gridDim.x;
         if (gnext < ngroups) corner_async<T, JV>(A, id_next, row(buf ^ 1));
         cp_commit();
         const int32_t id_after = gnext + gridDim.x < ngroups ? corner_id(gnext + gridDim.x) : 0;
+        const int lp_next = gnext < ngroups ? level_prob(gnext) : 0;
         cp_wait<1>();
-        __syncwarp();
-        {   // corner values -> monomial coefficients: thread c transforms column c of the element's rows
-            T* nd = s_nd + (buf * EPB + le) * ESTR;
-            if (c < 7) {
-                column_to_monomial<T>(nd + c);
-                if (JV) column_to_monomial<T>(nd + CT + c);
-            }
-            if (A.ndf && c < 3) column_to_monomial<T>(nd + CF + c);
-        }
-        __syncwarp();
         const int64_t idx = gi * EPB + le;
-        const bool valid = idx < n;
-        const int lv = __ldg(olev + (valid ? idx : n - 1));
-        const T g = lvl_g<T>(A, lv);
-        const Phys<T> P(A, oprob ? (int)oprob[valid ? idx : n - 1] : -1);
-        S cf[16];
-        vms_point_modal<S, T>(A, P, m, s_nd + (buf * EPB + le) * ESTR, CS, g, cf);
-        const T wq = lvl_w<T>(A, lv), wqg = wq * g;
-        // F, G multiply phi; S, H multiply physical gradients = g x reference gradients
-        T w16[16];
-        for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
-        T M[32];
-        for (int k = 0; k < 32; ++k) M[k] = T(0);
-        add_moments<T, true>(m, w16, M);
-        for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
-        __syncwarp();
-        T r[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            T v[4];
-            ld4s<T>(mcol + q * MSTR, v);
-            r[0] += v[0]; r[1] += v[1]; r[2] += v[2]; r[3] += v[3];
-        }
-        for (int k = 0; k < 4; ++k) r[k] = hadamard_bwd<1>(r[k], c);
-        if (A.sv) {
-            // deterministic scatter: node c's 4 rows into the element's slot (one 16- or 32-byte store)
-            if (valid) st4s<T>((T*)A.sv + 32 * idx + 4 * c, r[0], r[1], r[2], r[3]);
-        } else if constexpr (sizeof(T) == 4) {
-            // corners of this warp's 4 elements that are the same node add their rows in shared memory
-            // first; one lane per node scatters (fewer float64 atomics; float64: the plain scatter is faster)
-            const int lane = threadIdx.x & 31;
-            const unsigned grp = __match_any_sync(0xffffffffu, valid ? id_cur : -1 - lane);
-            __syncwarp();   // every lane has read its moment columns
-            st4s<T>(mrow, r[0], r[1], r[2], r[3]);
-            __syncwarp();
-            if (valid && lane == __ffs(grp) - 1) {
-                const T* rows = s_m + (threadIdx.x & ~31u) * MSTR;
-                T t[4] = {T(0), T(0), T(0), T(0)};
-                for (unsigned g = grp; g; g &= g - 1) {
-                    T v[4];
-                    ld4s<T>(rows + (__ffs(g) - 1) * MSTR, v);
-                    for (int k = 0; k < 4; ++k) t[k] += v[k];
-                }
-                scatter_t(A, id_cur, t);
-            }
-        } else {
-            if (valid) scatter_t(A, id_cur, r);
-        }
-        __syncwarp();   // this buffer and the moments are rewritten by later iterations
+        interior_element<T, JV>(A, s_nd + (buf * EPB + le) * ESTR, s_mw, m, lane, idx, idx < n, lp_cur & 255,
+                                lp_cur >> 8, id_cur);
         id_cur = id_next;
         id_next = id_after;
+        lp_cur = lp_next;
         buf ^= 1;
     }
     cp_wait<0>();
@@ -202,20 +225,13 @@ __device__ __forceinline__ void warp_scatter_moments(const Args& A, const T M[32
     if ((lane & 3) == 0) scatter(A, id, r);
 }
 
-// W warps per block (a tile shape the autotuner picks); `order` (or null) permutes the list
-template <class T, bool JV, int W>
-__global__ void __launch_bounds__(32 * W, (sizeof(T) == 4 ? 16 : 8) / W) vms_cut(Args A, const int32_t* __restrict__ list,
-                                                    const int64_t* __restrict__ off, const void* __restrict__ pts,
-                                                    const int32_t* __restrict__ order, int64_t n) {
+// One Intercepted element on one warp: lane l evaluates sub-cell points l, l + 32, ... and accumulates
+// their monomial moments, summed over the lanes at the end (warp_scatter_moments).  s_nd [8 * CS] and
+// s_m [32 * MSTR] are the warp's shared rows; idx the element's position in the list.
+template <class T, bool JV>
+__device__ __forceinline__ void cut_element(const Args& A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
+                                            const void* __restrict__ pts, int64_t idx, T* s_nd, T* s_m, int lane) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
-    constexpr int PAD = 16 / (int)sizeof(T), MSTR = 32 + PAD;
-    __shared__ __align__(16) T s_nd[W][8 * CS];
-    __shared__ __align__(16) T s_m[W][32 * MSTR];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t slot = (int64_t)blockIdx.x * W + w;
-    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
-    if (slot >= n) return;
-    const int64_t idx = order ? (int64_t)order[slot] : slot;
     const int32_t e = list[idx];
     // every 8-lane group gathers the 8 corner rows and forms their monomial coefficients; lanes 0-7 store them
     const int c8 = lane & 7;
@@ -229,7 +245,7 @@ __global__ void __launch_bounds__(32 * W, (sizeof(T) == 4 ? 16 : 8) / W) vms_cut
         if (A.ndf)
             for (int j = 0; j < 3; ++j) rw[CF + j] = hadamard_fwd(rw[CF + j], c8);
         if (lane < 8)
-            for (int j = 0; j < CS; ++j) s_nd[w][lane * CS + j] = rw[j];
+            for (int j = 0; j < CS; ++j) s_nd[lane * CS + j] = rw[j];
     }
     __syncwarp();
     const T g = lvl_g<T>(A, A.lev[e]);
@@ -245,26 +261,37 @@ __global__ void __launch_bounds__(32 * W, (sizeof(T) == 4 ? 16 : 8) / W) vms_cut
         T m[8];
         monomials<T>(pt, m);
         S cf[16];
-        vms_point_modal<S, T>(A, P, m, &s_nd[w][0], CS, g, cf);
+        vms_point_modal<S, T>(A, P, m, s_nd, CS, g, cf);
         const T wq = pt[3] * det, wqg = wq * g;
         T w16[16];
         for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
         add_moments<T, false>(m, w16, M);
     }
-    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id, 0.0, A.sv ? (T*)A.sv + 32 * (A.n_out_slots + idx) : nullptr);
+    warp_scatter_moments<T>(A, M, s_m, lane, my_id, 0.0, A.sv ? (T*)A.sv + 32 * (A.n_out_slots + idx) : nullptr);
+}
+
+// W warps per block (a tile shape the autotuner picks); `order` (or null) permutes the list
+template <class T, bool JV, int W>
+__global__ void __launch_bounds__(32 * W, (sizeof(T) == 4 ? 16 : 8) / W) vms_cut(Args A, const int32_t* __restrict__ list,
+                                                    const int64_t* __restrict__ off, const void* __restrict__ pts,
+                                                    const int32_t* __restrict__ order, int64_t n) {
+    constexpr int PAD = 16 / (int)sizeof(T), MSTR = 32 + PAD;
+    __shared__ __align__(16) T s_nd[W][8 * CS];
+    __shared__ __align__(16) T s_m[W][32 * MSTR];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t slot = (int64_t)blockIdx.x * W + w;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
+    if (slot >= n) return;
+    cut_element<T, JV>(A, list, off, pts, order ? (int64_t)order[slot] : slot, &s_nd[w][0], &s_m[w][0], lane);
 }
 
 // ------------------------------------------------------------------------------------------
 // Nitsche surface terms (Eq. weakbc), one thread per surface point: elements hosting few points
 // ------------------------------------------------------------------------------------------
 template <class T, bool JV>
-__global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict__ el, const double* __restrict__ xr,
-                                               const double* __restrict__ nr, const double* __restrict__ wr,
-                                               const double* __restrict__ taub, int64_t n) {
+__device__ __forceinline__ void surface_point(const Args& A, const int32_t* __restrict__ el, const double* __restrict__ xr,
+                                              const double* __restrict__ nr, const double* __restrict__ wr, int64_t i) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     NitschePoint<S, T> P;
     const int32_t e = el[i];
     nitsche_fields<S, T, JV, false>(A, e, i, xr + 3 * i, nr + 3 * i, P);
@@ -286,6 +313,16 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
     }
 }
 
+template <class T, bool JV>
+__global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict__ el, const double* __restrict__ xr,
+                                               const double* __restrict__ nr, const double* __restrict__ wr,
+                                               const double* __restrict__ taub, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
+    surface_point<T, JV>(A, el, xr, nr, wr, i);
+}
+
 // ------------------------------------------------------------------------------------------
 // Nitsche surface terms (Eq. weakbc), one warp per element hosting many surface points; lane l takes
 // points l, l + 32, ... of the element.  Per point the 4 rows of corner c are
@@ -294,18 +331,10 @@ __global__ void __launch_bounds__(128) nitsche(Args A, const int32_t* __restrict
 // i.e. coefficients of phi_c and of its reference gradient, accumulated as monomial moments.
 // ------------------------------------------------------------------------------------------
 template <class T, bool JV>
-__global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(Args A, const int32_t* __restrict__ list,
-                                                    const int64_t* __restrict__ off, const double* __restrict__ xr,
-                                                    const double* __restrict__ nr, const double* __restrict__ wr,
-                                                    const double* __restrict__ taub, int64_t n) {
+__device__ __forceinline__ void surface_element(const Args& A, const int32_t* __restrict__ list, const int64_t* __restrict__ off,
+                                                const double* __restrict__ xr, const double* __restrict__ nr,
+                                                const double* __restrict__ wr, int64_t idx, T* s_nd, T* s_m, int lane) {
     typedef typename std::conditional<JV, Dual<T>, T>::type S;
-    constexpr int PAD = 16 / (int)sizeof(T), MSTR = 32 + PAD;
-    __shared__ __align__(16) T s_nd[WPB][8 * CS];
-    __shared__ __align__(16) T s_m[WPB][32 * MSTR];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t idx = (int64_t)blockIdx.x * WPB + w;
-    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
-    if (idx >= n) return;
     const int32_t e = list[idx];
     // corner rows: u_s (0-2), p (3), jump d = u_s - g_body formed in float64 (4-6), tangents at CT
     // (the penalty is added per element in float64 by nitsche_penalty)
@@ -332,9 +361,9 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         if (JV)
             for (int j = 0; j < 7; ++j) rw[CT + j] = hadamard_fwd(rw[CT + j], c8);
         if (lane < 8) {
-            for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + j] = rw[j];
+            for (int j = 0; j < 7; ++j) s_nd[lane * CS + j] = rw[j];
             if (JV)
-                for (int j = 0; j < 7; ++j) s_nd[w][lane * CS + CT + j] = rw[CT + j];
+                for (int j = 0; j < 7; ++j) s_nd[lane * CS + CT + j] = rw[CT + j];
         }
     }
     __syncwarp();
@@ -365,7 +394,7 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         p = zero<S>();
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-            const T* r = &s_nd[w][t * CS];
+            const T* r = &s_nd[t * CS];
             S a[7];
             for (int j = 0; j < 7; ++j) a[j] = make<S, T>(r[j], JV ? r[CT + j] : T(0));
             for (int i = 0; i < 3; ++i) {
@@ -398,7 +427,176 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
         c[13] = c[14] = c[15] = T(0);
         add_moments<T, false>(m, c, M);
     }
-    warp_scatter_moments<T>(A, M, &s_m[w][0], lane, my_id, 0.0, nullptr, A.ss ? A.ss + 32 * idx : nullptr);
+    warp_scatter_moments<T>(A, M, s_m, lane, my_id, 0.0, nullptr, A.ss ? A.ss + 32 * idx : nullptr);
+}
+
+template <class T, bool JV>
+__global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(Args A, const int32_t* __restrict__ list,
+                                                    const int64_t* __restrict__ off, const double* __restrict__ xr,
+                                                    const double* __restrict__ nr, const double* __restrict__ wr,
+                                                    const double* __restrict__ taub, int64_t n) {
+    constexpr int PAD = 16 / (int)sizeof(T), MSTR = 32 + PAD;
+    __shared__ __align__(16) T s_nd[WPB][8 * CS];
+    __shared__ __align__(16) T s_m[WPB][32 * MSTR];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t idx = (int64_t)blockIdx.x * WPB + w;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
+    if (idx >= n) return;
+    surface_element<T, JV>(A, list, off, xr, nr, wr, idx, &s_nd[w][0], &s_m[w][0], lane);
+}
+
+// ------------------------------------------------------------------------------------------
+// One persistent launch over the quadrature buckets.  Every warp drains a device work queue on its
+// own: first the items that are not Out elements -- an Intercepted element (8 .. 4096 sub-cell
+// points), an element hosting many surface points, or a group of 32 surface points of elements
+// hosting few -- one per claim, in the order of decreasing estimated cost that the host gave them
+// (the cost model of Eq. Wpart: volume points at T_v, surface points at T_s); then the Out elements,
+// 4 per warp item, kFusedChunk items per claim, with their node rows double-buffered by cp.async as
+// in vms_interior.  Longest items first, then small uniform ones, keeps every SM busy to the end
+// whatever the mix of buckets (one mesh or many problems of a batch).
+// ------------------------------------------------------------------------------------------
+constexpr int kFusedWarps = 4;   // warps per block
+constexpr int kFusedChunk = 8;   // Out warp items per claim
+
+struct FusedQueue {
+    const uint32_t* items;       // bits 30-31 kind (0 Intercepted, 1 dense surface element, 2 sparse group), 0-29 index
+    int64_t n_items;
+    unsigned long long* cnt;     // [3] claimed items, claimed Out warp items, finished blocks (zero at launch)
+    const int32_t* oconn;
+    const uint8_t* olev;
+    const uint16_t* oprob;
+    int64_t n_out;
+    const int32_t* cut_list;
+    const int64_t* cut_off;
+    const void* cut_pts;
+    int heavy_warps;             // warps per block that take the costly items before the Out elements
+    const int32_t* sq_list;
+    const int64_t* sq_off;
+    const int32_t* sq_elem;
+    const double *sq_x, *sq_n, *sq_w;
+    int64_t n_sparse;
+};
+
+template <class T> struct FusedShape {
+    static constexpr int ESTR = IntShape<T>::ESTR, MSTR = IntShape<T>::MSTR;
+    // per warp: the Out layout (2 buffers x 4 elements of rows, 32 moment rows); the per-element
+    // layouts (8 rows, 32 moment rows) fit inside it
+    static constexpr int WARP = 2 * 4 * ESTR + 32 * MSTR;
+    static_assert(8 * CS + 32 * MSTR <= WARP, "per-element layout");
+    static_assert((WARP * sizeof(T)) % 16 == 0 && (8 * CS * sizeof(T)) % 16 == 0, "16-byte rows");
+    static constexpr size_t smem = (size_t)kFusedWarps * WARP * sizeof(T);
+};
+
+template <class T, bool JV>
+__global__ void __launch_bounds__(32 * kFusedWarps, sizeof(T) == 4 ? 4 : 2) vms_fused(Args A, FusedQueue Q) {
+    constexpr int ESTR = FusedShape<T>::ESTR, MSTR = FusedShape<T>::MSTR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    T* base = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * FusedShape<T>::WARP;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
+    // the costly items, one per claim
+    auto drain_costly = [&]() {
+        for (;;) {
+            unsigned long long h = 0;
+            if (lane == 0) h = atomicAdd(Q.cnt, 1ull);
+            h = __shfl_sync(0xffffffffu, h, 0);
+            if ((int64_t)h >= Q.n_items) break;
+            const uint32_t it = Q.items[h];
+            const int64_t i = (int64_t)(it & 0x3FFFFFFFu);
+            const uint32_t kind = it >> 30;
+            if (kind == 0) {
+                cut_element<T, JV>(A, Q.cut_list, Q.cut_off, Q.cut_pts, i, base, base + 8 * CS, lane);
+            } else if (kind == 1) {
+                surface_element<T, JV>(A, Q.sq_list, Q.sq_off, Q.sq_x, Q.sq_n, Q.sq_w, i, base, base + 8 * CS, lane);
+            } else {
+                const int64_t q = 32 * i + lane;
+                if (q < Q.n_sparse) surface_point<T, JV>(A, Q.sq_elem, Q.sq_x, Q.sq_n, Q.sq_w, q);
+            }
+            __syncwarp();   // the shared rows are reused by the next item
+        }
+    };
+    // 1. the first heavy_warps warps of every block start on the costly items (the others go straight
+    //    to the Out elements, so latency-bound costly work shares each SM with arithmetic-bound Out work)
+    const bool heavy_first = (int)(threadIdx.x >> 5) < Q.heavy_warps;
+    // 2. Out elements
+    auto drain_out = [&]() {
+        if (Q.n_out > 0) {
+            const int c = lane & 7, le = lane >> 3;
+            const int64_t n_wi = (Q.n_out + 3) / 4;
+            int64_t pos = 0, end = 0;
+            bool more = true;
+            auto claim = [&]() -> int64_t {   // warp-uniform
+                if (pos < end) return pos++;
+                if (!more) return -1;
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(Q.cnt + 1, (unsigned long long)kFusedChunk);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if ((int64_t)b >= n_wi) { more = false; return -1; }
+                pos = (int64_t)b + 1;
+                end = (int64_t)b + kFusedChunk < n_wi ? (int64_t)b + kFusedChunk : n_wi;
+                return (int64_t)b;
+            };
+            auto corner_id = [&](int64_t wi) -> int32_t {
+                int64_t idx = 4 * wi + le;
+                if (idx >= Q.n_out) idx = Q.n_out - 1;
+                return __ldg(Q.oconn + 8 * idx + c);
+            };
+            auto level_prob = [&](int64_t wi) -> int {   // loaded an item ahead of its use
+                int64_t idx = 4 * wi + le;
+                if (idx >= Q.n_out) idx = Q.n_out - 1;
+                return (int)__ldg(Q.olev + idx) | (Q.oprob ? (int)Q.oprob[idx] << 8 : -256);
+            };
+            auto row = [&](int buf) -> T* { return base + (buf * 4 + le) * ESTR + c * CS; };
+            T* s_mw = base + 8 * ESTR;
+            int64_t cur = claim();
+            if (cur >= 0) {
+                T m[8];
+                gauss_monomials<T>(c, m);
+                int32_t id_cur = corner_id(cur);
+                corner_async<T, JV>(A, id_cur, row(0));
+                cp_commit();
+                int lp_cur = level_prob(cur);
+                int64_t nxt = claim();
+                int32_t id_next = nxt >= 0 ? corner_id(nxt) : 0;
+                int buf = 0;
+                while (cur >= 0) {
+                    if (nxt >= 0) corner_async<T, JV>(A, id_next, row(buf ^ 1));
+                    cp_commit();
+                    const int64_t aft = nxt >= 0 ? claim() : -1;
+                    const int32_t id_after = aft >= 0 ? corner_id(aft) : 0;
+                    const int lp_next = nxt >= 0 ? level_prob(nxt) : 0;
+                    cp_wait<1>();
+                    const int64_t idx = 4 * cur + le;
+                    interior_element<T, JV>(A, base + (buf * 4 + le) * ESTR, s_mw, m, lane, idx, idx < Q.n_out,
+                                            lp_cur & 255, lp_cur >> 8, id_cur);
+                    cur = nxt;
+                    nxt = aft;
+                    id_cur = id_next;
+                    id_next = id_after;
+                    lp_cur = lp_next;
+                    buf ^= 1;
+                }
+                cp_wait<0>();
+            }
+        }
+    };
+    // one call site each (the bodies are inlined once): costly items then Out elements, or the reverse
+    for (int phase = 0; phase < 2; ++phase) {
+        if ((phase == 0) == heavy_first) drain_costly();
+        else drain_out();
+    }
+    // 3. the last block to finish zeroes the counters for the next launch (every claim of every block
+    //    precedes its count here)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(Q.cnt + 2, 1ull) == (unsigned long long)gridDim.x - 1) {
+            Q.cnt[0] = 0;
+            Q.cnt[1] = 0;
+            Q.cnt[2] = 0;
+            __threadfence();
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -506,73 +704,57 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
     lo = __fadd_rn(lo, e);
 }
 
-// Deterministic o2n (Algorithm 2): every independent node sums the slot rows of its incidence list in
-// list order (a hanging corner's rows times 1/2 or 1/4 for each parent), then its strong rows take
-// U - g (R) or v (J v) as in strong_rows.  Writes every row of out: no zeroing before the call.
-template <class T>
-__device__ __forceinline__ void gather_entry(const Args& A, uint32_t e, int64_t nv, double acc[4], float hi[4], float lo[4]) {
-    const int c = (int)(e & 7), wc = (int)((e >> 3) & 3);
-    const int64_t s = (int64_t)(e >> 5);
-    if (s < nv) {
-        T v[4];
-        ld4<T>((const T*)A.sv + 32 * s, c, v);
-        const T w = wc == 0 ? T(1) : (wc == 1 ? T(0.5) : T(0.25));
-        if constexpr (sizeof(T) == 4) {
-            for (int k = 0; k < 4; ++k) ff_add(hi[k], lo[k], w * v[k]);
-        } else {
-            for (int k = 0; k < 4; ++k) acc[k] += w * v[k];
-        }
-    } else {
-        const double* d = A.ss + 32 * (s - nv) + 4 * c;
-        const double2 a = reinterpret_cast<const double2*>(d)[0], b = reinterpret_cast<const double2*>(d)[1];
-        const double w = wc == 0 ? 1.0 : (wc == 1 ? 0.5 : 0.25);
-        acc[0] += w * a.x; acc[1] += w * a.y; acc[2] += w * b.x; acc[3] += w * b.y;
-    }
-}
+// Deterministic o2n (Algorithm 2): one thread per node sums the slot rows of its incidence list in
+// list order (a hanging corner's rows times 1/2 or 1/4 for each parent; float-float in mixed
+// precision), then the node's strong rows take U - g (R) or v (J v) as in strong_rows.  The list is
+// read in batches of 8 (float) or 4 (double) entries whose code and row loads are all issued before the first
+// sum: the kernel is bound by the latency of these two dependent loads, so each thread keeps many
+// in flight.  Writes every row of out: no zeroing before the call.
+template <class T> struct GatherBatch { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 
-// (hi, lo) += the float-float pair of the partner lane at distance `off` (fixed pattern)
-__device__ __forceinline__ void ff_merge(float& hi, float& lo, int off) {
-    const float oh = __shfl_xor_sync(0xffffffffu, hi, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
-    // lanes of a pair add in the same order (lower lane's pair first): identical bits in both
-    const bool low = (threadIdx.x & off) == 0;
-    float h = low ? hi : oh, l = low ? lo : ol;
-    ff_add(h, l, low ? oh : hi);
-    l = __fadd_rn(l, low ? ol : lo);
-    hi = h;
-    lo = l;
-}
-
-// Deterministic o2n (Algorithm 2): four threads per node; thread j of the quad sums entries j, j + 4,
-// ... of the node's incidence list in list order (a hanging corner's rows times 1/2 or 1/4 for each
-// parent), then the quad merges its four partial sums in a fixed pattern (float-float in mixed
-// precision), and the node's strong rows take U - g (R) or v (J v) as in strong_rows.  Writes every
-// row of out: no zeroing before the call.
 template <class T>
-__global__ void __launch_bounds__(256) node_gather(Args A, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) node_gather(Args A, const int64_t* __restrict__ ptr,
                                                    const uint32_t* __restrict__ inc, int64_t nv,
                                                    const uint8_t* __restrict__ flag, const uint8_t* __restrict__ umask,
                                                    const double* __restrict__ uval, double ux, double uy, double uz,
                                                    int jv) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n = t >> 2;
-    const int j = (int)(t & 3);
-    const bool live = n < A.n_nodes;
-    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended (uniform over the grid)
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= A.n_nodes) return;
+    if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    if (live) {
-        const int64_t q1 = ptr[n + 1];
-        for (int64_t q = ptr[n] + j; q < q1; q += 4) gather_entry<T>(A, __ldg(inc + q), nv, acc, hi, lo);
-    }
-    // merge the quad (every lane takes part in the shuffles)
-    for (int off = 1; off < 4; off <<= 1) {
-        for (int k = 0; k < 4; ++k) {
-            if constexpr (sizeof(T) == 4) ff_merge(hi[k], lo[k], off);
-            const double o = __shfl_xor_sync(0xffffffffu, acc[k], off);
-            acc[k] = (threadIdx.x & off) == 0 ? acc[k] + o : o + acc[k];
+    const int64_t q1 = ptr[n + 1];
+    constexpr int kGatherBatch = GatherBatch<T>::value;
+    for (int64_t q0 = ptr[n]; q0 < q1; q0 += kGatherBatch) {
+        uint32_t e[kGatherBatch];
+        T v[kGatherBatch][4];
+#pragma unroll
+        for (int i = 0; i < kGatherBatch; ++i) e[i] = q0 + i < q1 ? __ldg(inc + q0 + i) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < kGatherBatch; ++i) {
+            const int64_t sl = (int64_t)(e[i] >> 5);
+            if (e[i] != 0xFFFFFFFFu && sl < nv) ld4<T>((const T*)A.sv + 32 * sl, e[i] & 7, v[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kGatherBatch; ++i) {
+            if (e[i] == 0xFFFFFFFFu) continue;
+            const int c = (int)(e[i] & 7), wc = (int)((e[i] >> 3) & 3);
+            const int64_t sl = (int64_t)(e[i] >> 5);
+            if (sl < nv) {
+                const T w = wc == 0 ? T(1) : (wc == 1 ? T(0.5) : T(0.25));
+                if constexpr (sizeof(T) == 4) {
+                    for (int k = 0; k < 4; ++k) ff_add(hi[k], lo[k], w * v[i][k]);
+                } else {
+                    for (int k = 0; k < 4; ++k) acc[k] += w * v[i][k];
+                }
+            } else {   // a float64 surface slot
+                const double* d = A.ss + 32 * (sl - nv) + 4 * c;
+                const double2 x = reinterpret_cast<const double2*>(d)[0], y = reinterpret_cast<const double2*>(d)[1];
+                const double w = wc == 0 ? 1.0 : (wc == 1 ? 0.5 : 0.25);
+                acc[0] += w * x.x; acc[1] += w * x.y; acc[2] += w * y.x; acc[3] += w * y.y;
+            }
         }
     }
-    if (!live || j != 0) return;
     if constexpr (sizeof(T) == 4)
         for (int k = 0; k < 4; ++k) acc[k] += f2d(hi[k]) + f2d(lo[k]);
     // strong rows (as strong_rows)
@@ -638,13 +820,15 @@ void launch_cut(const Mesh& m, const Args& A, cudaStream_t s, int wpb, int lpt) 
     }
 }
 
-template <class T, bool JV>
+template <class T, bool JV, int MINB = (sizeof(T) == 4 ? 4 : 2)>
 int interior_blocks_per_sm();
+template <class T, bool JV>
+void launch_interior(const Mesh& m, const Args& A, cudaStream_t s, int bps);
 
 // Autotuner of the Intercepted-element bucket: with the node data of this call prepared, time every
 // (warps per block, element order) candidate on the call's own inputs (3 launches each after one
 // untimed) and keep the fastest; then the Out-element bucket: the persistent interior kernel with
-// 1 .. 4 resident blocks per SM.  Writes into the output vector, which the call then recomputes.
+// 1 .. 4 resident blocks per SM, and 5 with the smaller register allocation (float).  Writes into the output vector, which the call then recomputes.
 template <class T, bool JV>
 int autotune_cut(Mesh& m, Args A, cudaStream_t s) {
     const int64_t nc = (int64_t)m.cut_list.size();
@@ -688,13 +872,12 @@ int autotune_cut(Mesh& m, Args A, cudaStream_t s) {
     // the Out-element bucket: the persistent interior kernel with 1 .. (occupancy limit) blocks per SM
     const int64_t no = (int64_t)m.out_list.size();
     constexpr int EPB = Epb<T>::value;
-    const int maxb = std::min(4, interior_blocks_per_sm<T, JV>());
+    int maxb = std::min(4, interior_blocks_per_sm<T, JV>());
+    if constexpr (sizeof(T) == 4)
+        if (maxb == 4 && interior_blocks_per_sm<T, JV, 5>() >= 5) maxb = 5;
     float best_out = 1e30f;
     for (int b = 1; b <= maxb && no > 0; ++b) {
-        const int64_t grid = std::min<int64_t>((no + EPB - 1) / EPB, (int64_t)b * m.n_sm);
-        auto run = [&]() {
-            vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, IntShape<T>::smem, s>>>(A, m.d.out_conn, m.d.out_lev, m.d.out_prob, no);
-        };
+        auto run = [&]() { launch_interior<T, JV>(m, A, s, b); };
         run();
         cudaEventRecord(e0, s);
         for (int r = 0; r < 3; ++r) run();
@@ -712,17 +895,88 @@ int autotune_cut(Mesh& m, Args A, cudaStream_t s) {
 }
 
 // Resident CTAs of the persistent interior kernel per SM (queried once; also sets its dynamic smem opt-in).
-template <class T, bool JV>
+template <class T, bool JV, int MINB>
 int interior_blocks_per_sm() {
     static int bps = 0;
     if (bps == 0) {
         const size_t smem = IntShape<T>::smem;
         int b = 0;
-        cudaFuncSetAttribute(vms_interior<T, JV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, vms_interior<T, JV>, 8 * Epb<T>::value, smem);
+        cudaFuncSetAttribute(vms_interior<T, JV, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, vms_interior<T, JV, MINB>, 8 * Epb<T>::value, smem);
         bps = b < 1 ? 1 : b;
     }
     return bps;
+}
+
+// The persistent interior kernel at bps resident blocks per SM: the 5-block register allocation for
+// bps = 5 (float only), else the default one.
+template <class T, bool JV>
+void launch_interior(const Mesh& m, const Args& A, cudaStream_t s, int bps) {
+    const int64_t no = (int64_t)m.out_list.size();
+    constexpr int EPB = Epb<T>::value;
+    const int64_t grid = std::min<int64_t>((no + EPB - 1) / EPB, (int64_t)bps * m.n_sm);
+    if constexpr (sizeof(T) == 4) {
+        if (bps >= 5) {
+            vms_interior<T, JV, 5><<<(unsigned)grid, 8 * EPB, IntShape<T>::smem, s>>>(A, m.d.out_conn, m.d.out_lev, m.d.out_prob, no);
+            return;
+        }
+    }
+    vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, IntShape<T>::smem, s>>>(A, m.d.out_conn, m.d.out_lev, m.d.out_prob, no);
+}
+
+// Resident CTAs of the fused kernel per SM (queried once; also sets its dynamic smem opt-in).
+template <class T, bool JV>
+int fused_blocks_per_sm() {
+    static int bps = 0;
+    if (bps == 0) {
+        const size_t smem = FusedShape<T>::smem;
+        int b = 0;
+        cudaFuncSetAttribute(vms_fused<T, JV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, vms_fused<T, JV>, 32 * kFusedWarps, smem);
+        bps = b < 1 ? 1 : b;
+    }
+    return bps;
+}
+
+template <class T, bool JV>
+void launch_penalty(const Mesh& m, const Args& A, cudaStream_t s, bool timed) {
+    const int64_t np = (int64_t)m.pen_elem.size();
+    if (np <= 0) return;
+    Timed t(m, 2, s, 1, timed);
+    nitsche_penalty<JV><<<(unsigned)((8 * np + 127) / 128), 128, 0, s>>>(A, m.d.pen_elem, m.d.pen_q, m.d.pen_slot, m.d.pen,
+                                                                        m.d.sq_x, m.d.sq_w, m.d.sq_taub, np);
+}
+
+// the Out, Intercepted and surface buckets in one launch (vms_fused), then the float64 penalty
+template <class T, bool JV>
+void launch_fused(const Mesh& m, const Args& A, cudaStream_t s, bool timed) {
+    FusedQueue Q;
+    Q.items = m.d.fq_items;
+    Q.n_items = m.fq_n;
+    Q.cnt = m.d.fq_cnt;
+    Q.oconn = m.d.out_conn;
+    Q.olev = m.d.out_lev;
+    Q.oprob = m.d.out_prob;
+    Q.n_out = (int64_t)m.out_list.size();
+    Q.cut_list = m.d.cut_list;
+    Q.cut_off = m.d.cut_off;
+    Q.cut_pts = std::is_same<T, float>::value ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
+    Q.heavy_warps = m.fused_heavy_warps;
+    Q.sq_list = m.d.sq_list;
+    Q.sq_off = m.d.sq_off;
+    Q.sq_elem = m.d.sq_elem;
+    Q.sq_x = m.d.sq_x;
+    Q.sq_n = m.d.sq_n;
+    Q.sq_w = m.d.sq_w;
+    Q.n_sparse = m.n_sq_sparse;
+    if (Q.n_items + Q.n_out > 0) {
+        Timed t(m, 5, s, 1, timed);
+        const int64_t work = Q.n_items + (Q.n_out + 3) / 4;   // warp items
+        const int64_t blocks = (work + kFusedWarps - 1) / kFusedWarps;
+        const int64_t grid = std::min<int64_t>(blocks, (int64_t)fused_blocks_per_sm<T, JV>() * m.n_sm);
+        vms_fused<T, JV><<<(unsigned)grid, 32 * kFusedWarps, FusedShape<T>::smem, s>>>(A, Q);
+    }
+    launch_penalty<T, JV>(m, A, s, timed);
 }
 
 template <class T, bool JV>
@@ -739,6 +993,10 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         Timed t(m, 4, s, (A.n_nodes > 0) + (A.n_hang > 0), !ws);
         launch_node_prep<T, JV>(A, ndv, ndt, ndf, s);
     }
+    if (m.fused && m.d.fq_cnt) {
+        launch_fused<T, JV>(m, A, s, !ws);
+        return;
+    }
     // fork: the Intercepted-element and surface kernels run beside the Out-element kernel
     const cudaStream_t sc = s_cut ? s_cut : s, ss = s_sur ? s_sur : s;
     if (ev) {
@@ -751,11 +1009,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
     if (no > 0) {
         Timed t(m, 0, s, 1, !ws);
         const int tuned = m.out_bps[sizeof(T) == 4][JV];
-        const int bps = tuned > 0 ? tuned : interior_blocks_per_sm<T, JV>();
-        const size_t smem = IntShape<T>::smem;
-        const int64_t groups = (no + EPB - 1) / EPB;
-        const int64_t grid = std::min<int64_t>(groups, (int64_t)bps * m.n_sm);
-        vms_interior<T, JV><<<(unsigned)grid, 8 * EPB, smem, s>>>(A, m.d.out_conn, m.d.out_lev, m.d.out_prob, no);
+        launch_interior<T, JV>(m, A, s, tuned > 0 ? tuned : interior_blocks_per_sm<T, JV>());
     }
     if (nc > 0) {
         Timed t(m, 1, sc, 1, !ws);
@@ -773,12 +1027,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         nitsche_el<T, JV><<<(unsigned)((nse + WPB - 1) / WPB), 32 * WPB, 0, ss>>>(A, m.d.sq_list, m.d.sq_off, m.d.sq_x,
                                                                                 m.d.sq_n, m.d.sq_w, m.d.sq_taub, nse);
     }
-    const int64_t np = (int64_t)m.pen_elem.size();
-    if (np > 0) {   // after both surface kernels (same stream): the slots hold their rows
-        Timed t(m, 2, ss, 1, !ws);
-        nitsche_penalty<JV><<<(unsigned)((8 * np + 127) / 128), 128, 0, ss>>>(A, m.d.pen_elem, m.d.pen_q, m.d.pen_slot, m.d.pen,
-                                                                        m.d.sq_x, m.d.sq_w, m.d.sq_taub, np);
-    }
+    launch_penalty<T, JV>(m, A, ss, !ws);   // after both surface kernels (same stream): the slots hold their rows
     if (ev) {   // join
         cudaEventRecord(ev[1], sc);
         cudaEventRecord(ev[2], ss);
@@ -795,7 +1044,7 @@ void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bo
     if (nn > 0 && A.sv) {
         const uint8_t* um = m.user_bc ? m.d.bcmask_user : nullptr;
         const double* uv = m.user_bc ? m.d.bcval_user : nullptr;
-        const unsigned g4 = (unsigned)((4 * nn + 255) / 256);   // four threads per node
+        const unsigned g4 = (unsigned)((nn + 255) / 256);
         if (precision == 0)
             node_gather<double><<<g4, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
                                                   ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
@@ -811,6 +1060,48 @@ void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bo
 }
 
 }  // namespace
+
+// The work queue of the fused launch: one item per Intercepted element, per element hosting at least
+// kNitscheDenseMin surface points, and per group of 32 points of the other surface-hosting elements,
+// by decreasing estimated cost.  The cost of an item is what one warp spends on it: its rounds of 32
+// points (lanes over points) plus one for gathering and scattering, surface points weighted by
+// T_s / T_v (Eq. Wpart), the ratio measured for these kernels on this GPU (about 4).
+int fused_prepare(Mesh& m, std::string& err) {
+    constexpr double kSurfaceCost = 4.0;
+    std::vector<std::pair<double, uint32_t>> it;
+    const int64_t nc = (int64_t)m.cut_list.size(), nd = m.n_sq_elem, ng = (m.n_sq_sparse + 31) / 32;
+    if (nc >= (1 << 30) || nd >= (1 << 30) || ng >= (1 << 30)) { err = "too many items for the fused launch"; return 1; }
+    if ((int64_t)m.sq_off_h.size() != nd + 1 && nd > 0) { err = "surface point ranges missing"; return 1; }
+    it.reserve((size_t)(nc + nd + ng));
+    for (int64_t i = 0; i < nc; ++i)
+        it.push_back({1.0 + (double)((m.cut_off[i + 1] - m.cut_off[i] + 31) / 32), (uint32_t)i});
+    for (int64_t i = 0; i < nd; ++i)
+        it.push_back({1.0 + kSurfaceCost * (double)((m.sq_off_h[i + 1] - m.sq_off_h[i] + 31) / 32), (1u << 30) | (uint32_t)i});
+    for (int64_t g = 0; g < ng; ++g) it.push_back({1.0 + kSurfaceCost, (2u << 30) | (uint32_t)g});
+    std::stable_sort(it.begin(), it.end(), [](const std::pair<double, uint32_t>& a, const std::pair<double, uint32_t>& b) {
+        return a.first > b.first;
+    });
+    std::vector<uint32_t> items(it.size());
+    for (size_t i = 0; i < it.size(); ++i) items[i] = it[i].second;
+    if (m.d.fq_items) { cudaFree(m.d.fq_items); m.d.fq_items = nullptr; }
+    if (m.d.fq_cnt) { cudaFree(m.d.fq_cnt); m.d.fq_cnt = nullptr; }
+    if (cudaMalloc((void**)&m.d.fq_items, std::max<size_t>(1, items.size()) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc((void**)&m.d.fq_cnt, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        (!items.empty() && cudaMemcpy(m.d.fq_items, items.data(), items.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemset(m.d.fq_cnt, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+        err = "fused queue upload";
+        return 1;
+    }
+    m.fq_n = (int64_t)items.size();
+    m.fq_counts[0] = nc;
+    m.fq_counts[1] = nd;
+    m.fq_counts[2] = ng;
+    fused_blocks_per_sm<double, true>();
+    fused_blocks_per_sm<double, false>();
+    fused_blocks_per_sm<float, true>();
+    fused_blocks_per_sm<float, false>();
+    return 0;
+}
 
 void graphs_free(Mesh& m) {
     for (auto& g : m.graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
@@ -858,8 +1149,7 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
         for (auto& g : mm.graphs)
             if (std::memcmp(&g.first, &key, sizeof(key)) == 0) { exec = (cudaGraphExec_t)g.second; break; }
         if (!exec) {
-            if (precision == 0) { interior_blocks_per_sm<double, true>(); interior_blocks_per_sm<double, false>(); }
-            else { interior_blocks_per_sm<float, true>(); interior_blocks_per_sm<float, false>(); }
+            vms_prepare();
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return 1;
             if (!A.sv) cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), cs);
@@ -1021,6 +1311,8 @@ void vms_prepare() {
     interior_blocks_per_sm<double, false>();
     interior_blocks_per_sm<float, true>();
     interior_blocks_per_sm<float, false>();
+    interior_blocks_per_sm<float, true, 5>();
+    interior_blocks_per_sm<float, false, 5>();
 }
 
 int vms_apply(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
@@ -1087,7 +1379,7 @@ int surface_force(const Mesh& m, const double* u, const double* up, const imga_p
 }
 
 void profile_reset(Mesh& m) {
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < kProfKinds; ++k) {
         for (auto& p : m.prof_ev[k]) { cudaEventDestroy((cudaEvent_t)p.a); cudaEventDestroy((cudaEvent_t)p.b); }
         m.prof_ev[k].clear();
         m.prof_ms[k] = 0.0;
@@ -1097,7 +1389,7 @@ void profile_reset(Mesh& m) {
 
 int profile_collect(Mesh& m) {
     if (cudaDeviceSynchronize() != cudaSuccess) return 1;
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < kProfKinds; ++k) {
         for (auto& p : m.prof_ev[k]) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, (cudaEvent_t)p.a, (cudaEvent_t)p.b);
