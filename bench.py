@@ -707,9 +707,11 @@ def run_batched_newton(B, sep, probs, states, dev, max_newton=4, max_krylov=600)
         t0 = time.perf_counter()
         st = B.newton_step(probs[0].physics, T(u0), up, **kw)
         torch.cuda.synchronize()
-        out["one_batched_graph"] = {"s": time.perf_counter() - t0, "newton_its": st["newton_its"],
+        dt = time.perf_counter() - t0
+        out["one_batched_graph"] = {"s": dt, "newton_its": st["newton_its"],
                                     "krylov_its": st["krylov_its"], "converged": bool(st["converged"]),
-                                    "rel_res": st["res_norm"][-1] / max(st["res_norm"][0], 1e-300)}
+                                    "rel_res": st["res_norm"][-1] / max(st["res_norm"][0], 1e-300),
+                                    "problem_krylov_its_per_s": len(sep) * st["krylov_its"] / dt}
     finally:
         B.use_graphs(False)
     rels, conv, kits = [], 0, 0
@@ -727,8 +729,10 @@ def run_batched_newton(B, sep, probs, states, dev, max_newton=4, max_krylov=600)
             conv += bool(st["converged"])
             kits += st["krylov_its"]
         torch.cuda.synchronize()
-        out["sequential_64_graphs"] = {"s": time.perf_counter() - t0, "converged": conv, "krylov_its": kits,
-                                       "rel_res_max": max(rels), "rel_res_median": float(np.median(rels))}
+        dt = time.perf_counter() - t0
+        out["sequential_64_graphs"] = {"s": dt, "converged": conv, "krylov_its": kits,
+                                       "rel_res_max": max(rels), "rel_res_median": float(np.median(rels)),
+                                       "problem_krylov_its_per_s": kits / dt}
     finally:
         for m in sep:
             m.use_graphs(False)
@@ -1045,13 +1049,48 @@ def parse_args(argv=None):
     ap.add_argument("--no-bluff", action="store_true", help="skip the 19.8 M-element bluff-body pair measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner training and evaluation")
     ap.add_argument("--krylov-rtol", type=float, default=1e-3)
+    ap.add_argument("--kernel-profile", action="store_true",
+                    help="only a few J v calls on the sphere LES (for ncu counter captures)")
     return ap.parse_args(argv)
+
+
+def run_kernel_profile(args):
+    """A short fixed sequence for counter captures (ncu): the sphere-LES mesh, untuned launch shapes,
+    mixed-precision J v calls -- bucketed, fused (IMGA_OPT_FUSED), bucketed, bucketed -- then one
+    float64 J v call, no other work.  Prints the per-call milliseconds (not a bench value)."""
+    import torch
+
+    from paper_2009_00706_gb300 import _lib, api
+    _lib.build()
+    dev = torch.device("cuda", 0)
+    w = I.sphere_les(0)
+    mesh = api.Mesh.from_workload(w, device=0)
+    u, up, v = I.state(mesh.n_nodes, 0)
+    ud, upd, vd = (torch.from_numpy(a).to(dev) for a in (u, up, v))
+    out = torch.empty_like(ud)
+    st = torch.cuda.current_stream()
+    ms = []
+    for prec, fused in ((1, False), (1, True), (1, False), (1, False), (0, False)):
+        mesh.fused(fused)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        mesh.jvp(w.physics, ud, upd, vd, upd, precision=prec, out=out, stream=st)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    mesh.fused(False)
+    print(json.dumps({"kernel_profile": "sphere_les J v: mixed, mixed fused, mixed x2, float64", "ms": ms,
+                      "out_elements": mesh.info["n_out"]}))
+    mesh.close()
+    return 0
 
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_profile:
+        return run_kernel_profile(args)
     return run_ours(args)
 
 

@@ -586,13 +586,14 @@ __device__ __forceinline__ void monomials(const T xi[3], T m[8]) {
     m[7] = m[3] * xi[2];
 }
 
-// forward butterfly across the lanes (lane & 7) = corner c of an 8-lane group: corner value -> a_c
+// forward butterfly across the lanes (lane & 7) = corner c of an 8-lane group: corner value -> a_c.
+// Each stage is one fused multiply-add by +-1 (exact: the same bits as the sum or difference).
 template <class T>
 __device__ __forceinline__ T hadamard_fwd(T x, int c) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const T o = __shfl_xor_sync(0xffffffffu, x, 1 << k);
-        x = ((c >> k) & 1) ? x - o : x + o;
+        x = fma(((c >> k) & 1) ? T(-1) : T(1), o, x);
     }
     return x;
 }
@@ -603,7 +604,7 @@ __device__ __forceinline__ T hadamard_bwd(T x, int c) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const T o = __shfl_xor_sync(0xffffffffu, x, LS << k);
-        x = ((c >> k) & 1) ? x + o : x - o;
+        x = fma(((c >> k) & 1) ? T(1) : T(-1), o, x);
     }
     return x;
 }
