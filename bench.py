@@ -67,9 +67,13 @@ def kernel_rooflines(prof, steps, info, n_nodes, pk):
         scale = 1e12 if unit == "TFLOP/s" else 1e9
         ach = units / (ms / 1e3) / scale
         out[k] = {"ms_per_step": ms, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
-    # strong rows read a 1-byte flag per node and rewrite only the Dirichlet / inactive rows: a few
-    # microseconds, bound by launch latency rather than by a pipe
-    out["strong_rows"] = {"ms_per_step": prof["strong_rows"][0] / max(1, steps), "bound": "launch latency"}
+    # class 3: with the deterministic scatter (the default) the node sums, which also write the strong
+    # rows: bound by the latency of two dependent loads per incidence entry (code, then a 16-byte slot
+    # row); with the atomic scatter only the strong rows, a few microseconds of launch latency
+    ms3 = prof["strong_rows"][0] / max(1, steps)
+    out["strong_rows"] = {"ms_per_step": ms3, "nodes_per_s": n_nodes / (ms3 / 1e3) if ms3 > 0 else None,
+                          "bound": "latency of dependent loads (node sums of the deterministic scatter)"
+                          if ms3 > 0.05 else "launch latency (strong rows only)"}
     return out
 
 
@@ -365,11 +369,32 @@ def run_ours(args):
             "frac": achieved / pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None,
             "traffic": interior_traffic() if prec == api.PRECISION_MIXED else None,
             "peak_source": pk["fp_source"], "peaks": {k: v for k, v in pk.items() if k.endswith("tflops") or k == "sm_count"},
-            "flops_per_element": FLOPS_JV_OUT_ELEMENT, "avg_launch_ms": k_avg}
-    kern_share = {k: v[0] / max(1e-9, sum(x[0] for x in prof.values())) for k, v in prof.items()}
-    kern_roof = kernel_rooflines(prof, args.steps, info, nn, pk)
+            "flops_per_element": FLOPS_JV_OUT_ELEMENT, "avg_launch_ms": k_avg,
+            "timing": "inside the timed steps, where the Intercepted and surface kernels run beside it on side "
+                      "streams and share its SMs"}
+    # the same step with every kernel alone (IMGA_OPT_CONCURRENT off), L2 flushed: the per-kernel
+    # rooflines, time shares and Eq. Wpart costs, and the dominant kernel's fraction by itself
+    mesh.concurrent(False)
+    prof_steps = 20
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    mesh.profile(True)
+    for _ in range(prof_steps):
+        flush.zero_()
+        step()
+    palone = mesh.profile_read()
+    mesh.profile(False)
+    mesh.concurrent(True)
+    ka = palone["out_elements"][0] / max(palone["out_elements"][1], 1)
+    aa = flops / (ka / 1e3) / 1e12
+    roof["alone"] = {"avg_launch_ms": ka, "achieved": aa,
+                     "frac": aa / pk["fp32_tflops"] if prec == api.PRECISION_MIXED else None,
+                     "timing": f"{prof_steps} steps with IMGA_OPT_CONCURRENT off (every kernel by itself), L2 flushed"}
+    kern_share = {k: v[0] / max(1e-9, sum(x[0] for x in palone.values())) for k, v in palone.items()}
+    kern_roof = kernel_rooflines(palone, prof_steps, info, nn, pk)
     try:
-        wpart = wpart_costs(prof, args.steps, info)
+        wpart = wpart_costs(palone, prof_steps, info)
     except Exception as ex:          # reported, never fatal
         wpart = {"error": repr(ex)}
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region: every

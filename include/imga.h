@@ -452,8 +452,14 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * start on the costly items; the others start on the Out elements and take what is left of the
  * costly items at the end, so latency-bound costly work can share the SMs with the arithmetic-bound
  * Out elements. */
+/* IMGA_OPT_CONCURRENT (value 1 on, the default; 0 off): the bucketed imga_residual / imga_jvp launch
+ * the Intercepted-element and surface kernels on two side streams of the mesh, forked after the node
+ * preparation and joined before the node sums, so they run beside the Out-element kernel (direct
+ * calls and captured graphs alike).  Off: every kernel on the caller's stream, one after the other
+ * (each kernel then runs alone, e.g. to time it).  The results are the same bit for bit with
+ * IMGA_OPT_DETERMINISTIC. */
 enum { IMGA_OPT_GRAPHS = 1, IMGA_OPT_AUTOTUNE = 2, IMGA_OPT_CLASSIFY_RAYS = 3, IMGA_OPT_DETERMINISTIC = 4, IMGA_OPT_FUSED = 5,
-       IMGA_OPT_FUSED_SPLIT = 6 };
+       IMGA_OPT_FUSED_SPLIT = 6, IMGA_OPT_CONCURRENT = 7 };
 imga_status imga_set_option(imga_mesh mesh, int option, int64_t value);
 
 /* The tile shapes in use.  shape[8] = {warps per block, longest-first order} for

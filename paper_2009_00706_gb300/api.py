@@ -421,6 +421,10 @@ class Mesh:
         """IMGA_OPT_FUSED: the Out, Intercepted and surface buckets in one persistent launch."""
         check(_lib.load().imga_set_option(self.h, 5, int(bool(on))))
 
+    def concurrent(self, on=True):
+        """IMGA_OPT_CONCURRENT: Intercepted / surface kernels on side streams beside the Out kernel."""
+        check(_lib.load().imga_set_option(self.h, 7, 1 if on else 0))
+
     def fused_split(self, heavy_warps):
         """IMGA_OPT_FUSED_SPLIT: warps per block (1 .. 4) that start on the costly items."""
         check(_lib.load().imga_set_option(self.h, 6, int(heavy_warps)))

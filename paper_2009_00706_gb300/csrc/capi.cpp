@@ -723,6 +723,10 @@ imga_status imga_set_option(imga_mesh h, int option, int64_t value) {
             imga::graphs_free(h->m);   // captured launches carry the kernels
             return IMGA_OK;
         }
+        case IMGA_OPT_CONCURRENT:
+            h->m.concurrent = value != 0;
+            imga::graphs_free(h->m);
+            return IMGA_OK;
         case IMGA_OPT_FUSED_SPLIT:
             if (value < 1 || value > 4) return fail(IMGA_ERR_INVALID_ARG, "IMGA_OPT_FUSED_SPLIT takes 1 .. 4");
             h->m.fused_heavy_warps = (int)value;

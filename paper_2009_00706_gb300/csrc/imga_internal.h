@@ -206,6 +206,7 @@ struct Mesh {
     float out_tune_ms[2][2][5] = {};
     // one persistent launch over the Out, Intercepted and surface buckets (IMGA_OPT_FUSED): the
     // queue of per-warp items that are not Out elements, by decreasing estimated cost (Eq. Wpart)
+    bool concurrent = true;              // IMGA_OPT_CONCURRENT: Intercepted / surface kernels on side streams
     bool fused = false;
     int fused_heavy_warps = 4;           // warps per block that start on the costly items (1 .. 4)
     int64_t fq_n = 0;                    // items in fq_items

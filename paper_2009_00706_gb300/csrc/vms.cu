@@ -62,7 +62,9 @@ template <class T> struct IntShape {
 // writes the point's 32 monomial moments, then sums moment column S = c over the 8 points and runs
 // the backward butterfly: node c's rows, scattered (or stored to the element's slot).  Every lane of
 // the warp takes part (valid: this lane's element exists).
-template <class T, bool JV>
+// IL: with packed float duals, rewrite the rows with (value, tangent) interleaved so every 16-byte
+// row load yields two dual pairs in place (off in the fused kernel, whose register budget it strains)
+template <class T, bool JV, bool IL = (JV && sizeof(T) == 4)>
 __device__ __forceinline__ void interior_element(const Args& A, T* nd, T* s_mw, const T m[8], int lane, int64_t idx,
                                                  bool valid, int lv, int prob, int32_t id) {
     typedef typename std::conditional<JV, Dual<T, sizeof(T) == 4>, T>::type S;
@@ -72,7 +74,9 @@ __device__ __forceinline__ void interior_element(const Args& A, T* nd, T* s_mw, 
     const T* mcol = s_mw + (lane >> 3) * 8 * MSTR + 4 * c;
     __syncwarp();
     {   // corner values -> monomial coefficients: thread c transforms column c of the element's rows
-        if (c < 7) {
+        if constexpr (IL) {
+            columns_to_monomial_interleaved<T>(nd, c);
+        } else if (c < 7) {
             column_to_monomial<T>(nd + c);
             if (JV) column_to_monomial<T>(nd + CT + c);
         }
@@ -82,7 +86,7 @@ __device__ __forceinline__ void interior_element(const Args& A, T* nd, T* s_mw, 
     const T g = lvl_g<T>(A, lv);
     const Phys<T> P(A, prob);
     S cf[16];
-    vms_point_modal<S, T>(A, P, m, nd, CS, g, cf);
+    vms_point_modal<S, T, IL>(A, P, m, nd, CS, g, cf);
     const T wq = lvl_w<T>(A, lv), wqg = wq * g;
     // F, G multiply phi; S, H multiply physical gradients = g x reference gradients
     T w16[16];
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, sizeof(T) == 4 ? 4 : 2) vms_
                     const int lp_next = nxt >= 0 ? level_prob(nxt) : 0;
                     cp_wait<1>();
                     const int64_t idx = 4 * cur + le;
-                    interior_element<T, JV>(A, base + (buf * 4 + le) * ESTR, s_mw, m, lane, idx, idx < Q.n_out,
+                    interior_element<T, JV, false>(A, base + (buf * 4 + le) * ESTR, s_mw, m, lane, idx, idx < Q.n_out,
                                             lp_cur & 255, lp_cur >> 8, id_cur);
                     cur = nxt;
                     nxt = aft;
@@ -1110,6 +1114,16 @@ void graphs_free(Mesh& m) {
     for (int k = 0; k < 5; ++k) if (m.fork_ev[k]) { cudaEventDestroy((cudaEvent_t)m.fork_ev[k]); m.fork_ev[k] = nullptr; }
 }
 
+// the mesh's side streams and fork / join events (created on first use)
+static int side_streams(Mesh& mm) {
+    if (mm.side[0]) return 0;
+    for (int k = 0; k < 3; ++k)
+        if (cudaStreamCreateWithFlags((cudaStream_t*)&mm.side[k], cudaStreamNonBlocking) != cudaSuccess) return 1;
+    for (int k = 0; k < 5; ++k)
+        if (cudaEventCreateWithFlags((cudaEvent_t*)&mm.fork_ev[k], cudaEventDisableTiming) != cudaSuccess) return 1;
+    return 0;
+}
+
 static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const double* up2, const double* f,
                         const imga_physics& ph, int precision, const double* v, double* out, void* stream, void* ws) {
     cudaStream_t s = (cudaStream_t)stream;
@@ -1137,12 +1151,7 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
         key.precision = precision;
         key.ph = ph;
         key.user_bc = m.user_bc;
-        if (!mm.side[0]) {
-            for (int k = 0; k < 3; ++k)
-                if (cudaStreamCreateWithFlags((cudaStream_t*)&mm.side[k], cudaStreamNonBlocking) != cudaSuccess) return 1;
-            for (int k = 0; k < 5; ++k)
-                if (cudaEventCreateWithFlags((cudaEvent_t*)&mm.fork_ev[k], cudaEventDisableTiming) != cudaSuccess) return 1;
-        }
+        if (side_streams(mm)) return 1;
         cudaStream_t s1 = (cudaStream_t)mm.side[0], s2 = (cudaStream_t)mm.side[1], cs = (cudaStream_t)mm.side[2];
         cudaEvent_t* ev = (cudaEvent_t*)mm.fork_ev;
         cudaGraphExec_t exec = nullptr;
@@ -1153,10 +1162,12 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return 1;
             if (!A.sv) cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), cs);
+            cudaStream_t b1 = m.concurrent ? s1 : cs, b2 = m.concurrent ? s2 : cs;
+            cudaEvent_t* bev = m.concurrent ? ev : nullptr;
             if (precision == 0) {
-                if (jv) launch_all<double, true>(m, A, cs, nullptr, s1, s2, ev); else launch_all<double, false>(m, A, cs, nullptr, s1, s2, ev);
+                if (jv) launch_all<double, true>(m, A, cs, nullptr, b1, b2, bev); else launch_all<double, false>(m, A, cs, nullptr, b1, b2, bev);
             } else {
-                if (jv) launch_all<float, true>(m, A, cs, nullptr, s1, s2, ev); else launch_all<float, false>(m, A, cs, nullptr, s1, s2, ev);
+                if (jv) launch_all<float, true>(m, A, cs, nullptr, b1, b2, bev); else launch_all<float, false>(m, A, cs, nullptr, b1, b2, bev);
             }
             launch_strong_rows(m, A, ph, jv, cs, true, precision);
             const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
@@ -1176,10 +1187,21 @@ static int vms_apply_ws(const Mesh& m, const double* u, const double* up, const 
         return 0;
     }
     if (!A.sv && cudaMemsetAsync(out, 0, (size_t)m.n_nodes() * 4 * sizeof(double), s) != cudaSuccess) return 1;
+    // the Intercepted-element and surface kernels on the mesh's side streams, beside the Out-element
+    // kernel, as in the captured graph (not for calls on a caller's workspace, which create nothing)
+    cudaStream_t s1 = nullptr, s2 = nullptr;
+    cudaEvent_t* ev = nullptr;
+    if (!ws && m.concurrent) {
+        Mesh& mm = const_cast<Mesh&>(m);
+        if (side_streams(mm)) return 1;
+        s1 = (cudaStream_t)mm.side[0];
+        s2 = (cudaStream_t)mm.side[1];
+        ev = (cudaEvent_t*)mm.fork_ev;
+    }
     if (precision == 0) {
-        if (jv) launch_all<double, true>(m, A, s, ws); else launch_all<double, false>(m, A, s, ws);
+        if (jv) launch_all<double, true>(m, A, s, ws, s1, s2, ev); else launch_all<double, false>(m, A, s, ws, s1, s2, ev);
     } else {
-        if (jv) launch_all<float, true>(m, A, s, ws); else launch_all<float, false>(m, A, s, ws);
+        if (jv) launch_all<float, true>(m, A, s, ws, s1, s2, ev); else launch_all<float, false>(m, A, s, ws, s1, s2, ev);
     }
     launch_strong_rows(m, A, ph, jv, s, !ws, precision);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;

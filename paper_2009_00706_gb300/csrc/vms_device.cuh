@@ -612,10 +612,13 @@ __device__ __forceinline__ T hadamard_bwd(T x, int c) {
 // Fields at a point from the monomial coefficients of the 8 corner rows (row S holds a_S of every
 // column; layout as the corner rows: values | tangents at CT | force at CF; rows 16-byte aligned),
 // monomials m of the point.  Rows are read whole and accumulated into every field they enter.
-template <class S, class T>
+// IL: the rows hold (value, tangent) pairs interleaved in their first 16 entries (the packed float
+// duals of the interior kernel: each 16-byte load yields two dual pairs in place).
+template <class S, class T, bool IL = false>
 __device__ __forceinline__ void interp_modal(const Args& A, const T m[8], const T* nd, int stride, T g,
                                              Fields<S, T>& F) {
     constexpr bool JV = !std::is_same<S, T>::value;
+    static_assert(!IL || JV, "interleaved rows carry tangents");
     for (int i = 0; i < 3; ++i) {
         F.us[i] = zero<S>(); F.at[i] = zero<S>(); F.gp[i] = zero<S>(); F.f[i] = T(0);
         for (int j = 0; j < 3; ++j) F.Gu[i][j] = zero<S>();
@@ -625,18 +628,25 @@ __device__ __forceinline__ void interp_modal(const Args& A, const T m[8], const 
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const T* r = nd + t * stride;
-        T v[8], d[8];
-        ld4s<T>(r, v);
-        ld4s<T>(r + 4, v + 4);
-        if constexpr (JV) {
-            ld4s<T>(r + CT, d);
-            ld4s<T>(r + CT + 4, d + 4);
-        }
         S a[7];
+        if constexpr (IL) {
+            T q[16];
+            for (int k = 0; k < 16; k += 4) ld4s<T>(r + k, q + k);
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            if constexpr (JV) a[j] = make<S, T>(v[j], d[j]);
-            else a[j] = v[j];
+            for (int j = 0; j < 7; ++j) a[j] = make<S, T>(q[2 * j], q[2 * j + 1]);
+        } else {
+            T v[8], d[8];
+            ld4s<T>(r, v);
+            ld4s<T>(r + 4, v + 4);
+            if constexpr (JV) {
+                ld4s<T>(r + CT, d);
+                ld4s<T>(r + CT + 4, d + 4);
+            }
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                if constexpr (JV) a[j] = make<S, T>(v[j], d[j]);
+                else a[j] = v[j];
+            }
         }
         const T mv = m[t];
         for (int i = 0; i < 3; ++i) {
@@ -693,11 +703,42 @@ __device__ __forceinline__ void column_to_monomial(T* col) {
     for (int t = 0; t < 8; ++t) col[t * CS] = x[t];
 }
 
-template <class S, class T>
+// forward butterfly of value column c and tangent column c (c < 7) of an element's 8 corner rows,
+// then, after every lane of the warp has read its columns, the results stored interleaved as
+// (value, tangent) pairs at entries 2c, 2c + 1 of each row (layout of interp_modal<IL = true>)
+template <class T>
+__device__ __forceinline__ void columns_to_monomial_interleaved(T* nd, int c) {
+    T x[8], y[8];
+    if (c < 7) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) { x[t] = nd[t * CS + c]; y[t] = nd[t * CS + CT + c]; }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (!(t & (1 << k))) {
+                    const T lo = x[t], hi = x[t | (1 << k)], lod = y[t], hid = y[t | (1 << k)];
+                    x[t] = lo + hi;
+                    x[t | (1 << k)] = hi - lo;
+                    y[t] = lod + hid;
+                    y[t | (1 << k)] = hid - lod;
+                }
+    }
+    __syncwarp();
+    if (c < 7) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(nd + t * CS + 2 * c) = make_float2(x[t], y[t]);
+            else *reinterpret_cast<double2*>(nd + t * CS + 2 * c) = make_double2(x[t], y[t]);
+        }
+    }
+}
+
+template <class S, class T, bool IL = false>
 __device__ __forceinline__ void vms_point_modal(const Args& A, const Phys<T>& P, const T m[8], const T* nd,
                                                 int stride, T g, S out[16]) {
     Fields<S, T> F;
-    interp_modal<S, T>(A, m, nd, stride, g, F);
+    interp_modal<S, T, IL>(A, m, nd, stride, g, F);
     pointwise<S, T>(A, P, F, g, out);
 }
 

@@ -108,3 +108,27 @@ def test_krylov_solves_repeat_exactly(dev, sphere, graphs):
     print(f"graphs {graphs}: Krylov {s0['krylov_per_newton']} |R| {s0['res_norm']}")
     assert s0["krylov_per_newton"] == s1["krylov_per_newton"] and s0["res_norm"] == s1["res_norm"]
     assert np.array_equal(u0r, u1r)
+
+
+@pytest.mark.parametrize("prec", [api.PRECISION_FP64, api.PRECISION_MIXED])
+def test_side_streams_give_the_same_bits(dev, sphere, prec):
+    """The Intercepted-element and surface kernels on side streams beside the Out-element kernel
+    (IMGA_OPT_CONCURRENT, the default) or all on the caller's stream: the same slots, the same sums."""
+    w, g, o = sphere
+    u, up, v = I.state(g.n_nodes, 5)
+    ph = w.physics
+    ut, upt, vt = T(u, dev), T(up, dev), T(v, dev)
+    out = {}
+    try:
+        for conc in (True, False):
+            g.concurrent(conc)
+            out[conc] = (g.residual(ph, ut, upt, precision=prec).cpu().numpy(),
+                         g.jvp(ph, ut, upt, vt, precision=prec).cpu().numpy())
+            g.use_graphs(True)
+            out[(conc, "graph")] = g.jvp(ph, ut, upt, vt, precision=prec).cpu().numpy()
+            g.use_graphs(False)
+    finally:
+        g.use_graphs(False)
+        g.concurrent(True)
+    assert np.array_equal(out[True][0], out[False][0]) and np.array_equal(out[True][1], out[False][1])
+    assert np.array_equal(out[(True, "graph")], out[True][1]) and np.array_equal(out[(False, "graph")], out[True][1])
