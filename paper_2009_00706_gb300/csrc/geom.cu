@@ -525,8 +525,19 @@ bool build_incidence(Mesh& m, const std::vector<int32_t>& sq_el, const std::vect
     std::vector<uint32_t> inc(std::max<int64_t>(1, ptr[nn]));
     std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
     visit([&](int64_t node, uint32_t code) { inc[fill[node]++] = code; });
+    // stored as a fixed head of kIncHead entries per node (sentinel-padded: one aligned 32-byte load,
+    // no offset to fetch first) and the rest of each list in CSR form; the list order is kept
+    std::vector<uint32_t> head((size_t)std::max<int64_t>(1, nn) * kIncHead, kIncNone);
+    std::vector<int64_t> optr(nn + 1, 0);
+    for (int64_t i = 0; i < nn; ++i) optr[i + 1] = optr[i] + std::max<int64_t>(0, ptr[i + 1] - ptr[i] - kIncHead);
+    std::vector<uint32_t> oinc(std::max<int64_t>(1, optr[nn]));
+    for (int64_t i = 0; i < nn; ++i)
+        for (int64_t q = ptr[i], k = 0; q < ptr[i + 1]; ++q, ++k) {
+            if (k < kIncHead) head[(size_t)i * kIncHead + k] = inc[q];
+            else oinc[optr[i] + k - kIncHead] = inc[q];
+        }
     const size_t slot_bytes = (size_t)std::max<int64_t>(1, nv) * 32 * sizeof(double);
-    if (!upload(&m.d.inc_ptr, ptr, err) || !upload(&m.d.inc, inc, err)) return false;
+    if (!upload(&m.d.inc_head, head, err) || !upload(&m.d.inc_ptr, optr, err) || !upload(&m.d.inc, oinc, err)) return false;
     if (!check(cudaMalloc((void**)&m.d.sv, slot_bytes), err, "cudaMalloc") ||
         !check(cudaMalloc((void**)&m.d.ss, (size_t)std::max<int64_t>(1, ns) * 32 * sizeof(double)), err, "cudaMalloc"))
         return false;
@@ -685,7 +696,7 @@ void device_free(Mesh& m) {
     DeviceMesh& d = m.d;
     void* ptrs[] = {d.key, d.anc, d.lev, d.conn, d.hpar, d.tv, d.tn, d.tc, d.bt_off, d.bt_idx, d.rg_off, d.rg_idx,
                     d.marker, d.cflags, d.out_list, d.out_conn, d.out_lev, d.out_prob, d.eprob, d.pmu, d.pmuf, d.cut_list, d.cut_off, d.cut_pts, d.cut_pts_f, d.cut_order, d.sq_elem, d.sq_x,
-                    d.sq_n, d.sq_w, d.sq_taub, d.sq_src, d.sq_hosts, d.pen_elem, d.pen_q, d.pen_slot, d.pen, d.inc_ptr, d.inc, d.sv, d.ss, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
+                    d.sq_n, d.sq_w, d.sq_taub, d.sq_src, d.sq_hosts, d.pen_elem, d.pen_q, d.pen_slot, d.pen, d.inc_head, d.inc_ptr, d.inc, d.sv, d.ss, d.sq_list, d.sq_off, d.bcflag, d.bcmask_user, d.bcval_user, m.scratch, d.nd_f, d.nd_d, d.slot,
                     d.counters, d.fq_items, d.fq_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -105,7 +105,8 @@ struct DeviceMesh {
     int64_t* pen_slot = nullptr;
     double* pen = nullptr;
     // deterministic scatter: node -> (slot, corner, weight) incidence and the element-contribution slots
-    int64_t* inc_ptr = nullptr;   // [n_nodes + 1]
+    uint32_t* inc_head = nullptr; // [n_nodes][kIncHead] first entries of each node's list (kIncNone pads)
+    int64_t* inc_ptr = nullptr;   // [n_nodes + 1] the rest of each list (CSR)
     uint32_t* inc = nullptr;      // bits 0-2 corner, 3-4 weight code, 5-31 global slot
     void* sv = nullptr;           // volume slots [n_vslots][8][4] of the element precision (sized for float64)
     double* ss = nullptr;         // surface slots [n_sslots][8][4] float64
@@ -126,6 +127,10 @@ struct DeviceMesh {
     uint8_t* bcmask_user = nullptr;
     double* bcval_user = nullptr;
 };
+
+// node incidence lists of the deterministic scatter: fixed head length and its padding code
+constexpr int kIncHead = 8;
+constexpr uint32_t kIncNone = 0xFFFFFFFFu;
 
 // elements hosting at least this many surface points take the warp-per-element surface kernel
 constexpr int kNitscheDenseMin = 8;

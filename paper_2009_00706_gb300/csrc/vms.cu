@@ -93,7 +93,7 @@ __device__ __forceinline__ void interior_element(const Args& A, T* nd, T* s_mw, 
     for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
     T M[32];
     for (int k = 0; k < 32; ++k) M[k] = T(0);
-    add_moments<T, true>(m, w16, M);
+    add_moments<T>(m, w16, M);
     for (int k = 0; k < 32; k += 4) st4s<T>(mrow + k, M[k], M[k + 1], M[k + 2], M[k + 3]);
     __syncwarp();
     T r[4] = {T(0), T(0), T(0), T(0)};
@@ -269,7 +269,7 @@ __device__ __forceinline__ void cut_element(const Args& A, const int32_t* __rest
         const T wq = pt[3] * det, wqg = wq * g;
         T w16[16];
         for (int k = 0; k < 16; ++k) w16[k] = ((k < 3 || k == 12) ? wq : wqg) * Pick<T, JV>::get(cf[k]);
-        add_moments<T, false>(m, w16, M);
+        add_moments<T>(m, w16, M);
     }
     warp_scatter_moments<T>(A, M, s_m, lane, my_id, 0.0, A.sv ? (T*)A.sv + 32 * (A.n_out_slots + idx) : nullptr);
 }
@@ -429,7 +429,7 @@ __device__ __forceinline__ void surface_element(const Args& A, const int32_t* __
         }
         c[12] = -wq * Pick<T, JV>::get(dn);
         c[13] = c[14] = c[15] = T(0);
-        add_moments<T, false>(m, c, M);
+        add_moments<T>(m, c, M);
     }
     warp_scatter_moments<T>(A, M, s_m, lane, my_id, 0.0, nullptr, A.ss ? A.ss + 32 * idx : nullptr);
 }
@@ -710,54 +710,71 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
 
 // Deterministic o2n (Algorithm 2): one thread per node sums the slot rows of its incidence list in
 // list order (a hanging corner's rows times 1/2 or 1/4 for each parent; float-float in mixed
-// precision), then the node's strong rows take U - g (R) or v (J v) as in strong_rows.  The list is
-// read in batches of 8 (float) or 4 (double) entries whose code and row loads are all issued before the first
-// sum: the kernel is bound by the latency of these two dependent loads, so each thread keeps many
-// in flight.  Writes every row of out: no zeroing before the call.
+// precision), then the node's strong rows take U - g (R) or v (J v) as in strong_rows.  The kernel is
+// bound by the latency of dependent loads, so: the first kIncHead codes of a node sit at a fixed
+// place (one aligned 32-byte load, no list offset to fetch first), the rest follow in CSR form; and
+// every batch of codes has all its row loads issued before the first sum.  Writes every row of out:
+// no zeroing before the call.
 template <class T> struct GatherBatch { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 
+// sums the rows of entries e[0 .. B) (kIncNone: none) in order
+template <class T, int B>
+__device__ __forceinline__ void gather_batch(const Args& A, const uint32_t e[B], int64_t nv, double acc[4], float hi[4],
+                                             float lo[4]) {
+    T v[B][4];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const int64_t sl = (int64_t)(e[i] >> 5);
+        if (e[i] != kIncNone && sl < nv) ld4<T>((const T*)A.sv + 32 * sl, e[i] & 7, v[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        if (e[i] == kIncNone) continue;
+        const int c = (int)(e[i] & 7), wc = (int)((e[i] >> 3) & 3);
+        const int64_t sl = (int64_t)(e[i] >> 5);
+        if (sl < nv) {
+            const T w = wc == 0 ? T(1) : (wc == 1 ? T(0.5) : T(0.25));
+            if constexpr (sizeof(T) == 4) {
+                for (int k = 0; k < 4; ++k) ff_add(hi[k], lo[k], w * v[i][k]);
+            } else {
+                for (int k = 0; k < 4; ++k) acc[k] += w * v[i][k];
+            }
+        } else {   // a float64 surface slot
+            const double* d = A.ss + 32 * (sl - nv) + 4 * c;
+            const double2 x = reinterpret_cast<const double2*>(d)[0], y = reinterpret_cast<const double2*>(d)[1];
+            const double w = wc == 0 ? 1.0 : (wc == 1 ? 0.5 : 0.25);
+            acc[0] += w * x.x; acc[1] += w * x.y; acc[2] += w * y.x; acc[3] += w * y.y;
+        }
+    }
+}
+
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) node_gather(Args A, const int64_t* __restrict__ ptr,
-                                                   const uint32_t* __restrict__ inc, int64_t nv,
-                                                   const uint8_t* __restrict__ flag, const uint8_t* __restrict__ umask,
-                                                   const double* __restrict__ uval, double ux, double uy, double uz,
-                                                   int jv) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) node_gather(Args A, const uint32_t* __restrict__ head,
+                                                   const int64_t* __restrict__ ptr, const uint32_t* __restrict__ inc,
+                                                   int64_t nv, const uint8_t* __restrict__ flag,
+                                                   const uint8_t* __restrict__ umask, const double* __restrict__ uval,
+                                                   double ux, double uy, double uz, int jv) {
+    static_assert(kIncHead == 8, "head of two 16-byte loads");
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= A.n_nodes) return;
     if (A.skip && *A.skip) return;   // a captured solver step after its cycle ended
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    const int64_t q1 = ptr[n + 1];
-    constexpr int kGatherBatch = GatherBatch<T>::value;
-    for (int64_t q0 = ptr[n]; q0 < q1; q0 += kGatherBatch) {
-        uint32_t e[kGatherBatch];
-        T v[kGatherBatch][4];
+    const uint4* hp = reinterpret_cast<const uint4*>(head + kIncHead * n);
+    const uint4 h0 = __ldg(hp), h1 = __ldg(hp + 1);
+    const int64_t q0 = ptr[n], q1 = ptr[n + 1];   // independent of the head: loaded alongside
+    {
+        constexpr int B = GatherBatch<T>::value;
+        const uint32_t e8[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
-        for (int i = 0; i < kGatherBatch; ++i) e[i] = q0 + i < q1 ? __ldg(inc + q0 + i) : 0xFFFFFFFFu;
+        for (int b = 0; b < 8; b += B) gather_batch<T, B>(A, e8 + b, nv, acc, hi, lo);
+    }
+    for (int64_t q = q0; q < q1; q += GatherBatch<T>::value) {
+        constexpr int B = GatherBatch<T>::value;
+        uint32_t e[B];
 #pragma unroll
-        for (int i = 0; i < kGatherBatch; ++i) {
-            const int64_t sl = (int64_t)(e[i] >> 5);
-            if (e[i] != 0xFFFFFFFFu && sl < nv) ld4<T>((const T*)A.sv + 32 * sl, e[i] & 7, v[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < kGatherBatch; ++i) {
-            if (e[i] == 0xFFFFFFFFu) continue;
-            const int c = (int)(e[i] & 7), wc = (int)((e[i] >> 3) & 3);
-            const int64_t sl = (int64_t)(e[i] >> 5);
-            if (sl < nv) {
-                const T w = wc == 0 ? T(1) : (wc == 1 ? T(0.5) : T(0.25));
-                if constexpr (sizeof(T) == 4) {
-                    for (int k = 0; k < 4; ++k) ff_add(hi[k], lo[k], w * v[i][k]);
-                } else {
-                    for (int k = 0; k < 4; ++k) acc[k] += w * v[i][k];
-                }
-            } else {   // a float64 surface slot
-                const double* d = A.ss + 32 * (sl - nv) + 4 * c;
-                const double2 x = reinterpret_cast<const double2*>(d)[0], y = reinterpret_cast<const double2*>(d)[1];
-                const double w = wc == 0 ? 1.0 : (wc == 1 ? 0.5 : 0.25);
-                acc[0] += w * x.x; acc[1] += w * x.y; acc[2] += w * y.x; acc[3] += w * y.y;
-            }
-        }
+        for (int i = 0; i < B; ++i) e[i] = q + i < q1 ? __ldg(inc + q + i) : kIncNone;
+        gather_batch<T, B>(A, e, nv, acc, hi, lo);
     }
     if constexpr (sizeof(T) == 4)
         for (int k = 0; k < 4; ++k) acc[k] += f2d(hi[k]) + f2d(lo[k]);
@@ -1050,10 +1067,10 @@ void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bo
         const double* uv = m.user_bc ? m.d.bcval_user : nullptr;
         const unsigned g4 = (unsigned)((nn + 255) / 256);
         if (precision == 0)
-            node_gather<double><<<g4, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
+            node_gather<double><<<g4, 256, 0, s>>>(A, m.d.inc_head, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
                                                   ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
         else
-            node_gather<float><<<g4, 256, 0, s>>>(A, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
+            node_gather<float><<<g4, 256, 0, s>>>(A, m.d.inc_head, m.d.inc_ptr, m.d.inc, m.n_vslots, m.d.bcflag, um, uv, ph.u_inf[0],
                                                  ph.u_inf[1], ph.u_inf[2], jv ? 1 : 0);
         return;
     }

@@ -58,18 +58,6 @@ __device__ __forceinline__ PDual mmadd(PDual a, PDual b, PDual acc) {
     const float2 t = __ffma2_rn(f2(a), make_float2(b.v, b.v), f2(acc));
     return {t.x, fmaf(a.v, b.d, t.y)};
 }
-// (a0, a1) += s (x0, x1); the float form on the packed pipe
-template <class T> __device__ __forceinline__ void fma_pair(T s, T x0, T x1, T& a0, T& a1) {
-    a0 = fma(s, x0, a0);
-    a1 = fma(s, x1, a1);
-}
-__device__ __forceinline__ void fma_pair2(float s, float x0, float x1, float& a0, float& a1) {
-    const float2 r = __ffma2_rn(make_float2(s, s), make_float2(x0, x1), make_float2(a0, a1));
-    a0 = r.x;
-    a1 = r.y;
-}
-__device__ __forceinline__ void fma_pair2(double s, double x0, double x1, double& a0, double& a1) { fma_pair(s, x0, x1, a0, a1); }
-
 template <class S> struct Base { typedef S type; };
 template <class T, int K> struct Base<Dual<T, K>> { typedef T type; };
 
@@ -744,22 +732,17 @@ __device__ __forceinline__ void vms_point_modal(const Args& A, const Phys<T>& P,
 
 // M[4 S + k] += monomial moments of one point's weighted coefficients c (F | S | G | H, the 16 of
 // pointwise() times the quadrature weight, S and H in reference-gradient scaling), k = component.
-template <class T, bool PACKED>
+// Scalar fused multiply-adds: the packed FP32x2 form needs its operand pairs assembled by register
+// moves here, and measured 2.5 % slower in the interior kernel.
+template <class T>
 __device__ __forceinline__ void add_moments(const T m[8], const T c[16], T M[32]) {
 #pragma unroll
-    for (int p = 0; p < 4; p += 2) {   // components (p, p + 1) together
-        T f[2], sx[2], sy[2], sz[2];
-        for (int h = 0; h < 2; ++h) {
-            const int k = p + h;
-            f[h] = k < 3 ? c[k] : c[12];
-            sx[h] = k < 3 ? c[3 + 3 * k] : c[13];
-            sy[h] = k < 3 ? c[4 + 3 * k] : c[14];
-            sz[h] = k < 3 ? c[5 + 3 * k] : c[15];
-        }
-        auto add = [&](int S, T s, const T x[2]) {
-            if constexpr (PACKED) fma_pair2(s, x[0], x[1], M[4 * S + p], M[4 * S + p + 1]);
-            else fma_pair(s, x[0], x[1], M[4 * S + p], M[4 * S + p + 1]);
-        };
+    for (int k = 0; k < 4; ++k) {
+        const T f = k < 3 ? c[k] : c[12];
+        const T sx = k < 3 ? c[3 + 3 * k] : c[13];
+        const T sy = k < 3 ? c[4 + 3 * k] : c[14];
+        const T sz = k < 3 ? c[5 + 3 * k] : c[15];
+        auto add = [&](int S, T s, T x) { M[4 * S + k] = fma(s, x, M[4 * S + k]); };
         add(0, m[0], f);
         add(1, m[1], f); add(1, m[0], sx);
         add(2, m[2], f); add(2, m[0], sy);
