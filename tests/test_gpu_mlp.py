@@ -75,32 +75,49 @@ def _elements(mesh):
 
 
 def test_learned_preconditioner_in_gmres(dev):
-    w = I.small_sphere(0)
-    mesh = api.Mesh.from_workload(w, device=0)
-    elems = torch.from_numpy(_elements(mesh)).to(dev)
+    """Config-5 protocol at test size: trained on the element Jacobians of geometry seeds 0-3 (the
+    jitter of the immersed sphere and the state both follow the seed), evaluated on held-out
+    geometries 16-19 in Newton-GMRES(50) to 1e-8, judged by the oracle's float64 residual.  What the
+    network gains is recorded against both the method without any preconditioner and block-Jacobi:
+    it must beat the former (fewer GMRES iterations on every held-out problem); against block-Jacobi
+    it loses (no element-local correction removes the global pressure coupling of these systems),
+    and the test pins that its fallback keeps it within a factor 2.5 of block-Jacobi's iterations."""
+    from oracle.oracle import OracleMesh
     Xs, Ts = [], []
     for seed in range(4):
+        w = I.small_sphere(seed)
+        mesh = api.Mesh.from_workload(w, device=0)
+        elems = torch.from_numpy(_elements(mesh)).to(dev)
         u, up, _ = I.state(mesh.n_nodes, seed)
         X, Tt, _ = mesh.precond_dataset(w.physics, torch.from_numpy(u).to(dev), torch.from_numpy(up).to(dev), elems)
         Xs.append(X)
         Ts.append(Tt)
+        mesh.close()
     X, Tt = torch.cat(Xs), torch.cat(Ts)
     net = api.Mlp(seed=11)
     hist = net.train(X, Tt, epochs=20, batch=1024, lr=1e-3)
     assert hist[-1] < hist[0]
     out = {}
-    from oracle.oracle import OracleMesh
-    o = OracleMesh(w.lo, w.hi, w.base_level, w.regions, w.triangles(), w.lmax)
-    for seed in (16, 17):
+    for seed in (16, 17, 18, 19):
+        w = I.small_sphere(seed)
+        mesh = api.Mesh.from_workload(w, device=0)
+        o = OracleMesh(w.lo, w.hi, w.base_level, w.regions, w.triangles(), w.lmax)
         u, up, _ = I.state(mesh.n_nodes, seed)
         R0 = np.linalg.norm(o.residual(w.physics, u, up))
-        for name, kw in (("block_jacobi", dict(precond=1)), ("exact_correction", dict(precond=3, learned_omega=0.5)),
-                         ("learned", dict(precond=2, learned=net, learned_omega=0.5))):
+        for name, kw in (("block_jacobi", dict(precond=1)), ("learned", dict(precond=2, learned=net, learned_omega=0.5)),
+                         ("none", dict(precond=0, max_newton=10, max_krylov=3000))):
             ud = torch.from_numpy(u).to(dev)
-            st = mesh.newton_step(w.physics, ud, torch.from_numpy(up).to(dev), precision=api.PRECISION_FP64,
+            st = mesh.newton_step(w.physics, ud, torch.from_numpy(up).to(dev), precision=api.PRECISION_MIXED,
                                   rtol=1e-8, gmres_m=50, raise_on_failure=False, **kw)
-            out.setdefault(name, []).append((st["krylov_its"], st["fallbacks"], st["converged"]))
-            # the float64 residual decides: the oracle's residual at the result
-            assert st["converged"], (name, st)
-            assert np.linalg.norm(o.residual(w.physics, ud.cpu().numpy(), up)) <= 1.5e-8 * R0
-    print("GMRES iterations (its, fallbacks, converged):", out, "training loss", hist[0], hist[-1])
+            rel = np.linalg.norm(o.residual(w.physics, ud.cpu().numpy(), up)) / R0
+            out.setdefault(name, []).append((st["krylov_its"], st["fallbacks"], bool(st["converged"]), rel))
+            if name != "none":
+                # the float64 residual decides: the oracle's residual at the result
+                assert st["converged"] and rel <= 1.5e-8, (name, seed, st)
+        mesh.close()
+    print("held-out geometries 16-19, (GMRES its, fallbacks, converged, oracle |R|/|R0|):", out,
+          "training loss", hist[0], hist[-1])
+    for k in range(4):
+        learned, bj, none = out["learned"][k][0], out["block_jacobi"][k][0], out["none"][k][0]
+        assert learned < none, (k, out)
+        assert learned <= 2.5 * bj, (k, out)
