@@ -327,7 +327,10 @@ typedef struct {
  * step solved by right-preconditioned GMRES(m) with classical Gram-Schmidt applied twice, every
  * vector and reduction in float64; convergence is judged on the float64 residual.  Synchronous.
  * The mesh keeps the Krylov workspace ((m + 1) + 8 vectors + 2 x 16 n_nodes doubles) for later
- * calls.  Returns IMGA_ERR_NOT_CONVERGED (stats filled) when the tolerance is not reached. */
+ * calls.  On a batched mesh one solve covers every problem (the system is block diagonal over
+ * them); the Krylov space, the norms and the stopping test are global, so the hardest problem sets
+ * the iteration count.  With IMGA_OPT_GRAPHS the whole solve replays as one CUDA graph.
+ * Returns IMGA_ERR_NOT_CONVERGED (stats filled) when the tolerance is not reached. */
 imga_status imga_newton_step(imga_mesh mesh, double* u_inout, const double* u_prev, const double* u_prev2,
                              const double* f, const imga_physics* phys, const imga_solver_opts* opts,
                              imga_solver_stats* stats, void* stream);

@@ -133,9 +133,18 @@ def test_invalid_arguments_are_rejected(lib):
 
 def test_options_and_queries_reject_bad_arguments(lib):
     m = api.Mesh((0, 0, 0), (1, 1, 1), 1, [], None, 3, device=-1)
-    for opt in (1, 2, 3):                                                 # graphs, autotune, ray-only classify
+    # graphs, autotune, ray-only classify, deterministic, fused, fused split, side streams
+    for opt in (1, 2, 3, 4, 5, 6, 7):
         assert lib.imga_set_option(m.h, opt, 1) == 1                      # host-only mesh
     assert lib.imga_set_option(None, 1, 1) == 1
+    fused = np.zeros(6, np.int64)
+    assert lib.imga_fused_info(None, fused.ctypes.data_as(C.c_void_p)) == 1
+    assert lib.imga_fused_info(m.h, None) == 1
+    assert lib.imga_fused_info(m.h, fused.ctypes.data_as(C.c_void_p)) == 0
+    assert fused[0] == 0 and fused[5] == 4                                # off; all 4 warps start on costly items
+    bps = np.zeros(4, np.int32)
+    assert lib.imga_tuning_interior(None, bps.ctypes.data_as(C.c_void_p), None) == 1
+    assert lib.imga_tuning_interior(m.h, bps.ctypes.data_as(C.c_void_p), None) == 0 and (bps == 0).all()   # not tuned
     counts = np.zeros(4, np.int64)
     assert lib.imga_classify_counts(m.h, counts.ctypes.data_as(C.c_void_p), 0) == 1   # host-only: no counts
     assert lib.imga_classify_counts(None, counts.ctypes.data_as(C.c_void_p), 0) == 1
