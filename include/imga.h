@@ -443,18 +443,17 @@ imga_status imga_gemm_bf16(int M, int N, int K, const float* A, const float* B, 
  * the output with float64 atomics, whose order, and so the last bits, vary from run to run.  Both
  * values drop the cached graphs. */
 /* IMGA_OPT_FUSED (value 1 on, 0 off, default off): imga_residual and imga_jvp (and the solvers built
- * on them) evaluate the Out, Intercepted and surface buckets in ONE persistent launch.  Its warps
- * drain a device work queue: first the Intercepted elements, the elements hosting many surface
- * points and the groups of 32 points of the others, one per claim, in decreasing order of a cost
- * estimate from Eq. (Wpart) (rounds of 32 points, surface points weighted by T_s/T_v = 4); then the
- * Out elements, 4 per warp item and 8 items per claim.  The float64 Nitsche penalty follows as a
- * second launch.  Results equal the bucketed launches' up to the order of the float64 atomic
- * additions, and bit for bit with IMGA_OPT_DETERMINISTIC.  The first switch-on builds the queue (a
- * synchronous upload).  Fails with IMGA_ERR_CUDA if that fails. */
+ * on them) evaluate the Out and Intercepted buckets in ONE persistent launch.  Its warps drain a
+ * device work queue: first the Intercepted elements, one per claim, by decreasing point count (a
+ * warp's rounds of 32 points: Eq. (Wpart)'s volume cost); then the Out elements, 4 per warp item
+ * and 8 items per claim.  The surface (Nitsche) kernels and the float64 penalty run beside it on a
+ * side stream (IMGA_OPT_CONCURRENT) or after it.  Results equal the bucketed launches' up to the
+ * order of the float64 atomic additions, and bit for bit with IMGA_OPT_DETERMINISTIC.  The first
+ * switch-on builds the queue (a synchronous upload).  Fails with IMGA_ERR_CUDA if that fails. */
 /* IMGA_OPT_FUSED_SPLIT (value 1 .. 4, default 4): how many of the fused kernel's 4 warps per block
- * start on the costly items; the others start on the Out elements and take what is left of the
- * costly items at the end, so latency-bound costly work can share the SMs with the arithmetic-bound
- * Out elements. */
+ * start on the Intercepted elements; the others start on the Out elements and take what is left of
+ * the Intercepted ones at the end, so latency-bound work can share the SMs with the
+ * arithmetic-bound Out elements. */
 /* IMGA_OPT_CONCURRENT (value 1 on, the default; 0 off): the bucketed imga_residual / imga_jvp launch
  * the Intercepted-element and surface kernels on two side streams of the mesh, forked after the node
  * preparation and joined before the node sums, so they run beside the Out-element kernel (direct
@@ -476,8 +475,9 @@ imga_status imga_tuning(imga_mesh mesh, int32_t* shape, float* ms);
  * limit is used); if ms is non-null, ms[20] the per-launch milliseconds of the candidates 1 .. 5
  * (0 where not measured). */
 imga_status imga_tuning_interior(imga_mesh mesh, int32_t* bps, float* ms);
-/* The fused launch's queue (IMGA_OPT_FUSED): counts[6] = {1 if on, Intercepted elements, dense
- * surface elements, groups of 32 sparse surface points, Out elements, IMGA_OPT_FUSED_SPLIT}. */
+/* The fused launch (IMGA_OPT_FUSED): counts[6] = {1 if on, Intercepted elements in its queue, elements
+ * of the warp-per-element surface kernel, points of the thread-per-point surface kernel (those two
+ * run beside it), Out elements, IMGA_OPT_FUSED_SPLIT}. */
 imga_status imga_fused_info(imga_mesh mesh, int64_t* counts);
 
 /* Per-kernel timing with CUDA events recorded on the caller's stream around every kernel that

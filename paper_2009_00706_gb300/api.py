@@ -418,7 +418,7 @@ class Mesh:
         return out
 
     def fused(self, on=True):
-        """IMGA_OPT_FUSED: the Out, Intercepted and surface buckets in one persistent launch."""
+        """IMGA_OPT_FUSED: the Out and Intercepted buckets in one persistent launch (surface kernels beside it)."""
         check(_lib.load().imga_set_option(self.h, 5, int(bool(on))))
 
     def concurrent(self, on=True):
@@ -426,14 +426,14 @@ class Mesh:
         check(_lib.load().imga_set_option(self.h, 7, 1 if on else 0))
 
     def fused_split(self, heavy_warps):
-        """IMGA_OPT_FUSED_SPLIT: warps per block (1 .. 4) that start on the costly items."""
+        """IMGA_OPT_FUSED_SPLIT: warps per block (1 .. 4) that start on the Intercepted elements."""
         check(_lib.load().imga_set_option(self.h, 6, int(heavy_warps)))
 
     def fused_info(self):
         c = np.zeros(6, np.int64)
         check(_lib.load().imga_fused_info(self.h, c.ctypes.data_as(C.c_void_p)))
-        return {"on": bool(c[0]), "cut_items": int(c[1]), "dense_surface_items": int(c[2]),
-                "sparse_surface_groups": int(c[3]), "out_elements": int(c[4]), "heavy_first_warps": int(c[5])}
+        return {"on": bool(c[0]), "cut_items": int(c[1]), "dense_surface_elements": int(c[2]),
+                "sparse_surface_points": int(c[3]), "out_elements": int(c[4]), "heavy_first_warps": int(c[5])}
 
     def tuning_interior(self):
         """{(precision, 'residual' | 'jvp'): (blocks per SM in use (0: occupancy limit), candidate ms[5])}"""

@@ -209,13 +209,13 @@ struct Mesh {
     // limit), per [float64 / mixed][residual / J v], and the candidate times of the last tuning
     int out_bps[2][2] = {{0, 0}, {0, 0}};
     float out_tune_ms[2][2][5] = {};
-    // one persistent launch over the Out, Intercepted and surface buckets (IMGA_OPT_FUSED): the
-    // queue of per-warp items that are not Out elements, by decreasing estimated cost (Eq. Wpart)
     bool concurrent = true;              // IMGA_OPT_CONCURRENT: Intercepted / surface kernels on side streams
+    // one persistent launch over the Out and Intercepted buckets (IMGA_OPT_FUSED): its queue holds the
+    // Intercepted elements by decreasing point count (Eq. Wpart's volume cost)
     bool fused = false;
-    int fused_heavy_warps = 4;           // warps per block that start on the costly items (1 .. 4)
+    int fused_heavy_warps = 4;           // warps per block that start on the Intercepted elements (1 .. 4)
     int64_t fq_n = 0;                    // items in fq_items
-    int64_t fq_counts[3] = {0, 0, 0};    // Intercepted elements, dense surface elements, sparse point groups
+    int64_t fq_counts[3] = {0, 0, 0};    // queued Intercepted elements, dense surface elements, sparse surface points
     std::vector<std::pair<GraphKey, void*>> graphs;
     void* side[3] = {nullptr, nullptr, nullptr};   // two branch streams + the private capture stream
     void* fork_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // fork, 2 joins, caller->graph, graph->caller

@@ -450,20 +450,19 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(T) == 4 ? 2 : 1) nitsche_el(A
 }
 
 // ------------------------------------------------------------------------------------------
-// One persistent launch over the quadrature buckets.  Every warp drains a device work queue on its
-// own: first the items that are not Out elements -- an Intercepted element (8 .. 4096 sub-cell
-// points), an element hosting many surface points, or a group of 32 surface points of elements
-// hosting few -- one per claim, in the order of decreasing estimated cost that the host gave them
-// (the cost model of Eq. Wpart: volume points at T_v, surface points at T_s); then the Out elements,
-// 4 per warp item, kFusedChunk items per claim, with their node rows double-buffered by cp.async as
-// in vms_interior.  Longest items first, then small uniform ones, keeps every SM busy to the end
-// whatever the mix of buckets (one mesh or many problems of a batch).
+// One persistent launch over the volume quadrature buckets.  Every warp drains a device work queue
+// on its own: first the Intercepted elements (8 .. 4096 sub-cell points), one per claim, longest
+// first (the cost model of Eq. Wpart: a warp's time grows with its rounds of 32 points); then the
+// Out elements, 4 per warp item, kFusedChunk items per claim, with their node rows double-buffered
+// by cp.async as in vms_interior.  Longest items first, then small uniform ones, keeps every SM
+// busy to the end whatever the mix (one mesh or many problems of a batch).  The surface terms run
+// as their own kernels beside this one (their register budget would spill in it).
 // ------------------------------------------------------------------------------------------
 constexpr int kFusedWarps = 4;   // warps per block
 constexpr int kFusedChunk = 8;   // Out warp items per claim
 
 struct FusedQueue {
-    const uint32_t* items;       // bits 30-31 kind (0 Intercepted, 1 dense surface element, 2 sparse group), 0-29 index
+    const uint32_t* items;       // Intercepted-list positions, by decreasing point count
     int64_t n_items;
     unsigned long long* cnt;     // [3] claimed items, claimed Out warp items, finished blocks (zero at launch)
     const int32_t* oconn;
@@ -474,11 +473,6 @@ struct FusedQueue {
     const int64_t* cut_off;
     const void* cut_pts;
     int heavy_warps;             // warps per block that take the costly items before the Out elements
-    const int32_t* sq_list;
-    const int64_t* sq_off;
-    const int32_t* sq_elem;
-    const double *sq_x, *sq_n, *sq_w;
-    int64_t n_sparse;
 };
 
 template <class T> struct FusedShape {
@@ -505,17 +499,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, sizeof(T) == 4 ? 4 : 2) vms_
             if (lane == 0) h = atomicAdd(Q.cnt, 1ull);
             h = __shfl_sync(0xffffffffu, h, 0);
             if ((int64_t)h >= Q.n_items) break;
-            const uint32_t it = Q.items[h];
-            const int64_t i = (int64_t)(it & 0x3FFFFFFFu);
-            const uint32_t kind = it >> 30;
-            if (kind == 0) {
-                cut_element<T, JV>(A, Q.cut_list, Q.cut_off, Q.cut_pts, i, base, base + 8 * CS, lane);
-            } else if (kind == 1) {
-                surface_element<T, JV>(A, Q.sq_list, Q.sq_off, Q.sq_x, Q.sq_n, Q.sq_w, i, base, base + 8 * CS, lane);
-            } else {
-                const int64_t q = 32 * i + lane;
-                if (q < Q.n_sparse) surface_point<T, JV>(A, Q.sq_elem, Q.sq_x, Q.sq_n, Q.sq_w, q);
-            }
+            cut_element<T, JV>(A, Q.cut_list, Q.cut_off, Q.cut_pts, (int64_t)Q.items[h], base, base + 8 * CS, lane);
             __syncwarp();   // the shared rows are reused by the next item
         }
     };
@@ -571,7 +555,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, sizeof(T) == 4 ? 4 : 2) vms_
                     const int lp_next = nxt >= 0 ? level_prob(nxt) : 0;
                     cp_wait<1>();
                     const int64_t idx = 4 * cur + le;
-                    interior_element<T, JV, false>(A, base + (buf * 4 + le) * ESTR, s_mw, m, lane, idx, idx < Q.n_out,
+                    interior_element<T, JV>(A, base + (buf * 4 + le) * ESTR, s_mw, m, lane, idx, idx < Q.n_out,
                                             lp_cur & 255, lp_cur >> 8, id_cur);
                     cur = nxt;
                     nxt = aft;
@@ -968,9 +952,34 @@ void launch_penalty(const Mesh& m, const Args& A, cudaStream_t s, bool timed) {
                                                                         m.d.sq_x, m.d.sq_w, m.d.sq_taub, np);
 }
 
-// the Out, Intercepted and surface buckets in one launch (vms_fused), then the float64 penalty
+// the surface buckets: thread-per-point and warp-per-element Nitsche kernels, then the float64
+// penalty (same stream: the slots hold their rows first)
 template <class T, bool JV>
-void launch_fused(const Mesh& m, const Args& A, cudaStream_t s, bool timed) {
+void launch_surface(const Mesh& m, const Args& A, cudaStream_t ss, bool timed) {
+    const int64_t nsp = m.n_sq_sparse, nse = m.n_sq_elem;
+    if (nsp > 0) {
+        Timed t(m, 2, ss, 1, timed);
+        nitsche<T, JV><<<(unsigned)((nsp + 127) / 128), 128, 0, ss>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
+                                                                      m.d.sq_taub, nsp);
+    }
+    if (nse > 0) {
+        Timed t(m, 2, ss, 1, timed);
+        nitsche_el<T, JV><<<(unsigned)((nse + WPB - 1) / WPB), 32 * WPB, 0, ss>>>(A, m.d.sq_list, m.d.sq_off, m.d.sq_x,
+                                                                                m.d.sq_n, m.d.sq_w, m.d.sq_taub, nse);
+    }
+    launch_penalty<T, JV>(m, A, ss, timed);
+}
+
+// the Out and Intercepted buckets in one persistent launch (vms_fused); the surface kernels beside
+// it on the side stream ss (forked and joined with the events ev), or after it on s
+template <class T, bool JV>
+void launch_fused(const Mesh& m, const Args& A, cudaStream_t s, cudaStream_t ss, cudaEvent_t* ev, bool timed) {
+    const bool fork = ev && ss && ss != s;
+    if (fork) {   // the surface kernels first: their blocks take their SMs, the persistent queue fills the rest
+        cudaEventRecord(ev[0], s);
+        cudaStreamWaitEvent(ss, ev[0], 0);
+        launch_surface<T, JV>(m, A, ss, timed);
+    }
     FusedQueue Q;
     Q.items = m.d.fq_items;
     Q.n_items = m.fq_n;
@@ -983,13 +992,6 @@ void launch_fused(const Mesh& m, const Args& A, cudaStream_t s, bool timed) {
     Q.cut_off = m.d.cut_off;
     Q.cut_pts = std::is_same<T, float>::value ? (const void*)m.d.cut_pts_f : (const void*)m.d.cut_pts;
     Q.heavy_warps = m.fused_heavy_warps;
-    Q.sq_list = m.d.sq_list;
-    Q.sq_off = m.d.sq_off;
-    Q.sq_elem = m.d.sq_elem;
-    Q.sq_x = m.d.sq_x;
-    Q.sq_n = m.d.sq_n;
-    Q.sq_w = m.d.sq_w;
-    Q.n_sparse = m.n_sq_sparse;
     if (Q.n_items + Q.n_out > 0) {
         Timed t(m, 5, s, 1, timed);
         const int64_t work = Q.n_items + (Q.n_out + 3) / 4;   // warp items
@@ -997,7 +999,12 @@ void launch_fused(const Mesh& m, const Args& A, cudaStream_t s, bool timed) {
         const int64_t grid = std::min<int64_t>(blocks, (int64_t)fused_blocks_per_sm<T, JV>() * m.n_sm);
         vms_fused<T, JV><<<(unsigned)grid, 32 * kFusedWarps, FusedShape<T>::smem, s>>>(A, Q);
     }
-    launch_penalty<T, JV>(m, A, s, timed);
+    if (fork) {
+        cudaEventRecord(ev[2], ss);
+        cudaStreamWaitEvent(s, ev[2], 0);
+    } else {
+        launch_surface<T, JV>(m, A, s, timed);
+    }
 }
 
 template <class T, bool JV>
@@ -1015,7 +1022,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         launch_node_prep<T, JV>(A, ndv, ndt, ndf, s);
     }
     if (m.fused && m.d.fq_cnt) {
-        launch_fused<T, JV>(m, A, s, !ws);
+        launch_fused<T, JV>(m, A, s, s_sur, ev, !ws);
         return;
     }
     // fork: the Intercepted-element and surface kernels run beside the Out-element kernel
@@ -1037,18 +1044,7 @@ void launch_all(const Mesh& m, Args A, cudaStream_t s, void* ws = nullptr, cudaS
         const Mesh::CutTune& ct = m.cut_tune[sizeof(T) == 4][JV];
         launch_cut<T, JV>(m, A, sc, ct.wpb, ct.lpt);
     }
-    const int64_t nsp = m.n_sq_sparse, nse = m.n_sq_elem;
-    if (nsp > 0) {
-        Timed t(m, 2, ss, 1, !ws);
-        nitsche<T, JV><<<(unsigned)((nsp + 127) / 128), 128, 0, ss>>>(A, m.d.sq_elem, m.d.sq_x, m.d.sq_n, m.d.sq_w,
-                                                                      m.d.sq_taub, nsp);
-    }
-    if (nse > 0) {
-        Timed t(m, 2, ss, 1, !ws);
-        nitsche_el<T, JV><<<(unsigned)((nse + WPB - 1) / WPB), 32 * WPB, 0, ss>>>(A, m.d.sq_list, m.d.sq_off, m.d.sq_x,
-                                                                                m.d.sq_n, m.d.sq_w, m.d.sq_taub, nse);
-    }
-    launch_penalty<T, JV>(m, A, ss, !ws);   // after both surface kernels (same stream): the slots hold their rows
+    launch_surface<T, JV>(m, A, ss, !ws);
     if (ev) {   // join
         cudaEventRecord(ev[1], sc);
         cudaEventRecord(ev[2], ss);
@@ -1082,28 +1078,16 @@ void launch_strong_rows(const Mesh& m, const Args& A, const imga_physics& ph, bo
 
 }  // namespace
 
-// The work queue of the fused launch: one item per Intercepted element, per element hosting at least
-// kNitscheDenseMin surface points, and per group of 32 points of the other surface-hosting elements,
-// by decreasing estimated cost.  The cost of an item is what one warp spends on it: its rounds of 32
-// points (lanes over points) plus one for gathering and scattering, surface points weighted by
-// T_s / T_v (Eq. Wpart), the ratio measured for these kernels on this GPU (about 4).
+// The work queue of the fused launch: the Intercepted elements by decreasing point count (the cost
+// of an element on a warp is its rounds of 32 sub-cell points, Eq. Wpart's volume term), claimed
+// first; the Out elements follow in Morton order, claimed in chunks.
 int fused_prepare(Mesh& m, std::string& err) {
-    constexpr double kSurfaceCost = 4.0;
-    std::vector<std::pair<double, uint32_t>> it;
-    const int64_t nc = (int64_t)m.cut_list.size(), nd = m.n_sq_elem, ng = (m.n_sq_sparse + 31) / 32;
-    if (nc >= (1 << 30) || nd >= (1 << 30) || ng >= (1 << 30)) { err = "too many items for the fused launch"; return 1; }
-    if ((int64_t)m.sq_off_h.size() != nd + 1 && nd > 0) { err = "surface point ranges missing"; return 1; }
-    it.reserve((size_t)(nc + nd + ng));
-    for (int64_t i = 0; i < nc; ++i)
-        it.push_back({1.0 + (double)((m.cut_off[i + 1] - m.cut_off[i] + 31) / 32), (uint32_t)i});
-    for (int64_t i = 0; i < nd; ++i)
-        it.push_back({1.0 + kSurfaceCost * (double)((m.sq_off_h[i + 1] - m.sq_off_h[i] + 31) / 32), (1u << 30) | (uint32_t)i});
-    for (int64_t g = 0; g < ng; ++g) it.push_back({1.0 + kSurfaceCost, (2u << 30) | (uint32_t)g});
-    std::stable_sort(it.begin(), it.end(), [](const std::pair<double, uint32_t>& a, const std::pair<double, uint32_t>& b) {
-        return a.first > b.first;
+    const int64_t nc = (int64_t)m.cut_list.size();
+    std::vector<uint32_t> items((size_t)nc);
+    for (int64_t i = 0; i < nc; ++i) items[i] = (uint32_t)i;
+    std::stable_sort(items.begin(), items.end(), [&](uint32_t a, uint32_t b) {
+        return m.cut_off[a + 1] - m.cut_off[a] > m.cut_off[b + 1] - m.cut_off[b];
     });
-    std::vector<uint32_t> items(it.size());
-    for (size_t i = 0; i < it.size(); ++i) items[i] = it[i].second;
     if (m.d.fq_items) { cudaFree(m.d.fq_items); m.d.fq_items = nullptr; }
     if (m.d.fq_cnt) { cudaFree(m.d.fq_cnt); m.d.fq_cnt = nullptr; }
     if (cudaMalloc((void**)&m.d.fq_items, std::max<size_t>(1, items.size()) * sizeof(uint32_t)) != cudaSuccess ||
@@ -1113,10 +1097,10 @@ int fused_prepare(Mesh& m, std::string& err) {
         err = "fused queue upload";
         return 1;
     }
-    m.fq_n = (int64_t)items.size();
+    m.fq_n = nc;
     m.fq_counts[0] = nc;
-    m.fq_counts[1] = nd;
-    m.fq_counts[2] = ng;
+    m.fq_counts[1] = m.n_sq_elem;
+    m.fq_counts[2] = m.n_sq_sparse;
     fused_blocks_per_sm<double, true>();
     fused_blocks_per_sm<double, false>();
     fused_blocks_per_sm<float, true>();

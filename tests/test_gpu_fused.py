@@ -1,8 +1,8 @@
-"""GPU: the buckets in one persistent launch (IMGA_OPT_FUSED).
+"""GPU: the volume buckets in one persistent launch (IMGA_OPT_FUSED).
 
-One kernel drains a device work queue: the Intercepted elements, the elements hosting many surface
-points and the groups of 32 points of the other surface-hosting elements, by decreasing cost
-(Eq. Wpart), then the Out elements.  The per-item arithmetic is the bucketed kernels', so:
+One kernel drains a device work queue: the Intercepted elements by decreasing point count (Eq.
+Wpart's volume cost), then the Out elements; the surface kernels run beside it.  The per-item
+arithmetic is the bucketed kernels', so:
 
 * with the deterministic scatter, the fused R and J v equal the bucketed ones row by row to the
   last bits that FMA contraction may change (relative 1e-13 in float64, 1e-6 in mixed), repeated
@@ -73,7 +73,7 @@ def test_fused_equals_bucketed_and_oracle(dev, sphere, prec, det):
         g.deterministic(True)
     mk, _ = g.markers()
     assert info["on"] and info["cut_items"] == int((mk == 2).sum()) and info["out_elements"] == int((mk == 0).sum())
-    assert info["dense_surface_items"] + info["sparse_surface_groups"] > 0
+    assert info["dense_surface_elements"] + info["sparse_surface_points"] > 0
     tol = 1e-13 if prec == api.PRECISION_FP64 else 1e-6
     print(f"prec {prec} det {det}: fused vs bucketed R {rowmax(Rf, Rb):.2e} J v {rowmax(Jf, Jb):.2e}")
     assert rowmax(Rf, Rb) <= tol and rowmax(Jf, Jb) <= tol
@@ -131,7 +131,7 @@ def test_fused_inside_the_whole_graph_newton_solve(dev, sphere):
 
 
 def test_fused_split_gives_the_same_bits(dev, sphere):
-    """However many warps per block start on the costly items, every item is evaluated once by the
+    """However many warps per block start on the Intercepted elements, every item is evaluated once by the
     same code: with the deterministic scatter the result is the same bit for bit."""
     w, g, o = sphere
     u, up, v = I.state(g.n_nodes, 24)
