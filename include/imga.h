@@ -30,7 +30,8 @@
  *   - One mesh handle belongs to the device it was built on; calls using it must run with that
  *     device current or pass pointers of that device.  A mesh owns one per-call node workspace,
  *     so residual / J v calls on the same mesh must not overlap on the GPU (issue them on one
- *     stream, or order the streams).
+ *     stream, or order the streams), and must come from one host thread at a time (the mesh's
+ *     side streams, fork / join events and cached graphs are shared by its calls).
  */
 #ifndef IMGA_H
 #define IMGA_H
