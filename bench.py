@@ -60,6 +60,7 @@ def kernel_rooflines(prof, steps, info, n_nodes, pk):
         "nitsche": ("alu (estimated flop)", FLOPS_JV_SURFACE_POINT_EST * info["n_surface_points"], fp32, "TFLOP/s"),
         "node_prep": ("hbm", BYTES_NODE_PREP_NODE * n_nodes + BYTES_NODE_PREP_HANGING * info["n_hanging"], hbm, "GB/s"),
     }
+    rec = step_kernel_record()
     for k, (bound, units, peak, unit) in work.items():
         ms = prof[k][0] / max(1, steps)
         if ms <= 0:
@@ -67,6 +68,16 @@ def kernel_rooflines(prof, steps, info, n_nodes, pk):
         scale = 1e12 if unit == "TFLOP/s" else 1e9
         ach = units / (ms / 1e3) / scale
         out[k] = {"ms_per_step": ms, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
+        ex = rec.get(k)
+        if ex:   # executed work from the committed ncu counters of this source (per launch of the class)
+            if unit == "TFLOP/s":
+                f32, f64 = ex["fp32_flop"], ex["fp64_flop"]
+                out[k]["executed"] = {"fp32_tflops": f32 / (ms / 1e3) / 1e12, "fp32_frac": f32 / (ms / 1e3) / 1e12 / fp32,
+                                      "fp64_tflops": f64 / (ms / 1e3) / 1e12,
+                                      "fp64_frac": f64 / (ms / 1e3) / 1e12 / pk["fp64_tflops"]}
+            else:
+                out[k]["dram"] = {"bytes": ex["dram_bytes"], "gbs": ex["dram_bytes"] / (ms / 1e3) / 1e9,
+                                  "frac": ex["dram_bytes"] / (ms / 1e3) / 1e9 / hbm}
     # class 3: with the deterministic scatter (the default) the node sums, which also write the strong
     # rows: bound by the latency of two dependent loads per incidence entry (code, then a 16-byte slot
     # row); with the atomic scatter only the strong rows, a few microseconds of launch latency
@@ -103,6 +114,21 @@ def interior_record():
         for f in ("paper_2009_00706_gb300/csrc/vms.cu", "paper_2009_00706_gb300/csrc/vms_device.cuh"):
             h.update(open(os.path.join(ROOT, f), "rb").read())
         return rec if h.hexdigest() == rec["source_sha256"] else {}
+    except Exception:
+        return {}
+
+
+def step_kernel_record():
+    """Executed flops / DRAM bytes per step of the Intercepted, surface and node-preparation kernels
+    from the committed ncu record (profiles/step_kernel_counters.json), or {} when the kernel source
+    changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "step_kernel_counters.json")))
+        h = hashlib.sha256()
+        for f in ("paper_2009_00706_gb300/csrc/vms.cu", "paper_2009_00706_gb300/csrc/vms_device.cuh"):
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["classes"] if h.hexdigest() == rec["source_sha256"] else {}
     except Exception:
         return {}
 
