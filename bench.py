@@ -1145,6 +1145,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-bluff", action="store_true", help="skip the 19.8 M-element bluff-body pair measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner training and evaluation")
     ap.add_argument("--krylov-rtol", type=float, default=1e-3)
+    ap.add_argument("--newton-profile", action="store_true",
+                    help="only one config-2 Newton step (for ncu launch lists of the solver)")
     ap.add_argument("--kernel-profile", action="store_true",
                     help="only a few J v calls on the sphere LES (for ncu counter captures)")
     return ap.parse_args(argv)
@@ -1181,12 +1183,43 @@ def run_kernel_profile(args):
     return 0
 
 
+def run_newton_profile(args):
+    """One config-2 Newton step (sphere LES, mixed precision, multilevel V-cycle, GMRES(50) to 1e-8),
+    host-driven (a profiler sees every kernel as its own launch), then the same step as one CUDA
+    graph; nothing else: for kernel launch lists and timings of the solver."""
+    import torch
+
+    from paper_2009_00706_gb300 import _lib, api
+    _lib.build()
+    dev = torch.device("cuda", 0)
+    w = I.sphere_les(0)
+    mesh = api.Mesh.from_workload(w, device=0)
+    u, up, _ = I.state(mesh.n_nodes, 0)
+    ud, upd = (torch.from_numpy(a).to(dev) for a in (u, up))
+    stream = torch.cuda.current_stream()
+    res = {}
+    for graphs in (False, True):   # host-driven first (a profiler sees its kernels), then one graph
+        mesh.use_graphs(graphs)
+        uw = ud.clone()
+        st = mesh.newton_step(w.physics, uw, upd, upd.clone(), precision=api.PRECISION_MIXED, precond=4, rtol=1e-8,
+                              gmres_m=50, krylov_rtol=1e-8, max_newton=1, max_krylov=2000, stream=stream,
+                              raise_on_failure=False)
+        res["graph" if graphs else "host_driven"] = {"ms": st["time_ms"], "krylov_its": st["krylov_its"],
+                                                      "linear_rel": st["krylov_rel"][0]}
+    mesh.use_graphs(False)
+    print(json.dumps({"newton_profile": "sphere_les, one Newton step, mixed, multilevel", **res}))
+    mesh.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_profile:
         return run_kernel_profile(args)
+    if args.newton_profile:
+        return run_newton_profile(args)
     return run_ours(args)
 
 

@@ -130,8 +130,14 @@ def test_newton_multilevel_converges_with_fewer_iterations(dev, sphere, precisio
 
 
 def test_newton_bicgstab_on_assembled_matrix(dev, sphere):
+    """Newton with BiCGStab on the assembled matrix (multilevel or block-Jacobi) reaches the same
+    tolerance as Newton-GMRES, judged by the oracle's float64 residual.  (The solutions themselves
+    are not compared: rows that no equation constrains -- dofs of Intercepted elements whose points
+    are all In -- keep whatever the linear solvers leave there, and differ between them.)"""
     w, g = sphere
+    o = OracleMesh(w.lo, w.hi, w.base_level, w.regions, w.triangles(), w.lmax)
     u0, up, _ = I.state(g.n_nodes, 16)
+    R0 = np.linalg.norm(o.residual(w.physics, u0, up))
     upt = T(up, dev)
     res = {}
     for ls, pc in ((0, 4), (1, 4), (1, 1)):
@@ -140,5 +146,5 @@ def test_newton_bicgstab_on_assembled_matrix(dev, sphere):
         res[(ls, pc)] = u.cpu().numpy()
         print(f"linear solver {ls} precond {pc}: Newton {st['newton_its']} Krylov {st['krylov_its']} {st['time_ms']:.0f} ms")
         assert st["converged"]
-    assert rel(res[(1, 4)], res[(0, 4)]) <= 1e-6
-    assert rel(res[(1, 1)], res[(0, 4)]) <= 1e-6
+        assert np.linalg.norm(o.residual(w.physics, res[(ls, pc)], up)) <= 1.5e-8 * R0, (ls, pc)
+    print("solutions differ by", rel(res[(1, 4)], res[(0, 4)]), rel(res[(1, 1)], res[(0, 4)]))
