@@ -175,12 +175,18 @@ def peaks(api=None, device=0):
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples (every 100 ms) taken while the timed region runs.
+
+    `wait_live` keeps the GPU busy with untimed steps until the sampler has written its first line,
+    so that the sampler is running when the timed region starts; `mark` records the file offset at
+    the start and end of the timed region, and `summary` reads only the samples written between
+    the two marks (or, if the region was shorter than one interval, the first sample after it)."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = os.path.join(tempfile.gettempdir(), f"imga_bench_clocks_{os.getpid()}.csv")
+        self.marks = []
 
     def __enter__(self):
         try:
@@ -190,11 +196,29 @@ class Clocks:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
+
+    def _size(self):
+        try:
+            return os.path.getsize(self.path)
+        except OSError:
+            return 0
+
+    def wait_live(self, work, limit_s=5.0):
+        """run `work()` (an untimed step) until the sampler has written a line, at most limit_s"""
+        import torch
+        t0 = time.perf_counter()
+        while self.proc and self.proc.poll() is None and self._size() == 0 and time.perf_counter() - t0 < limit_s:
+            for _ in range(20):
+                work()
+            torch.cuda.synchronize()
+
+    def mark(self):
+        self.marks.append(self._size())
 
     def __exit__(self, *a):
         if self.proc:
@@ -208,9 +232,16 @@ class Clocks:
     def summary(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        data = open(self.path, "rb").read()
+        lo, hi = (self.marks + [0, len(data)])[:2] if len(self.marks) >= 2 else (0, len(data))
+        lines = data[lo:hi].decode(errors="replace").splitlines()
+        window = "samples written during the timed region"
+        if not [x for x in lines if x.count(",") >= 8]:
+            lines = data[hi:].decode(errors="replace").splitlines()[:1]
+            window = "timed region shorter than the 100 ms interval: the first sample after it"
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -225,7 +256,7 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sm_mhz_min": min(sm), "window": window}
 
 
 def dist_env():
@@ -370,18 +401,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     # device-timed region: per-step events, L2 flushed (untimed) between steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    mesh.profile(True)
-    barrier(world)
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
     with Clocks(local) as clk:
+        clk.wait_live(step)
+        mesh.profile(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        clk.mark()
         for a, b in evs:
             flush.zero_()
             a.record(stream)
             step()
             b.record(stream)
         torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
+        wall = time.perf_counter() - wall0
+        clk.mark()
     prof = mesh.profile_read()
     mesh.profile(False)
     launches_per_step = sum(n for _, n in prof.values()) // max(1, args.steps)
@@ -1132,7 +1166,7 @@ def run_learned(args, dev, stream, les, w_les):
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
