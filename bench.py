@@ -175,7 +175,7 @@ def peaks(api=None, device=0):
 
 
 class Clocks:
-    """nvidia-smi samples (every 100 ms) taken while the timed region runs.
+    """nvidia-smi samples (every 50 ms) taken while the timed region runs.
 
     `wait_live` keeps the GPU busy with untimed steps until the sampler has written its first line,
     so that the sampler is running when the timed region starts; `mark` records the file offset at
@@ -196,7 +196,7 @@ class Clocks:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -238,7 +238,7 @@ class Clocks:
         window = "samples written during the timed region"
         if not [x for x in lines if x.count(",") >= 8]:
             lines = data[hi:].decode(errors="replace").splitlines()[:1]
-            window = "timed region shorter than the 100 ms interval: the first sample after it"
+            window = "timed region shorter than the 50 ms interval: the first sample after it"
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in lines:
@@ -338,7 +338,10 @@ def run_reference(args):
         return 0
     w = I.sphere_les(0)
     om, u, up, v = oracle_sample(w, 0)
-    rng_sel = lambda k: np.unique(I.splitmix64(1000 + k, args.ref_sample_nodes) % om.n_nodes).astype(np.int64)
+    # per-step sample: at most ref_sample_nodes seeded nodes, and about 4 M node samples over the
+    # whole run, so that any --steps ends within a few minutes on the host cores
+    nodes = max(1000, min(args.ref_sample_nodes, 4_000_000 // max(1, args.steps)))
+    rng_sel = lambda k: np.unique(I.splitmix64(1000 + k, nodes) % om.n_nodes).astype(np.int64)
     cores = os.cpu_count() or 1
     for k in range(args.warmup):
         time_oracle(om, w, u, up, v, rng_sel(k), threads=cores)
@@ -352,7 +355,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "sphere_les", "elements": om.n_elem, "sample": "elements touching "
-                       f"{args.ref_sample_nodes} seeded nodes per step, residual + J v", "l2": "n/a (CPU)"},
+                       f"{nodes} seeded nodes per step, residual + J v", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{ne_tot} element evaluations over {args.steps} steps, element loop on "
                                        f"{cores} threads (os.cpu_count())"},
@@ -1166,7 +1169,7 @@ def run_learned(args, dev, stream, les, w_les):
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
